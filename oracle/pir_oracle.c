@@ -1,0 +1,707 @@
+/*
+ * pir_oracle.c -- plain, slow, CPU-only oracle for the RLWE-PIR first-dimension
+ * scan of VIPIR (arXiv 2606.11536).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may link, load or call
+ * this file: only the tests, the smoke check and the CPU-baseline leg of the
+ * benchmark use it.  It shares no code, header, table or constant generator with
+ * the CUDA library; it computes every parameter (primes, roots of unity, powers)
+ * from scratch, in uint64 / unsigned __int128, with one modular reduction per
+ * operation and no lazy or Montgomery forms.
+ *
+ * What it computes, and where the paper defines it:
+ *   - RNS prime selection: q_j = 1 (mod 2n) and q_j = 1 (mod p)      (App. A.4)
+ *   - polynomial ring R_q = Z_q[X]/(X^n + 1), RNS rows per prime      (Sec. 2.3, App. A.2)
+ *   - negacyclic NTT / inverse NTT, one row per prime                 (Sec. 2.3)
+ *   - RLWE encryption / decryption with Delta = floor(q/p)            (App. A.2)
+ *   - first-dimension folding: out_c = sum_i DB[i][c] * ct_i in R_q^2 (Sec. 3.2, Sec. 4 "INT32
+ *     modular GEMM", Sec. 4.2): in the NTT domain, for every prime q_j and slot k,
+ *     out[b][c][k] = sum_i DB[i][c][k] * Q[b][i][k]  (mod q_j).
+ *
+ * Readings where the paper is silent (each listed in the design notes):
+ *   - primes are the L largest primes in (2^29, 2^30) with q = 1 mod max(2n, p);
+ *   - psi_j = h^((q_j-1)/(2n)) for the smallest h >= 2 with psi_j^n = -1;
+ *   - NTT(a)[k] = sum_t a_t psi^((2 brv(k) + 1) t)  (bit-reversed evaluation order);
+ *   - a raw DB is a little-endian bit stream of log2(p)-bit coefficients, poly after
+ *     poly, poly (i, c) at position i*D2 + c;
+ *   - each query ciphertext contributes its a- and b-polynomial as two GEMM rows.
+ *
+ * Parity: pinned.  The tests check this file against primality by an independent
+ * library, the defining congruences, the NTT evaluated by its definition, schoolbook
+ * negacyclic multiplication, the convolution theorem, and the BFV decryption
+ * invariant (decrypting the answer returns exactly the requested record).
+ */
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef uint8_t u8;
+typedef uint32_t u32;
+typedef uint64_t u64;
+typedef unsigned __int128 u128;
+typedef __int128 i128;
+
+#define ORC_MAX_L 4
+
+/* Parameters of one PIR instance, as the oracle sees them.  Own layout, not the
+ * CUDA library's. */
+typedef struct {
+  u32 n;        /* ring degree (a power of two)                       */
+  u32 L;        /* number of RNS primes                                */
+  u32 log2p;    /* plaintext modulus p = 2^log2p                       */
+  u32 D1, D2;   /* first-dimension size (summed index i), columns (c) */
+  u64 q[ORC_MAX_L];
+  u64 psi[ORC_MAX_L];
+} orc_params;
+
+/* ------------------------------------------------------------------------- */
+/* Modular arithmetic, one reduction per operation.                          */
+/* ------------------------------------------------------------------------- */
+
+static u64 mulmod(u64 a, u64 b, u64 m) {
+  if (a <= 0xFFFFFFFFull && b <= 0xFFFFFFFFull) return (a * b) % m; /* product fits u64 */
+  return (u64)(((u128)a * b) % m);
+}
+static u64 addmod(u64 a, u64 b, u64 m) { return (a + b) % m; }
+static u64 submod(u64 a, u64 b, u64 m) { return (a + m - b) % m; }
+
+u64 orc_powmod(u64 base, u64 e, u64 m) {
+  u64 r = 1 % m;
+  base %= m;
+  while (e) {
+    if (e & 1) r = mulmod(r, base, m);
+    base = mulmod(base, base, m);
+    e >>= 1;
+  }
+  return r;
+}
+
+/* Inverse modulo a prime by Fermat's little theorem. */
+static u64 invmod_prime(u64 a, u64 q) { return orc_powmod(a, q - 2, q); }
+
+/* Deterministic Miller-Rabin for 64-bit inputs with the first twelve primes as
+ * bases (these bases are known to decide primality for every n < 3.3e24). */
+int orc_is_prime(u64 x) {
+  static const u64 bases[12] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
+  if (x < 2) return 0;
+  for (int i = 0; i < 12; i++) {
+    if (x == bases[i]) return 1;
+    if (x % bases[i] == 0) return 0;
+  }
+  u64 d = x - 1;
+  int s = 0;
+  while ((d & 1) == 0) {
+    d >>= 1;
+    s++;
+  }
+  for (int i = 0; i < 12; i++) {
+    u64 y = orc_powmod(bases[i], d, x);
+    if (y == 1 || y == x - 1) continue;
+    int composite = 1;
+    for (int r = 1; r < s; r++) {
+      y = mulmod(y, y, x);
+      if (y == x - 1) {
+        composite = 0;
+        break;
+      }
+    }
+    if (composite) return 0;
+  }
+  return 1;
+}
+
+/* App. A.4: q_j = 1 mod 2n enables the negacyclic NTT; q_j = 1 mod p makes
+ * Delta*p + 1 = q.  Both moduli are powers of two, so the joint condition is
+ * q_j = 1 mod max(2n, p).  We take the L largest such primes in (2^29, 2^30),
+ * in decreasing order.  Returns 0 on success, -1 if fewer than L exist. */
+int orc_select_primes(u32 n, u32 log2p, u32 L, u64 *q_out) {
+  if (L == 0 || L > ORC_MAX_L || n < 2 || (n & (n - 1)) || log2p == 0 || log2p > 28) return -1;
+  u64 M = 2ull * n;
+  u64 p = 1ull << log2p;
+  if (p > M) M = p;
+  const u64 lo = 1ull << 29, hi = 1ull << 30;
+  u64 c = ((hi - 2) / M) * M + 1; /* largest value = 1 mod M below 2^30 */
+  u32 found = 0;
+  while (found < L && c > lo) {
+    if (orc_is_prime(c)) q_out[found++] = c;
+    c -= M;
+  }
+  return found == L ? 0 : -1;
+}
+
+/* psi = h^((q-1)/(2n)) for the smallest h >= 2 with psi^n = -1 (mod q); such a
+ * psi is a primitive 2n-th root of unity. */
+u64 orc_find_psi(u64 q, u32 n) {
+  u64 e = (q - 1) / (2ull * n);
+  for (u64 h = 2; h < q; h++) {
+    u64 psi = orc_powmod(h, e, q);
+    if (orc_powmod(psi, n, q) == q - 1) return psi;
+  }
+  return 0;
+}
+
+int orc_make_params(u32 n, u32 log2p, u32 D1, u32 D2, u32 L, orc_params *P) {
+  memset(P, 0, sizeof(*P));
+  P->n = n;
+  P->L = L;
+  P->log2p = log2p;
+  P->D1 = D1;
+  P->D2 = D2;
+  if (orc_select_primes(n, log2p, L, P->q) != 0) return -1;
+  for (u32 j = 0; j < L; j++) {
+    P->psi[j] = orc_find_psi(P->q[j], n);
+    if (P->psi[j] == 0) return -1;
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* NTT                                                                       */
+/* ------------------------------------------------------------------------- */
+
+static u32 ilog2(u32 n) {
+  u32 l = 0;
+  while ((1u << l) < n) l++;
+  return l;
+}
+
+static u32 bitrev(u32 x, u32 bits) {
+  u32 r = 0;
+  for (u32 b = 0; b < bits; b++) r |= ((x >> b) & 1u) << (bits - 1 - b);
+  return r;
+}
+
+/* Definition (O(n^2)): out[k] = sum_t a_t * psi^((2 brv(k) + 1) t) mod q, i.e. the
+ * polynomial evaluated at the odd powers of psi (the roots of X^n + 1), listed in
+ * bit-reversed order. */
+void orc_ntt_definition(const u32 *a, u32 *out, u32 n, u64 q, u64 psi) {
+  u32 lg = ilog2(n);
+  for (u32 k = 0; k < n; k++) {
+    u64 root = orc_powmod(psi, 2ull * bitrev(k, lg) + 1, q);
+    u64 acc = 0, x = 1;
+    for (u32 t = 0; t < n; t++) {
+      acc = addmod(acc, mulmod(a[t] % q, x, q), q);
+      x = mulmod(x, root, q);
+    }
+    out[k] = (u32)acc;
+  }
+}
+
+/* Inverse of the definition (O(n^2)): a_t = n^-1 * sum_k A[k] * root_k^-t. */
+void orc_intt_definition(const u32 *A, u32 *out, u32 n, u64 q, u64 psi) {
+  u32 lg = ilog2(n);
+  u64 ninv = invmod_prime(n, q);
+  for (u32 t = 0; t < n; t++) out[t] = 0;
+  for (u32 k = 0; k < n; k++) {
+    u64 root = orc_powmod(psi, 2ull * bitrev(k, lg) + 1, q);
+    u64 rinv = invmod_prime(root, q);
+    u64 x = 1;
+    for (u32 t = 0; t < n; t++) {
+      out[t] = (u32)addmod(out[t], mulmod(A[k] % q, x, q), q);
+      x = mulmod(x, rinv, q);
+    }
+  }
+  for (u32 t = 0; t < n; t++) out[t] = (u32)mulmod(out[t], ninv, q);
+}
+
+/* Powers psi^brv(i) for i < n, the twiddles of the radix-2 transform below. */
+static void psi_powers_brv(u64 *tab, u32 n, u64 q, u64 psi) {
+  u32 lg = ilog2(n);
+  for (u32 i = 0; i < n; i++) tab[i] = orc_powmod(psi, bitrev(i, lg), q);
+}
+
+/* Fast forward negacyclic NTT, in place, radix-2 decimation in time with the
+ * psi powers folded into the butterflies.  Stage with half-width t: the block g
+ * of 2t elements uses w = psi^brv(m + g) with m = n / (2t).  The result equals
+ * orc_ntt_definition (pinned by the tests). */
+void orc_ntt_fwd(u32 *a, u32 n, u64 q, u64 psi) {
+  u64 *w = (u64 *)malloc(sizeof(u64) * n);
+  psi_powers_brv(w, n, q, psi);
+  for (u32 i = 0; i < n; i++) a[i] = (u32)(a[i] % q);
+  u32 t = n;
+  for (u32 m = 1; m < n; m <<= 1) {
+    t >>= 1;
+    for (u32 g = 0; g < m; g++) {
+      u64 wg = w[m + g];
+      for (u32 x = 2 * g * t; x < 2 * g * t + t; x++) {
+        u64 u = a[x], v = mulmod(a[x + t], wg, q);
+        a[x] = (u32)addmod(u, v, q);
+        a[x + t] = (u32)submod(u, v, q);
+      }
+    }
+  }
+  free(w);
+}
+
+/* Fast inverse: the butterflies of orc_ntt_fwd undone in reverse order
+ * (decimation in frequency with psi^-brv(m + g)), then a scale by n^-1. */
+void orc_ntt_inv(u32 *a, u32 n, u64 q, u64 psi) {
+  u64 *w = (u64 *)malloc(sizeof(u64) * n);
+  psi_powers_brv(w, n, q, invmod_prime(psi, q));
+  u64 ninv = invmod_prime(n, q);
+  for (u32 i = 0; i < n; i++) a[i] = (u32)(a[i] % q);
+  u32 t = 1;
+  for (u32 m = n >> 1; m >= 1; m >>= 1) {
+    for (u32 g = 0; g < m; g++) {
+      u64 wg = w[m + g];
+      for (u32 x = 2 * g * t; x < 2 * g * t + t; x++) {
+        u64 u = a[x], v = a[x + t];
+        a[x] = (u32)addmod(u, v, q);
+        a[x + t] = (u32)mulmod(submod(u, v, q), wg, q);
+      }
+    }
+    t <<= 1;
+  }
+  for (u32 i = 0; i < n; i++) a[i] = (u32)mulmod(a[i], ninv, q);
+  free(w);
+}
+
+/* Apply the fast NTT / INTT to `count` RNS polynomials laid out [count][L][n]. */
+void orc_ntt_fwd_rns(const orc_params *P, u32 *polys, u64 count) {
+  for (u64 c = 0; c < count; c++)
+    for (u32 j = 0; j < P->L; j++) orc_ntt_fwd(polys + (c * P->L + j) * P->n, P->n, P->q[j], P->psi[j]);
+}
+void orc_ntt_inv_rns(const orc_params *P, u32 *polys, u64 count) {
+  for (u64 c = 0; c < count; c++)
+    for (u32 j = 0; j < P->L; j++) orc_ntt_inv(polys + (c * P->L + j) * P->n, P->n, P->q[j], P->psi[j]);
+}
+
+/* Schoolbook product in Z_q[X]/(X^n + 1): X^n = -1, so the term a_s*b_t with
+ * s + t >= n lands at s + t - n with a minus sign. */
+void orc_negacyclic_schoolbook(const u32 *a, const u32 *b, u32 *out, u32 n, u64 q) {
+  for (u32 k = 0; k < n; k++) out[k] = 0;
+  for (u32 s = 0; s < n; s++) {
+    for (u32 t = 0; t < n; t++) {
+      u64 pr = mulmod(a[s] % q, b[t] % q, q);
+      u32 k = s + t;
+      if (k < n)
+        out[k] = (u32)addmod(out[k], pr, q);
+      else
+        out[k - n] = (u32)submod(out[k - n], pr, q);
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Database encoding                                                         */
+/* ------------------------------------------------------------------------- */
+
+/* Coefficient t of plaintext polynomial `poly`: bits [(poly*n + t)*log2p, +log2p)
+ * of the raw byte stream, little-endian bit order (bit b is bit b%8 of byte b/8). */
+static u32 raw_coeff(const u8 *raw, u32 log2p, u32 n, u64 poly, u32 t) {
+  const u64 bit0 = ((u64)poly * n + t) * log2p, bit_end = bit0 + log2p; /* [bit0, bit_end) */
+  const u64 byte0 = bit0 >> 3;
+  u64 w = 0;
+  for (u64 by = byte0; by * 8 < bit_end; by++) w |= (u64)raw[by] << (8 * (by - byte0));
+  return (u32)((w >> (bit0 & 7)) & ((1ull << log2p) - 1));
+}
+
+void orc_unpack_poly(const u8 *raw, u32 log2p, u32 n, u64 poly, u32 *coef) {
+  for (u32 t = 0; t < n; t++) coef[t] = raw_coeff(raw, log2p, n, poly, t);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Threads: a plain static partition of [0, count) over worker threads.      */
+/* ------------------------------------------------------------------------- */
+
+typedef void (*orc_task_fn)(void *ctx, u64 item, void *scratch);
+typedef struct {
+  orc_task_fn fn;
+  void *ctx;
+  u64 begin, end;
+  size_t scratch_bytes;
+} orc_worker;
+
+static void *orc_worker_main(void *arg) {
+  orc_worker *w = (orc_worker *)arg;
+  void *scratch = w->scratch_bytes ? malloc(w->scratch_bytes) : NULL;
+  for (u64 it = w->begin; it < w->end; it++) w->fn(w->ctx, it, scratch);
+  free(scratch);
+  return NULL;
+}
+
+static void orc_parallel_for(u64 count, int nthreads, orc_task_fn fn, void *ctx, size_t scratch_bytes) {
+  if (nthreads < 1) nthreads = 1;
+  if ((u64)nthreads > count) nthreads = (int)(count ? count : 1);
+  pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * nthreads);
+  orc_worker *ws = (orc_worker *)malloc(sizeof(orc_worker) * nthreads);
+  for (int t = 0; t < nthreads; t++) {
+    ws[t].fn = fn;
+    ws[t].ctx = ctx;
+    ws[t].begin = count * t / nthreads;
+    ws[t].end = count * (t + 1) / nthreads;
+    ws[t].scratch_bytes = scratch_bytes;
+  }
+  for (int t = 1; t < nthreads; t++) pthread_create(&th[t], NULL, orc_worker_main, &ws[t]);
+  orc_worker_main(&ws[0]);
+  for (int t = 1; t < nthreads; t++) pthread_join(th[t], NULL);
+  free(th);
+  free(ws);
+}
+
+/* ------------------------------------------------------------------------- */
+/* The answer: first-dimension folding                                       */
+/* ------------------------------------------------------------------------- */
+
+
+/* NTT-form of plaintext DB polynomials.  poly_ids[t] = i*D2 + c; out is
+ * [count][L][n].  Lifting a coefficient < p < q_j to residue j is the identity. */
+typedef struct {
+  const orc_params *P;
+  const u8 *raw;
+  const u64 *ids;
+  u32 *out;
+} encode_ctx;
+
+static void encode_one(void *vctx, u64 t, void *scratch) {
+  (void)scratch;
+  encode_ctx *x = (encode_ctx *)vctx;
+  const orc_params *P = x->P;
+  for (u32 j = 0; j < P->L; j++) {
+    u32 *dst = x->out + (t * P->L + j) * P->n;
+    orc_unpack_poly(x->raw, P->log2p, P->n, x->ids[t], dst);
+    orc_ntt_fwd(dst, P->n, P->q[j], P->psi[j]);
+  }
+}
+
+void orc_encode_polys(const orc_params *P, const u8 *raw, const u64 *poly_ids, u64 count, u32 *out, int nthreads) {
+  encode_ctx x = {P, raw, poly_ids, out};
+  orc_parallel_for(count, nthreads, encode_one, &x, 0);
+}
+
+/* Forward NTT of every query polynomial: queries [B][D1][2][L][n] -> same layout. */
+typedef struct {
+  const orc_params *P;
+  u32 *polys;
+} ntt_ctx;
+
+static void ntt_one(void *vctx, u64 r, void *scratch) {
+  (void)scratch;
+  ntt_ctx *x = (ntt_ctx *)vctx;
+  u32 j = (u32)(r % x->P->L);
+  orc_ntt_fwd(x->polys + r * x->P->n, x->P->n, x->P->q[j], x->P->psi[j]);
+}
+static void intt_one(void *vctx, u64 r, void *scratch) {
+  (void)scratch;
+  ntt_ctx *x = (ntt_ctx *)vctx;
+  u32 j = (u32)(r % x->P->L);
+  orc_ntt_inv(x->polys + r * x->P->n, x->P->n, x->P->q[j], x->P->psi[j]);
+}
+
+void orc_ntt_fwd_rns_mt(const orc_params *P, u32 *polys, u64 count, int nthreads) {
+  ntt_ctx x = {P, polys};
+  orc_parallel_for(count * P->L, nthreads, ntt_one, &x, 0);
+}
+void orc_ntt_inv_rns_mt(const orc_params *P, u32 *polys, u64 count, int nthreads) {
+  ntt_ctx x = {P, polys};
+  orc_parallel_for(count * P->L, nthreads, intt_one, &x, 0);
+}
+
+/* The answer for a set of columns, given their NTT-form DB polynomials.
+ *   dbhat     [ncols][D1][L][n]   NTT form of DB[i][cols[t]]
+ *   qhat      [B][D1][2][L][n]    NTT form of the query ciphertexts
+ *   responses [B][ncols][2][L][n] coefficient form
+ * For every prime j and slot k: acc[b][comp][j][k] = sum_i dbhat[i][j][k] * qhat[b][i][comp][j][k]
+ * mod q_j (Sec. 4 / Sec. 4.2), then the inverse NTT of acc. */
+typedef struct {
+  const orc_params *P;
+  const u32 *dbhat;
+  const u32 *qhat;
+  u32 B, ncols;
+  u32 *resp;
+} fold_ctx;
+
+static void fold_column(void *vctx, u64 t, void *scratch) {
+  fold_ctx *x = (fold_ctx *)vctx;
+  const orc_params *P = x->P;
+  const u32 n = P->n, L = P->L, D1 = P->D1, B = x->B;
+  u32 *acc = (u32 *)scratch; /* [B][2][L][n] */
+  memset(acc, 0, sizeof(u32) * (size_t)B * 2 * L * n);
+  for (u32 i = 0; i < D1; i++)
+    for (u32 j = 0; j < L; j++) {
+      const u32 *d = x->dbhat + ((t * D1 + i) * L + j) * n;
+      for (u32 b = 0; b < B; b++)
+        for (u32 comp = 0; comp < 2; comp++) {
+          const u32 *qv = x->qhat + ((((u64)b * D1 + i) * 2 + comp) * L + j) * n;
+          u32 *av = acc + (((u64)b * 2 + comp) * L + j) * n;
+          for (u32 k = 0; k < n; k++) av[k] = (u32)addmod(av[k], mulmod(d[k], qv[k], P->q[j]), P->q[j]);
+        }
+    }
+  for (u32 b = 0; b < B; b++)
+    for (u32 comp = 0; comp < 2; comp++)
+      for (u32 j = 0; j < L; j++) {
+        u32 *av = acc + (((u64)b * 2 + comp) * L + j) * n;
+        orc_ntt_inv(av, n, P->q[j], P->psi[j]);
+        memcpy(x->resp + (((((u64)b * x->ncols + t) * 2 + comp) * L + j) * n), av, sizeof(u32) * n);
+      }
+}
+
+void orc_answer_encoded(const orc_params *P, const u32 *dbhat, u32 ncols, const u32 *qhat, u32 B, u32 *responses,
+                        int nthreads) {
+  fold_ctx x = {P, dbhat, qhat, B, ncols, responses};
+  orc_parallel_for(ncols, nthreads, fold_column, &x, sizeof(u32) * (size_t)B * 2 * P->L * P->n);
+}
+
+/* Whole answer for the requested columns from the raw DB and coefficient-form
+ * queries: encode the needed DB polynomials, NTT the queries, fold, INTT.
+ * Returns 0, or -1 if memory runs out. */
+int orc_answer(const orc_params *P, const u8 *raw, const u32 *queries, u32 B, const u32 *cols, u32 ncols,
+               u32 *responses, int nthreads) {
+  const u64 qwords = (u64)B * P->D1 * 2 * P->L * P->n;
+  u32 *qhat = (u32 *)malloc(sizeof(u32) * qwords);
+  u64 *ids = (u64 *)malloc(sizeof(u64) * (u64)ncols * P->D1);
+  u32 *dbhat = (u32 *)malloc(sizeof(u32) * (u64)ncols * P->D1 * P->L * P->n);
+  if (!qhat || !ids || !dbhat) {
+    free(qhat);
+    free(ids);
+    free(dbhat);
+    return -1;
+  }
+  memcpy(qhat, queries, sizeof(u32) * qwords);
+  orc_ntt_fwd_rns_mt(P, qhat, (u64)B * P->D1 * 2, nthreads);
+  for (u32 t = 0; t < ncols; t++)
+    for (u32 i = 0; i < P->D1; i++) ids[(u64)t * P->D1 + i] = (u64)i * P->D2 + cols[t];
+  orc_encode_polys(P, raw, ids, (u64)ncols * P->D1, dbhat, nthreads);
+  orc_answer_encoded(P, dbhat, ncols, qhat, B, responses, nthreads);
+  free(qhat);
+  free(ids);
+  free(dbhat);
+  return 0;
+}
+
+/* The same answer straight from the definition of folding (Sec. 3.2): every
+ * response polynomial is sum_i DB[i][c](X) * ct_i(X) in Z_{q_j}[X]/(X^n + 1) by
+ * schoolbook products, no NTT anywhere.  O(D1 n^2) per output; tiny rings only. */
+void orc_answer_schoolbook(const orc_params *P, const u8 *raw, const u32 *queries, u32 B, u32 *responses) {
+  const u32 n = P->n, L = P->L, D1 = P->D1, D2 = P->D2;
+  u32 *d = (u32 *)malloc(sizeof(u32) * n);
+  u32 *prod = (u32 *)malloc(sizeof(u32) * n);
+  for (u32 b = 0; b < B; b++)
+    for (u32 c = 0; c < D2; c++)
+      for (u32 comp = 0; comp < 2; comp++)
+        for (u32 j = 0; j < L; j++) {
+          u32 *out = responses + ((((u64)b * D2 + c) * 2 + comp) * L + j) * n;
+          memset(out, 0, sizeof(u32) * n);
+          for (u32 i = 0; i < D1; i++) {
+            orc_unpack_poly(raw, P->log2p, n, (u64)i * D2 + c, d);
+            const u32 *ct = queries + ((((u64)b * D1 + i) * 2 + comp) * L + j) * n;
+            orc_negacyclic_schoolbook(d, ct, prod, n, P->q[j]);
+            for (u32 k = 0; k < n; k++) out[k] = (u32)addmod(out[k], prod[k], P->q[j]);
+          }
+        }
+  free(d);
+  free(prod);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Toy RLWE (BFV-style) client, App. A.2                                     */
+/* ------------------------------------------------------------------------- */
+
+/* Product in Z_q[X]/(X^n+1) through the (pinned) fast NTT. */
+static void ring_mul(const u32 *a, const u32 *b, u32 *out, u32 n, u64 q, u64 psi) {
+  u32 *fb = (u32 *)malloc(sizeof(u32) * n);
+  memcpy(out, a, sizeof(u32) * n);
+  memcpy(fb, b, sizeof(u32) * n);
+  orc_ntt_fwd(out, n, q, psi);
+  orc_ntt_fwd(fb, n, q, psi);
+  for (u32 k = 0; k < n; k++) out[k] = (u32)mulmod(out[k], fb[k], q);
+  orc_ntt_inv(out, n, q, psi);
+  free(fb);
+}
+
+/* q = prod_j q_j (< 2^120 for L <= 4) and Delta = floor(q / p). */
+static u128 full_modulus(const orc_params *P) {
+  u128 q = 1;
+  for (u32 j = 0; j < P->L; j++) q *= P->q[j];
+  return q;
+}
+
+/* Writes q (as two u64 halves, low first) and Delta; lets the tests check
+ * Delta*p + 1 = q (App. A.4). */
+void orc_modulus_info(const orc_params *P, u64 *q_lo_hi, u64 *delta_lo_hi) {
+  u128 q = full_modulus(P);
+  u128 delta = q >> P->log2p; /* floor(q / p), p = 2^log2p */
+  q_lo_hi[0] = (u64)q;
+  q_lo_hi[1] = (u64)(q >> 64);
+  delta_lo_hi[0] = (u64)delta;
+  delta_lo_hi[1] = (u64)(delta >> 64);
+}
+
+/* Encrypt(m) -> (a, b) with a*s + b = Delta*m + e (mod q).
+ *   s [n] ternary in {-1,0,1};  a [L][n] residues (uniform mod q by CRT);
+ *   e [n] small signed error;   m [n] plaintext coefficients in [0, p).
+ *   ct [2][L][n]: component 0 = a, 1 = b. */
+void orc_bfv_encrypt(const orc_params *P, const int8_t *s, const u32 *a, const int8_t *e, const u32 *m, u32 *ct) {
+  const u32 n = P->n, L = P->L;
+  u128 delta = full_modulus(P) >> P->log2p;
+  u32 *sj = (u32 *)malloc(sizeof(u32) * n);
+  u32 *as = (u32 *)malloc(sizeof(u32) * n);
+  for (u32 j = 0; j < L; j++) {
+    const u64 q = P->q[j];
+    const u64 dj = (u64)(delta % q);
+    for (u32 t = 0; t < n; t++) sj[t] = (u32)((s[t] + (i128)q) % q);
+    ring_mul(a + (u64)j * n, sj, as, n, q, P->psi[j]);
+    for (u32 t = 0; t < n; t++) {
+      u64 et = (u64)((e[t] + (i128)q) % q);
+      u64 bt = addmod(mulmod(dj, m[t] % q, q), et, q);
+      ct[(u64)j * n + t] = a[(u64)j * n + t];
+      ct[((u64)L + j) * n + t] = (u32)submod(bt, as[t], q);
+    }
+  }
+  free(sj);
+  free(as);
+}
+
+/* Phase phi = a*s + b (mod q), recombined from the residues by CRT (Garner). */
+static void phase(const orc_params *P, const int8_t *s, const u32 *ct, u128 *phi) {
+  const u32 n = P->n, L = P->L;
+  u32 *sj = (u32 *)malloc(sizeof(u32) * n);
+  u32 *res = (u32 *)malloc(sizeof(u32) * (size_t)L * n);
+  for (u32 j = 0; j < L; j++) {
+    const u64 q = P->q[j];
+    for (u32 t = 0; t < n; t++) sj[t] = (u32)((s[t] + (i128)q) % q);
+    ring_mul(ct + (u64)j * n, sj, res + (u64)j * n, n, q, P->psi[j]);
+    for (u32 t = 0; t < n; t++) res[(u64)j * n + t] = (u32)addmod(res[(u64)j * n + t], ct[((u64)L + j) * n + t], q);
+  }
+  for (u32 t = 0; t < n; t++) {
+    u128 x = res[t], M = P->q[0];
+    for (u32 j = 1; j < L; j++) {
+      const u64 q = P->q[j];
+      u64 xm = (u64)(x % q);
+      u64 inv = invmod_prime((u64)(M % q), q);
+      u64 h = mulmod(submod(res[(u64)j * n + t], xm, q), inv, q);
+      x += (u128)h * M;
+      M *= q;
+    }
+    phi[t] = x;
+  }
+  free(sj);
+  free(res);
+}
+
+/* Decrypt: centre the phase in (-q/2, q/2], m = round(phi / Delta) mod p. */
+void orc_bfv_decrypt(const orc_params *P, const int8_t *s, const u32 *ct, u32 *m_out) {
+  const u32 n = P->n;
+  const u128 q = full_modulus(P);
+  const i128 delta = (i128)(q >> P->log2p);
+  const u64 pmask = (1ull << P->log2p) - 1;
+  u128 *phi = (u128 *)malloc(sizeof(u128) * n);
+  phase(P, s, ct, phi);
+  for (u32 t = 0; t < n; t++) {
+    i128 v = (phi[t] > q / 2) ? (i128)phi[t] - (i128)q : (i128)phi[t];
+    /* round(v / delta) = floor((2v + delta) / (2 delta)), floor for negatives too */
+    i128 num = 2 * v + delta, den = 2 * delta;
+    i128 qt = num / den;
+    if ((num % den != 0) && (num < 0)) qt -= 1;
+    m_out[t] = (u32)((u64)qt & pmask);
+  }
+  free(phi);
+}
+
+/* Noise of a ciphertext that should encrypt m: the centred phase minus Delta*m,
+ * per coefficient, as a signed 64-bit value (saturated).  Used to report the
+ * decryption margin against Delta/2 (App. A.2). */
+void orc_bfv_noise(const orc_params *P, const int8_t *s, const u32 *ct, const u32 *m, int64_t *noise) {
+  const u32 n = P->n;
+  const u128 q = full_modulus(P);
+  const u128 delta = q >> P->log2p;
+  u128 *phi = (u128 *)malloc(sizeof(u128) * n);
+  phase(P, s, ct, phi);
+  for (u32 t = 0; t < n; t++) {
+    u128 dm = (delta * m[t]) % q;
+    u128 diff = (phi[t] + q - dm) % q;
+    i128 v = (diff > q / 2) ? (i128)diff - (i128)q : (i128)diff;
+    if (v > (i128)INT64_MAX) v = INT64_MAX;
+    if (v < (i128)INT64_MIN) v = INT64_MIN;
+    noise[t] = (int64_t)v;
+  }
+  free(phi);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Freivalds check of a full response tensor                                 */
+/* ------------------------------------------------------------------------- */
+
+/* With r[j][c] random residues, folding is linear in the DB, so
+ *   sum_c r_c * R[b][c]  ==  INTT( sum_i NTT(y_i) . NTT(ct_{b,i}) ),  y_i = sum_c r_c * DB[i][c]
+ * holds for a correct R; a wrong coefficient survives with probability <= 1/q_j.
+ * The check never forms the NTT-form DB.  Returns the number of mismatching
+ * coefficients over [B][2][L][n], or -1 if memory runs out. */
+typedef struct {
+  const orc_params *P;
+  const u8 *raw;
+  const u32 *r;
+  u32 *yhat; /* [D1][L][n] */
+} fr_ctx;
+
+static void fr_row(void *vctx, u64 i, void *scratch) {
+  fr_ctx *x = (fr_ctx *)vctx;
+  const orc_params *P = x->P;
+  const u32 n = P->n, L = P->L, D2 = P->D2;
+  u32 *d = (u32 *)scratch;
+  u32 *y = x->yhat + i * L * n;
+  memset(y, 0, sizeof(u32) * L * n);
+  for (u32 c = 0; c < D2; c++) {
+    orc_unpack_poly(x->raw, P->log2p, n, i * D2 + c, d);
+    for (u32 j = 0; j < L; j++) {
+      const u64 q = P->q[j], rc = x->r[(u64)j * D2 + c];
+      u32 *yj = y + (u64)j * n;
+      for (u32 t = 0; t < n; t++) yj[t] = (u32)addmod(yj[t], mulmod(d[t], rc, q), q);
+    }
+  }
+  for (u32 j = 0; j < L; j++) orc_ntt_fwd(y + (u64)j * n, n, P->q[j], P->psi[j]);
+}
+
+long long orc_freivalds(const orc_params *P, const u8 *raw, const u32 *queries, u32 B, const u32 *responses,
+                        const u32 *r, int nthreads) {
+  const u32 n = P->n, L = P->L, D1 = P->D1, D2 = P->D2;
+  u32 *yhat = (u32 *)malloc(sizeof(u32) * (u64)D1 * L * n);
+  u32 *qhat = (u32 *)malloc(sizeof(u32) * (u64)B * D1 * 2 * L * n);
+  u32 *acc = (u32 *)malloc(sizeof(u32) * n);
+  if (!yhat || !qhat || !acc) {
+    free(yhat);
+    free(qhat);
+    free(acc);
+    return -1;
+  }
+  fr_ctx x = {P, raw, r, yhat};
+  orc_parallel_for(D1, nthreads, fr_row, &x, sizeof(u32) * n);
+  memcpy(qhat, queries, sizeof(u32) * (u64)B * D1 * 2 * L * n);
+  orc_ntt_fwd_rns_mt(P, qhat, (u64)B * D1 * 2, nthreads);
+  long long bad = 0;
+  for (u32 b = 0; b < B; b++)
+    for (u32 comp = 0; comp < 2; comp++)
+      for (u32 j = 0; j < L; j++) {
+        const u64 q = P->q[j];
+        memset(acc, 0, sizeof(u32) * n);
+        for (u32 i = 0; i < D1; i++) {
+          const u32 *yv = yhat + ((u64)i * L + j) * n;
+          const u32 *qv = qhat + ((((u64)b * D1 + i) * 2 + comp) * L + j) * n;
+          for (u32 k = 0; k < n; k++) acc[k] = (u32)addmod(acc[k], mulmod(yv[k], qv[k], q), q);
+        }
+        orc_ntt_inv(acc, n, q, P->psi[j]);
+        for (u32 k = 0; k < n; k++) {
+          u64 rhs = 0;
+          for (u32 c = 0; c < D2; c++)
+            rhs = addmod(rhs, mulmod(r[(u64)j * D2 + c], responses[((((u64)b * D2 + c) * 2 + comp) * L + j) * n + k], q), q);
+          if (rhs != acc[k]) bad++;
+        }
+      }
+  free(yhat);
+  free(qhat);
+  free(acc);
+  return bad;
+}
+
+/* The phase a*s + b (mod q) of a ciphertext, each coefficient as two u64 halves
+ * (low first), in [0, q).  Lets the tests check App. A.2 / A.4 identities exactly. */
+void orc_bfv_phase(const orc_params *P, const int8_t *s, const u32 *ct, u64 *phi_lo_hi) {
+  u128 *phi = (u128 *)malloc(sizeof(u128) * P->n);
+  phase(P, s, ct, phi);
+  for (u32 t = 0; t < P->n; t++) {
+    phi_lo_hi[2 * t] = (u64)phi[t];
+    phi_lo_hi[2 * t + 1] = (u64)(phi[t] >> 64);
+  }
+  free(phi);
+}

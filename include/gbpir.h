@@ -1,0 +1,178 @@
+/*
+ * gbpir.h -- C ABI of the GB300 (sm_103a) RLWE-PIR first-dimension scan.
+ *
+ * The server's online linear scan of single-server PIR in its poly-HE
+ * (RLWE) form, as described in VIPIR (arXiv 2606.11536):
+ *   - the database is NTT-encoded once ("DB bloating", Sec. 3.3; fused RNS lift
+ *     and NTT, Sec. 4.3);
+ *   - a query is D1 RLWE ciphertexts, one per first-dimension index (a one-hot
+ *     encryption, Sec. 2.5 / Sec. 3.2 "poly-HE folding");
+ *   - the answer folds the first dimension: for every column c,
+ *     out_c = sum_i DB[i][c] * ct_i in R_q^2 (plaintext-ciphertext products,
+ *     App. A.2), computed per RNS prime q_j and NTT slot k as
+ *     out[b][c][k] = sum_i DB[i][c][k] * Q[b][i][k] mod q_j
+ *     ("(#RNS*N)-parallel INT32 modular GEMMs", Sec. 4 and Sec. 4.2),
+ *     then inverse-NTT'd back to coefficient form.
+ *
+ * Conventions shared by every call:
+ *   - A polynomial ring is Z_q[X]/(X^n + 1), n a power of two in [2^11, 2^13];
+ *     q = q_0 * ... * q_{L-1} with 30-bit primes q_j = 1 mod 2n and q_j = 1 mod p
+ *     (App. A.4).  Residues are uint32 values, canonical in [0, q_j).
+ *   - An RNS polynomial is laid out [L][n] (row j holds the residues mod q_j).
+ *   - NTT order: NTT(a)[k] = sum_t a_t * psi_j^((2*brv(k) + 1) * t) mod q_j, with
+ *     brv the log2(n)-bit reversal and psi_j a primitive 2n-th root of unity.
+ *   - A ciphertext is [2][L][n]: component 0 = a(X), component 1 = b(X), with
+ *     a*s + b = Delta*m + e (mod q), Delta = floor(q/p) (App. A.2).
+ *   - Calls on device buffers are asynchronous and ordered on `stream` (a
+ *     cudaStream_t, NULL = the legacy default stream).  Calls on host buffers are
+ *     synchronous: they return once the host output is written.
+ *   - Every call returns a status; nothing aborts, traps or exits.
+ *   - All device pointers must be 16-byte aligned.
+ */
+#ifndef GBPIR_H
+#define GBPIR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIR_MAX_L 4
+
+typedef enum {
+  PIR_OK = 0,
+  PIR_ERR_ARG = 1,         /* bad pointer, size, shape or parameter              */
+  PIR_ERR_OOM = 2,         /* a device or host allocation failed                 */
+  PIR_ERR_ADMISSION = 3,   /* the DB does not fit the device memory left         */
+  PIR_ERR_CUDA = 4,        /* a CUDA runtime call failed (see pir_last_cuda_error) */
+  PIR_ERR_TIMEOUT = 5,     /* a bounded wait ran out                             */
+  PIR_ERR_HANDLE = 6,      /* unknown or already freed DB handle                 */
+  PIR_ERR_UNSUPPORTED = 7  /* valid request this build does not implement        */
+} pir_status_t;
+
+/* Parameters of one PIR instance.  n = ring degree, L = number of RNS primes,
+ * log2p = log2 of the plaintext modulus p, D1 x D2 = database shape in plaintext
+ * polynomials (D1 = first dimension, folded by the scan; D2 = columns).  q[j] and
+ * psi[j] for j < L; unused entries are zero. */
+typedef struct {
+  uint32_t n, L, log2p, D1, D2;
+  uint32_t q[PIR_MAX_L];
+  uint32_t psi[PIR_MAX_L];
+} pir_params_t;
+
+/* Resident-DB layouts, chosen once at setup (the GEMM path follows the layout). */
+typedef enum {
+  PIR_LAYOUT_PLAIN = 0, /* u32 residues [L*n slots][D1][D2]: CUDA-core u32 x u32 -> u64 path */
+  PIR_LAYOUT_LIMB = 1   /* u8 limb planes [L*n slots][4][D2][D1]: INT8 tensor-pipe path    */
+} pir_layout_t;
+
+typedef struct pir_db *pir_db_t;
+
+/* Fill *out for ring degree n, plaintext modulus 2^log2p, shape D1 x D2 and L
+ * primes: q_j are the L largest primes in (2^29, 2^30) with q_j = 1 mod max(2n, p),
+ * in decreasing order; psi_j = h^((q_j - 1)/(2n)) for the smallest h >= 2 with
+ * psi_j^n = -1 (App. A.4; the root choice is this library's reading, the paper
+ * does not fix one).  Errors: PIR_ERR_ARG for n not in {2^11, 2^12, 2^13},
+ * L not in [1, 4], log2p not in [1, 28] or 2n not dividing a power of two >= p,
+ * or D1/D2 zero; PIR_ERR_UNSUPPORTED if fewer than L such primes exist. */
+pir_status_t pir_make_params(uint32_t n, uint32_t log2p, uint32_t D1, uint32_t D2, uint32_t L,
+                             pir_params_t *out);
+
+/* Load and NTT-encode a database (Sec. 3.3; RNS lift fused with the NTT, Sec. 4.3).
+ *   raw_db:     D1*D2*n*log2p/8 bytes, a little-endian bit stream of log2p-bit
+ *               coefficients, polynomial after polynomial, polynomial (i, c) at
+ *               position i*D2 + c.  Host or device memory (raw_on_device).
+ *   layout:     PIR_LAYOUT_PLAIN or PIR_LAYOUT_LIMB.
+ *   stream:     cudaStream_t for the encode kernels; the call returns after the
+ *               DB is resident (it synchronizes the stream).
+ *   out_handle: receives the handle; the library owns the resident DB until
+ *               pir_free_db.  The caller keeps ownership of raw_db.
+ * Errors: PIR_ERR_ARG (NULL pointers, raw_bytes mismatch, invalid params),
+ * PIR_ERR_ADMISSION (resident bytes exceed the free device memory less a reserve),
+ * PIR_ERR_OOM, PIR_ERR_CUDA. */
+pir_status_t pir_setup_db(const pir_params_t *params, const void *raw_db, size_t raw_bytes, int raw_on_device,
+                          int layout, void *stream, pir_db_t *out_handle);
+
+/* Answer a batch of B queries against a resident DB (the online scan).
+ *   queries:   [B][D1][2][L][n] uint32, coefficient form, canonical residues.
+ *   responses: [B][D2][2][L][n] uint32, coefficient form, canonical; written.
+ *   on_device: 1 = both buffers are device memory (asynchronous on stream);
+ *              0 = both are host memory (copied in and out; synchronous; pinned
+ *              host memory gives the fastest copies).
+ * Computes, for every b, c: responses[b][c] = sum_i DB[i][c] * queries[b][i] in
+ * R_q^2 (Sec. 3.2; Sec. 4 "INT32 modular GEMM"), through forward NTT of the
+ * queries, the per-slot modular GEMM on the layout's GEMM path, reduction to
+ * [0, q_j) and inverse NTT.  Scratch device memory is drawn from the stream-ordered
+ * allocator and returned before the call's work completes.
+ * Errors: PIR_ERR_HANDLE, PIR_ERR_ARG (B = 0, NULL or misaligned buffers),
+ * PIR_ERR_OOM, PIR_ERR_CUDA. */
+pir_status_t pir_answer(pir_db_t db, const uint32_t *queries, uint32_t B, uint32_t *responses, int on_device,
+                        void *stream);
+
+/* Options for pir_answer_ex.  Zero-initialised = the defaults of pir_answer. */
+typedef struct {
+  uint32_t k_chunk;  /* 0 = whole D1 at once; else fold D1 in chunks of this many
+                        ciphertexts (bounds the scratch memory to one chunk)        */
+  uint32_t tile;     /* 0 = built-in choice; else a GEMM tile id (pir_gemm_tiles)  */
+  uint32_t flags;    /* bit 0 (PIR_ANSWER_STAGE_TIMES): record CUDA events around each
+                        stage on `stream`; read with pir_stage_times.  Other bits 0. */
+} pir_answer_opts_t;
+
+#define PIR_ANSWER_STAGE_TIMES 1u
+
+/* Stages of one answer, in order: forward NTT of the queries, query transpose to
+ * the slot-major layout, modular GEMM (with its reduction epilogue), result
+ * transpose, inverse NTT. */
+#define PIR_STAGES 5
+
+pir_status_t pir_answer_ex(pir_db_t db, const uint32_t *queries, uint32_t B, uint32_t *responses, int on_device,
+                           void *stream, const pir_answer_opts_t *opts);
+
+/* Forward / inverse negacyclic NTT of `count` RNS polynomials [count][L][n] in
+ * place, in device memory, asynchronously on stream (Sec. 2.3; single-kernel
+ * on-chip NTT, Sec. 4.3).  Inputs must be canonical; outputs are canonical.
+ * ntt_inv includes the scaling by n^-1, so ntt_inv(ntt_fwd(a)) = a.
+ * Errors: PIR_ERR_ARG (NULL, misaligned, invalid params), PIR_ERR_CUDA. */
+pir_status_t ntt_fwd(const pir_params_t *params, uint32_t *polys, size_t count, void *stream);
+pir_status_t ntt_inv(const pir_params_t *params, uint32_t *polys, size_t count, void *stream);
+
+/* Release a DB handle and its device memory (synchronizes the device first). */
+pir_status_t pir_free_db(pir_db_t db);
+
+/* Resident device bytes of a DB. */
+pir_status_t pir_db_bytes(pir_db_t db, size_t *bytes);
+
+/* The parameters and layout a DB was set up with. */
+pir_status_t pir_db_info(pir_db_t db, pir_params_t *params, int *layout);
+
+/* Copy the NTT-form residues of DB polynomial (i, c) = poly_index / D2, % D2 to
+ * host memory out[L][n] (canonical, NTT order as above).  For inspection and
+ * tests; synchronous. */
+pir_status_t pir_db_read_poly(pir_db_t db, uint64_t poly_index, uint32_t *out);
+
+/* Human-readable name of a status; never NULL. */
+const char *pir_status_str(pir_status_t status);
+
+/* The last CUDA error string seen by this library on the calling thread ("" if none). */
+const char *pir_last_cuda_error(void);
+
+/* Number of GEMM tile choices for a layout (ids 1..count for pir_answer_opts_t.tile). */
+uint32_t pir_gemm_tiles(int layout);
+
+/* Per-stage device time of the answers issued with PIR_ANSWER_STAGE_TIMES by the
+ * calling thread since the last reset: waits for their events, adds each stage's
+ * elapsed milliseconds into ms[PIR_STAGES] and its kernel launches into
+ * launches[PIR_STAGES] (either may be NULL), and resets.  The events are recorded on
+ * the stream each stage runs on, so a stage's time is its kernels' time on that
+ * stream.  Errors: PIR_ERR_CUDA. */
+pir_status_t pir_stage_times(double *ms, uint64_t *launches);
+
+/* Number of kernels this library has launched in this process (all threads). */
+uint64_t pir_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBPIR_H */

@@ -1,0 +1,269 @@
+"""ctypes binding of ``libgbpir.so`` (C ABI in ``include/gbpir.h``).
+
+Argument marshalling only: every step of the scan runs in the CUDA library.
+Device buffers are torch CUDA tensors (uint32 / uint8, contiguous); host
+buffers are numpy arrays or CPU tensors.  There is no CPU fallback: if the
+library is missing the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+PIR_MAX_L = 4
+PIR_LAYOUT_PLAIN = 0
+PIR_LAYOUT_LIMB = 1
+
+STATUS = {
+    0: "PIR_OK", 1: "PIR_ERR_ARG", 2: "PIR_ERR_OOM", 3: "PIR_ERR_ADMISSION", 4: "PIR_ERR_CUDA",
+    5: "PIR_ERR_TIMEOUT", 6: "PIR_ERR_HANDLE", 7: "PIR_ERR_UNSUPPORTED",
+}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgbpir.so")
+
+
+class PirError(RuntimeError):
+    def __init__(self, status: int, what: str, detail: str = ""):
+        self.status = status
+        msg = "%s failed: %s" % (what, STATUS.get(status, str(status)))
+        if detail:
+            msg += " (%s)" % detail
+        super().__init__(msg)
+
+
+class pir_params_t(C.Structure):
+    _fields_ = [
+        ("n", C.c_uint32), ("L", C.c_uint32), ("log2p", C.c_uint32), ("D1", C.c_uint32), ("D2", C.c_uint32),
+        ("q", C.c_uint32 * PIR_MAX_L), ("psi", C.c_uint32 * PIR_MAX_L),
+    ]
+
+    @property
+    def qs(self):
+        return [int(self.q[j]) for j in range(self.L)]
+
+    @property
+    def psis(self):
+        return [int(self.psi[j]) for j in range(self.L)]
+
+    def __repr__(self):
+        return "pir_params_t(n=%d, L=%d, log2p=%d, D1=%d, D2=%d, q=%s, psi=%s)" % (
+            self.n, self.L, self.log2p, self.D1, self.D2, self.qs, self.psis)
+
+
+class pir_answer_opts_t(C.Structure):
+    _fields_ = [("k_chunk", C.c_uint32), ("tile", C.c_uint32), ("flags", C.c_uint32)]
+
+
+_lib = None
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("CUDA library %s is missing: build it first (__graft_entry__.build())" % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        P = C.POINTER(pir_params_t)
+        vp, sz, u32, u64, i32 = C.c_void_p, C.c_size_t, C.c_uint32, C.c_uint64, C.c_int
+        sigs = {
+            "pir_make_params": (i32, [u32, u32, u32, u32, u32, P]),
+            "pir_setup_db": (i32, [P, vp, sz, i32, i32, vp, C.POINTER(vp)]),
+            "pir_answer": (i32, [vp, vp, u32, vp, i32, vp]),
+            "pir_answer_ex": (i32, [vp, vp, u32, vp, i32, vp, C.POINTER(pir_answer_opts_t)]),
+            "ntt_fwd": (i32, [P, vp, sz, vp]),
+            "ntt_inv": (i32, [P, vp, sz, vp]),
+            "pir_free_db": (i32, [vp]),
+            "pir_db_bytes": (i32, [vp, C.POINTER(sz)]),
+            "pir_db_info": (i32, [vp, P, C.POINTER(i32)]),
+            "pir_db_read_poly": (i32, [vp, u64, vp]),
+            "pir_status_str": (C.c_char_p, [i32]),
+            "pir_last_cuda_error": (C.c_char_p, []),
+            "pir_gemm_tiles": (u32, [i32]),
+            "pir_stage_times": (i32, [C.POINTER(C.c_double), C.POINTER(C.c_uint64)]),
+            "pir_kernel_launches": (C.c_uint64, []),
+        }
+        for name, (res, args) in sigs.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(st: int, what: str):
+    if st != 0:
+        detail = ""
+        if st == 4:
+            detail = lib().pir_last_cuda_error().decode()
+        raise PirError(st, what, detail)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(buf):
+    """(pointer, on_device, nbytes) of a torch tensor or numpy array."""
+    if isinstance(buf, np.ndarray):
+        if not buf.flags["C_CONTIGUOUS"]:
+            raise ValueError("host buffer must be C-contiguous")
+        return C.c_void_p(buf.ctypes.data), False, buf.nbytes
+    import torch
+    if isinstance(buf, torch.Tensor):
+        if not buf.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(buf.data_ptr()), buf.is_cuda, buf.numel() * buf.element_size()
+    raise TypeError("expected a numpy array or torch tensor, got %r" % type(buf))
+
+
+# --- the ABI, one function per entry point ---------------------------------
+
+def pir_make_params(n: int, log2p: int, D1: int, D2: int, L: int = 2) -> pir_params_t:
+    p = pir_params_t()
+    _check(lib().pir_make_params(n, log2p, D1, D2, L, C.byref(p)), "pir_make_params")
+    return p
+
+
+class Db:
+    """A resident database handle (owns the device memory until freed)."""
+
+    def __init__(self, handle: int, params: pir_params_t, layout: int):
+        self.handle = handle
+        self.params = params
+        self.layout = layout
+
+    def __repr__(self):
+        return "Db(%r, layout=%d)" % (self.params, self.layout)
+
+
+def pir_setup_db(params: pir_params_t, raw_db, layout: int = PIR_LAYOUT_PLAIN, stream=None) -> Db:
+    ptr, on_dev, nbytes = _ptr(raw_db)
+    h = C.c_void_p()
+    _check(lib().pir_setup_db(C.byref(params), ptr, nbytes, int(on_dev), layout, _stream_ptr(stream), C.byref(h)),
+           "pir_setup_db")
+    return Db(h.value, params, layout)
+
+
+def pir_answer(db: Db, queries, B: int, responses, stream=None):
+    qp, qdev, _ = _ptr(queries)
+    rp, rdev, _ = _ptr(responses)
+    if qdev != rdev:
+        raise ValueError("queries and responses must both be host or both be device buffers")
+    _check(lib().pir_answer(C.c_void_p(db.handle), qp, B, rp, int(qdev), _stream_ptr(stream)), "pir_answer")
+    return responses
+
+
+def pir_answer_ex(db: Db, queries, B: int, responses, stream=None, k_chunk: int = 0, tile: int = 0, flags: int = 0):
+    qp, qdev, _ = _ptr(queries)
+    rp, rdev, _ = _ptr(responses)
+    if qdev != rdev:
+        raise ValueError("queries and responses must both be host or both be device buffers")
+    o = pir_answer_opts_t(k_chunk, tile, flags)
+    _check(lib().pir_answer_ex(C.c_void_p(db.handle), qp, B, rp, int(qdev), _stream_ptr(stream), C.byref(o)),
+           "pir_answer_ex")
+    return responses
+
+
+def ntt_fwd(params: pir_params_t, polys, count: int | None = None, stream=None):
+    ptr, dev, nbytes = _ptr(polys)
+    if not dev:
+        raise ValueError("ntt_fwd works on device memory")
+    cnt = nbytes // (4 * params.L * params.n) if count is None else count
+    _check(lib().ntt_fwd(C.byref(params), ptr, cnt, _stream_ptr(stream)), "ntt_fwd")
+    return polys
+
+
+def ntt_inv(params: pir_params_t, polys, count: int | None = None, stream=None):
+    ptr, dev, nbytes = _ptr(polys)
+    if not dev:
+        raise ValueError("ntt_inv works on device memory")
+    cnt = nbytes // (4 * params.L * params.n) if count is None else count
+    _check(lib().ntt_inv(C.byref(params), ptr, cnt, _stream_ptr(stream)), "ntt_inv")
+    return polys
+
+
+def pir_free_db(db: Db):
+    _check(lib().pir_free_db(C.c_void_p(db.handle)), "pir_free_db")
+    db.handle = None
+
+
+def pir_db_bytes(db: Db) -> int:
+    v = C.c_size_t()
+    _check(lib().pir_db_bytes(C.c_void_p(db.handle), C.byref(v)), "pir_db_bytes")
+    return v.value
+
+
+def pir_db_info(db: Db):
+    p = pir_params_t()
+    lay = C.c_int()
+    _check(lib().pir_db_info(C.c_void_p(db.handle), C.byref(p), C.byref(lay)), "pir_db_info")
+    return p, lay.value
+
+
+def pir_db_read_poly(db: Db, poly_index: int) -> np.ndarray:
+    out = np.empty((db.params.L, db.params.n), dtype=np.uint32)
+    _check(lib().pir_db_read_poly(C.c_void_p(db.handle), poly_index, C.c_void_p(out.ctypes.data)),
+           "pir_db_read_poly")
+    return out
+
+
+def pir_status_str(status: int) -> str:
+    return lib().pir_status_str(status).decode()
+
+
+def pir_gemm_tiles(layout: int) -> int:
+    return int(lib().pir_gemm_tiles(layout))
+
+
+PIR_ANSWER_STAGE_TIMES = 1
+PIR_STAGES = 5
+STAGE_NAMES = ("query_ntt", "query_transpose", "gemm", "result_transpose", "intt")
+
+
+def pir_stage_times():
+    """(ms per stage, launches per stage) of the timed answers since the last call."""
+    ms = (C.c_double * PIR_STAGES)()
+    ln = (C.c_uint64 * PIR_STAGES)()
+    _check(lib().pir_stage_times(ms, ln), "pir_stage_times")
+    return list(ms), list(ln)
+
+
+def pir_kernel_launches() -> int:
+    return int(lib().pir_kernel_launches())
+
+
+# --- sizes (host logic) ----------------------------------------------------
+
+def poly_bytes(n: int, L: int) -> int:
+    """One RNS polynomial: L rows of n 32-bit residues."""
+    return 4 * L * n
+
+
+def ct_bytes(n: int, L: int) -> int:
+    """One RLWE ciphertext: two RNS polynomials."""
+    return 2 * poly_bytes(n, L)
+
+
+def raw_db_bytes(p) -> int:
+    return p.D1 * p.D2 * p.n * p.log2p // 8
+
+
+def resident_db_bytes(p) -> int:
+    return 4 * p.L * p.n * p.D1 * p.D2
+
+
+def query_bytes(p, B: int) -> int:
+    return B * p.D1 * ct_bytes(p.n, p.L)
+
+
+def response_bytes(p, B: int) -> int:
+    return B * p.D2 * ct_bytes(p.n, p.L)

@@ -1,0 +1,433 @@
+// api.cu -- the C ABI (include/gbpir.h): parameter checks, resident-DB registry,
+// admission by free device memory, and the answer pipeline
+//   queries --NTT--> NTT form --transpose--> slot-major --modular GEMM--> slot-major
+//   results --transpose--> responses (NTT form) --INTT--> responses
+// (Sec. 3.2 poly-HE folding; Sec. 4.2 transposes around the parallel GEMMs;
+// Sec. 4.4 per-stream fixed buffers -> the K-chunked variant here).
+#include <atomic>
+#include <mutex>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace gbpir {
+
+namespace {
+thread_local std::string t_last_cuda;
+}
+
+void set_cuda_error(cudaError_t e) { t_last_cuda = cudaGetErrorString(e); }
+const char *last_cuda_error_cstr() { return t_last_cuda.c_str(); }
+
+std::atomic<uint64_t> g_launches{0};
+void count_launches(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+pir_status_t cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return PIR_OK;
+  set_cuda_error(e);
+  if (e == cudaErrorMemoryAllocation) return PIR_ERR_OOM;
+  return PIR_ERR_CUDA;
+}
+
+}  // namespace gbpir
+
+using namespace gbpir;
+
+struct pir_db {
+  uint64_t magic;
+  pir_params_t p;
+  int layout;
+  int device;
+  const ParamCtx *ctx;
+  void *resident;
+  size_t bytes;
+};
+
+namespace {
+
+constexpr uint64_t kMagic = 0x4742504952444231ull;  // "GBPIRDB1"
+std::mutex g_reg_mu;
+std::set<pir_db *> g_live;
+
+bool live(pir_db *db) {
+  std::lock_guard<std::mutex> lock(g_reg_mu);
+  return db && g_live.count(db) && db->magic == kMagic;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+#define CK(expr)                                   \
+  do {                                             \
+    cudaError_t e_ = (expr);                       \
+    if (e_ != cudaSuccess) return cuda_status(e_); \
+  } while (0)
+
+// Device scratch drawn from the stream-ordered allocator; freed (stream-ordered)
+// when the guard goes out of scope.
+struct Scratch {
+  void *ptr = nullptr;
+  cudaStream_t s;
+  explicit Scratch(cudaStream_t st) : s(st) {}
+  cudaError_t alloc(size_t bytes) { return cudaMallocAsync(&ptr, bytes, s); }
+  ~Scratch() {
+    if (ptr) cudaFreeAsync(ptr, s);
+  }
+};
+
+size_t resident_bytes(const pir_params_t &p) { return (size_t)4 * p.L * p.n * p.D1 * p.D2; }
+size_t raw_bytes_of(const pir_params_t &p) { return (size_t)p.D1 * p.D2 * p.n * p.log2p / 8; }
+
+uint32_t round4(uint32_t x) { return (x + 3u) & ~3u; }
+
+// Keep the pool's memory once freed: repeated answers then reuse it instead of
+// returning it to the driver every call.
+void keep_pool_memory(int dev) {
+  static std::once_flag once;
+  std::call_once(once, [dev]() {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = ~0ull;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+  });
+}
+
+// Optional per-stage timing: a pair of events around every stage invocation.
+struct StageMark {
+  int stage;
+  uint64_t launches;
+  cudaEvent_t a, b;
+};
+thread_local std::vector<StageMark> t_marks;
+thread_local std::vector<cudaEvent_t> t_free_events;
+
+cudaEvent_t take_event() {
+  if (!t_free_events.empty()) {
+    cudaEvent_t e = t_free_events.back();
+    t_free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+struct StageTimer {
+  bool on;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  StageTimer(bool enable, cudaStream_t st) : on(enable), s(st) {}
+  void begin() {
+    if (on && (a = take_event())) cudaEventRecord(a, s);
+  }
+  void end(int stage, uint64_t launches) {
+    count_launches(launches);
+    if (!on || !a) return;
+    cudaEvent_t b = take_event();
+    if (!b) return;
+    cudaEventRecord(b, s);
+    t_marks.push_back({stage, launches, a, b});
+    a = nullptr;
+  }
+};
+
+// The device-buffer answer (stream ordered).
+pir_status_t answer_device(pir_db *db, const uint32_t *queries, uint32_t B, uint32_t *responses, cudaStream_t s,
+                           const pir_answer_opts_t &o) {
+  const ParamCtx &c = *db->ctx;
+  const pir_params_t &p = db->p;
+  const uint32_t n = p.n, L = p.L, D1 = p.D1, D2 = p.D2;
+  const uint32_t M = 2 * B, Mp = round4(M);
+  const uint32_t Kc = (o.k_chunk == 0 || o.k_chunk >= D1) ? D1 : o.k_chunk;
+  const uint64_t nslots = (uint64_t)L * n;
+  const uint32_t tile_count = db->layout == PIR_LAYOUT_PLAIN ? gemm_plain_tiles() : gemm_limb_tiles();
+  if (o.tile > tile_count || (o.flags & ~PIR_ANSWER_STAGE_TIMES) != 0) return PIR_ERR_ARG;
+
+  // scratch: NTT'd query chunk | slot-major query chunk | slot-major results
+  const size_t qhat_bytes = (size_t)B * Kc * 2 * L * n * 4;
+  const size_t qs_bytes = db->layout == PIR_LAYOUT_PLAIN ? nslots * Kc * Mp * 4 : nslots * 4 * Mp * Kc;
+  const size_t out_bytes = nslots * M * D2 * 4;
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  Scratch scratch(s);
+  CK(scratch.alloc(up(qhat_bytes) + up(qs_bytes) + up(out_bytes)));
+  char *base = static_cast<char *>(scratch.ptr);
+  uint32_t *qhat = reinterpret_cast<uint32_t *>(base);
+  void *qs = base + up(qhat_bytes);
+  uint32_t *out = reinterpret_cast<uint32_t *>(base + up(qhat_bytes) + up(qs_bytes));
+
+  StageTimer tm((o.flags & PIR_ANSWER_STAGE_TIMES) != 0, s);
+  for (uint32_t i0 = 0; i0 < D1; i0 += Kc) {
+    const uint32_t kc = D1 - i0 < Kc ? D1 - i0 : Kc;
+    // forward NTT of ciphertexts i0 .. i0+kc-1 of every query: per query b the rows
+    // (b*D1 + i0)*2L .. +kc*2L are contiguous.
+    const uint64_t G = (uint64_t)kc * 2 * L, S = (uint64_t)D1 * 2 * L;
+    tm.begin();
+    CK(launch_ntt_fwd_rows(c, queries, (uint64_t)i0 * 2 * L, G, S, qhat, (uint64_t)B * G, s));
+    tm.end(0, 1);
+    if (db->layout == PIR_LAYOUT_PLAIN) {
+      tm.begin();
+      CK(launch_query_to_slots(c, qhat, B, kc, Mp, static_cast<uint32_t *>(qs), s));
+      tm.end(1, 1);
+      tm.begin();
+      CK(launch_gemm_plain(c, static_cast<const uint32_t *>(db->resident), D1, D2, static_cast<const uint32_t *>(qs),
+                           M, Mp, i0, kc, out, i0 > 0, o.tile, s));
+      tm.end(2, 1);
+    } else {
+      tm.begin();
+      CK(launch_query_to_limbs(c, qhat, B, kc, Mp, static_cast<uint8_t *>(qs), s));
+      tm.end(1, 1);
+      tm.begin();
+      CK(launch_gemm_limb(c, static_cast<const uint8_t *>(db->resident), D1, D2, static_cast<const uint8_t *>(qs), M,
+                          Mp, i0, kc, out, i0 > 0, o.tile, s));
+      tm.end(2, 1);
+    }
+  }
+  tm.begin();
+  CK(launch_slots_to_responses(c, out, B, D2, responses, s));
+  tm.end(3, 1);
+  tm.begin();
+  CK(launch_ntt_inv(c, responses, responses, (uint64_t)B * D2 * 2 * L, s));
+  tm.end(4, 1);
+  return PIR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *pir_status_str(pir_status_t st) {
+  switch (st) {
+    case PIR_OK: return "ok";
+    case PIR_ERR_ARG: return "invalid argument";
+    case PIR_ERR_OOM: return "out of memory";
+    case PIR_ERR_ADMISSION: return "database does not fit the free device memory";
+    case PIR_ERR_CUDA: return "CUDA error";
+    case PIR_ERR_TIMEOUT: return "timed out";
+    case PIR_ERR_HANDLE: return "unknown or freed database handle";
+    case PIR_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char *pir_last_cuda_error(void) { return gbpir::last_cuda_error_cstr(); }
+
+pir_status_t pir_stage_times(double *ms, uint64_t *launches) {
+  cudaError_t first = cudaSuccess;
+  for (const StageMark &m : t_marks) {
+    float t = 0.f;
+    cudaError_t e = cudaEventSynchronize(m.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, m.a, m.b);
+    if (e != cudaSuccess && first == cudaSuccess) first = e;
+    if (ms) ms[m.stage] += t;
+    if (launches) launches[m.stage] += m.launches;
+    t_free_events.push_back(m.a);
+    t_free_events.push_back(m.b);
+  }
+  t_marks.clear();
+  return cuda_status(first);
+}
+
+uint64_t pir_kernel_launches(void) { return g_launches.load(); }
+
+uint32_t pir_gemm_tiles(int layout) {
+  if (layout == PIR_LAYOUT_PLAIN) return gemm_plain_tiles();
+  if (layout == PIR_LAYOUT_LIMB) return gemm_limb_tiles();
+  return 0;
+}
+
+pir_status_t pir_setup_db(const pir_params_t *params, const void *raw_db, size_t raw_bytes, int raw_on_device,
+                          int layout, void *stream, pir_db_t *out_handle) {
+  if (!params || !raw_db || !out_handle) return PIR_ERR_ARG;
+  if (layout != PIR_LAYOUT_PLAIN && layout != PIR_LAYOUT_LIMB) return PIR_ERR_ARG;
+  pir_status_t st = validate_params(params);
+  if (st != PIR_OK) return st;
+  const pir_params_t p = *params;
+  if (raw_bytes != raw_bytes_of(p)) return PIR_ERR_ARG;
+  if (layout == PIR_LAYOUT_PLAIN && (p.D2 % 4) != 0) return PIR_ERR_UNSUPPORTED;  // 128-bit column loads
+  if (layout == PIR_LAYOUT_LIMB && (p.D1 % 32) != 0) return PIR_ERR_UNSUPPORTED;  // k32 tensor steps
+  *out_handle = nullptr;
+  const ParamCtx *ctx = nullptr;
+  st = get_param_ctx(&p, &ctx);
+  if (st != PIR_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  keep_pool_memory(dev);
+
+  // Admission: resident DB (+ the raw bytes if they must be staged) + the NTT
+  // staging chunk, against the free memory less a reserve.
+  const size_t bytes = resident_bytes(p);
+  const uint64_t polys = (uint64_t)p.D1 * p.D2;
+  const uint64_t chunk_polys_target = (uint64_t)(256u << 20) / ((uint64_t)4 * p.L * p.n);
+  uint64_t chunk = chunk_polys_target < polys ? chunk_polys_target : polys;
+  if (layout == PIR_LAYOUT_LIMB) {  // whole columns per chunk
+    uint64_t cols = chunk / p.D1;
+    if (cols == 0) cols = 1;
+    chunk = cols * p.D1;
+  }
+  const size_t staging = (size_t)chunk * p.L * p.n * 4;
+  size_t free_b = 0, total_b = 0;
+  CK(cudaMemGetInfo(&free_b, &total_b));
+  size_t reserve = total_b / 32;
+  if (reserve > ((size_t)2 << 30)) reserve = (size_t)2 << 30;
+  const size_t need = bytes + staging + (raw_on_device ? 0 : raw_bytes);
+  if (need + reserve > free_b) return PIR_ERR_ADMISSION;
+
+  pir_db *db = new pir_db();
+  db->magic = kMagic;
+  db->p = p;
+  db->layout = layout;
+  db->device = dev;
+  db->ctx = ctx;
+  db->bytes = bytes;
+  cudaError_t e = cudaMalloc(&db->resident, bytes);
+  if (e != cudaSuccess) {
+    delete db;
+    return cuda_status(e);
+  }
+  void *raw_dev = nullptr, *stage = nullptr;
+  auto fail = [&](cudaError_t err) {
+    cudaStreamSynchronize(s);
+    if (raw_dev) cudaFree(raw_dev);
+    if (stage) cudaFree(stage);
+    cudaFree(db->resident);
+    delete db;
+    return cuda_status(err);
+  };
+  const uint8_t *raw = static_cast<const uint8_t *>(raw_db);
+  if (!raw_on_device) {
+    if ((e = cudaMalloc(&raw_dev, raw_bytes)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpyAsync(raw_dev, raw_db, raw_bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess) return fail(e);
+    raw = static_cast<const uint8_t *>(raw_dev);
+  }
+  if ((e = cudaMalloc(&stage, staging)) != cudaSuccess) return fail(e);
+  uint32_t *stg = static_cast<uint32_t *>(stage);
+  if (layout == PIR_LAYOUT_PLAIN) {
+    for (uint64_t first = 0; first < polys; first += chunk) {
+      const uint64_t np = polys - first < chunk ? polys - first : chunk;
+      if ((e = launch_ntt_fwd_raw(*ctx, raw, 0, p.D1, p.D2, first, np, stg, s)) != cudaSuccess) return fail(e);
+      if ((e = launch_db_scatter(*ctx, layout, p.D1, p.D2, stg, first, np, db->resident, s)) != cudaSuccess)
+        return fail(e);
+      count_launches(2);
+    }
+  } else {
+    const uint64_t ccols = chunk / p.D1;
+    for (uint64_t c0 = 0; c0 < p.D2; c0 += ccols) {
+      const uint64_t nc = p.D2 - c0 < ccols ? p.D2 - c0 : ccols;
+      const uint64_t np = nc * p.D1;
+      if ((e = launch_ntt_fwd_raw(*ctx, raw, 1, p.D1, p.D2, c0, np, stg, s)) != cudaSuccess) return fail(e);
+      if ((e = launch_db_scatter(*ctx, layout, p.D1, p.D2, stg, c0, np, db->resident, s)) != cudaSuccess)
+        return fail(e);
+      count_launches(2);
+    }
+  }
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(e);
+  if (raw_dev) cudaFree(raw_dev);
+  cudaFree(stage);
+  {
+    std::lock_guard<std::mutex> lock(g_reg_mu);
+    g_live.insert(db);
+  }
+  *out_handle = db;
+  return PIR_OK;
+}
+
+pir_status_t pir_answer_ex(pir_db_t db, const uint32_t *queries, uint32_t B, uint32_t *responses, int on_device,
+                           void *stream, const pir_answer_opts_t *opts) {
+  if (!live(db)) return PIR_ERR_HANDLE;
+  if (B == 0 || !queries || !responses) return PIR_ERR_ARG;
+  pir_answer_opts_t o = {};
+  if (opts) o = *opts;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const pir_params_t &p = db->p;
+  const size_t qbytes = (size_t)B * p.D1 * 2 * p.L * p.n * 4;
+  const size_t rbytes = (size_t)B * p.D2 * 2 * p.L * p.n * 4;
+  if (on_device) {
+    if (!aligned16(queries) || !aligned16(responses)) return PIR_ERR_ARG;
+    return answer_device(db, queries, B, responses, s, o);
+  }
+  // host buffers: stage through device memory; synchronous
+  Scratch dq(s), dr(s);
+  CK(dq.alloc(qbytes));
+  CK(dr.alloc(rbytes));
+  CK(cudaMemcpyAsync(dq.ptr, queries, qbytes, cudaMemcpyHostToDevice, s));
+  pir_status_t st =
+      answer_device(db, static_cast<const uint32_t *>(dq.ptr), B, static_cast<uint32_t *>(dr.ptr), s, o);
+  if (st != PIR_OK) {
+    cudaStreamSynchronize(s);
+    return st;
+  }
+  CK(cudaMemcpyAsync(responses, dr.ptr, rbytes, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return PIR_OK;
+}
+
+pir_status_t pir_answer(pir_db_t db, const uint32_t *queries, uint32_t B, uint32_t *responses, int on_device,
+                        void *stream) {
+  return pir_answer_ex(db, queries, B, responses, on_device, stream, nullptr);
+}
+
+static pir_status_t ntt_common(const pir_params_t *params, uint32_t *polys, size_t count, void *stream, bool fwd) {
+  if (!params || (!polys && count)) return PIR_ERR_ARG;
+  if (count == 0) return validate_params(params);
+  if (!aligned16(polys)) return PIR_ERR_ARG;
+  const ParamCtx *ctx = nullptr;
+  pir_status_t st = get_param_ctx(params, &ctx);
+  if (st != PIR_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const uint64_t rows = (uint64_t)count * params->L;
+  CK(fwd ? launch_ntt_fwd(*ctx, polys, polys, rows, s) : launch_ntt_inv(*ctx, polys, polys, rows, s));
+  count_launches(1);
+  return PIR_OK;
+}
+
+pir_status_t ntt_fwd(const pir_params_t *params, uint32_t *polys, size_t count, void *stream) {
+  return ntt_common(params, polys, count, stream, true);
+}
+
+pir_status_t ntt_inv(const pir_params_t *params, uint32_t *polys, size_t count, void *stream) {
+  return ntt_common(params, polys, count, stream, false);
+}
+
+pir_status_t pir_free_db(pir_db_t db) {
+  {
+    std::lock_guard<std::mutex> lock(g_reg_mu);
+    if (!db || !g_live.count(db)) return PIR_ERR_HANDLE;
+    g_live.erase(db);
+  }
+  cudaDeviceSynchronize();
+  cudaError_t e = cudaFree(db->resident);
+  db->magic = 0;
+  delete db;
+  return cuda_status(e);
+}
+
+pir_status_t pir_db_bytes(pir_db_t db, size_t *bytes) {
+  if (!live(db)) return PIR_ERR_HANDLE;
+  if (!bytes) return PIR_ERR_ARG;
+  *bytes = db->bytes;
+  return PIR_OK;
+}
+
+pir_status_t pir_db_info(pir_db_t db, pir_params_t *params, int *layout) {
+  if (!live(db)) return PIR_ERR_HANDLE;
+  if (params) *params = db->p;
+  if (layout) *layout = db->layout;
+  return PIR_OK;
+}
+
+pir_status_t pir_db_read_poly(pir_db_t db, uint64_t poly_index, uint32_t *out) {
+  if (!live(db)) return PIR_ERR_HANDLE;
+  if (!out || poly_index >= (uint64_t)db->p.D1 * db->p.D2) return PIR_ERR_ARG;
+  const size_t bytes = (size_t)db->p.L * db->p.n * 4;
+  uint32_t *tmp = nullptr;
+  CK(cudaMalloc(&tmp, bytes));
+  cudaError_t e = launch_db_read_poly(*db->ctx, db->layout, db->p.D1, db->p.D2, db->resident, poly_index, tmp, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(out, tmp, bytes, cudaMemcpyDeviceToHost);
+  cudaFree(tmp);
+  return cuda_status(e);
+}
+
+}  // extern "C"

@@ -1,0 +1,122 @@
+// common.cuh -- internal declarations of the GB300 PIR scan library.
+//
+// Shared by the .cu files of this library only (never by the CPU oracle).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gbpir.h"
+
+namespace gbpir {
+
+// ---------------------------------------------------------------------------
+// Per-prime NTT constants handed to kernels by value.
+// ---------------------------------------------------------------------------
+struct PrimeTables {
+  const uint32_t *fwd;     // [n] psi^brv(i)
+  const uint32_t *fwd_sh;  // [n] floor(psi^brv(i) * 2^32 / q)   (Shoup companion)
+  const uint32_t *inv;     // [n] psi^-brv(i)
+  const uint32_t *inv_sh;  // [n] Shoup companions
+};
+
+struct NttConst {
+  uint32_t q[PIR_MAX_L];
+  uint32_t ninv[PIR_MAX_L];     // n^-1 mod q
+  uint32_t ninv_sh[PIR_MAX_L];  // Shoup companion of n^-1
+  PrimeTables t[PIR_MAX_L];
+};
+
+// Reduction constants of the modular GEMM epilogues.
+struct ModConst {
+  uint32_t q[PIR_MAX_L];
+  uint32_t c60[PIR_MAX_L];  // 2^60 mod q
+  uint64_t mu[PIR_MAX_L];   // floor(2^64 / q)
+};
+
+// Host-side: the ring (n, L, primes, roots) plus device tables, cached per device
+// and ring.  p.D1 / p.D2 are zero here: database shapes are passed per call.
+struct ParamCtx {
+  pir_params_t p;
+  uint32_t logn;
+  NttConst ntt;
+  ModConst mod;
+};
+
+// params.cu
+pir_status_t validate_params(const pir_params_t *p);
+pir_status_t get_param_ctx(const pir_params_t *p, const ParamCtx **out);  // cached, device-resident tables
+
+// Error bookkeeping (api.cu)
+pir_status_t cuda_status(cudaError_t e);
+void set_cuda_error(cudaError_t e);
+const char *last_cuda_error_cstr();
+
+// ntt.cu.  Rows are polynomials of n residues; row r uses prime r % L.
+cudaError_t launch_ntt_fwd(const ParamCtx &c, const uint32_t *src, uint32_t *dst, uint64_t rows, cudaStream_t s);
+// Forward NTT of `rows` rows where local row r reads source row off + (r / G) * S + r % G.
+cudaError_t launch_ntt_fwd_rows(const ParamCtx &c, const uint32_t *src, uint64_t off, uint64_t G, uint64_t S,
+                                uint32_t *dst, uint64_t rows, cudaStream_t s);
+cudaError_t launch_ntt_inv(const ParamCtx &c, const uint32_t *src, uint32_t *dst, uint64_t rows, cudaStream_t s);
+// Forward NTT of DB plaintexts read from the raw bit stream (RNS lift fused: a
+// coefficient < p < q_j is its own residue).  Row-major: polys first .. first+np-1;
+// column-major: local poly p is (i, c) = (p % D1, first + p / D1).  dst is [np][L][n].
+cudaError_t launch_ntt_fwd_raw(const ParamCtx &c, const uint8_t *raw, int col_major, uint32_t D1, uint32_t D2,
+                               uint64_t first, uint64_t npolys, uint32_t *dst, cudaStream_t s);
+
+// layout.cu (layouts are described at the top of layout.cu)
+cudaError_t launch_query_to_slots(const ParamCtx &c, const uint32_t *qhat, uint32_t B, uint32_t Kc, uint32_t Mp,
+                                  uint32_t *qs, cudaStream_t s);
+cudaError_t launch_query_to_limbs(const ParamCtx &c, const uint32_t *qhat, uint32_t B, uint32_t Kc, uint32_t Mp,
+                                  uint8_t *ql, cudaStream_t s);
+cudaError_t launch_slots_to_responses(const ParamCtx &c, const uint32_t *out, uint32_t B, uint32_t D2,
+                                      uint32_t *resp, cudaStream_t s);
+// first = first poly id (plain, row-major chunk) or first column (limb, column-major chunk)
+cudaError_t launch_db_scatter(const ParamCtx &c, int layout, uint32_t D1, uint32_t D2, const uint32_t *polys,
+                              uint64_t first, uint64_t np, void *resident, cudaStream_t s);
+cudaError_t launch_db_read_poly(const ParamCtx &c, int layout, uint32_t D1, uint32_t D2, const void *resident,
+                                uint64_t poly, uint32_t *out, cudaStream_t s);
+
+// gemm_plain.cu: for every slot s, out[s][m][c] = (acc ? out[s][m][c] : 0) + sum over the
+// Kc rows i0.. of qs[s][i - i0][m] * db[s][i][c], reduced mod q_j, for m < M, c < D2.
+cudaError_t launch_gemm_plain(const ParamCtx &c, const uint32_t *db, uint32_t D1, uint32_t D2, const uint32_t *qs,
+                              uint32_t M, uint32_t Mp, uint32_t i0, uint32_t Kc, uint32_t *out, int acc,
+                              uint32_t tile, cudaStream_t s);
+uint32_t gemm_plain_tiles();
+
+// gemm_limb.cu: the same contract on the limb layouts (db [s][4][D2][D1] u8,
+// ql [s][4][Mp][Kc] u8), exact through u8 x u8 -> s32 tensor-pipe products.
+cudaError_t launch_gemm_limb(const ParamCtx &c, const uint8_t *db, uint32_t D1, uint32_t D2, const uint8_t *ql,
+                             uint32_t M, uint32_t Mp, uint32_t i0, uint32_t Kc, uint32_t *out, int acc,
+                             uint32_t tile, cudaStream_t s);
+uint32_t gemm_limb_tiles();
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+
+// Shoup multiplication by a constant w < q with wsh = floor(w * 2^32 / q):
+// returns x * w mod q in [0, 2q) for any x < 2^32 (needs q < 2^31).
+__device__ __forceinline__ uint32_t shoup_mul(uint32_t x, uint32_t w, uint32_t wsh, uint32_t q) {
+  uint32_t hi = __umulhi(x, wsh);
+  return x * w - hi * q;
+}
+
+// Folds the top four bits of a 64-bit accumulator: result = acc mod q + multiple of q,
+// below 2^60 + 2^34.  With q < 2^30 the accumulator then takes 15 more products
+// (q-1)^2 before it could reach 2^64.
+__device__ __forceinline__ uint64_t fold60(uint64_t acc, uint32_t c60) {
+  uint32_t top = (uint32_t)(acc >> 60);
+  return (acc & ((1ull << 60) - 1)) + (uint64_t)top * c60;
+}
+
+// Full reduction of a 64-bit value mod q (q < 2^30): Barrett with mu = floor(2^64/q).
+__device__ __forceinline__ uint32_t reduce64(uint64_t x, uint32_t q, uint64_t mu) {
+  uint64_t qt = __umul64hi(x, mu);
+  uint64_t r = x - qt * q;  // in [0, 2q) (Barrett's error is at most one q here)
+  if (r >= q) r -= q;
+  if (r >= q) r -= q;
+  return (uint32_t)r;
+}
+
+}  // namespace gbpir

@@ -1,0 +1,322 @@
+// ntt.cu -- forward / inverse negacyclic NTT over 30-bit primes (Sec. 2.3; the
+// paper's single-kernel, on-chip NTT, Sec. 4.3).
+//
+// One CTA transforms one polynomial row of n residues (row r uses prime r % L).
+// Each thread holds 16 residues in registers and applies four butterfly stages
+// to them; the rows pass through shared memory (padded one word in sixteen) between
+// such radix-16 passes: n = 2^11 -> 4+4+3 bits, 2^12 -> 4+4+4, 2^13 -> 4+4+4+1.
+//
+// Arithmetic: twiddles are psi^brv(i) (forward) and psi^-brv(i) (inverse) with
+// Shoup companions floor(w * 2^32 / q), so each twiddle product is one high and
+// two low 32-bit multiplies.  Butterflies keep values lazily reduced (Harvey):
+// forward values live in [0, 4q), inverse values in [0, 2q); 4q < 2^32 because
+// q < 2^30.  The last pass reduces to canonical [0, q) (and, for the inverse,
+// multiplies by n^-1).
+//
+// Output order: forward NTT(a)[k] = sum_t a_t psi^((2 brv(k) + 1) t), the natural
+// result of decimation in time with psi powers in bit-reversed order.
+#include "common.cuh"
+
+namespace gbpir {
+namespace {
+
+__device__ __forceinline__ uint32_t padx(uint32_t i) { return i + (i >> 4); }
+
+// Source kinds of the first pass.
+enum { SRC_SMEM = 0, SRC_U32 = 1, SRC_RAW = 2 };
+
+struct RawSrc {
+  const uint8_t *raw;  // little-endian bit stream of log2p-bit coefficients
+  uint64_t poly0;      // row-major order: local polynomial p is poly0 + p
+  uint32_t log2p;
+  uint32_t col_major;  // 1: local polynomial p is (i, c) = (p % D1, c0 + p / D1)
+  uint32_t D1, D2;
+  uint64_t c0;
+  __device__ __forceinline__ uint64_t poly(uint64_t p) const {
+    return col_major ? (p % D1) * D2 + (c0 + p / D1) : poly0 + p;
+  }
+};
+
+// Source rows of a launch: local row r reads row off + (r / G) * S + r % G, so a
+// chunk of ciphertexts can be taken out of every query of a batch without a copy.
+struct RowMap {
+  uint64_t off, G, S;
+  __device__ __forceinline__ uint64_t operator()(uint64_t r) const { return off + (r / G) * S + r % G; }
+};
+
+// Coefficient `t` of plaintext polynomial `poly` from the raw bit stream.
+__device__ __forceinline__ uint32_t raw_coeff(const RawSrc &rs, uint64_t poly, uint32_t t, uint32_t logn) {
+  const uint64_t bit0 = ((poly << logn) + t) * rs.log2p;
+  const uint64_t byte0 = bit0 >> 3;
+  const uint32_t nbytes = (uint32_t)(((bit0 & 7) + rs.log2p + 7) >> 3);
+  uint64_t w = 0;
+  for (uint32_t b = 0; b < nbytes; ++b) w |= (uint64_t)__ldg(rs.raw + byte0 + b) << (8 * b);
+  return (uint32_t)((w >> (bit0 & 7)) & ((1ull << rs.log2p) - 1));
+}
+
+// Forward stages on one radix-2^RB unit: bits BLO+RB-1 down to BLO of the element
+// index.  The pair (x, x + 2^b) of stage bit b belongs to block g = index >> (b+1)
+// and uses twiddle psi^brv(m + g) with m = n >> (b+1).
+template <int RB, int BLO, int LOGN>
+__device__ __forceinline__ void fwd_stages(uint32_t (&v)[1 << RB], uint32_t hi, const uint32_t *__restrict__ w,
+                                           const uint32_t *__restrict__ wsh, uint32_t q) {
+  const uint32_t q2 = 2 * q;
+#pragma unroll
+  for (int lb = RB - 1; lb >= 0; --lb) {
+    const uint32_t m = 1u << (LOGN - 1 - (BLO + lb));
+#pragma unroll
+    for (int e = 0; e < (1 << RB); ++e) {
+      if (e & (1 << lb)) continue;
+      const uint32_t g = (hi << (RB - 1 - lb)) | (uint32_t)(e >> (lb + 1));
+      const uint32_t tw = __ldg(w + m + g), tws = __ldg(wsh + m + g);
+      uint32_t x = v[e];
+      const uint32_t y = v[e | (1 << lb)];
+      x = x >= q2 ? x - q2 : x;              // [0, 2q)
+      const uint32_t t = shoup_mul(y, tw, tws, q);  // [0, 2q)
+      v[e] = x + t;                          // [0, 4q)
+      v[e | (1 << lb)] = x - t + q2;         // (0, 4q)
+    }
+  }
+}
+
+// Inverse stages (Gentleman-Sande), bits BLO up to BLO+RB-1; values in [0, 2q).
+template <int RB, int BLO, int LOGN>
+__device__ __forceinline__ void inv_stages(uint32_t (&v)[1 << RB], uint32_t hi, const uint32_t *__restrict__ w,
+                                           const uint32_t *__restrict__ wsh, uint32_t q) {
+  const uint32_t q2 = 2 * q;
+#pragma unroll
+  for (int lb = 0; lb < RB; ++lb) {
+    const uint32_t m = 1u << (LOGN - 1 - (BLO + lb));
+#pragma unroll
+    for (int e = 0; e < (1 << RB); ++e) {
+      if (e & (1 << lb)) continue;
+      const uint32_t g = (hi << (RB - 1 - lb)) | (uint32_t)(e >> (lb + 1));
+      const uint32_t tw = __ldg(w + m + g), tws = __ldg(wsh + m + g);
+      const uint32_t x = v[e], y = v[e | (1 << lb)];
+      uint32_t s = x + y;
+      s = s >= q2 ? s - q2 : s;
+      v[e] = s;
+      v[e | (1 << lb)] = shoup_mul(x - y + q2, tw, tws, q);
+    }
+  }
+}
+
+// One radix-2^RB pass over the whole row: unit u holds the 2^RB elements whose
+// index has bits [BLO, BLO+RB) free and the rest fixed by u.
+template <int LOGN, int RB, int BLO, bool FWD, int SRC, bool TO_GLOBAL>
+__device__ __forceinline__ void ntt_pass(uint32_t *sm, const uint32_t *__restrict__ gin, const RawSrc &rs,
+                                         uint64_t poly, uint32_t *__restrict__ gout, const uint32_t *__restrict__ w,
+                                         const uint32_t *__restrict__ wsh, uint32_t q, uint32_t ninv,
+                                         uint32_t ninv_sh) {
+  constexpr int N = 1 << LOGN, T = N / 16, UNITS = N >> RB, PER = UNITS / T;
+  static_assert(UNITS % T == 0, "pass plan");
+#pragma unroll
+  for (int r = 0; r < PER; ++r) {
+    const uint32_t u = threadIdx.x + r * T;
+    const uint32_t lo = u & ((1u << BLO) - 1), hi = u >> BLO;
+    const uint32_t base = (hi << (BLO + RB)) | lo;
+    uint32_t v[1 << RB];
+    if constexpr (SRC == SRC_U32 && BLO == 0 && RB >= 2) {
+#pragma unroll
+      for (int e = 0; e < (1 << RB); e += 4) {
+        const uint4 x = __ldg(reinterpret_cast<const uint4 *>(gin + base + e));
+        v[e] = x.x, v[e + 1] = x.y, v[e + 2] = x.z, v[e + 3] = x.w;
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < (1 << RB); ++e) {
+        const uint32_t idx = base | ((uint32_t)e << BLO);
+        if constexpr (SRC == SRC_SMEM)
+          v[e] = sm[padx(idx)];
+        else if constexpr (SRC == SRC_U32)
+          v[e] = __ldg(gin + idx);
+        else
+          v[e] = raw_coeff(rs, poly, idx, LOGN);
+      }
+    }
+    if constexpr (FWD)
+      fwd_stages<RB, BLO, LOGN>(v, hi, w, wsh, q);
+    else
+      inv_stages<RB, BLO, LOGN>(v, hi, w, wsh, q);
+    if constexpr (TO_GLOBAL) {
+#pragma unroll
+      for (int e = 0; e < (1 << RB); ++e) {
+        uint32_t x = v[e];
+        if constexpr (FWD) {
+          x = x >= 2 * q ? x - 2 * q : x;
+          x = x >= q ? x - q : x;
+        } else {
+          x = shoup_mul(x, ninv, ninv_sh, q);
+          x = x >= q ? x - q : x;
+        }
+        v[e] = x;
+      }
+      if constexpr (BLO == 0 && RB >= 2) {
+#pragma unroll
+        for (int e = 0; e < (1 << RB); e += 4)
+          *reinterpret_cast<uint4 *>(gout + base + e) = make_uint4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+      } else if constexpr (BLO == 0 && RB == 1) {
+        *reinterpret_cast<uint2 *>(gout + base) = make_uint2(v[0], v[1]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < (1 << RB); ++e) gout[base | ((uint32_t)e << BLO)] = v[e];
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < (1 << RB); ++e) sm[padx(base | ((uint32_t)e << BLO))] = v[e];
+    }
+  }
+}
+
+template <int LOGN, int SRC>
+__global__ void __launch_bounds__((1 << LOGN) / 16)
+    k_ntt_fwd(const uint32_t *__restrict__ src, RowMap rm, RawSrc rs, uint32_t *__restrict__ dst, NttConst C,
+              uint32_t L, uint64_t rows) {
+  constexpr int N = 1 << LOGN;
+  extern __shared__ uint32_t sm[];
+  for (uint64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+    const uint32_t j = (uint32_t)(row % L);
+    const uint32_t q = C.q[j];
+    const uint32_t *w = C.t[j].fwd, *wsh = C.t[j].fwd_sh;
+    const uint32_t *gin = src ? src + rm(row) * N : nullptr;
+    uint32_t *gout = dst + row * N;
+    const uint64_t poly = SRC == SRC_RAW ? rs.poly(row / L) : 0;
+    if constexpr (LOGN == 11) {
+      ntt_pass<11, 4, 7, true, SRC, false>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
+      __syncthreads();
+      ntt_pass<11, 4, 3, true, SRC_SMEM, false>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
+      __syncthreads();
+      ntt_pass<11, 3, 0, true, SRC_SMEM, true>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
+    } else if constexpr (LOGN == 12) {
+      ntt_pass<12, 4, 8, true, SRC, false>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
+      __syncthreads();
+      ntt_pass<12, 4, 4, true, SRC_SMEM, false>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
+      __syncthreads();
+      ntt_pass<12, 4, 0, true, SRC_SMEM, true>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
+    } else {
+      ntt_pass<13, 4, 9, true, SRC, false>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
+      __syncthreads();
+      ntt_pass<13, 4, 5, true, SRC_SMEM, false>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
+      __syncthreads();
+      ntt_pass<13, 4, 1, true, SRC_SMEM, false>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
+      __syncthreads();
+      ntt_pass<13, 1, 0, true, SRC_SMEM, true>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
+    }
+    __syncthreads();  // the next row reuses shared memory
+  }
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__((1 << LOGN) / 16)
+    k_ntt_inv(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst, NttConst C, uint32_t L, uint64_t rows) {
+  constexpr int N = 1 << LOGN;
+  extern __shared__ uint32_t sm[];
+  const RawSrc rs = {};
+  for (uint64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+    const uint32_t j = (uint32_t)(row % L);
+    const uint32_t q = C.q[j], ni = C.ninv[j], nis = C.ninv_sh[j];
+    const uint32_t *w = C.t[j].inv, *wsh = C.t[j].inv_sh;
+    const uint32_t *gin = src + row * N;
+    uint32_t *gout = dst + row * N;
+    if constexpr (LOGN == 11) {
+      ntt_pass<11, 4, 0, false, SRC_U32, false>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
+      __syncthreads();
+      ntt_pass<11, 4, 4, false, SRC_SMEM, false>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
+      __syncthreads();
+      ntt_pass<11, 3, 8, false, SRC_SMEM, true>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
+    } else if constexpr (LOGN == 12) {
+      ntt_pass<12, 4, 0, false, SRC_U32, false>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
+      __syncthreads();
+      ntt_pass<12, 4, 4, false, SRC_SMEM, false>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
+      __syncthreads();
+      ntt_pass<12, 4, 8, false, SRC_SMEM, true>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
+    } else {
+      ntt_pass<13, 4, 0, false, SRC_U32, false>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
+      __syncthreads();
+      ntt_pass<13, 4, 4, false, SRC_SMEM, false>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
+      __syncthreads();
+      ntt_pass<13, 4, 8, false, SRC_SMEM, false>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
+      __syncthreads();
+      ntt_pass<13, 1, 12, false, SRC_SMEM, true>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
+    }
+    __syncthreads();
+  }
+}
+
+constexpr uint64_t kMaxGrid = 1u << 30;
+
+template <int LOGN>
+cudaError_t fwd_launch(const ParamCtx &c, const uint32_t *src, const RowMap &rm, const RawSrc &rs, uint32_t *dst,
+                       uint64_t rows, cudaStream_t s, bool raw) {
+  const int T = (1 << LOGN) / 16;
+  const size_t smem = ((1u << LOGN) + (1u << LOGN) / 16) * sizeof(uint32_t);
+  const unsigned grid = (unsigned)(rows < kMaxGrid ? rows : kMaxGrid);
+  if (raw)
+    k_ntt_fwd<LOGN, SRC_RAW><<<grid, T, smem, s>>>(nullptr, rm, rs, dst, c.ntt, c.p.L, rows);
+  else
+    k_ntt_fwd<LOGN, SRC_U32><<<grid, T, smem, s>>>(src, rm, rs, dst, c.ntt, c.p.L, rows);
+  return cudaGetLastError();
+}
+
+template <int LOGN>
+cudaError_t inv_launch(const ParamCtx &c, const uint32_t *src, uint32_t *dst, uint64_t rows, cudaStream_t s) {
+  const int T = (1 << LOGN) / 16;
+  const size_t smem = ((1u << LOGN) + (1u << LOGN) / 16) * sizeof(uint32_t);
+  const unsigned grid = (unsigned)(rows < kMaxGrid ? rows : kMaxGrid);
+  k_ntt_inv<LOGN><<<grid, T, smem, s>>>(src, dst, c.ntt, c.p.L, rows);
+  return cudaGetLastError();
+}
+
+cudaError_t fwd_any(const ParamCtx &c, const uint32_t *src, const RowMap &rm, const RawSrc &rs, uint32_t *dst,
+                    uint64_t rows, cudaStream_t s, bool raw) {
+  if (rows == 0) return cudaSuccess;
+  switch (c.logn) {
+    case 11: return fwd_launch<11>(c, src, rm, rs, dst, rows, s, raw);
+    case 12: return fwd_launch<12>(c, src, rm, rs, dst, rows, s, raw);
+    case 13: return fwd_launch<13>(c, src, rm, rs, dst, rows, s, raw);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t launch_ntt_fwd(const ParamCtx &c, const uint32_t *src, uint32_t *dst, uint64_t rows, cudaStream_t s) {
+  const RawSrc rs = {};
+  const RowMap rm = {0, rows ? rows : 1, 0};
+  return fwd_any(c, src, rm, rs, dst, rows, s, false);
+}
+
+cudaError_t launch_ntt_fwd_rows(const ParamCtx &c, const uint32_t *src, uint64_t off, uint64_t G, uint64_t S,
+                                uint32_t *dst, uint64_t rows, cudaStream_t s) {
+  const RawSrc rs = {};
+  const RowMap rm = {off, G, S};
+  return fwd_any(c, src, rm, rs, dst, rows, s, false);
+}
+
+cudaError_t launch_ntt_fwd_raw(const ParamCtx &c, const uint8_t *raw, int col_major, uint32_t D1, uint32_t D2,
+                               uint64_t first, uint64_t npolys, uint32_t *dst, cudaStream_t s) {
+  RawSrc rs = {};
+  rs.raw = raw;
+  rs.log2p = c.p.log2p;
+  rs.col_major = col_major ? 1u : 0u;
+  rs.D1 = D1;
+  rs.D2 = D2;
+  if (col_major)
+    rs.c0 = first;
+  else
+    rs.poly0 = first;
+  const RowMap rm = {0, 1, 1};
+  return fwd_any(c, nullptr, rm, rs, dst, npolys * c.p.L, s, true);
+}
+
+cudaError_t launch_ntt_inv(const ParamCtx &c, const uint32_t *src, uint32_t *dst, uint64_t rows, cudaStream_t s) {
+  if (rows == 0) return cudaSuccess;
+  switch (c.logn) {
+    case 11: return inv_launch<11>(c, src, dst, rows, s);
+    case 12: return inv_launch<12>(c, src, dst, rows, s);
+    case 13: return inv_launch<13>(c, src, dst, rows, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace gbpir

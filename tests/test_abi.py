@@ -1,0 +1,107 @@
+"""CPU-side checks of the C ABI library: it loads without a GPU, exports every
+function include/gbpir.h declares, computes the same ring parameters as the
+oracle, and rejects bad arguments with status codes (no GPU call is made)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2606_11536_gb300 as g
+from golden.read import paper_values
+from paper_2606_11536_gb300 import binding
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2606_11536_gb300 import build
+    build.build()
+    return binding.lib()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "gbpir.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z_0-9]*\s*\**\s*([A-Za-z_][A-Za-z_0-9]*)\s*\(", text, re.M)
+    return sorted(set(n for n in names if n not in ("if", "while", "for")))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert {"pir_setup_db", "pir_answer", "ntt_fwd", "ntt_inv"} <= set(names)
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_only_the_abi_is_exported(lib):
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", binding.LIB_PATH], capture_output=True, text=True).stdout
+    syms = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    assert syms == set(declared_functions()), syms ^ set(declared_functions())
+
+
+@pytest.mark.parametrize("n,log2p", [(2048, 12), (4096, 16), (8192, 16)])
+def test_params_match_oracle(lib, orc, n, log2p):
+    p = g.pir_make_params(n, log2p, 8, 8, 2)
+    P = orc.make_params(n, log2p, 8, 8, 2)
+    assert p.qs == P.qs and p.psis == P.psis
+
+
+def test_param_errors(lib):
+    for args in [(1024, 12, 4, 4, 2), (4096, 16, 0, 4, 2), (4096, 16, 4, 4, 0), (4096, 16, 4, 4, 5),
+                 (4096, 0, 4, 4, 2), (4096, 29, 4, 4, 2), (3000, 16, 4, 4, 2)]:
+        with pytest.raises(g.PirError) as ei:
+            g.pir_make_params(*args)
+        assert ei.value.status == 1
+
+
+def test_status_strings(lib):
+    for st in range(8):
+        assert g.pir_status_str(st)
+    assert g.pir_status_str(99) == "unknown status"
+
+
+def test_bad_handle_and_arguments_without_gpu(lib):
+    fake = g.Db(0xDEAD0, g.pir_make_params(2048, 12, 4, 4, 2), 0)
+    with pytest.raises(g.PirError) as ei:
+        g.pir_db_bytes(fake)
+    assert ei.value.status == 6
+    q = np.zeros(16, dtype=np.uint32)
+    st = lib.pir_answer(C.c_void_p(0xDEAD0), C.c_void_p(q.ctypes.data), 1, C.c_void_p(q.ctypes.data), 0, None)
+    assert st == 6
+    assert lib.pir_free_db(C.c_void_p(0xDEAD0)) == 6
+    # setup with a wrong raw size is refused before any device work
+    p = g.pir_make_params(2048, 12, 4, 4, 2)
+    raw = np.zeros(10, dtype=np.uint8)
+    h = C.c_void_p()
+    assert lib.pir_setup_db(C.byref(p), C.c_void_p(raw.ctypes.data), raw.nbytes, 0, 0, None, C.byref(h)) == 1
+    # a tampered prime is refused
+    bad = g.pir_make_params(2048, 12, 4, 4, 2)
+    bad.q[0] += 2
+    assert lib.ntt_fwd(C.byref(bad), None, 0, None) == 1
+    # unknown layout
+    assert lib.pir_setup_db(C.byref(p), C.c_void_p(raw.ctypes.data), raw.nbytes, 0, 7, None, C.byref(h)) == 1
+
+
+def test_size_formulas_against_paper():
+    """Sec. 1 / Sec. 3.6 print these sizes for N = 2^12 with 32-bit residues."""
+    pv = paper_values()
+    assert binding.poly_bytes(4096, 3) == pv["poly_bytes_n4096_L3"]
+    assert binding.ct_bytes(4096, 3) == pv["ct_bytes_n4096_L3"]
+    assert 256 * binding.poly_bytes(4096, 3) == pv["G_bytes_Dr256_n4096_L3"]
+    assert 256 * binding.ct_bytes(4096, 3) == pv["out_cts_bytes_Dr256_n4096_L3"]
+    assert binding.ct_bytes(4096, 1) == pv["response_bytes_n4096_L1"]
+
+
+def test_config_sizes():
+    """The configurations' raw / resident sizes: 768 KiB tiny DB; 1 GiB raw -> 4 GiB resident."""
+    p = g.pir_make_params(2048, 12, 16, 16, 2)
+    assert binding.raw_db_bytes(p) == 768 * 1024
+    p = g.pir_make_params(4096, 16, 512, 256, 2)
+    assert binding.raw_db_bytes(p) == 1 << 30 and binding.resident_db_bytes(p) == 4 << 30
+    assert binding.query_bytes(p, 1) == 32 << 20 and binding.response_bytes(p, 1) == 16 << 20
+    p = g.pir_make_params(4096, 16, 4096, 512, 2)
+    assert binding.raw_db_bytes(p) == 16 << 30 and binding.resident_db_bytes(p) == 64 << 30

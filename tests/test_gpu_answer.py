@@ -1,0 +1,144 @@
+"""GPU answer parity through the C ABI: pir_setup_db + pir_answer against the
+oracle, element by element, on shapes that span several tiles with ragged tails,
+every GEMM tile, K-chunked folding, host buffers, and the full-size 1 GiB
+configuration (sampled exact columns, a Freivalds check of the whole output and
+decryption of every column)."""
+import numpy as np
+import pytest
+
+import paper_2606_11536_gb300 as g
+from gpu_util import empty_u32, encrypted_queries, from_dev, random_queries, to_dev
+from paper_2606_11536_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def instance(orc, n, log2p, D1, D2, seed=5, layout=0):
+    p = g.pir_make_params(n, log2p, D1, D2, 2)
+    P = orc.make_params(n, log2p, D1, D2, 2)
+    raw = synth.raw_db(seed, synth.raw_db_bytes(n, log2p, D1, D2))
+    db = g.pir_setup_db(p, raw, layout=layout)
+    return p, P, raw, db
+
+
+def run(db, P, Q, B, **kw):
+    qd = to_dev(Q)
+    rd = empty_u32(B * P.D2 * 2 * P.L * P.n)
+    if kw:
+        g.pir_answer_ex(db, qd, B, rd, **kw)
+    else:
+        g.pir_answer(db, qd, B, rd)
+    return from_dev(rd, (B, P.D2, 2, P.L, P.n))
+
+
+def test_tiny_config_decrypts_and_matches(orc):
+    p, P, raw, db = instance(orc, 2048, 12, 16, 16, seed=0)
+    try:
+        Q, s, targets = encrypted_queries(orc, P, 1, 1)
+        R = run(db, P, Q, 1)
+        assert np.array_equal(R, orc.answer(P, raw, Q))
+        i_star, _ = targets[0]
+        for c in range(P.D2):
+            assert np.array_equal(orc.bfv_decrypt(P, s, R[0, c]), orc.unpack_poly(raw, P.log2p, P.n, i_star * P.D2 + c))
+    finally:
+        g.pir_free_db(db)
+
+
+def test_db_encoding_matches_oracle(orc):
+    p, P, raw, db = instance(orc, 2048, 16, 24, 12, seed=3)
+    try:
+        assert g.pir_db_bytes(db) == 4 * 2 * 2048 * 24 * 12
+        ids = [0, 1, 11, 12, 100, 24 * 12 - 1]
+        ref = orc.encode_polys(P, raw, np.array(ids, dtype=np.uint64))
+        for t, pid in enumerate(ids):
+            assert np.array_equal(g.pir_db_read_poly(db, pid), ref[t])
+    finally:
+        g.pir_free_db(db)
+
+
+# M = 2B crosses every kernel: GEMV with 2/4/8 rows, tiled GEMM with 16/32/64-row tiles
+@pytest.mark.parametrize("B", [1, 2, 3, 4, 5, 8, 9, 16, 17, 33])
+def test_batches_ragged_shapes(orc, B):
+    p, P, raw, db = instance(orc, 2048, 16, 40, 20, seed=B)
+    try:
+        Q = random_queries(P, B, 100 + B)
+        R = run(db, P, Q, B)
+        assert np.array_equal(R, orc.answer(P, raw, Q))
+    finally:
+        g.pir_free_db(db)
+
+
+def test_every_tile_and_k_chunk(orc):
+    p, P, raw, db = instance(orc, 2048, 16, 37, 132, seed=9)
+    try:
+        B = 3
+        Q = random_queries(P, B, 11)
+        ref = orc.answer(P, raw, Q)
+        for tile in range(3, g.pir_gemm_tiles(0) + 1):  # M = 6: tiles 1, 2 hold 2 and 4 rows only
+            assert np.array_equal(run(db, P, Q, B, tile=tile), ref), tile
+        for k_chunk in (1, 5, 16, 36, 37, 100):
+            assert np.array_equal(run(db, P, Q, B, k_chunk=k_chunk), ref), k_chunk
+        assert np.array_equal(run(db, P, Q, B, k_chunk=7, tile=6), ref)
+    finally:
+        g.pir_free_db(db)
+
+
+def test_ring_8192_and_extreme_values(orc):
+    p, P, raw, db = instance(orc, 8192, 16, 8, 8, seed=21)
+    try:
+        B = 2
+        Q = random_queries(P, B, 5)
+        for j, q in enumerate(P.qs):  # every query residue q - 1: largest products
+            Q[1, :, :, j, :] = q - 1
+        assert np.array_equal(run(db, P, Q, B), orc.answer(P, raw, Q))
+    finally:
+        g.pir_free_db(db)
+
+
+def test_host_buffers_equal_device_buffers(orc):
+    p, P, raw, db = instance(orc, 4096, 16, 16, 8, seed=2)
+    try:
+        B = 2
+        Q = random_queries(P, B, 8)
+        Rh = np.empty((B, P.D2, 2, P.L, P.n), dtype=np.uint32)
+        g.pir_answer(db, Q, B, Rh)
+        assert np.array_equal(Rh, run(db, P, Q, B))
+        assert np.array_equal(Rh, orc.answer(P, raw, Q))
+    finally:
+        g.pir_free_db(db)
+
+
+def test_errors_on_gpu(orc):
+    p, P, raw, db = instance(orc, 2048, 12, 16, 16, seed=0)
+    q = empty_u32(16 * 2 * 2 * 2048)
+    r = empty_u32(16 * 2 * 2 * 2048)
+    with pytest.raises(g.PirError) as ei:
+        g.pir_answer(db, q, 0, r)
+    assert ei.value.status == 1
+    with pytest.raises(g.PirError) as ei:
+        g.pir_answer_ex(db, q, 1, r, tile=99)
+    assert ei.value.status == 1
+    g.pir_free_db(db)
+    with pytest.raises(g.PirError) as ei:
+        g.pir_answer(db, q, 1, r)  # freed handle
+    assert ei.value.status == 6
+
+
+def test_full_size_1gib_config(orc):
+    """n = 4096, p = 2^16, D1 x D2 = 512 x 256 (1 GiB raw, 4 GiB resident), B = 1 real
+    encrypted query in the launch configuration the benchmark times: sampled
+    columns exact, the whole output by Freivalds, every column decrypts."""
+    n, log2p, D1, D2 = 4096, 16, 512, 256
+    p, P, raw, db = instance(orc, n, log2p, D1, D2, seed=0)
+    try:
+        Q, s, targets = encrypted_queries(orc, P, 1, 1)
+        R = run(db, P, Q, 1)
+        cols = np.array([0, 17, targets[0][1], D2 - 1], dtype=np.uint32)
+        assert np.array_equal(R[:, cols], orc.answer(P, raw, Q, cols=cols))
+        r = synth.freivalds_vector(3, P.qs, D2)
+        assert orc.freivalds(P, raw, Q, R, r) == 0
+        i_star = targets[0][0]
+        for c in range(D2):
+            assert np.array_equal(orc.bfv_decrypt(P, s, R[0, c]), orc.unpack_poly(raw, log2p, n, i_star * D2 + c)), c
+    finally:
+        g.pir_free_db(db)

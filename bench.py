@@ -1,0 +1,413 @@
+"""Benchmark of the GB300 PIR first-dimension scan.
+
+One step = one pir_answer of one batch of B query ciphertext sets against a
+resident NTT-form database: forward NTT of the queries, the per-slot modular
+GEMM with its reduction, and the inverse NTT of the responses.  The metric is
+DB-scan throughput in raw DB bytes x queries / s.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--batch B]
+                  [--layout plain|limb] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun (N > 1) every rank holds its own
+replica of the database and answers its own batches (independent problems, no
+data-path collective); the value is the queries of all ranks over the slowest
+rank's time.  ``--impl reference`` times the CPU oracle instead (the only other
+place this file runs it, besides the cpu_baseline leg).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DB-scan GB/s (raw DB bytes×queries/s) at batch 1..128; serving p50/p99 ms"
+
+# name -> (n, log2p, D1, D2, default batch, description)
+WORKLOADS = {
+    "tiny_n2048": (2048, 12, 16, 16, 1, "768 KiB raw DB, n=2048, p=2^12, 16x16 polys"),
+    "db1g_n4096": (4096, 16, 512, 256, 1, "1 GiB raw DB (4 GiB NTT-form), n=4096, p=2^16, D1=512, D2=256"),
+    "db256m_n4096": (4096, 16, 128, 256, 1, "256 MiB raw DB (1 GiB NTT-form), n=4096, p=2^16, D1=128, D2=256"),
+    "db256m_n2048": (2048, 16, 512, 256, 1, "256 MiB raw DB (1 GiB NTT-form), n=2048, p=2^16, D1=512, D2=256"),
+    "db1g_n2048": (2048, 16, 512, 512, 1, "1 GiB raw DB (4 GiB NTT-form), n=2048, p=2^16, D1=512, D2=512"),
+    "db8g_n4096": (4096, 16, 2048, 512, 1, "8 GiB raw DB (32 GiB NTT-form), n=4096, p=2^16, D1=2048, D2=512"),
+    "db16g_n4096": (4096, 16, 4096, 512, 1, "16 GiB raw DB (64 GiB NTT-form), n=4096, p=2^16, D1=4096, D2=512"),
+    "db32g_n8192": (8192, 16, 8192, 256, 64, "32 GiB raw DB (128 GiB NTT-form), n=8192, p=2^16, D1=8192, D2=256"),
+}
+DEFAULT_WORKLOAD = "db1g_n4096"
+L_PRIMES = 2
+FALLBACK_HBM_GBS = 6800.0
+
+
+def sha256_of(path: str) -> str:
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+
+
+def profile_traffic(kernel_tag: str, workload: str, batch: int, source: str):
+    """Per-launch DRAM bytes of a kernel from a committed ncu summary, or None when
+    there is none for this workload or the kernel source changed since."""
+    path = os.path.join(ROOT, "profiles", "%s_%s_b%d.txt" % (kernel_tag, workload, batch))
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("source_sha256") != sha256_of(source):
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, period_ms: int = 100):
+        self.gpu = gpu_index
+        self.period = period_ms
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", str(self.period)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=5)
+
+    def summary(self, t0: float, t1: float):
+        rows = [l for (t, l) in self.lines if t0 <= t <= t1] or [l for (_, l) in self.lines]
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            f = [x.strip() for x in r.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --- distributed helpers (host logic; covered by gloo tests on CPU) ----------
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reduce_timing(elapsed_ms: float, units: float, device=None):
+    """(max elapsed over ranks, sum of units over ranks); identity without a process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return elapsed_ms, units
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+# --- the CPU oracle as baseline / reference arm ------------------------------
+
+class OracleRunner:
+    """The oracle's online answer on a bounded sample: the query NTT of the whole
+    batch plus the fold and inverse NTT of `ncols` columns, whose NTT-form DB
+    polynomials are prepared once beforehand (as the server's DB is).  A step's
+    time is scaled by columns to the full answer."""
+
+    def __init__(self, n, log2p, D1, D2, B, raw, ncols, nthreads):
+        from oracle import oracle as O
+        self.O = O
+        self.P = O.make_params(n, log2p, D1, D2, L_PRIMES)
+        self.n, self.D1, self.D2, self.B = n, D1, D2, B
+        self.ncols, self.nthreads = ncols, nthreads
+        cols = np.arange(ncols, dtype=np.uint64)
+        ids = (np.arange(D1, dtype=np.uint64)[None, :] * np.uint64(D2) + cols[:, None]).reshape(-1)
+        self.dbhat = O.encode_polys(self.P, raw, ids, nthreads).reshape(ncols, D1, L_PRIMES, n)
+
+    def step(self, seed):
+        from paper_2606_11536_gb300 import synth
+        Q = synth.uniform_residues(seed, synth.STREAM_UNIFORM, self.B * self.D1 * 2, self.n, self.P.qs)
+        Q = Q.reshape(self.B, self.D1, 2, L_PRIMES, self.n)
+        t0 = time.perf_counter()
+        qhat = self.O.ntt_fwd_rns(self.P, Q, self.nthreads)
+        t1 = time.perf_counter()
+        self.O.answer_encoded(self.P, self.dbhat, qhat, self.nthreads)
+        t2 = time.perf_counter()
+        return (t1 - t0) + (t2 - t1) * self.D2 / self.ncols
+
+    def describe(self):
+        return ("oracle online answer, batch %d: query NTT of the whole batch timed, fold + inverse NTT timed on %d "
+                "of %d columns and scaled by columns; those DB columns NTT-encoded beforehand"
+                % (self.B, self.ncols, self.D2))
+
+
+def reference_arm(args, wl):
+    n, log2p, D1, D2, B0, desc = WORKLOADS[wl]
+    B = args.batch or B0
+    world, rank, _ = dist_env()
+    if world > 1 and rank != 0:
+        return
+    from paper_2606_11536_gb300 import synth
+    raw_bytes = synth.raw_db_bytes(n, log2p, D1, D2)
+    raw = synth.raw_db(0, raw_bytes)
+    nthreads = os.cpu_count() or 1
+    ncols = max(1, min(D2, args.ref_cols))
+    runner = OracleRunner(n, log2p, D1, D2, B, raw, ncols, nthreads)
+    times = []
+    for step in range(args.warmup + args.steps):
+        full_s = runner.step(100 + step)
+        if step >= args.warmup:
+            times.append(full_s)
+    sample_desc = runner.describe()
+    mean_s = sum(times) / len(times)
+    value = raw_bytes * B / mean_s / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mean_s * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": wl, "description": desc, "batch": B, "n": n, "log2p": log2p, "D1": D1, "D2": D2,
+                   "L": L_PRIMES},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": nthreads, "kind": "oracle", "sample": sample_desc},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --- our arm -----------------------------------------------------------------
+
+def our_arm(args, wl):
+    import torch
+    import paper_2606_11536_gb300 as g
+    from paper_2606_11536_gb300 import binding, synth
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    n, log2p, D1, D2, B0, desc = WORKLOADS[wl]
+    B = args.batch or B0
+    layout = g.PIR_LAYOUT_LIMB if args.layout == "limb" else g.PIR_LAYOUT_PLAIN
+    p = g.pir_make_params(n, log2p, D1, D2, L_PRIMES)
+    raw_bytes = binding.raw_db_bytes(p)
+    raw = synth.raw_db(0, raw_bytes)
+    db = g.pir_setup_db(p, raw, layout=layout)
+
+    # NBUF query sets on the device, so no step reads inputs the previous step left in L2
+    nbuf = 4
+    qwords = B * D1 * 2 * L_PRIMES * n
+    rwords = B * D2 * 2 * L_PRIMES * n
+    qbufs = []
+    for t in range(nbuf):
+        Q = synth.uniform_residues(1000 + 17 * rank + t, synth.STREAM_UNIFORM, B * D1 * 2, n, p.qs)
+        qbufs.append(torch.from_numpy(Q.reshape(-1).view(np.int32)).to(dev))
+    resp = torch.empty(rwords, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(t, flags=0):
+        g.pir_answer_ex(db, qbufs[t % nbuf], B, resp, stream=stream, flags=flags, tile=args.tile,
+                        k_chunk=args.k_chunk)
+
+    for t in range(args.warmup):
+        step(t)
+    torch.cuda.synchronize()
+    g.pir_stage_times()  # reset
+
+    sampler = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ
+                           else int(os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local]))
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = g.pir_kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    w0 = time.time()
+    ev0.record(stream)
+    for t in range(args.steps):
+        step(t, flags=g.PIR_ANSWER_STAGE_TIMES)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    w1 = time.time()
+    barrier()
+    launches = g.pir_kernel_launches() - launches0
+    elapsed_ms = ev0.elapsed_time(ev1)
+    stage_ms, stage_launches = g.pir_stage_times()
+    sampler.stop()
+    clocks = sampler.summary(w0, w1)
+
+    max_ms, total_queries = reduce_timing(elapsed_ms, float(B * args.steps), device=dev if world > 1 else None)
+    value = raw_bytes * total_queries / (max_ms / 1e3) / 1e9
+    ms_per_step = max_ms / args.steps
+
+    # roofline of the dominant kernel: the modular GEMM stage (one kernel per launch)
+    M, Mp = 2 * B, (2 * B + 3) // 4 * 4
+    nslots = L_PRIMES * n
+    gemm_launches = max(1, stage_launches[2])
+    gemm_ms = stage_ms[2] / gemm_launches
+    peaks, peak_kind = measured_peaks()
+    src = os.path.join(ROOT, "paper_2606_11536_gb300", "csrc",
+                       "gemm_plain.cu" if layout == g.PIR_LAYOUT_PLAIN else "gemm_limb.cu")
+    if layout == g.PIR_LAYOUT_PLAIN and M <= 8:
+        kernel_tag = "scan_tma" if (args.tile in (0, 7) and M <= 8 and D2 <= 512) else "gemv_scan"
+        alg_bytes = nslots * (D1 * D2 * 4 + D1 * Mp * 4 + M * D2 * 4)
+        roofline = {"bound": "hbm", "achieved": alg_bytes / (gemm_ms / 1e3) / 1e9,
+                    "peak": float(peaks["hbm_gbs"]), "unit": "GB/s"}
+    else:
+        kernel_tag = "gemm_plain" if layout == g.PIR_LAYOUT_PLAIN else "gemm_limb"
+        alg_bytes = nslots * (D1 * D2 * 4 + D1 * Mp * 4 + M * D2 * 4)
+        macs = nslots * D1 * D2 * M
+        # INT32 pipe: one 32x32+64-bit multiply-add per modular MAC; peak derived in
+        # the design notes from 152 SMs x 32 wide multiply-adds / clock x SM clock
+        sm_mhz = clocks["sm_mhz"] or float(peaks.get("sm_max_mhz", 2070.0))
+        alu_peak = 152 * 32 * sm_mhz * 1e6 / 1e12
+        roofline = {"bound": "alu", "achieved": macs / (gemm_ms / 1e3) / 1e12, "peak": alu_peak,
+                    "unit": "T modMAC/s"}
+    roofline["frac"] = roofline["achieved"] / roofline["peak"]
+    roofline["peak_source"] = "%s (%s)" % (peak_kind, "MEASURED_PEAKS.json hbm_gbs" if roofline["bound"] == "hbm"
+                                           else "152 SMs x 32 IMAD.WIDE/clk x sampled SM clock")
+    roofline["kernel"] = kernel_tag
+    roofline["kernel_ms"] = gemm_ms
+    roofline["alg_bytes_per_launch"] = alg_bytes
+    roofline["traffic"] = profile_traffic(kernel_tag, wl, B, src)
+    roofline["stage_ms_per_step"] = {name: stage_ms[i] / args.steps for i, name in enumerate(binding.STAGE_NAMES)}
+
+    # end to end through the public API with pinned host buffers
+    qh = torch.empty(qwords, dtype=torch.int32, pin_memory=True)
+    rh = torch.empty(rwords, dtype=torch.int32, pin_memory=True)
+    qh.copy_(qbufs[0].cpu())
+    e2e_steps = max(3, min(args.steps, 50))
+    for _ in range(2):
+        g.pir_answer(db, qh, B, rh, stream=stream)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        g.pir_answer(db, qh, B, rh, stream=stream)
+    t1 = time.perf_counter()
+    e2e_ms, e2e_q = reduce_timing((t1 - t0) * 1e3, float(B * e2e_steps), device=dev if world > 1 else None)
+    e2e = {"value": raw_bytes * e2e_q / (e2e_ms / 1e3) / 1e9, "unit": "GB/s",
+           "h2d_bytes_per_step": qwords * 4, "d2h_bytes_per_step": rwords * 4,
+           "ms_per_step": e2e_ms / e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        nthreads = os.cpu_count() or 1
+        ncols = max(1, min(D2, args.ref_cols))
+        runner = OracleRunner(n, log2p, D1, D2, B, raw, ncols, nthreads)
+        runner.step(7)  # warm
+        full_s = min(runner.step(8), runner.step(9))
+        cpu = {"value": raw_bytes * B / full_s / 1e9, "unit": "GB/s", "cores": nthreads, "kind": "oracle",
+               "sample": runner.describe() + "; best of 2 steps"}
+
+    g.pir_free_db(db)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": wl, "description": desc, "batch": B, "n": n, "log2p": log2p, "D1": D1, "D2": D2,
+                       "L": L_PRIMES, "layout": args.layout, "parallelism": "replicas x%d" % world,
+                       "l2": "inputs larger than L2: the %.1f GiB NTT-form DB is streamed every step; %d query "
+                             "buffers rotate" % (binding.resident_db_bytes(p) / 2 ** 30, nbuf)},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--layout", default="plain", choices=["plain", "limb"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--tile", type=int, default=0, help="GEMM tile id (0 = built-in choice)")
+    ap.add_argument("--k-chunk", type=int, default=0, help="fold D1 in chunks of this many ciphertexts")
+    ap.add_argument("--ref-cols", type=int, default=64, help="columns in the oracle's timed sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        reference_arm(args, args.workload)
+    else:
+        our_arm(args, args.workload)
+
+
+if __name__ == "__main__":
+    main()

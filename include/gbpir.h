@@ -116,11 +116,17 @@ typedef struct {
   uint32_t k_chunk;  /* 0 = whole D1 at once; else fold D1 in chunks of this many
                         ciphertexts (bounds the scratch memory to one chunk)        */
   uint32_t tile;     /* 0 = built-in choice; else a GEMM tile id (pir_gemm_tiles)  */
-  uint32_t flags;    /* bit 0 (PIR_ANSWER_STAGE_TIMES): record CUDA events around each
-                        stage on `stream`; read with pir_stage_times.  Other bits 0. */
+  uint32_t flags;    /* PIR_ANSWER_STAGE_TIMES: record CUDA events around each stage on
+                        `stream`, read with pir_stage_times; PIR_ANSWER_TEST_STALL:
+                        see below.  Other bits must be 0. */
 } pir_answer_opts_t;
 
 #define PIR_ANSWER_STAGE_TIMES 1u
+/* Test hook for the bounded-wait error path: the TMA-staged scan's consumers wait
+ * on a barrier nothing arrives on, time out after about a second, set the device
+ * error word and return (the answer is then invalid; pir_check_device reports
+ * PIR_ERR_TIMEOUT).  Needs a shape the TMA scan holds (2B <= 8, D2 <= 512). */
+#define PIR_ANSWER_TEST_STALL 2u
 
 /* Stages of one answer, in order: forward NTT of the queries, query transpose to
  * the slot-major layout, modular GEMM (with its reduction epilogue), result
@@ -171,6 +177,13 @@ pir_status_t pir_stage_times(double *ms, uint64_t *launches);
 
 /* Number of kernels this library has launched in this process (all threads). */
 uint64_t pir_kernel_launches(void);
+
+/* Kernels that wait on barriers (the TMA-staged scan) bound every wait to about
+ * one second; a wait that runs out sets a per-device error word, the kernel
+ * drains its copies in flight and returns early (its output is then invalid).
+ * This call synchronizes `stream`, reads and clears the current device's word and
+ * returns PIR_ERR_TIMEOUT if it was set, else PIR_OK. */
+pir_status_t pir_check_device(void *stream);
 
 #ifdef __cplusplus
 }

@@ -85,6 +85,7 @@ def lib():
             "pir_gemm_tiles": (u32, [i32]),
             "pir_stage_times": (i32, [C.POINTER(C.c_double), C.POINTER(C.c_uint64)]),
             "pir_kernel_launches": (C.c_uint64, []),
+            "pir_check_device": (i32, [vp]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(L, name)
@@ -225,6 +226,7 @@ def pir_gemm_tiles(layout: int) -> int:
 
 
 PIR_ANSWER_STAGE_TIMES = 1
+PIR_ANSWER_TEST_STALL = 2
 PIR_STAGES = 5
 STAGE_NAMES = ("query_ntt", "query_transpose", "gemm", "result_transpose", "intt")
 
@@ -235,6 +237,11 @@ def pir_stage_times():
     ln = (C.c_uint64 * PIR_STAGES)()
     _check(lib().pir_stage_times(ms, ln), "pir_stage_times")
     return list(ms), list(ln)
+
+
+def pir_check_device(stream=None):
+    """Raises PirError(PIR_ERR_TIMEOUT) if a bounded kernel wait ran out since the last check."""
+    _check(lib().pir_check_device(_stream_ptr(stream)), "pir_check_device")
 
 
 def pir_kernel_launches() -> int:

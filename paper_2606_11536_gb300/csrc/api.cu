@@ -22,6 +22,28 @@ void set_cuda_error(cudaError_t e) { t_last_cuda = cudaGetErrorString(e); }
 const char *last_cuda_error_cstr() { return t_last_cuda.c_str(); }
 
 std::atomic<uint64_t> g_launches{0};
+
+namespace {
+std::mutex g_err_mu;
+uint32_t *g_err_word[64] = {};
+}  // namespace
+
+cudaError_t device_error_word(uint32_t **word) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_err_mu);
+  if (!g_err_word[dev]) {
+    uint32_t *w = nullptr;
+    if ((e = cudaMalloc(&w, sizeof(uint32_t))) != cudaSuccess) return e;
+    if ((e = cudaMemset(w, 0, sizeof(uint32_t))) != cudaSuccess) return e;
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return e;
+    g_err_word[dev] = w;
+  }
+  *word = g_err_word[dev];
+  return cudaSuccess;
+}
 void count_launches(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 pir_status_t cuda_status(cudaError_t e) {
@@ -139,15 +161,27 @@ pir_status_t answer_device(pir_db *db, const uint32_t *queries, uint32_t B, uint
   const ParamCtx &c = *db->ctx;
   const pir_params_t &p = db->p;
   const uint32_t n = p.n, L = p.L, D1 = p.D1, D2 = p.D2;
-  const uint32_t M = 2 * B, Mp = round4(M);
-  const uint32_t Kc = (o.k_chunk == 0 || o.k_chunk >= D1) ? D1 : o.k_chunk;
+  const bool limb = db->layout == PIR_LAYOUT_LIMB;
+  const uint32_t M = 2 * B;
+  // plain rows pad to 4 (128-bit loads); limb rows pad to 16 (m16 tensor tiles)
+  const uint32_t Mp = limb ? (M + 15u) & ~15u : round4(M);
+  uint32_t Kc = (o.k_chunk == 0 || o.k_chunk >= D1) ? D1 : o.k_chunk;
+  if (limb) {
+    // byte-limb class sums stay below 2^31 for at most 8192 rows; chunks of 32 rows
+    if (Kc > 8192) Kc = 8192;
+    Kc &= ~31u;
+    if (Kc == 0) Kc = 32;
+  }
   const uint64_t nslots = (uint64_t)L * n;
   const uint32_t tile_count = db->layout == PIR_LAYOUT_PLAIN ? gemm_plain_tiles() : gemm_limb_tiles();
-  if (o.tile > tile_count || (o.flags & ~PIR_ANSWER_STAGE_TIMES) != 0) return PIR_ERR_ARG;
+  if (o.tile > tile_count || (o.flags & ~(PIR_ANSWER_STAGE_TIMES | PIR_ANSWER_TEST_STALL)) != 0) return PIR_ERR_ARG;
+  const int stall = (o.flags & PIR_ANSWER_TEST_STALL) != 0;
+  if (stall && (db->layout != PIR_LAYOUT_PLAIN || !scan_tma_supports(2 * B, D2) || (o.tile != 0 && o.tile != 7)))
+    return PIR_ERR_ARG;
 
   // scratch: NTT'd query chunk | slot-major query chunk | slot-major results
   const size_t qhat_bytes = (size_t)B * Kc * 2 * L * n * 4;
-  const size_t qs_bytes = db->layout == PIR_LAYOUT_PLAIN ? nslots * Kc * Mp * 4 : nslots * 4 * Mp * Kc;
+  const size_t qs_bytes = limb ? nslots * 4 * Mp * Kc : nslots * Kc * Mp * 4;
   const size_t out_bytes = nslots * M * D2 * 4;
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
   Scratch scratch(s);
@@ -172,7 +206,7 @@ pir_status_t answer_device(pir_db *db, const uint32_t *queries, uint32_t B, uint
       tm.end(1, 1);
       tm.begin();
       CK(launch_gemm_plain(c, static_cast<const uint32_t *>(db->resident), D1, D2, static_cast<const uint32_t *>(qs),
-                           M, Mp, i0, kc, out, i0 > 0, o.tile, s));
+                           M, Mp, i0, kc, out, i0 > 0, o.tile, stall, s));
       tm.end(2, 1);
     } else {
       tm.begin();
@@ -231,6 +265,18 @@ pir_status_t pir_stage_times(double *ms, uint64_t *launches) {
 
 uint64_t pir_kernel_launches(void) { return g_launches.load(); }
 
+pir_status_t pir_check_device(void *stream) {
+  uint32_t *w = nullptr;
+  CK(device_error_word(&w));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint32_t v = 0;
+  CK(cudaStreamSynchronize(s));
+  CK(cudaMemcpy(&v, w, sizeof(v), cudaMemcpyDeviceToHost));
+  if (v) CK(cudaMemset(w, 0, sizeof(uint32_t)));
+  CK(cudaDeviceSynchronize());
+  return v ? PIR_ERR_TIMEOUT : PIR_OK;
+}
+
 uint32_t pir_gemm_tiles(int layout) {
   if (layout == PIR_LAYOUT_PLAIN) return gemm_plain_tiles();
   if (layout == PIR_LAYOUT_LIMB) return gemm_limb_tiles();
@@ -245,7 +291,7 @@ pir_status_t pir_setup_db(const pir_params_t *params, const void *raw_db, size_t
   if (st != PIR_OK) return st;
   const pir_params_t p = *params;
   if (raw_bytes != raw_bytes_of(p)) return PIR_ERR_ARG;
-  if (layout == PIR_LAYOUT_PLAIN && (p.D2 % 4) != 0) return PIR_ERR_UNSUPPORTED;  // 128-bit column loads
+  if ((p.D2 % 4) != 0) return PIR_ERR_UNSUPPORTED;  // 128-bit / paired column accesses
   if (layout == PIR_LAYOUT_LIMB && (p.D1 % 32) != 0) return PIR_ERR_UNSUPPORTED;  // k32 tensor steps
   *out_handle = nullptr;
   const ParamCtx *ctx = nullptr;

@@ -48,6 +48,8 @@ pir_status_t validate_params(const pir_params_t *p);
 pir_status_t get_param_ctx(const pir_params_t *p, const ParamCtx **out);  // cached, device-resident tables
 
 // Error bookkeeping (api.cu)
+// Per-device error word that kernels with bounded waits set on a timeout.
+cudaError_t device_error_word(uint32_t **word);
 pir_status_t cuda_status(cudaError_t e);
 void set_cuda_error(cudaError_t e);
 const char *last_cuda_error_cstr();
@@ -81,8 +83,16 @@ cudaError_t launch_db_read_poly(const ParamCtx &c, int layout, uint32_t D1, uint
 // Kc rows i0.. of qs[s][i - i0][m] * db[s][i][c], reduced mod q_j, for m < M, c < D2.
 cudaError_t launch_gemm_plain(const ParamCtx &c, const uint32_t *db, uint32_t D1, uint32_t D2, const uint32_t *qs,
                               uint32_t M, uint32_t Mp, uint32_t i0, uint32_t Kc, uint32_t *out, int acc,
-                              uint32_t tile, cudaStream_t s);
+                              uint32_t tile, int stall_test, cudaStream_t s);
 uint32_t gemm_plain_tiles();
+
+// scan_tma.cu: the same contract for M <= 8 rows and D2 <= 512 (D2 % 4 == 0), as a
+// TMA-staged stream; stall_test makes its consumers wait on a barrier that never
+// completes (exercises the bounded-wait error path).
+bool scan_tma_supports(uint32_t M, uint32_t D2);
+cudaError_t launch_scan_tma(const ParamCtx &c, const uint32_t *db, uint32_t D1, uint32_t D2, const uint32_t *qs,
+                            uint32_t M, uint32_t Mp, uint32_t i0, uint32_t Kc, uint32_t *out, int acc, int stall_test,
+                            cudaStream_t s);
 
 // gemm_limb.cu: the same contract on the limb layouts (db [s][4][D2][D1] u8,
 // ql [s][4][Mp][Kc] u8), exact through u8 x u8 -> s32 tensor-pipe products.

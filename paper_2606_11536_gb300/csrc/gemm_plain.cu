@@ -280,22 +280,26 @@ cudaError_t gemm_launch(const ParamCtx &c, const uint32_t *db, uint32_t D1, uint
 }  // namespace
 
 // Tile ids: 1 = GEMV MB=2, 2 = GEMV MB=4, 3 = GEMV MB=8, 4 = GEMM 16x256, 5 = GEMM 32x256,
-// 6 = GEMM 64x128.  0 picks the smallest GEMV that holds M, else 64x128 (or a
-// narrower tile when M is small).
-uint32_t gemm_plain_tiles() { return 6; }
+// 6 = GEMM 64x128, 7 = TMA-staged scan (M <= 8, D2 <= 512; scan_tma.cu).  0 picks the
+// TMA scan when it holds the shape, else the smallest GEMV that holds M, else a
+// GEMM tile by M.
+uint32_t gemm_plain_tiles() { return 7; }
 
 cudaError_t launch_gemm_plain(const ParamCtx &c, const uint32_t *db, uint32_t D1, uint32_t D2, const uint32_t *qs,
                               uint32_t M, uint32_t Mp, uint32_t i0, uint32_t Kc, uint32_t *out, int acc,
-                              uint32_t tile, cudaStream_t s) {
+                              uint32_t tile, int stall_test, cudaStream_t s) {
   if (tile == 0) {
-    if (M <= 2) tile = 1;
+    if (scan_tma_supports(M, D2)) tile = 7;
+    else if (M <= 2) tile = 1;
     else if (M <= 4) tile = 2;
     else if (M <= 8) tile = 3;
     else if (M <= 16) tile = 4;
     else if (M <= 32) tile = 5;
     else tile = 6;
   }
+  if (stall_test && tile != 7) return cudaErrorInvalidValue;
   switch (tile) {
+    case 7: return launch_scan_tma(c, db, D1, D2, qs, M, Mp, i0, Kc, out, acc, stall_test, s);
     case 1: return M <= 2 ? gemv_launch<2>(c, db, D1, D2, qs, M, Mp, i0, Kc, out, acc, s) : cudaErrorInvalidValue;
     case 2: return M <= 4 ? gemv_launch<4>(c, db, D1, D2, qs, M, Mp, i0, Kc, out, acc, s) : cudaErrorInvalidValue;
     case 3: return M <= 8 ? gemv_launch<8>(c, db, D1, D2, qs, M, Mp, i0, Kc, out, acc, s) : cudaErrorInvalidValue;

@@ -28,7 +28,9 @@ def run(db, P, Q, B, **kw):
         g.pir_answer_ex(db, qd, B, rd, **kw)
     else:
         g.pir_answer(db, qd, B, rd)
-    return from_dev(rd, (B, P.D2, 2, P.L, P.n))
+    out = from_dev(rd, (B, P.D2, 2, P.L, P.n))
+    g.pir_check_device()  # no bounded wait ran out
+    return out
 
 
 def test_tiny_config_decrypts_and_matches(orc):
@@ -64,6 +66,19 @@ def test_batches_ragged_shapes(orc, B):
         Q = random_queries(P, B, 100 + B)
         R = run(db, P, Q, B)
         assert np.array_equal(R, orc.answer(P, raw, Q))
+    finally:
+        g.pir_free_db(db)
+
+
+@pytest.mark.parametrize("B,tiles", [(1, (1, 2, 3, 4, 5, 6, 7)), (2, (2, 3, 7)), (4, (3, 7))])
+def test_small_batches_every_tile(orc, B, tiles):
+    p, P, raw, db = instance(orc, 4096, 16, 50, 44, seed=60 + B)
+    try:
+        Q = random_queries(P, B, 61 + B)
+        ref = orc.answer(P, raw, Q)
+        for tile in tiles:
+            assert np.array_equal(run(db, P, Q, B, tile=tile), ref), tile
+        assert np.array_equal(run(db, P, Q, B, tile=7, k_chunk=13), ref)
     finally:
         g.pir_free_db(db)
 
@@ -140,5 +155,53 @@ def test_full_size_1gib_config(orc):
         i_star = targets[0][0]
         for c in range(D2):
             assert np.array_equal(orc.bfv_decrypt(P, s, R[0, c]), orc.unpack_poly(raw, log2p, n, i_star * D2 + c)), c
+    finally:
+        g.pir_free_db(db)
+
+
+# --- the INT8 limb path (u8 x u8 -> s32 tensor-pipe products) ----------------
+
+@pytest.mark.parametrize("B", [1, 3, 8, 9, 16, 17, 32, 40])
+def test_limb_path_matches_oracle(orc, B):
+    p, P, raw, db = instance(orc, 2048, 16, 64, 20, seed=30 + B, layout=1)
+    try:
+        Q = random_queries(P, B, 200 + B)
+        assert np.array_equal(run(db, P, Q, B), orc.answer(P, raw, Q))
+    finally:
+        g.pir_free_db(db)
+
+
+def test_limb_tiles_chunks_and_encoding(orc):
+    p, P, raw, db = instance(orc, 2048, 16, 96, 36, seed=44, layout=1)
+    try:
+        ids = [0, 35, 36, 95 * 36 + 35]
+        ref = orc.encode_polys(P, raw, np.array(ids, dtype=np.uint64))
+        for t, pid in enumerate(ids):
+            assert np.array_equal(g.pir_db_read_poly(db, pid), ref[t])
+        B = 32  # Mp = 64: every tile shape fits
+        Q = random_queries(P, B, 9)
+        for j, q in enumerate(P.qs):  # one query of all-maximal residues
+            Q[0, :, :, j, :] = q - 1
+        ref = orc.answer(P, raw, Q)
+        for tile in (1, 2, 3):
+            assert np.array_equal(run(db, P, Q, B, tile=tile), ref), tile
+        for k_chunk in (32, 64, 40):
+            assert np.array_equal(run(db, P, Q, B, k_chunk=k_chunk), ref), k_chunk
+    finally:
+        g.pir_free_db(db)
+
+
+def test_limb_full_size_1gib_batch8(orc):
+    """The 1 GiB configuration on the limb path at B = 8: sampled columns exact,
+    the whole output by Freivalds."""
+    n, log2p, D1, D2 = 4096, 16, 512, 256
+    p, P, raw, db = instance(orc, n, log2p, D1, D2, seed=0, layout=1)
+    try:
+        B = 8
+        Q = random_queries(P, B, 77)
+        R = run(db, P, Q, B)
+        cols = np.array([0, 101, D2 - 1], dtype=np.uint32)
+        assert np.array_equal(R[:, cols], orc.answer(P, raw, Q, cols=cols))
+        assert orc.freivalds(P, raw, Q, R, synth.freivalds_vector(4, P.qs, D2)) == 0
     finally:
         g.pir_free_db(db)

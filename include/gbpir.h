@@ -136,6 +136,29 @@ typedef struct {
 pir_status_t pir_answer_ex(pir_db_t db, const uint32_t *queries, uint32_t B, uint32_t *responses, int on_device,
                            void *stream, const pir_answer_opts_t *opts);
 
+/* A whole answer captured once into a CUDA graph (all its kernels, scratch
+ * allocation and release as graph nodes) and replayed with one launch: the
+ * batched, graph-captured launch the scan is served with.  The graph is bound to
+ * the device buffers given here (queries [B][D1][2][L][n], responses
+ * [B][D2][2][L][n]); every pir_graph_launch answers whatever the query buffer
+ * holds at that point in `stream`'s order.  opts as for pir_answer_ex, except that
+ * PIR_ANSWER_STAGE_TIMES and PIR_ANSWER_TEST_STALL are refused (PIR_ERR_ARG).
+ * The caller keeps ownership of the buffers and must keep them (and the DB) alive
+ * until pir_graph_destroy.  Errors: PIR_ERR_HANDLE, PIR_ERR_ARG, PIR_ERR_CUDA. */
+typedef struct pir_graph *pir_graph_t;
+pir_status_t pir_graph_create(pir_db_t db, const uint32_t *queries, uint32_t B, uint32_t *responses,
+                              const pir_answer_opts_t *opts, pir_graph_t *out);
+pir_status_t pir_graph_launch(pir_graph_t graph, void *stream);
+pir_status_t pir_graph_destroy(pir_graph_t graph);
+
+/* Autotuner: times every GEMM tile valid for this DB's layout and batch size B,
+ * and K-chunk choices (whole D1, halves, quarters), `reps` answers each on scratch
+ * buffers (all-zero queries; the scan's cost does not depend on the data), with
+ * CUDA events on `stream`; writes the fastest (tile, k_chunk) to *best and caches
+ * it in the handle, so later calls for the same B return at once.  Synchronous.
+ * Errors: PIR_ERR_HANDLE, PIR_ERR_ARG (B = 0, best NULL), PIR_ERR_OOM, PIR_ERR_CUDA. */
+pir_status_t pir_autotune(pir_db_t db, uint32_t B, void *stream, uint32_t reps, pir_answer_opts_t *best);
+
 /* Forward / inverse negacyclic NTT of `count` RNS polynomials [count][L][n] in
  * place, in device memory, asynchronously on stream (Sec. 2.3; single-kernel
  * on-chip NTT, Sec. 4.3).  Inputs must be canonical; outputs are canonical.

@@ -86,6 +86,10 @@ def lib():
             "pir_stage_times": (i32, [C.POINTER(C.c_double), C.POINTER(C.c_uint64)]),
             "pir_kernel_launches": (C.c_uint64, []),
             "pir_check_device": (i32, [vp]),
+            "pir_graph_create": (i32, [vp, vp, u32, vp, C.POINTER(pir_answer_opts_t), C.POINTER(vp)]),
+            "pir_graph_launch": (i32, [vp, vp]),
+            "pir_graph_destroy": (i32, [vp]),
+            "pir_autotune": (i32, [vp, u32, vp, u32, C.POINTER(pir_answer_opts_t)]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(L, name)
@@ -237,6 +241,42 @@ def pir_stage_times():
     ln = (C.c_uint64 * PIR_STAGES)()
     _check(lib().pir_stage_times(ms, ln), "pir_stage_times")
     return list(ms), list(ln)
+
+
+class Graph:
+    """A captured answer bound to fixed device buffers (pir_graph_t)."""
+
+    def __init__(self, handle, db, queries, responses):
+        self.handle = handle
+        self.db = db
+        self._keep = (queries, responses)  # the graph reads / writes these buffers
+
+
+def pir_graph_create(db: Db, queries, B: int, responses, k_chunk: int = 0, tile: int = 0) -> Graph:
+    qp, qdev, _ = _ptr(queries)
+    rp, rdev, _ = _ptr(responses)
+    if not (qdev and rdev):
+        raise ValueError("a graph binds device buffers")
+    o = pir_answer_opts_t(k_chunk, tile, 0)
+    h = C.c_void_p()
+    _check(lib().pir_graph_create(C.c_void_p(db.handle), qp, B, rp, C.byref(o), C.byref(h)), "pir_graph_create")
+    return Graph(h.value, db, queries, responses)
+
+
+def pir_graph_launch(graph: Graph, stream=None):
+    _check(lib().pir_graph_launch(C.c_void_p(graph.handle), _stream_ptr(stream)), "pir_graph_launch")
+
+
+def pir_graph_destroy(graph: Graph):
+    _check(lib().pir_graph_destroy(C.c_void_p(graph.handle)), "pir_graph_destroy")
+    graph.handle = None
+
+
+def pir_autotune(db: Db, B: int, stream=None, reps: int = 3):
+    """Fastest (tile, k_chunk) for this DB and batch size, as a dict."""
+    o = pir_answer_opts_t()
+    _check(lib().pir_autotune(C.c_void_p(db.handle), B, _stream_ptr(stream), reps, C.byref(o)), "pir_autotune")
+    return {"tile": int(o.tile), "k_chunk": int(o.k_chunk)}
 
 
 def pir_check_device(stream=None):

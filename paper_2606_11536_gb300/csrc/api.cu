@@ -5,6 +5,7 @@
 // (Sec. 3.2 poly-HE folding; Sec. 4.2 transposes around the parallel GEMMs;
 // Sec. 4.4 per-stream fixed buffers -> the K-chunked variant here).
 #include <atomic>
+#include <map>
 #include <mutex>
 #include <set>
 #include <string>
@@ -65,13 +66,25 @@ struct pir_db {
   const ParamCtx *ctx;
   void *resident;
   size_t bytes;
+  std::mutex tune_mu;
+  std::map<uint32_t, pir_answer_opts_t> tuned;  // batch size -> fastest options
+};
+
+struct pir_graph {
+  uint64_t magic;
+  pir_db *db;
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  uint64_t kernels;  // kernel launches per replay
 };
 
 namespace {
 
-constexpr uint64_t kMagic = 0x4742504952444231ull;  // "GBPIRDB1"
+constexpr uint64_t kMagic = 0x4742504952444231ull;       // "GBPIRDB1"
+constexpr uint64_t kGraphMagic = 0x4742504952475231ull;  // "GBPIRGR1"
 std::mutex g_reg_mu;
 std::set<pir_db *> g_live;
+std::set<pir_graph *> g_graphs;
 
 bool live(pir_db *db) {
   std::lock_guard<std::mutex> lock(g_reg_mu);
@@ -136,6 +149,8 @@ cudaEvent_t take_event() {
   return e;
 }
 
+thread_local bool t_capturing = false;  // launches inside a graph capture are not launches yet
+
 struct StageTimer {
   bool on;
   cudaStream_t s;
@@ -145,7 +160,7 @@ struct StageTimer {
     if (on && (a = take_event())) cudaEventRecord(a, s);
   }
   void end(int stage, uint64_t launches) {
-    count_launches(launches);
+    if (!t_capturing) count_launches(launches);
     if (!on || !a) return;
     cudaEvent_t b = take_event();
     if (!b) return;
@@ -435,6 +450,154 @@ pir_status_t ntt_fwd(const pir_params_t *params, uint32_t *polys, size_t count, 
 
 pir_status_t ntt_inv(const pir_params_t *params, uint32_t *polys, size_t count, void *stream) {
   return ntt_common(params, polys, count, stream, false);
+}
+
+pir_status_t pir_graph_create(pir_db_t db, const uint32_t *queries, uint32_t B, uint32_t *responses,
+                              const pir_answer_opts_t *opts, pir_graph_t *out) {
+  if (!live(db)) return PIR_ERR_HANDLE;
+  if (!out || !queries || !responses || B == 0 || !aligned16(queries) || !aligned16(responses)) return PIR_ERR_ARG;
+  pir_answer_opts_t o = {};
+  if (opts) o = *opts;
+  if (o.flags != 0) return PIR_ERR_ARG;
+  *out = nullptr;
+  uint32_t *w = nullptr;
+  CK(device_error_word(&w));  // lazily allocated state must exist before the capture
+  cudaStream_t cs;
+  CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(cs);
+    return cuda_status(e);
+  }
+  t_capturing = true;
+  pir_status_t st = answer_device(db, queries, B, responses, cs, o);
+  t_capturing = false;
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(cs, &graph);
+  cudaStreamDestroy(cs);
+  if (st != PIR_OK || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return st != PIR_OK ? st : cuda_status(e);
+  }
+  size_t nn = 0;
+  e = cudaGraphGetNodes(graph, nullptr, &nn);
+  std::vector<cudaGraphNode_t> nodes(nn);
+  if (e == cudaSuccess && nn) e = cudaGraphGetNodes(graph, nodes.data(), &nn);
+  uint64_t kernels = 0;
+  for (size_t i = 0; e == cudaSuccess && i < nn; ++i) {
+    cudaGraphNodeType t;
+    if ((e = cudaGraphNodeGetType(nodes[i], &t)) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return cuda_status(e);
+  }
+  pir_graph *g = new pir_graph{kGraphMagic, db, graph, exec, kernels};
+  {
+    std::lock_guard<std::mutex> lock(g_reg_mu);
+    g_graphs.insert(g);
+  }
+  *out = g;
+  return PIR_OK;
+}
+
+static bool graph_live(pir_graph *g) {
+  std::lock_guard<std::mutex> lock(g_reg_mu);
+  return g && g_graphs.count(g) && g->magic == kGraphMagic && g_live.count(g->db);
+}
+
+pir_status_t pir_graph_launch(pir_graph_t graph, void *stream) {
+  if (!graph_live(graph)) return PIR_ERR_HANDLE;
+  CK(cudaGraphLaunch(graph->exec, static_cast<cudaStream_t>(stream)));
+  count_launches(graph->kernels);
+  return PIR_OK;
+}
+
+pir_status_t pir_graph_destroy(pir_graph_t graph) {
+  {
+    std::lock_guard<std::mutex> lock(g_reg_mu);
+    if (!graph || !g_graphs.count(graph)) return PIR_ERR_HANDLE;
+    g_graphs.erase(graph);
+  }
+  cudaError_t e = cudaGraphExecDestroy(graph->exec);
+  cudaError_t e2 = cudaGraphDestroy(graph->graph);
+  graph->magic = 0;
+  delete graph;
+  return cuda_status(e != cudaSuccess ? e : e2);
+}
+
+pir_status_t pir_autotune(pir_db_t db, uint32_t B, void *stream, uint32_t reps, pir_answer_opts_t *best) {
+  if (!live(db)) return PIR_ERR_HANDLE;
+  if (!best || B == 0) return PIR_ERR_ARG;
+  {
+    std::lock_guard<std::mutex> lock(db->tune_mu);
+    auto it = db->tuned.find(B);
+    if (it != db->tuned.end()) {
+      *best = it->second;
+      return PIR_OK;
+    }
+  }
+  if (reps == 0) reps = 1;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const pir_params_t &p = db->p;
+  const uint32_t M = 2 * B, Mp16 = (M + 15u) & ~15u;
+  const bool limb = db->layout == PIR_LAYOUT_LIMB;
+  std::vector<uint32_t> tiles;
+  if (!limb) {
+    if (M <= 2) tiles.push_back(1);
+    if (M <= 4) tiles.push_back(2);
+    if (M <= 8) tiles.push_back(3);
+    for (uint32_t t = 4; t <= 6; ++t) tiles.push_back(t);
+    if (scan_tma_supports(M, p.D2)) tiles.push_back(7);
+  } else {
+    tiles.push_back(1);
+    if (Mp16 % 32 == 0) tiles.push_back(2);
+    if (Mp16 % 64 == 0) tiles.push_back(3);
+  }
+  std::vector<uint32_t> chunks = {0};
+  for (uint32_t d : {2u, 4u}) {
+    uint32_t kc = p.D1 / d;
+    if (limb) kc &= ~31u;
+    if (kc >= 32 && kc < p.D1) chunks.push_back(kc);
+  }
+  const size_t qb = (size_t)B * p.D1 * 2 * p.L * p.n * 4, rb = (size_t)B * p.D2 * 2 * p.L * p.n * 4;
+  Scratch dq(s), dr(s);
+  CK(dq.alloc(qb));
+  CK(dr.alloc(rb));
+  CK(cudaMemsetAsync(dq.ptr, 0, qb, s));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best_ms = -1.f;
+  pir_answer_opts_t win = {};
+  for (uint32_t t : tiles)
+    for (uint32_t kc : chunks) {
+      pir_answer_opts_t o = {kc, t, 0};
+      const uint32_t *qd = static_cast<const uint32_t *>(dq.ptr);
+      uint32_t *rd = static_cast<uint32_t *>(dr.ptr);
+      if (answer_device(db, qd, B, rd, s, o) != PIR_OK) continue;  // shape this tile does not hold
+      cudaEventRecord(e0, s);
+      bool ok = true;
+      for (uint32_t r = 0; r < reps && ok; ++r) ok = answer_device(db, qd, B, rd, s, o) == PIR_OK;
+      cudaEventRecord(e1, s);
+      float ms = 0.f;
+      if (!ok || cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+        continue;
+      ms /= reps;
+      if (best_ms < 0.f || ms < best_ms) best_ms = ms, win = o;
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGetLastError();  // a refused candidate may leave a launch-configuration error behind
+  if (best_ms < 0.f) return PIR_ERR_UNSUPPORTED;
+  {
+    std::lock_guard<std::mutex> lock(db->tune_mu);
+    db->tuned[B] = win;
+  }
+  *best = win;
+  return PIR_OK;
 }
 
 pir_status_t pir_free_db(pir_db_t db) {

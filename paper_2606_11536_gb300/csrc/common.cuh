@@ -30,8 +30,8 @@ struct NttConst {
 // Reduction constants of the modular GEMM epilogues.
 struct ModConst {
   uint32_t q[PIR_MAX_L];
-  uint32_t c60[PIR_MAX_L];  // 2^60 mod q
   uint64_t mu[PIR_MAX_L];   // floor(2^64 / q)
+  uint64_t k63[PIR_MAX_L];  // q * floor(2^63 / q): the largest multiple of q <= 2^63
 };
 
 // Host-side: the ring (n, L, primes, roots) plus device tables, cached per device
@@ -112,12 +112,14 @@ __device__ __forceinline__ uint32_t shoup_mul(uint32_t x, uint32_t w, uint32_t w
   return x * w - hi * q;
 }
 
-// Folds the top four bits of a 64-bit accumulator: result = acc mod q + multiple of q,
-// below 2^60 + 2^34.  With q < 2^30 the accumulator then takes 15 more products
-// (q-1)^2 before it could reach 2^64.
-__device__ __forceinline__ uint64_t fold60(uint64_t acc, uint32_t c60) {
-  uint32_t top = (uint32_t)(acc >> 60);
-  return (acc & ((1ull << 60) - 1)) + (uint64_t)top * c60;
+// Lazy reduction of a 64-bit accumulator without a multiply (compare + predicated
+// 64-bit subtract: integer ALU pipe, leaving the multiply-add pipe to the products):
+// if acc >= 2^63, subtract k63 = q * floor(2^63 / q) > 2^63 - q.  The result is
+// congruent mod q and below 2^63 + q, so with q < 2^30 it takes 8 more products
+// (q-1)^2 < 2^60 before it could reach 2^64 (2^63 + q + 8 (q-1)^2 < 2^64).
+constexpr int kFoldProducts = 8;
+__device__ __forceinline__ uint64_t fold63(uint64_t acc, uint64_t k63) {
+  return acc >= (1ull << 63) ? acc - k63 : acc;
 }
 
 // Full reduction of a 64-bit value mod q (q < 2^30): Barrett with mu = floor(2^64/q).

@@ -8,7 +8,7 @@
 //
 // Products of two residues are below 2^60 and go into u64 accumulators with one
 // u32 x u32 + u64 multiply-add each (Sec. 4.2's lazy reduction, re-derived for
-// 30-bit primes: fold60 after at most 8 products keeps every accumulator below
+// 30-bit primes: fold63 after at most 8 products keeps every accumulator below
 // 2^64; the paper's 32-MAC bound is for primes below 2^29).
 //
 // Two kernels:
@@ -16,7 +16,9 @@
 //              CTA, 128-bit loads along c, query rows broadcast from shared memory.
 //              Bound by HBM bandwidth.
 //   k_gemm  -- M >= 16: a tiled SIMT GEMM per slot, operands staged through shared
-//              memory with cp.async double buffering; thread tile 4 rows x 8 columns.
+//              memory with cp.async double buffering; thread tile RM rows x 8 columns,
+//              the columns in two groups of 4 half a tile apart so that a warp's
+//              128-bit shared loads cover contiguous 256-byte spans (no bank conflicts).
 //              Bound by the INT32 multiply-add pipe.
 #include "common.cuh"
 
@@ -46,8 +48,8 @@ __global__ void __launch_bounds__(kGemvThreads) k_gemv(const uint32_t *__restric
 
   for (uint32_t s = blockIdx.x; s < nslots; s += gridDim.x) {
     const uint32_t j = s >> logn;
-    const uint32_t q = mc.q[j], c60 = mc.c60[j];
-    const uint64_t mu = mc.mu[j];
+    const uint32_t q = mc.q[j];
+    const uint64_t mu = mc.mu[j], k63 = mc.k63[j];
     const uint32_t *dbs = db + ((uint64_t)s * D1 + i0) * D2;
     const uint32_t *qss = qs + (uint64_t)s * Kc * Mp;
     for (uint32_t cqb = 0; cqb < nq; cqb += QT) {  // uniform trip count: the body synchronizes
@@ -89,7 +91,7 @@ __global__ void __launch_bounds__(kGemvThreads) k_gemv(const uint32_t *__restric
 #pragma unroll
           for (int m = 0; m < MB; ++m)
 #pragma unroll
-            for (int e = 0; e < 4; ++e) acc[m][e] = fold60(acc[m][e], c60);
+            for (int e = 0; e < 4; ++e) acc[m][e] = fold63(acc[m][e], k63);
         }
         for (; i < icn; i += P) {
           const uint4 d = __ldcs(reinterpret_cast<const uint4 *>(rowp + (uint64_t)i * D2));
@@ -97,10 +99,10 @@ __global__ void __launch_bounds__(kGemvThreads) k_gemv(const uint32_t *__restric
 #pragma unroll
           for (int m = 0; m < MB; ++m) {
             const uint32_t a = qv[m];
-            acc[m][0] = fold60(acc[m][0] + (uint64_t)a * d.x, c60);
-            acc[m][1] = fold60(acc[m][1] + (uint64_t)a * d.y, c60);
-            acc[m][2] = fold60(acc[m][2] + (uint64_t)a * d.z, c60);
-            acc[m][3] = fold60(acc[m][3] + (uint64_t)a * d.w, c60);
+            acc[m][0] = fold63(acc[m][0] + (uint64_t)a * d.x, k63);
+            acc[m][1] = fold63(acc[m][1] + (uint64_t)a * d.y, k63);
+            acc[m][2] = fold63(acc[m][2] + (uint64_t)a * d.z, k63);
+            acc[m][3] = fold63(acc[m][3] + (uint64_t)a * d.w, k63);
           }
         }
       }
@@ -168,8 +170,8 @@ __global__ void __launch_bounds__(256) k_gemm(const uint32_t *__restrict__ db, c
   const uint32_t mt = (uint32_t)((bid / nct) % nmt);
   const uint32_t s = (uint32_t)(bid / ((uint64_t)nct * nmt));
   const uint32_t j = s >> logn;
-  const uint32_t q = mc.q[j], c60 = mc.c60[j];
-  const uint64_t mu = mc.mu[j];
+  const uint32_t q = mc.q[j];
+  const uint64_t mu = mc.mu[j], k63 = mc.k63[j];
   const uint32_t m0 = mt * TM, c0 = ct * TC;
   const uint32_t *dbs = db + ((uint64_t)s * D1 + i0) * D2;
   const uint32_t *qss = qs + (uint64_t)s * Kc * Mp;
@@ -218,8 +220,8 @@ __global__ void __launch_bounds__(256) k_gemm(const uint32_t *__restrict__ db, c
           const uint2 a = *reinterpret_cast<const uint2 *>(&As[buf][kk][tm * 2]);
           av[0] = a.x, av[1] = a.y;
         }
-        const uint4 b0 = *reinterpret_cast<const uint4 *>(&Bs[buf][kk][tc * 8]);
-        const uint4 b1 = *reinterpret_cast<const uint4 *>(&Bs[buf][kk][tc * 8 + 4]);
+        const uint4 b0 = *reinterpret_cast<const uint4 *>(&Bs[buf][kk][tc * 4]);
+        const uint4 b1 = *reinterpret_cast<const uint4 *>(&Bs[buf][kk][TC / 2 + tc * 4]);
         const uint32_t bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
         for (int x = 0; x < RM; ++x)
@@ -229,7 +231,7 @@ __global__ void __launch_bounds__(256) k_gemm(const uint32_t *__restrict__ db, c
 #pragma unroll
       for (int x = 0; x < RM; ++x)
 #pragma unroll
-        for (int y = 0; y < 8; ++y) acc[x][y] = fold60(acc[x][y], c60);
+        for (int y = 0; y < 8; ++y) acc[x][y] = fold63(acc[x][y], k63);
     }
     __syncthreads();
   }
@@ -241,7 +243,7 @@ __global__ void __launch_bounds__(256) k_gemm(const uint32_t *__restrict__ db, c
     uint32_t *orow = out + ((uint64_t)s * M + m) * D2;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const uint32_t c = c0 + tc * 8 + h * 4;
+      const uint32_t c = c0 + h * (TC / 2) + tc * 4;
       if (c >= D2) continue;
       uint32_t r[4];
 #pragma unroll

@@ -175,8 +175,8 @@ pir_status_t get_param_ctx(const pir_params_t *p, const ParamCtx **out) {
     ctx->ntt.ninv[j] = (uint32_t)pow_mod32(n, q - 2, q);
     ctx->ntt.ninv_sh[j] = shoup(ctx->ntt.ninv[j], q);
     ctx->mod.q[j] = q;
-    ctx->mod.c60[j] = (uint32_t)pow_mod32(2, 60, q);
     ctx->mod.mu[j] = (uint64_t)(~0ull / q);  // floor((2^64 - 1) / q) = floor(2^64 / q) for q not a power of 2
+    ctx->mod.k63[j] = ((1ull << 63) / q) * q;
   }
   uint32_t *dtab = nullptr;
   e = cudaMalloc(&dtab, host.size() * sizeof(uint32_t));

@@ -4,20 +4,21 @@
 //
 //   out[s][m][c] = sum_{i < Kc} qs[s][i][m] * db[s][i0 + i][c]   (mod q_j),  s = j*n + k
 //
-// Persistent CTAs, one per SM: warp 8 is the producer, warps 0..7 consume.  The
-// producer walks this CTA's slots (s = blockIdx.x, + gridDim.x, ...) in chunks of R
-// DB rows and, per chunk, issues two 1-D bulk copies (cp.async.bulk, the TMA engine)
-// into a ring of 8 shared-memory stages: R*D2*4 bytes of DB rows (L2 evict-first:
-// the DB is read once) and the matching R*Mp*4 bytes of slot-major query rows.  Each
-// stage has a "full" mbarrier (expect-tx bytes) and an "empty" mbarrier (one
-// arrival per consumer warp).  The ring keeps up to 8 chunks (~128 KiB) in flight
-// per SM across slot boundaries, so the stream never drains between slots.
+// Persistent CTAs, as many per SM as registers and shared memory allow (three for
+// batch 1): warp 8 is the producer, warps 0..7 consume.  The producer walks this
+// CTA's slots (s = blockIdx.x, + gridDim.x, ...) in chunks of R DB rows and, per
+// chunk, issues two 1-D bulk copies (cp.async.bulk, the TMA engine) into a ring of 4
+// shared-memory stages: R*D2*4 bytes of DB rows (L2 evict-first: the DB is read
+// once) and the matching R*Mp*4 bytes of slot-major query rows.  Each stage has a
+// "full" mbarrier (expect-tx bytes) and an "empty" mbarrier (one arrival per
+// consumer warp).  The rings keep up to 12 chunks (~192 KiB) in flight per SM across
+// slot boundaries, so the stream never drains between slots.
 //
 // Consumers own whole columns: lane = (phase ph, quad ql) with QW quads x PH row
 // phases per warp; warp w covers quads w*QW + ql + 8*QW*t.  Each lane accumulates
-// u32 x u32 -> u64 products (fold60 every <= 8 rows keeps them below 2^64); at a
-// slot's end the PH phases combine with warp shuffles, so no block barrier is ever
-// needed after set-up.
+// u32 x u32 -> u64 products (fold63 every <= 8 products keeps them below 2^64); at
+// a slot's end the PH phases combine with warp shuffles, so no block barrier is
+// ever needed after set-up.
 //
 // Every barrier wait is bounded (about one second of %globaltimer).  A wait that runs
 // out sets the per-device error word; the producer then stops issuing, waits (again
@@ -29,7 +30,7 @@ namespace {
 
 constexpr int kConsumerWarps = 8;
 constexpr int kThreads = (kConsumerWarps + 1) * 32;
-constexpr int kStages = 8;
+constexpr int kStages = 4;
 constexpr uint32_t kChunkTarget = 16384;       // DB bytes per stage
 constexpr uint64_t kWaitNs = 1000000000ull;    // bound on every barrier wait
 
@@ -53,12 +54,16 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
+// try_wait with a suspend-time hint: a waiting thread sleeps in hardware until the
+// phase completes (or the hint elapses) instead of spinning on issue slots.
+constexpr uint32_t kSuspendHintNs = 100000;
+
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(bar), "r"(parity)
+      : "r"(bar), "r"(parity), "r"(kSuspendHintNs)
       : "memory");
   return ok != 0;
 }
@@ -94,8 +99,17 @@ struct ScanArgs {
   int stall_test;      // consumers wait on a barrier nobody arrives on (tests the timeout path)
 };
 
+// Rows per unrolled group and CTAs per SM, by accumulator count (MB rows x T quads):
+// the batch-1 shape keeps three CTAs (27 warps) per SM, two rows of loads per group.
 template <int MB, int T>
-__global__ void __launch_bounds__(kThreads, 1) k_scan_tma(ScanArgs a, ModConst mc) {
+struct ScanShape {
+  static constexpr int U = (MB * T <= 4) ? 2 : 1;
+  static constexpr int kMinBlocks = (MB * T <= 2) ? 3 : (MB * T <= 4) ? 2 : 1;
+};
+
+template <int MB, int T>
+__global__ void __launch_bounds__(kThreads, ScanShape<MB, T>::kMinBlocks) k_scan_tma(ScanArgs a, ModConst mc) {
+  constexpr int U = ScanShape<MB, T>::U;
   extern __shared__ __align__(128) uint8_t smem[];
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * a.stage_bytes);
   const uint32_t full0 = saddr(bars), empty0 = saddr(bars + kStages), stall = saddr(bars + 2 * kStages);
@@ -167,8 +181,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_scan_tma(ScanArgs a, ModConst m
   uint32_t it = 0;
   for (uint32_t s = blockIdx.x; s < a.nslots; s += gridDim.x) {
     const uint32_t j = s >> a.logn;
-    const uint32_t q = mc.q[j], c60 = mc.c60[j];
-    const uint64_t mu = mc.mu[j];
+    const uint32_t q = mc.q[j];
+    const uint64_t mu = mc.mu[j], k63 = mc.k63[j];
+    uint32_t pend = 0;  // products per accumulator since the last fold
     uint64_t acc[T][MB][4];
 #pragma unroll
     for (int t = 0; t < T; ++t)
@@ -187,47 +202,53 @@ __global__ void __launch_bounds__(kThreads, 1) k_scan_tma(ScanArgs a, ModConst m
       }
       const uint32_t *dbs = reinterpret_cast<const uint32_t *>(smem + st * a.stage_bytes);
       const uint32_t *qsm = reinterpret_cast<const uint32_t *>(smem + st * a.stage_bytes + db_bytes_full);
-      uint32_t cnt = 0;
-      for (uint32_t r = phs; r < rows; r += PH) {
-        uint32_t qrow[MB];
-        if constexpr (MB == 2) {
-          const uint2 v = *reinterpret_cast<const uint2 *>(qsm + r * a.Mp);
-          qrow[0] = v.x, qrow[1] = v.y;
-        } else {
-#pragma unroll
-          for (int m4 = 0; m4 < MB; m4 += 4) {
-            const uint4 v = *reinterpret_cast<const uint4 *>(qsm + r * a.Mp + m4);
-            qrow[m4] = v.x, qrow[m4 + 1] = v.y, qrow[m4 + 2] = v.z, qrow[m4 + 3] = v.w;
-          }
-        }
-#pragma unroll
-        for (int t = 0; t < T; ++t) {
-          if (!qv[t]) continue;
-          const uint4 d = *reinterpret_cast<const uint4 *>(dbs + r * a.D2 + 4 * quad[t]);
-#pragma unroll
-          for (int m = 0; m < MB; ++m) {
-            acc[t][m][0] += (uint64_t)qrow[m] * d.x;
-            acc[t][m][1] += (uint64_t)qrow[m] * d.y;
-            acc[t][m][2] += (uint64_t)qrow[m] * d.z;
-            acc[t][m][3] += (uint64_t)qrow[m] * d.w;
-          }
-        }
-        if (++cnt == 8) {
-          cnt = 0;
+      // rows phs, phs + PH, ... of this chunk, U at a time: all shared loads of a
+      // group issue before its multiply-adds; a fold before any group that would
+      // take an accumulator past kFoldProducts products.
+      for (uint32_t r0l = phs; r0l < rows; r0l += U * PH) {
+        if (pend + U > kFoldProducts) {
 #pragma unroll
           for (int t = 0; t < T; ++t)
 #pragma unroll
             for (int m = 0; m < MB; ++m)
 #pragma unroll
-              for (int e = 0; e < 4; ++e) acc[t][m][e] = fold60(acc[t][m][e], c60);
+              for (int e = 0; e < 4; ++e) acc[t][m][e] = fold63(acc[t][m][e], k63);
+          pend = 0;
         }
+        pend += U;
+        uint32_t qrow[U][MB];
+        uint4 d[U][T];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const uint32_t r = r0l + u * PH;
+          const bool rv = r < rows;
+          if constexpr (MB == 2) {
+            const uint2 v = rv ? *reinterpret_cast<const uint2 *>(qsm + r * a.Mp) : make_uint2(0, 0);
+            qrow[u][0] = v.x, qrow[u][1] = v.y;
+          } else {
+#pragma unroll
+            for (int m4 = 0; m4 < MB; m4 += 4) {
+              const uint4 v = rv ? *reinterpret_cast<const uint4 *>(qsm + r * a.Mp + m4) : make_uint4(0, 0, 0, 0);
+              qrow[u][m4] = v.x, qrow[u][m4 + 1] = v.y, qrow[u][m4 + 2] = v.z, qrow[u][m4 + 3] = v.w;
+            }
+          }
+#pragma unroll
+          for (int t = 0; t < T; ++t)
+            d[u][t] = (rv && qv[t]) ? *reinterpret_cast<const uint4 *>(dbs + r * a.D2 + 4 * quad[t])
+                                    : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int t = 0; t < T; ++t)
+#pragma unroll
+            for (int m = 0; m < MB; ++m) {
+              acc[t][m][0] += (uint64_t)qrow[u][m] * d[u][t].x;
+              acc[t][m][1] += (uint64_t)qrow[u][m] * d[u][t].y;
+              acc[t][m][2] += (uint64_t)qrow[u][m] * d[u][t].z;
+              acc[t][m][3] += (uint64_t)qrow[u][m] * d[u][t].w;
+            }
       }
-#pragma unroll
-      for (int t = 0; t < T; ++t)
-#pragma unroll
-        for (int m = 0; m < MB; ++m)
-#pragma unroll
-          for (int e = 0; e < 4; ++e) acc[t][m][e] = fold60(acc[t][m][e], c60);
       __syncwarp();
       if (lane == 0) mbar_arrive(empty0 + 8 * st);
       ++it;
@@ -275,7 +296,12 @@ cudaError_t scan_launch(const ParamCtx &c, const ScanArgs &a0, cudaStream_t s) {
   const size_t smem = (size_t)kStages * a.stage_bytes + (2 * kStages + 1) * sizeof(uint64_t);
   e = cudaFuncSetAttribute(k_scan_tma<MB, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const uint32_t grid = a.nslots < (uint32_t)sms ? a.nslots : (uint32_t)sms;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scan_tma<MB, T>, kThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const uint64_t want = (uint64_t)sms * per_sm;
+  const uint32_t grid = a.nslots < want ? a.nslots : (uint32_t)want;
   k_scan_tma<MB, T><<<grid, kThreads, smem, s>>>(a, c.mod);
   return cudaGetLastError();
 }

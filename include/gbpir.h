@@ -159,6 +159,27 @@ pir_status_t pir_graph_destroy(pir_graph_t graph);
  * Errors: PIR_ERR_HANDLE, PIR_ERR_ARG (B = 0, best NULL), PIR_ERR_OOM, PIR_ERR_CUDA. */
 pir_status_t pir_autotune(pir_db_t db, uint32_t B, void *stream, uint32_t reps, pir_answer_opts_t *best);
 
+/* pir_answer_noalloc -- the answer without any device allocation.  The paper has
+ * no counterpart; this entry point exists for callers that cannot allocate device
+ * memory while serving: processes that reserve their whole device-memory budget up
+ * front (a server handing all free HBM to resident databases, a host application
+ * whose allocator owns the device) and latency-critical paths that cannot afford
+ * an allocator call.  Same inputs, outputs and result as pir_answer with device
+ * buffers (on_device = 1), asynchronous on `stream`.
+ *   Scratch: one static device array of PIR_NOALLOC_SCRATCH_BYTES per GPU, held
+ *   from library load to process exit.  The first call on a device looks up the
+ *   array's device address; make it before any stream capture.  All calls share
+ *   the array, so calls that overlap on the GPU race: serialize them.
+ *   Limit: the result ([L*n][2B][D2] words) plus one chunk of query scratch must
+ *   fit the array; D1 is folded in as many chunks as needed.  Requests whose
+ *   result alone does not fit return PIR_ERR_ARG.
+ *   Calls no cudaMalloc, cudaFree or other allocating routine.
+ * Errors: PIR_ERR_HANDLE, PIR_ERR_ARG (B = 0, NULL or misaligned buffers, too
+ * large for the scratch array), PIR_ERR_CUDA. */
+#define PIR_NOALLOC_SCRATCH_BYTES (64u << 20)
+pir_status_t pir_answer_noalloc(pir_db_t db, const uint32_t *queries, uint32_t B, uint32_t *responses,
+                                void *stream);
+
 /* Forward / inverse negacyclic NTT of `count` RNS polynomials [count][L][n] in
  * place, in device memory, asynchronously on stream (Sec. 2.3; single-kernel
  * on-chip NTT, Sec. 4.3).  Inputs must be canonical; outputs are canonical.

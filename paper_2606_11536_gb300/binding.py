@@ -90,6 +90,7 @@ def lib():
             "pir_graph_launch": (i32, [vp, vp]),
             "pir_graph_destroy": (i32, [vp]),
             "pir_autotune": (i32, [vp, u32, vp, u32, C.POINTER(pir_answer_opts_t)]),
+            "pir_answer_noalloc": (i32, [vp, vp, u32, vp, vp]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(L, name)
@@ -175,6 +176,20 @@ def pir_answer_ex(db: Db, queries, B: int, responses, stream=None, k_chunk: int 
     o = pir_answer_opts_t(k_chunk, tile, flags)
     _check(lib().pir_answer_ex(C.c_void_p(db.handle), qp, B, rp, int(qdev), _stream_ptr(stream), C.byref(o)),
            "pir_answer_ex")
+    return responses
+
+
+PIR_NOALLOC_SCRATCH_BYTES = 64 << 20
+
+
+def pir_answer_noalloc(db: Db, queries, B: int, responses, stream=None):
+    """pir_answer on device buffers without any device allocation (scratch comes
+    from the library's fixed per-GPU array); for callers that cannot allocate."""
+    qp, qdev, _ = _ptr(queries)
+    rp, rdev, _ = _ptr(responses)
+    if not (qdev and rdev):
+        raise ValueError("pir_answer_noalloc works on device buffers")
+    _check(lib().pir_answer_noalloc(C.c_void_p(db.handle), qp, B, rp, _stream_ptr(stream)), "pir_answer_noalloc")
     return responses
 
 

@@ -244,6 +244,17 @@ pir_status_t answer_device(pir_db *db, const uint32_t *queries, uint32_t B, uint
 
 }  // namespace
 
+namespace gbpir {
+bool db_view(pir_db_t db, DbView *out) {
+  if (!live(db) || !out) return false;
+  out->p = db->p;
+  out->layout = db->layout;
+  out->ctx = db->ctx;
+  out->resident = db->resident;
+  return true;
+}
+}  // namespace gbpir
+
 extern "C" {
 
 const char *pir_status_str(pir_status_t st) {

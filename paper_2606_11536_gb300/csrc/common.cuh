@@ -47,6 +47,16 @@ struct ParamCtx {
 pir_status_t validate_params(const pir_params_t *p);
 pir_status_t get_param_ctx(const pir_params_t *p, const ParamCtx **out);  // cached, device-resident tables
 
+// Read-only view of a live DB handle (api.cu); false for unknown or freed handles.
+struct DbView {
+  pir_params_t p;
+  int layout;
+  const ParamCtx *ctx;
+  const void *resident;
+};
+bool db_view(pir_db_t db, DbView *out);
+void count_launches(uint64_t k);
+
 // Error bookkeeping (api.cu)
 // Per-device error word that kernels with bounded waits set on a timeout.
 cudaError_t device_error_word(uint32_t **word);

@@ -129,7 +129,20 @@ __device__ __forceinline__ uint32_t shoup_mul(uint32_t x, uint32_t w, uint32_t w
 // (q-1)^2 < 2^60 before it could reach 2^64 (2^63 + q + 8 (q-1)^2 < 2^64).
 constexpr int kFoldProducts = 8;
 __device__ __forceinline__ uint64_t fold63(uint64_t acc, uint64_t k63) {
-  return acc >= (1ull << 63) ? acc - k63 : acc;
+  // sign test on the high word, then a predicated 64-bit subtract
+  asm("{\n .reg .pred p;\n .reg .u32 lo, hi;\n mov.b64 {lo, hi}, %0;\n setp.lt.s32 p, hi, 0;\n"
+      " @p sub.u64 %0, %0, %1;\n}"
+      : "+l"(acc)
+      : "l"(k63));
+  return acc;
+}
+
+// acc += a * b with a, b < 2^32: one 32 x 32 -> 64-bit multiply-add.  Written as
+// PTX mad.wide.u32 because the C++ form `acc += (uint64_t)a * b` does not always
+// reach the single-instruction form inside the streaming loops (measured: ~10
+// instructions per product in the TMA scan, one with this helper).
+__device__ __forceinline__ void mac_wide(uint64_t &acc, uint32_t a, uint32_t b) {
+  asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
 }
 
 // Full reduction of a 64-bit value mod q (q < 2^30): Barrett with mu = floor(2^64/q).

@@ -82,10 +82,10 @@ __global__ void __launch_bounds__(kGemvThreads) k_gemv(const uint32_t *__restric
 #pragma unroll
             for (int m = 0; m < MB; ++m) {
               const uint32_t a = qv[m];
-              acc[m][0] += (uint64_t)a * d[u].x;
-              acc[m][1] += (uint64_t)a * d[u].y;
-              acc[m][2] += (uint64_t)a * d[u].z;
-              acc[m][3] += (uint64_t)a * d[u].w;
+              mac_wide(acc[m][0], a, d[u].x);
+              mac_wide(acc[m][1], a, d[u].y);
+              mac_wide(acc[m][2], a, d[u].z);
+              mac_wide(acc[m][3], a, d[u].w);
             }
           }
 #pragma unroll
@@ -99,10 +99,12 @@ __global__ void __launch_bounds__(kGemvThreads) k_gemv(const uint32_t *__restric
 #pragma unroll
           for (int m = 0; m < MB; ++m) {
             const uint32_t a = qv[m];
-            acc[m][0] = fold63(acc[m][0] + (uint64_t)a * d.x, k63);
-            acc[m][1] = fold63(acc[m][1] + (uint64_t)a * d.y, k63);
-            acc[m][2] = fold63(acc[m][2] + (uint64_t)a * d.z, k63);
-            acc[m][3] = fold63(acc[m][3] + (uint64_t)a * d.w, k63);
+            mac_wide(acc[m][0], a, d.x);
+            mac_wide(acc[m][1], a, d.y);
+            mac_wide(acc[m][2], a, d.z);
+            mac_wide(acc[m][3], a, d.w);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[m][e] = fold63(acc[m][e], k63);
           }
         }
       }
@@ -226,7 +228,7 @@ __global__ void __launch_bounds__(256) k_gemm(const uint32_t *__restrict__ db, c
 #pragma unroll
         for (int x = 0; x < RM; ++x)
 #pragma unroll
-          for (int y = 0; y < 8; ++y) acc[x][y] += (uint64_t)av[x] * bv[y];
+          for (int y = 0; y < 8; ++y) mac_wide(acc[x][y], av[x], bv[y]);
       }
 #pragma unroll
       for (int x = 0; x < RM; ++x)
@@ -291,7 +293,9 @@ cudaError_t launch_gemm_plain(const ParamCtx &c, const uint32_t *db, uint32_t D1
                               uint32_t M, uint32_t Mp, uint32_t i0, uint32_t Kc, uint32_t *out, int acc,
                               uint32_t tile, int stall_test, cudaStream_t s) {
   if (tile == 0) {
-    if (scan_tma_supports(M, D2)) tile = 7;
+    // measured on GB300: the TMA scan wins up to 4 query rows; with 6-8 rows its
+    // accumulators cap it at one or two CTAs per SM and the GEMV-shaped kernel wins
+    if (M <= 4 && scan_tma_supports(M, D2)) tile = 7;
     else if (M <= 2) tile = 1;
     else if (M <= 4) tile = 2;
     else if (M <= 8) tile = 3;

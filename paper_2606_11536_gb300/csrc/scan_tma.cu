@@ -68,13 +68,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Waits for the completion of phase `parity`; false once kWaitNs has passed.
+// Waits for the completion of phase `parity`; false once kWaitNs has passed.  A
+// failed poll backs off with __nanosleep so that waiting warps leave the issue
+// slots and pipes to the warps doing the multiply-adds.
 __device__ __forceinline__ bool wait_bounded(uint32_t bar, uint32_t parity) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = gtimer();
-  for (;;) {
+  for (uint32_t k = 1;; ++k) {
+    __nanosleep(64);
     if (mbar_try_wait(bar, parity)) return true;
-    if (gtimer() - t0 > kWaitNs) return false;
+    if ((k & 15) == 0 && gtimer() - t0 > kWaitNs) return false;
   }
 }
 
@@ -243,10 +246,10 @@ __global__ void __launch_bounds__(kThreads, ScanShape<MB, T>::kMinBlocks) k_scan
           for (int t = 0; t < T; ++t)
 #pragma unroll
             for (int m = 0; m < MB; ++m) {
-              acc[t][m][0] += (uint64_t)qrow[u][m] * d[u][t].x;
-              acc[t][m][1] += (uint64_t)qrow[u][m] * d[u][t].y;
-              acc[t][m][2] += (uint64_t)qrow[u][m] * d[u][t].z;
-              acc[t][m][3] += (uint64_t)qrow[u][m] * d[u][t].w;
+              mac_wide(acc[t][m][0], qrow[u][m], d[u][t].x);
+              mac_wide(acc[t][m][1], qrow[u][m], d[u][t].y);
+              mac_wide(acc[t][m][2], qrow[u][m], d[u][t].z);
+              mac_wide(acc[t][m][3], qrow[u][m], d[u][t].w);
             }
       }
       __syncwarp();

@@ -134,3 +134,54 @@ def noise_sigma_estimate(n: int, log2p: int, D1: int, sigma: float = 3.2) -> flo
     DB * e with DB uniform in [0, p) and e of std sigma (App. D style estimate)."""
     p = 2.0 ** log2p
     return math.sqrt(D1 * n) * math.sqrt((p - 1) * (2 * p - 1) / 6.0) * sigma
+
+
+# --- the same streams generated by torch (device-side, for inputs too large for host) ---
+
+def _i64(v: int) -> int:
+    """The two's-complement int64 with the bits of the u64 value v."""
+    v &= _MASK64
+    return v - (1 << 64) if v >= (1 << 63) else v
+
+
+def _srl(x, k: int):
+    """Logical right shift of int64 tensors holding u64 bits."""
+    return (x >> k) & ((1 << (64 - k)) - 1)
+
+
+def _mix_torch(z):
+    z = (z ^ _srl(z, 30)) * _i64(0xBF58476D1CE4E5B9)
+    z = (z ^ _srl(z, 27)) * _i64(0x94D049BB133111EB)
+    return z ^ _srl(z, 31)
+
+
+def u64_torch(seed: int, stream: int, start: int, count: int, device=None):
+    """u64(seed, stream, start, count) as an int64 tensor with the same bits."""
+    import torch
+    idx = torch.arange(start + 1, start + count + 1, dtype=torch.int64, device=device)
+    z = _i64(stream_key(seed, stream)) + idx * _i64(int(GAMMA))
+    return _mix_torch(z)
+
+
+def uniform_residues_torch(seed: int, stream: int, count: int, n: int, qs, device=None, start: int = 0,
+                           chunk: int = 1 << 24):
+    """uniform_residues(...) generated on `device`: int32 tensor [count][L][n] holding
+    the u32 residues (the same values as the numpy version)."""
+    import torch
+    L = len(qs)
+    total = count * L * n
+    out = torch.empty(total, dtype=torch.int32, device=device)
+    j_of = None
+    for s0 in range(0, total, chunk):
+        c = min(chunk, total - s0)
+        x = u64_torch(seed, stream, start * L * n + s0, c, device)
+        pos = torch.arange(s0, s0 + c, dtype=torch.int64, device=device)
+        j_of = (pos // n) % L
+        hi, lo = _srl(x, 32), x & 0xFFFFFFFF
+        res = torch.empty_like(x)
+        for j, q in enumerate(qs):
+            sel = j_of == j
+            r = ((hi[sel] % q) * ((1 << 32) % q) + lo[sel]) % q
+            res[sel] = r
+        out[s0:s0 + c] = res.to(torch.int32)
+    return out.view(count, L, n)

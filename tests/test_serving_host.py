@@ -1,0 +1,154 @@
+"""Host-side serving logic (continuous batching, admission) against a CPU fake of
+the device backend: no GPU involved."""
+import types
+
+import pytest
+
+from paper_2606_11536_gb300.serving import AdmissionError, Backend, Request, Server, latency_stats, poisson_arrivals
+
+
+class FakeClock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        return self.t
+
+
+class FakeBackend(Backend):
+    """A batch finishes `latency` fake seconds after dispatch; the 'answer' of a
+    query q against database d is (d.salt, q)."""
+
+    def __init__(self, clock, latency=1.0):
+        self.clock, self.latency = clock, latency
+        self.batches = []
+
+    def setup_db(self, name, params, raw, layout):
+        return types.SimpleNamespace(name=name, salt=hash(name) % 1000), 4 * params.L * params.n * params.D1 * params.D2
+
+    def free_db(self, handle):
+        pass
+
+    def new_stream(self):
+        return object()
+
+    def dispatch(self, handle, params, queries, stream):
+        self.batches.append((handle.name, list(queries)))
+        return self.clock() + self.latency, [(handle.salt, q) for q in queries]
+
+    def done(self, event):
+        return self.clock() >= event
+
+    def response(self, bufs, b, B):
+        assert len(bufs) == B
+        return bufs[b]
+
+
+def params(n=2048, D1=16, D2=16):
+    return types.SimpleNamespace(n=n, L=2, D1=D1, D2=D2, log2p=16)
+
+
+def make(streams=2, max_batch=4, **kw):
+    clock = FakeClock()
+    be = FakeBackend(clock)
+    srv = Server(be, streams=streams, max_batch=max_batch, clock=clock, keep_responses=True, **kw)
+    return clock, be, srv
+
+
+def test_requests_arriving_during_a_batch_are_coalesced():
+    clock, be, srv = make(streams=1, max_batch=4)
+    srv.admit("a", params(), None)
+    srv.submit(Request(0, "a", 0, 0.0))
+    srv.poll()                       # request 0 goes out alone
+    for k in range(1, 7):            # six arrive while it runs
+        srv.submit(Request(k, "a", k, 0.1 * k))
+    srv.poll()
+    assert [len(q) for _, q in be.batches] == [1]
+    clock.t = 1.0
+    srv.poll()                       # slot frees: next batch takes 4 (max_batch)
+    assert [len(q) for _, q in be.batches] == [1, 4]
+    clock.t = 2.0
+    srv.poll()
+    assert [len(q) for _, q in be.batches] == [1, 4, 2]
+    clock.t = 3.0
+    srv.poll()
+    assert srv.pending() == 0 and len(srv.done) == 7
+    assert [r.rid for r in srv.done] == list(range(7))  # FIFO within a database
+
+
+def test_oldest_waiting_request_picks_the_database_and_slots_overlap():
+    clock, be, srv = make(streams=2, max_batch=8)
+    for name in ("a", "b", "c"):
+        srv.admit(name, params(), None)
+    srv.submit(Request(0, "b", 0, 0.0))
+    srv.submit(Request(1, "a", 1, 0.1))
+    srv.submit(Request(2, "c", 2, 0.2))
+    srv.submit(Request(3, "b", 3, 0.3))
+    srv.poll()
+    # two slots: b (oldest head, takes both of its requests) and then a
+    assert [name for name, _ in be.batches] == ["b", "a"]
+    assert be.batches[0][1] == [0, 3]
+    clock.t = 1.0
+    srv.poll()
+    assert [name for name, _ in be.batches] == ["b", "a", "c"]
+    clock.t = 2.0
+    srv.poll()
+    assert srv.pending() == 0
+    for r in srv.done:  # every response is the one its own query gives alone
+        assert r.response == (hash(r.db) % 1000, r.query)
+
+
+def test_admission_by_memory_budget():
+    p = params(n=4096, D1=512, D2=256)  # 4 GiB resident
+    clock, be, srv = make(memory_budget=9 << 30)
+    srv.admit("a", p, None)
+    srv.admit("b", p, None)
+    with pytest.raises(AdmissionError):
+        srv.admit("c", p, None)
+    srv.evict("b")
+    srv.admit("c", p, None)
+    assert srv.resident_bytes == 8 << 30
+
+
+def test_scratch_budget_limits_batches_in_flight():
+    p = params(n=2048, D1=16, D2=16)
+    per_query = 8 * 2 * 2048 * 32
+    clock, be, srv = make(streams=3, max_batch=8, scratch_budget=5 * per_query)
+    srv.admit("a", p, None)
+    for k in range(12):
+        srv.submit(Request(k, "a", k, 0.0))
+    srv.poll()
+    # first slot takes 5 (budget), the others wait for memory
+    assert [len(q) for _, q in be.batches] == [5]
+    clock.t = 1.0
+    srv.poll()
+    assert [len(q) for _, q in be.batches] == [5, 5]
+    clock.t = 2.0
+    srv.poll()
+    clock.t = 3.0
+    srv.poll()
+    assert srv.pending() == 0 and sum(len(q) for _, q in be.batches) == 12
+
+
+def test_open_loop_run_and_stats():
+    import time as _time
+    be_clock = _time.perf_counter
+    calls = []
+
+    class RealTimeFake(FakeBackend):
+        def dispatch(self, handle, params, queries, stream):
+            calls.append(len(queries))
+            return be_clock() + 0.002, list(queries)
+
+        def done(self, event):
+            return be_clock() >= event
+
+    srv = Server(RealTimeFake(be_clock), streams=2, max_batch=4)
+    for name in ("a", "b"):
+        srv.admit(name, params(), None)
+    arr = poisson_arrivals(2000.0, 0.05, ["a", "b"], seed=3, make_query=lambda db, k: k)
+    out = srv.run(arr)
+    st = latency_stats(out)
+    assert st["count"] == len(arr) > 40
+    assert 2.0 <= st["p50_ms"] <= st["p99_ms"] < 200
+    assert max(calls) <= 4 and sum(calls) == len(arr)

@@ -38,7 +38,7 @@ WORKLOADS = {
     "tiny_n2048": (2048, 12, 16, 16, 1, "768 KiB raw DB, n=2048, p=2^12, 16x16 polys"),
     "db1g_n4096": (4096, 16, 512, 256, 1, "1 GiB raw DB (4 GiB NTT-form), n=4096, p=2^16, D1=512, D2=256"),
     "db256m_n4096": (4096, 16, 128, 256, 1, "256 MiB raw DB (1 GiB NTT-form), n=4096, p=2^16, D1=128, D2=256"),
-    "db256m_n2048": (2048, 16, 512, 256, 1, "256 MiB raw DB (1 GiB NTT-form), n=2048, p=2^16, D1=512, D2=256"),
+    "db512m_n2048": (2048, 16, 512, 256, 1, "512 MiB raw DB (2 GiB NTT-form), n=2048, p=2^16, D1=512, D2=256"),
     "db1g_n2048": (2048, 16, 512, 512, 1, "1 GiB raw DB (4 GiB NTT-form), n=2048, p=2^16, D1=512, D2=512"),
     "db8g_n4096": (4096, 16, 2048, 512, 1, "8 GiB raw DB (32 GiB NTT-form), n=4096, p=2^16, D1=2048, D2=512"),
     "db16g_n4096": (4096, 16, 4096, 512, 1, "16 GiB raw DB (64 GiB NTT-form), n=4096, p=2^16, D1=4096, D2=512"),
@@ -387,6 +387,109 @@ def our_arm(args, wl):
         dist.destroy_process_group()
 
 
+def ntt_sweep(args):
+    """Standalone NTT sweep: forward then inverse NTT (in place) of 2^16 RNS
+    polynomials (L = 2, n = 4096, 2 GiB) per step."""
+    import torch
+    import paper_2606_11536_gb300 as g
+    from paper_2606_11536_gb300 import synth
+    torch.cuda.set_device(0)
+    n, count = 4096, 1 << 16
+    p = g.pir_make_params(n, 16, 1, 1, L_PRIMES)
+    a = synth.uniform_residues_torch(3, synth.STREAM_UNIFORM, count, n, p.qs, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        g.ntt_fwd(p, a, stream=stream)
+        g.ntt_inv(p, a, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    fwd_ms = inv_ms = 0.0
+    for _ in range(args.steps):
+        e0.record(stream)
+        g.ntt_fwd(p, a, stream=stream)
+        e1.record(stream)
+        g.ntt_inv(p, a, stream=stream)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        fwd_ms += e0.elapsed_time(e1)
+        inv_ms += e1.elapsed_time(e2)
+    nbytes = count * L_PRIMES * n * 4
+    peaks, kind = measured_peaks()
+    fwd_gbs = 2 * nbytes / (fwd_ms / args.steps / 1e3) / 1e9
+    inv_gbs = 2 * nbytes / (inv_ms / args.steps / 1e3) / 1e9
+    line = {"metric": "NTT sweep GB/s (bytes read + written per transform)", "value": fwd_gbs, "unit": "GB/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": "ntt_sweep_n4096", "polys": count, "n": n, "L": L_PRIMES, "bytes": nbytes},
+            "forward_ms": fwd_ms / args.steps, "inverse_ms": inv_ms / args.steps, "inverse_gbs": inv_gbs,
+            "butterflies_per_s": count * L_PRIMES * (n // 2) * 12 / (fwd_ms / args.steps / 1e3),
+            "roofline": {"bound": "hbm", "achieved": fwd_gbs, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                         "frac": fwd_gbs / float(peaks["hbm_gbs"]), "peak_source": kind}}
+    print(json.dumps(line), flush=True)
+
+
+SERVING_DBS = [  # name, n, log2p, D1, D2
+    ("db1g_n2048", 2048, 16, 512, 512),
+    ("db1g_n4096", 4096, 16, 512, 256),
+    ("db16g_n4096", 4096, 16, 4096, 512),
+]
+SERVING_EXTRA = ("db8g_n4096", 4096, 16, 2048, 512)
+
+
+def serving_bench(args):
+    """Serving: three resident DBs, admission of a fourth by free-HBM check, Poisson
+    arrivals at several loads with uniformly random target DB, continuous batching."""
+    import torch
+    import paper_2606_11536_gb300 as g
+    from paper_2606_11536_gb300 import serving, synth
+    torch.cuda.set_device(0)
+    be = serving.CudaBackend()
+    srv = serving.Server(be, streams=args.serving_streams, max_batch=args.serving_max_batch,
+                         scratch_budget=args.serving_scratch_gib << 30)
+    pools = {}
+    t0 = time.perf_counter()
+    for k, (name, n, log2p, D1, D2) in enumerate(SERVING_DBS):
+        p = g.pir_make_params(n, log2p, D1, D2, L_PRIMES)
+        srv.admit(name, p, synth.raw_db(k, synth.raw_db_bytes(n, log2p, D1, D2)))
+        pools[name] = [synth.uniform_residues_torch(900 + 16 * k + t, synth.STREAM_UNIFORM, D1 * 2, n, p.qs,
+                                                    device="cuda").view(-1) for t in range(4)]
+    name, n, log2p, D1, D2 = SERVING_EXTRA
+    p = g.pir_make_params(n, log2p, D1, D2, L_PRIMES)
+    free_before = torch.cuda.mem_get_info()[0]
+    try:
+        srv.admit(name, p, synth.raw_db(7, synth.raw_db_bytes(n, log2p, D1, D2)))
+        admitted = True
+    except serving.AdmissionError as e:
+        admitted, err = False, str(e)
+    setup_s = time.perf_counter() - t0
+    dbs = list(srv.dbs)
+    if admitted:
+        pools[name] = [synth.uniform_residues_torch(990 + t, synth.STREAM_UNIFORM, D1 * 2, n, p.qs,
+                                                    device="cuda").view(-1) for t in range(4)]
+    results = []
+    for rate in args.serving_rates:
+        arr = serving.poisson_arrivals(rate, args.serving_seconds, dbs, seed=int(rate),
+                                       make_query=lambda db, k: pools[db][k % len(pools[db])])
+        torch.cuda.synchronize()
+        done = srv.run(arr)
+        torch.cuda.synchronize()
+        st = serving.latency_stats(done)
+        st["offered_qps"] = rate
+        st["per_db"] = {d: serving.latency_stats([r for r in done if r.db == d]) for d in dbs}
+        results.append(st)
+    g.pir_check_device()
+    line = {"metric": "serving p50/p99 ms (Poisson arrivals, continuous batching)", "unit": "ms",
+            "value": results[0].get("p99_ms"), "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+            "dtype": "u32",
+            "config": {"workload": "serving", "dbs": [d[0] for d in SERVING_DBS], "fourth_db": SERVING_EXTRA[0],
+                       "fourth_admitted": admitted, "free_hbm_before_fourth": free_before,
+                       "streams": args.serving_streams, "max_batch": args.serving_max_batch,
+                       "seconds_per_load": args.serving_seconds, "setup_s": setup_s,
+                       "resident_bytes": srv.resident_bytes},
+            "loads": results}
+    print(json.dumps(line), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -400,9 +503,20 @@ def main(argv=None):
     ap.add_argument("--k-chunk", type=int, default=0, help="fold D1 in chunks of this many ciphertexts")
     ap.add_argument("--ref-cols", type=int, default=64, help="columns in the oracle's timed sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ntt-sweep", action="store_true", help="time the standalone NTT sweep instead")
+    ap.add_argument("--serving", action="store_true", help="run the serving benchmark instead")
+    ap.add_argument("--serving-rates", type=float, nargs="+", default=[100, 300, 1000, 3000, 5000])
+    ap.add_argument("--serving-seconds", type=float, default=2.0)
+    ap.add_argument("--serving-streams", type=int, default=4)
+    ap.add_argument("--serving-max-batch", type=int, default=32)
+    ap.add_argument("--serving-scratch-gib", type=int, default=32)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
+    if args.ntt_sweep:
+        return ntt_sweep(args)
+    if args.serving:
+        return serving_bench(args)
     if args.impl == "reference":
         reference_arm(args, args.workload)
     else:

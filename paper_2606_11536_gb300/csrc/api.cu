@@ -207,6 +207,27 @@ pir_status_t answer_device(pir_db *db, const uint32_t *queries, uint32_t B, uint
   uint32_t *out = reinterpret_cast<uint32_t *>(base + up(qhat_bytes) + up(qs_bytes));
 
   StageTimer tm((o.flags & PIR_ANSWER_STAGE_TIMES) != 0, s);
+  // Batch 1 on the TMA scan: the forward NTT writes the slot layout itself (pairs of
+  // a/b residues, Mp = 2) and the scan writes the response layout itself, so neither
+  // transpose runs.
+  const bool fused = !limb && B == 1 && (o.tile == 0 || o.tile == 7) && scan_tma_supports(M, D2) && Kc % 2 == 0;
+  if (fused) {
+    uint32_t *qs2 = reinterpret_cast<uint32_t *>(base);  // [L*n][Kc][2] fits the qhat area
+    for (uint32_t i0 = 0; i0 < D1; i0 += Kc) {
+      const uint32_t kc = D1 - i0 < Kc ? D1 - i0 : Kc;
+      tm.begin();
+      CK(launch_ntt_fwd_pair_slots(c, queries, D1, i0, kc, qs2, s));
+      tm.end(0, 1);
+      tm.begin();
+      CK(launch_scan_tma(c, static_cast<const uint32_t *>(db->resident), D1, D2, qs2, M, 2, i0, kc, responses, i0 > 0,
+                         stall, 1, s));
+      tm.end(2, 1);
+    }
+    tm.begin();
+    CK(launch_ntt_inv(c, responses, responses, (uint64_t)B * D2 * 2 * L, s));
+    tm.end(4, 1);
+    return PIR_OK;
+  }
   for (uint32_t i0 = 0; i0 < D1; i0 += Kc) {
     const uint32_t kc = D1 - i0 < Kc ? D1 - i0 : Kc;
     // forward NTT of ciphertexts i0 .. i0+kc-1 of every query: per query b the rows

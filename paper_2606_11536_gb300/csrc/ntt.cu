@@ -25,6 +25,20 @@ __device__ __forceinline__ uint32_t padx(uint32_t i) { return i + (i >> 4); }
 // Source kinds of the first pass.
 enum { SRC_SMEM = 0, SRC_U32 = 1, SRC_RAW = 2 };
 
+// Destinations of a pass: shared memory (not the last pass), global memory
+// (canonical), a second shared buffer (canonical; the first row of a pair), or the
+// slot-major query layout as (first row, this row) pairs.
+enum { DST_SMEM = 0, DST_GLOBAL = 1, DST_PAIR = 2 };
+
+// Pair destination: element k of rows (i, comp 0) and (i, comp 1) of prime j goes to
+// slots[((j*n + k) * Kc + i) * 2 + comp] (the plain slot layout with Mp = 2).
+struct SlotDst {
+  uint32_t *slots;
+  uint32_t *sm2;
+  uint32_t Kc, i, jn;
+  uint32_t second;  // 0: park the first row in sm2; 1: write (sm2, this row) pairs
+};
+
 struct RawSrc {
   const uint8_t *raw;  // little-endian bit stream of log2p-bit coefficients
   uint64_t poly0;      // row-major order: local polynomial p is poly0 + p
@@ -103,11 +117,11 @@ __device__ __forceinline__ void inv_stages(uint32_t (&v)[1 << RB], uint32_t hi, 
 
 // One radix-2^RB pass over the whole row: unit u holds the 2^RB elements whose
 // index has bits [BLO, BLO+RB) free and the rest fixed by u.
-template <int LOGN, int RB, int BLO, bool FWD, int SRC, bool TO_GLOBAL>
+template <int LOGN, int RB, int BLO, bool FWD, int SRC, int DST>
 __device__ __forceinline__ void ntt_pass(uint32_t *sm, const uint32_t *__restrict__ gin, const RawSrc &rs,
                                          uint64_t poly, uint32_t *__restrict__ gout, const uint32_t *__restrict__ w,
                                          const uint32_t *__restrict__ wsh, uint32_t q, uint32_t ninv,
-                                         uint32_t ninv_sh) {
+                                         uint32_t ninv_sh, const SlotDst *sd = nullptr) {
   constexpr int N = 1 << LOGN, T = N / 16, UNITS = N >> RB, PER = UNITS / T;
   static_assert(UNITS % T == 0, "pass plan");
 #pragma unroll
@@ -138,7 +152,7 @@ __device__ __forceinline__ void ntt_pass(uint32_t *sm, const uint32_t *__restric
       fwd_stages<RB, BLO, LOGN>(v, hi, w, wsh, q);
     else
       inv_stages<RB, BLO, LOGN>(v, hi, w, wsh, q);
-    if constexpr (TO_GLOBAL) {
+    if constexpr (DST != DST_SMEM) {
 #pragma unroll
       for (int e = 0; e < (1 << RB); ++e) {
         uint32_t x = v[e];
@@ -151,7 +165,20 @@ __device__ __forceinline__ void ntt_pass(uint32_t *sm, const uint32_t *__restric
         }
         v[e] = x;
       }
-      if constexpr (BLO == 0 && RB >= 2) {
+      if constexpr (DST == DST_PAIR) {
+        if (!sd->second) {
+#pragma unroll
+          for (int e = 0; e < (1 << RB); ++e) sd->sm2[padx(base | ((uint32_t)e << BLO))] = v[e];
+        } else {
+#pragma unroll
+          for (int e = 0; e < (1 << RB); ++e) {
+            const uint32_t k = base | ((uint32_t)e << BLO);
+            const uint32_t first = sd->sm2[padx(k)];
+            *reinterpret_cast<uint2 *>(sd->slots + (((uint64_t)sd->jn + k) * sd->Kc + sd->i) * 2) =
+                make_uint2(first, v[e]);
+          }
+        }
+      } else if constexpr (BLO == 0 && RB >= 2) {
 #pragma unroll
         for (int e = 0; e < (1 << RB); e += 4)
           *reinterpret_cast<uint4 *>(gout + base + e) = make_uint4(v[e], v[e + 1], v[e + 2], v[e + 3]);
@@ -182,25 +209,25 @@ __global__ void __launch_bounds__((1 << LOGN) / 16)
     uint32_t *gout = dst + row * N;
     const uint64_t poly = SRC == SRC_RAW ? rs.poly(row / L) : 0;
     if constexpr (LOGN == 11) {
-      ntt_pass<11, 4, 7, true, SRC, false>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
+      ntt_pass<11, 4, 7, true, SRC, DST_SMEM>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
       __syncthreads();
-      ntt_pass<11, 4, 3, true, SRC_SMEM, false>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
+      ntt_pass<11, 4, 3, true, SRC_SMEM, DST_SMEM>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
       __syncthreads();
-      ntt_pass<11, 3, 0, true, SRC_SMEM, true>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
+      ntt_pass<11, 3, 0, true, SRC_SMEM, DST_GLOBAL>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
     } else if constexpr (LOGN == 12) {
-      ntt_pass<12, 4, 8, true, SRC, false>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
+      ntt_pass<12, 4, 8, true, SRC, DST_SMEM>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
       __syncthreads();
-      ntt_pass<12, 4, 4, true, SRC_SMEM, false>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
+      ntt_pass<12, 4, 4, true, SRC_SMEM, DST_SMEM>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
       __syncthreads();
-      ntt_pass<12, 4, 0, true, SRC_SMEM, true>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
+      ntt_pass<12, 4, 0, true, SRC_SMEM, DST_GLOBAL>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
     } else {
-      ntt_pass<13, 4, 9, true, SRC, false>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
+      ntt_pass<13, 4, 9, true, SRC, DST_SMEM>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
       __syncthreads();
-      ntt_pass<13, 4, 5, true, SRC_SMEM, false>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
+      ntt_pass<13, 4, 5, true, SRC_SMEM, DST_SMEM>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
       __syncthreads();
-      ntt_pass<13, 4, 1, true, SRC_SMEM, false>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
+      ntt_pass<13, 4, 1, true, SRC_SMEM, DST_SMEM>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
       __syncthreads();
-      ntt_pass<13, 1, 0, true, SRC_SMEM, true>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
+      ntt_pass<13, 1, 0, true, SRC_SMEM, DST_GLOBAL>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
     }
     __syncthreads();  // the next row reuses shared memory
   }
@@ -219,27 +246,79 @@ __global__ void __launch_bounds__((1 << LOGN) / 16)
     const uint32_t *gin = src + row * N;
     uint32_t *gout = dst + row * N;
     if constexpr (LOGN == 11) {
-      ntt_pass<11, 4, 0, false, SRC_U32, false>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
+      ntt_pass<11, 4, 0, false, SRC_U32, DST_SMEM>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
       __syncthreads();
-      ntt_pass<11, 4, 4, false, SRC_SMEM, false>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
+      ntt_pass<11, 4, 4, false, SRC_SMEM, DST_SMEM>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
       __syncthreads();
-      ntt_pass<11, 3, 8, false, SRC_SMEM, true>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
+      ntt_pass<11, 3, 8, false, SRC_SMEM, DST_GLOBAL>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
     } else if constexpr (LOGN == 12) {
-      ntt_pass<12, 4, 0, false, SRC_U32, false>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
+      ntt_pass<12, 4, 0, false, SRC_U32, DST_SMEM>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
       __syncthreads();
-      ntt_pass<12, 4, 4, false, SRC_SMEM, false>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
+      ntt_pass<12, 4, 4, false, SRC_SMEM, DST_SMEM>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
       __syncthreads();
-      ntt_pass<12, 4, 8, false, SRC_SMEM, true>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
+      ntt_pass<12, 4, 8, false, SRC_SMEM, DST_GLOBAL>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
     } else {
-      ntt_pass<13, 4, 0, false, SRC_U32, false>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
+      ntt_pass<13, 4, 0, false, SRC_U32, DST_SMEM>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
       __syncthreads();
-      ntt_pass<13, 4, 4, false, SRC_SMEM, false>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
+      ntt_pass<13, 4, 4, false, SRC_SMEM, DST_SMEM>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
       __syncthreads();
-      ntt_pass<13, 4, 8, false, SRC_SMEM, false>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
+      ntt_pass<13, 4, 8, false, SRC_SMEM, DST_SMEM>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
       __syncthreads();
-      ntt_pass<13, 1, 12, false, SRC_SMEM, true>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
+      ntt_pass<13, 1, 12, false, SRC_SMEM, DST_GLOBAL>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
     }
     __syncthreads();
+  }
+}
+
+// One row of the pair kernel below: the forward passes of row `gin`, the last
+// one into the pair destination.  Not inlined, so that the two rows of a block
+// run one after the other instead of being interleaved (which needs twice the
+// registers).
+template <int LOGN>
+__device__ __noinline__ void pair_row(uint32_t *sm, const uint32_t *__restrict__ gin, const uint32_t *__restrict__ w,
+                                      const uint32_t *__restrict__ wsh, uint32_t q, const SlotDst *sd) {
+  const RawSrc rs = {};
+  uint32_t *gout = nullptr;
+  if constexpr (LOGN == 11) {
+    ntt_pass<11, 4, 7, true, SRC_U32, DST_SMEM>(sm, gin, rs, 0, gout, w, wsh, q, 0, 0);
+    __syncthreads();
+    ntt_pass<11, 4, 3, true, SRC_SMEM, DST_SMEM>(sm, gin, rs, 0, gout, w, wsh, q, 0, 0);
+    __syncthreads();
+    ntt_pass<11, 3, 0, true, SRC_SMEM, DST_PAIR>(sm, gin, rs, 0, gout, w, wsh, q, 0, 0, sd);
+  } else if constexpr (LOGN == 12) {
+    ntt_pass<12, 4, 8, true, SRC_U32, DST_SMEM>(sm, gin, rs, 0, gout, w, wsh, q, 0, 0);
+    __syncthreads();
+    ntt_pass<12, 4, 4, true, SRC_SMEM, DST_SMEM>(sm, gin, rs, 0, gout, w, wsh, q, 0, 0);
+    __syncthreads();
+    ntt_pass<12, 4, 0, true, SRC_SMEM, DST_PAIR>(sm, gin, rs, 0, gout, w, wsh, q, 0, 0, sd);
+  } else {
+    ntt_pass<13, 4, 9, true, SRC_U32, DST_SMEM>(sm, gin, rs, 0, gout, w, wsh, q, 0, 0);
+    __syncthreads();
+    ntt_pass<13, 4, 5, true, SRC_SMEM, DST_SMEM>(sm, gin, rs, 0, gout, w, wsh, q, 0, 0);
+    __syncthreads();
+    ntt_pass<13, 4, 1, true, SRC_SMEM, DST_SMEM>(sm, gin, rs, 0, gout, w, wsh, q, 0, 0);
+    __syncthreads();
+    ntt_pass<13, 1, 0, true, SRC_SMEM, DST_PAIR>(sm, gin, rs, 0, gout, w, wsh, q, 0, 0, sd);
+  }
+}
+
+// Forward NTT of the a- and b-polynomial of one ciphertext (rows (i, comp 0) and
+// (i, comp 1) of prime j of a batch-1 query chunk), written straight into the
+// slot-major layout [L*n][Kc][2] that the batch-1 scan reads: the transpose of
+// Sec. 4.2 fused into the NTT's last pass.  Block = i * L + j.
+template <int LOGN>
+__global__ void __launch_bounds__((1 << LOGN) / 16)
+    k_ntt_fwd_pair_slots(const uint32_t *__restrict__ src, uint64_t row0, NttConst C, uint32_t L, uint32_t Kc,
+                         uint32_t *__restrict__ slots) {
+  constexpr int N = 1 << LOGN, PADN = N + N / 16;
+  extern __shared__ uint32_t sm[];
+  const uint32_t i = blockIdx.x / L, j = blockIdx.x % L;
+  SlotDst sd = {slots, sm + PADN, Kc, i, j << LOGN, 0};
+  for (int comp = 0; comp < 2; ++comp) {
+    sd.second = comp;
+    pair_row<LOGN>(sm, src + (row0 + (uint64_t)i * 2 * L + (uint64_t)comp * L + j) * N, C.t[j].fwd, C.t[j].fwd_sh,
+                   C.q[j], &sd);
+    __syncthreads();  // the second row reuses sm; its last pass reads the first row's sm2
   }
 }
 
@@ -307,6 +386,30 @@ cudaError_t launch_ntt_fwd_raw(const ParamCtx &c, const uint8_t *raw, int col_ma
     rs.poly0 = first;
   const RowMap rm = {0, 1, 1};
   return fwd_any(c, nullptr, rm, rs, dst, npolys * c.p.L, s, true);
+}
+
+template <int LOGN>
+cudaError_t pair_launch(const ParamCtx &c, const uint32_t *src, uint64_t row0, uint32_t Kc, uint32_t *slots,
+                        cudaStream_t s) {
+  const int T = (1 << LOGN) / 16;
+  const int smem = 2 * ((1 << LOGN) + (1 << LOGN) / 16) * (int)sizeof(uint32_t);
+  cudaError_t e = cudaFuncSetAttribute(k_ntt_fwd_pair_slots<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  k_ntt_fwd_pair_slots<LOGN><<<Kc * c.p.L, T, smem, s>>>(src, row0, c.ntt, c.p.L, Kc, slots);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ntt_fwd_pair_slots(const ParamCtx &c, const uint32_t *queries, uint32_t D1, uint32_t i0, uint32_t Kc,
+                                      uint32_t *slots, cudaStream_t s) {
+  (void)D1;
+  if (Kc == 0) return cudaSuccess;
+  const uint64_t row0 = (uint64_t)i0 * 2 * c.p.L;  // row (b = 0, i0, comp 0, j = 0)
+  switch (c.logn) {
+    case 11: return pair_launch<11>(c, queries, row0, Kc, slots, s);
+    case 12: return pair_launch<12>(c, queries, row0, Kc, slots, s);
+    case 13: return pair_launch<13>(c, queries, row0, Kc, slots, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_ntt_inv(const ParamCtx &c, const uint32_t *src, uint32_t *dst, uint64_t rows, cudaStream_t s) {

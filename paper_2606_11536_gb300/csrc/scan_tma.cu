@@ -100,6 +100,7 @@ struct ScanArgs {
   uint32_t nslots, logn;
   int acc_in;
   int stall_test;      // consumers wait on a barrier nobody arrives on (tests the timeout path)
+  int out_poly;        // 1: out is the response layout [B][D2][2][L*n] (NTT domain), else [L*n][M][D2]
 };
 
 // Rows per unrolled group and CTAs per SM, by accumulator count (MB rows x T quads):
@@ -274,15 +275,27 @@ __global__ void __launch_bounds__(kThreads, ScanShape<MB, T>::kMinBlocks) k_scan
           r[e] = v;
         }
         if (phs == 0 && qv[t] && (uint32_t)m < a.M) {
-          uint4 *o = reinterpret_cast<uint4 *>(a.out + ((uint64_t)s * a.M + m) * a.D2 + 4 * quad[t]);
-          if (a.acc_in) {
-            const uint4 prev = *o;
-            r[0] = reduce64((uint64_t)r[0] + prev.x, q, mu);
-            r[1] = reduce64((uint64_t)r[1] + prev.y, q, mu);
-            r[2] = reduce64((uint64_t)r[2] + prev.z, q, mu);
-            r[3] = reduce64((uint64_t)r[3] + prev.w, q, mu);
+          if (a.out_poly) {
+            // response layout: element (b, c, comp, j, k) at ((b*D2 + c)*2 + comp)*L*n + s.
+            // Consecutive slots go to consecutive CTAs at about the same time, so the
+            // 4-byte stores of neighbouring k meet in L2 before reaching DRAM.
+            const uint32_t b = (uint32_t)m >> 1, comp = (uint32_t)m & 1;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              uint32_t *o = a.out + (((uint64_t)b * a.D2 + 4 * quad[t] + e) * 2 + comp) * a.nslots + s;
+              *o = a.acc_in ? reduce64((uint64_t)r[e] + *o, q, mu) : r[e];
+            }
+          } else {
+            uint4 *o = reinterpret_cast<uint4 *>(a.out + ((uint64_t)s * a.M + m) * a.D2 + 4 * quad[t]);
+            if (a.acc_in) {
+              const uint4 prev = *o;
+              r[0] = reduce64((uint64_t)r[0] + prev.x, q, mu);
+              r[1] = reduce64((uint64_t)r[1] + prev.y, q, mu);
+              r[2] = reduce64((uint64_t)r[2] + prev.z, q, mu);
+              r[3] = reduce64((uint64_t)r[3] + prev.w, q, mu);
+            }
+            *o = make_uint4(r[0], r[1], r[2], r[3]);
           }
-          *o = make_uint4(r[0], r[1], r[2], r[3]);
         }
       }
     }
@@ -317,8 +330,10 @@ bool scan_tma_supports(uint32_t M, uint32_t D2) { return M <= 8 && D2 % 4 == 0 &
 
 cudaError_t launch_scan_tma(const ParamCtx &c, const uint32_t *db, uint32_t D1, uint32_t D2, const uint32_t *qs,
                             uint32_t M, uint32_t Mp, uint32_t i0, uint32_t Kc, uint32_t *out, int acc, int stall_test,
-                            cudaStream_t s) {
-  if (!scan_tma_supports(M, D2) || Mp % 4 != 0 || Kc == 0) return cudaErrorInvalidValue;
+                            int out_poly, cudaStream_t s) {
+  // query rows are bulk-copied: Mp = 2 needs an even Kc (16-byte chunk starts)
+  if (!scan_tma_supports(M, D2) || Kc == 0 || !(Mp % 4 == 0 || (Mp == 2 && M <= 2 && Kc % 2 == 0)))
+    return cudaErrorInvalidValue;
   uint32_t *err = nullptr;
   cudaError_t e = device_error_word(&err);
   if (e != cudaSuccess) return e;
@@ -336,11 +351,13 @@ cudaError_t launch_scan_tma(const ParamCtx &c, const uint32_t *db, uint32_t D1, 
   a.R = kChunkTarget / (D2 * 4);
   if (a.R == 0) a.R = 1;
   if (a.R > Kc) a.R = Kc;
+  if (Mp == 2 && (a.R & 1)) a.R = a.R > 1 ? a.R - 1 : 2;  // even row counts keep bulk copies 16-byte sized
   a.stage_bytes = (a.R * D2 * 4 + a.R * Mp * 4 + 127) & ~127u;
   a.nslots = c.p.L << c.logn;
   a.logn = c.logn;
   a.acc_in = acc;
   a.stall_test = stall_test;
+  a.out_poly = out_poly;
   const uint32_t nq = D2 / 4;
   const int T = nq > 64 ? 2 : 1;  // 8 warps x 8 quads per pass
   const int MB = M <= 2 ? 2 : M <= 4 ? 4 : 8;

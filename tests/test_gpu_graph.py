@@ -31,7 +31,9 @@ def test_graph_replays_match_oracle(orc, layout, B):
                 k0 = g.pir_kernel_launches()
                 g.pir_graph_launch(graph)
                 R = from_dev(rd, (B, D2, 2, 2, n))
-                assert g.pir_kernel_launches() - k0 == 5  # NTT, transpose, GEMM, transpose, INTT
+                # NTT, transpose, GEMM, transpose, INTT; batch 1 on the plain layout fuses both
+                # transposes away (NTT straight to the slot layout, scan straight to responses)
+                assert g.pir_kernel_launches() - k0 == (3 if (layout == 0 and B == 1) else 5)
                 assert np.array_equal(R, orc.answer(P, raw, Q)), seed
             g.pir_check_device()
         finally:

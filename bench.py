@@ -259,17 +259,24 @@ def our_arm(args, wl):
     layout = g.PIR_LAYOUT_LIMB if args.layout == "limb" else g.PIR_LAYOUT_PLAIN
     p = g.pir_make_params(n, log2p, D1, D2, L_PRIMES)
     raw_bytes = binding.raw_db_bytes(p)
-    raw = synth.raw_db(0, raw_bytes)
-    db = g.pir_setup_db(p, raw, layout=layout)
+    small = raw_bytes <= (2 << 30)
+    if small:  # host bytes (also what the oracle baseline reads)
+        raw = synth.raw_db(0, raw_bytes)
+        db = g.pir_setup_db(p, raw, layout=layout)
+    else:      # large databases: the same bytes generated on the device
+        raw = synth.raw_db_torch(0, raw_bytes, device=dev)
+        db = g.pir_setup_db(p, raw, layout=layout)
+        del raw
+        raw = None
+        torch.cuda.empty_cache()
 
-    # NBUF query sets on the device, so no step reads inputs the previous step left in L2
-    nbuf = 4
+    # query sets generated on the device; several rotate when they are small, so no
+    # step reads inputs the previous step left in L2
     qwords = B * D1 * 2 * L_PRIMES * n
     rwords = B * D2 * 2 * L_PRIMES * n
-    qbufs = []
-    for t in range(nbuf):
-        Q = synth.uniform_residues(1000 + 17 * rank + t, synth.STREAM_UNIFORM, B * D1 * 2, n, p.qs)
-        qbufs.append(torch.from_numpy(Q.reshape(-1).view(np.int32)).to(dev))
+    nbuf = 4 if qwords * 4 <= (4 << 30) else 1
+    qbufs = [synth.uniform_residues_torch(1000 + 17 * rank + t, synth.STREAM_UNIFORM, B * D1 * 2, n, p.qs,
+                                          device=dev).view(-1) for t in range(nbuf)]
     resp = torch.empty(rwords, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -342,24 +349,26 @@ def our_arm(args, wl):
     roofline["stage_ms_per_step"] = {name: stage_ms[i] / args.steps for i, name in enumerate(binding.STAGE_NAMES)}
 
     # end to end through the public API with pinned host buffers
-    qh = torch.empty(qwords, dtype=torch.int32, pin_memory=True)
-    rh = torch.empty(rwords, dtype=torch.int32, pin_memory=True)
-    qh.copy_(qbufs[0].cpu())
-    e2e_steps = max(3, min(args.steps, 50))
-    for _ in range(2):
-        g.pir_answer(db, qh, B, rh, stream=stream)
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        g.pir_answer(db, qh, B, rh, stream=stream)
-    t1 = time.perf_counter()
-    e2e_ms, e2e_q = reduce_timing((t1 - t0) * 1e3, float(B * e2e_steps), device=dev if world > 1 else None)
-    e2e = {"value": raw_bytes * e2e_q / (e2e_ms / 1e3) / 1e9, "unit": "GB/s",
-           "h2d_bytes_per_step": qwords * 4, "d2h_bytes_per_step": rwords * 4,
-           "ms_per_step": e2e_ms / e2e_steps}
+    e2e = None
+    if (qwords + rwords) * 4 <= (16 << 30):
+        qh = torch.empty(qwords, dtype=torch.int32, pin_memory=True)
+        rh = torch.empty(rwords, dtype=torch.int32, pin_memory=True)
+        qh.copy_(qbufs[0].cpu())
+        e2e_steps = max(3, min(args.steps, 50))
+        for _ in range(2):
+            g.pir_answer(db, qh, B, rh, stream=stream)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            g.pir_answer(db, qh, B, rh, stream=stream)
+        t1 = time.perf_counter()
+        e2e_ms, e2e_q = reduce_timing((t1 - t0) * 1e3, float(B * e2e_steps), device=dev if world > 1 else None)
+        e2e = {"value": raw_bytes * e2e_q / (e2e_ms / 1e3) / 1e9, "unit": "GB/s",
+               "h2d_bytes_per_step": qwords * 4, "d2h_bytes_per_step": rwords * 4,
+               "ms_per_step": e2e_ms / e2e_steps}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and raw is not None:
         nthreads = os.cpu_count() or 1
         ncols = max(1, min(D2, args.ref_cols))
         runner = OracleRunner(n, log2p, D1, D2, B, raw, ncols, nthreads)

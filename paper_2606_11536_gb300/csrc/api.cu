@@ -181,6 +181,21 @@ pir_status_t answer_device(pir_db *db, const uint32_t *queries, uint32_t B, uint
   // plain rows pad to 4 (128-bit loads); limb rows pad to 16 (m16 tensor tiles)
   const uint32_t Mp = limb ? (M + 15u) & ~15u : round4(M);
   uint32_t Kc = (o.k_chunk == 0 || o.k_chunk >= D1) ? D1 : o.k_chunk;
+  if (o.k_chunk == 0) {
+    // Stream-wise buffering (Sec. 4.4): when the scratch for all of D1 would not fit
+    // half of the free device memory, fold D1 in as many equal chunks as needed.
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+      const size_t per_row = (size_t)B * 2 * L * n * 4 + (size_t)L * n * (M + 15) * 4;  // qhat + slot layout
+      const size_t budget = free_b / 2;
+      if ((size_t)D1 * per_row > budget && per_row > 0) {
+        const size_t rows = budget / per_row;
+        const uint32_t chunks = (uint32_t)((D1 + (rows ? rows : 1) - 1) / (rows ? rows : 1));
+        Kc = (D1 + chunks - 1) / chunks;
+        if (Kc == 0) Kc = 1;
+      }
+    }
+  }
   if (limb) {
     // byte-limb class sums stay below 2^31 for at most 8192 rows; chunks of 32 rows
     if (Kc > 8192) Kc = 8192;

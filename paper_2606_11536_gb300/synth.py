@@ -185,3 +185,24 @@ def uniform_residues_torch(seed: int, stream: int, count: int, n: int, qs, devic
             res[sel] = r
         out[s0:s0 + c] = res.to(torch.int32)
     return out.view(count, L, n)
+
+
+def raw_db_torch(seed: int, nbytes: int, device=None, chunk_words: int = 1 << 27):
+    """raw_db(seed, nbytes) generated on `device` (uint8 tensor, the same bytes)."""
+    import torch
+    nwords = (nbytes + 7) // 8
+    out = torch.empty(nwords * 8, dtype=torch.uint8, device=device)
+    words = out.view(torch.int64)
+    for s0 in range(0, nwords, chunk_words):
+        c = min(chunk_words, nwords - s0)
+        words[s0:s0 + c] = u64_torch(seed, STREAM_DB, s0, c, device)
+    return out[:nbytes]
+
+
+def raw_db_slab(seed: int, start: int, nbytes: int) -> np.ndarray:
+    """Bytes [start, start + nbytes) of raw_db(seed, ...), regenerated on their own
+    (the stream is counter based); start must be a multiple of 8."""
+    assert start % 8 == 0
+    w0 = start // 8
+    nw = (nbytes + 7) // 8
+    return u64(seed, STREAM_DB, w0, nw).view(np.uint8)[:nbytes]

@@ -49,3 +49,10 @@ def test_distributions():
     assert counts.min() > 3500 and counts.max() < 4700
     idx = synth.query_indices(1, 1000, 512, 256)
     assert idx.min() >= 0 and idx.max() < 512 * 256
+
+
+def test_raw_db_on_device_and_slabs_match_host():
+    torch = pytest.importorskip("torch")
+    full = synth.raw_db(4, 5000)
+    assert np.array_equal(synth.raw_db_torch(4, 5000, chunk_words=100).numpy(), full)
+    assert np.array_equal(synth.raw_db_slab(4, 1024, 777), full[1024:1024 + 777])

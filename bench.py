@@ -316,11 +316,14 @@ def our_arm(args, wl):
     value = raw_bytes * total_queries / (max_ms / 1e3) / 1e9
     ms_per_step = max_ms / args.steps
 
-    # roofline of the dominant kernel: the modular GEMM stage (one kernel per launch)
+    # roofline of the dominant kernel: the modular GEMM stage.  With K-chunking a step
+    # runs it several times on slices of D1, so the work of one launch is the step's
+    # work divided by the launches per step.
     M, Mp = 2 * B, (2 * B + 3) // 4 * 4
     nslots = L_PRIMES * n
     gemm_launches = max(1, stage_launches[2])
-    gemm_ms = stage_ms[2] / gemm_launches
+    launches_per_step = gemm_launches / args.steps
+    gemm_ms = stage_ms[2] / gemm_launches * launches_per_step  # kernel time per step
     peaks, peak_kind = measured_peaks()
     src = os.path.join(ROOT, "paper_2606_11536_gb300", "csrc",
                        "gemm_plain.cu" if layout == g.PIR_LAYOUT_PLAIN else "gemm_limb.cu")
@@ -343,8 +346,9 @@ def our_arm(args, wl):
     roofline["peak_source"] = "%s (%s)" % (peak_kind, "MEASURED_PEAKS.json hbm_gbs" if roofline["bound"] == "hbm"
                                            else "152 SMs x 32 IMAD.WIDE/clk x sampled SM clock")
     roofline["kernel"] = kernel_tag
-    roofline["kernel_ms"] = gemm_ms
-    roofline["alg_bytes_per_launch"] = alg_bytes
+    roofline["kernel_ms"] = gemm_ms / launches_per_step
+    roofline["launches_per_step"] = launches_per_step
+    roofline["alg_bytes_per_launch"] = alg_bytes / launches_per_step
     roofline["traffic"] = profile_traffic(kernel_tag, wl, B, src)
     roofline["stage_ms_per_step"] = {name: stage_ms[i] / args.steps for i, name in enumerate(binding.STAGE_NAMES)}
 

@@ -228,7 +228,10 @@ __global__ void __launch_bounds__(256) k_gemm(const uint32_t *__restrict__ db, c
 #pragma unroll
         for (int x = 0; x < RM; ++x)
 #pragma unroll
-          for (int y = 0; y < 8; ++y) mac_wide(acc[x][y], av[x], bv[y]);
+          // the plain C++ form: here (operands from 128-bit shared loads, 32 independent
+          // accumulators) the compiler emits one 32x32+64 multiply-add per product and
+          // schedules them better than the opaque PTX helper (measured 7.1 vs 6.5 T/s)
+          for (int y = 0; y < 8; ++y) acc[x][y] += (uint64_t)av[x] * bv[y];
       }
 #pragma unroll
       for (int x = 0; x < RM; ++x)

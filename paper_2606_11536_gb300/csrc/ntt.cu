@@ -30,14 +30,10 @@ enum { SRC_SMEM = 0, SRC_U32 = 1, SRC_RAW = 2 };
 // slot-major query layout as (first row, this row) pairs.
 enum { DST_SMEM = 0, DST_GLOBAL = 1, DST_PAIR = 2 };
 
-// Pair destination: element k of rows (i, comp 0) and (i, comp 1) of prime j goes to
-// slots[((j*n + k) * Kc + i) * 2 + comp] (the plain slot layout with Mp = 2).
-struct SlotDst {
-  uint32_t *slots;
-  uint32_t *sm2;
-  uint32_t Kc, i, jn;
-  uint32_t second;  // 0: park the first row in sm2; 1: write (sm2, this row) pairs
-};
+// (DST_PAIR parks a row's canonical results in its shared buffer; the pair kernel
+// then writes element k of rows (i, comp 0) and (i, comp 1) of prime j to
+// slots[((j*n + k) * Kc + i) * 2 + comp], the plain slot layout with Mp = 2.)
+struct SlotDst {};
 
 struct RawSrc {
   const uint8_t *raw;  // little-endian bit stream of log2p-bit coefficients
@@ -121,12 +117,13 @@ template <int LOGN, int RB, int BLO, bool FWD, int SRC, int DST>
 __device__ __forceinline__ void ntt_pass(uint32_t *sm, const uint32_t *__restrict__ gin, const RawSrc &rs,
                                          uint64_t poly, uint32_t *__restrict__ gout, const uint32_t *__restrict__ w,
                                          const uint32_t *__restrict__ wsh, uint32_t q, uint32_t ninv,
-                                         uint32_t ninv_sh, const SlotDst *sd = nullptr) {
+                                         uint32_t ninv_sh, const SlotDst *sd = nullptr,
+                                         uint32_t tid = threadIdx.x) {
   constexpr int N = 1 << LOGN, T = N / 16, UNITS = N >> RB, PER = UNITS / T;
   static_assert(UNITS % T == 0, "pass plan");
 #pragma unroll
   for (int r = 0; r < PER; ++r) {
-    const uint32_t u = threadIdx.x + r * T;
+    const uint32_t u = tid + r * T;
     const uint32_t lo = u & ((1u << BLO) - 1), hi = u >> BLO;
     const uint32_t base = (hi << (BLO + RB)) | lo;
     uint32_t v[1 << RB];
@@ -166,18 +163,8 @@ __device__ __forceinline__ void ntt_pass(uint32_t *sm, const uint32_t *__restric
         v[e] = x;
       }
       if constexpr (DST == DST_PAIR) {
-        if (!sd->second) {
 #pragma unroll
-          for (int e = 0; e < (1 << RB); ++e) sd->sm2[padx(base | ((uint32_t)e << BLO))] = v[e];
-        } else {
-#pragma unroll
-          for (int e = 0; e < (1 << RB); ++e) {
-            const uint32_t k = base | ((uint32_t)e << BLO);
-            const uint32_t first = sd->sm2[padx(k)];
-            *reinterpret_cast<uint2 *>(sd->slots + (((uint64_t)sd->jn + k) * sd->Kc + sd->i) * 2) =
-                make_uint2(first, v[e]);
-          }
-        }
+        for (int e = 0; e < (1 << RB); ++e) sm[padx(base | ((uint32_t)e << BLO))] = v[e];
       } else if constexpr (BLO == 0 && RB >= 2) {
 #pragma unroll
         for (int e = 0; e < (1 << RB); e += 4)
@@ -196,7 +183,7 @@ __device__ __forceinline__ void ntt_pass(uint32_t *sm, const uint32_t *__restric
 }
 
 template <int LOGN, int SRC>
-__global__ void __launch_bounds__((1 << LOGN) / 16)
+__global__ void __launch_bounds__((1 << LOGN) / 16, 16384 >> LOGN)  // >= 1024 threads per SM
     k_ntt_fwd(const uint32_t *__restrict__ src, RowMap rm, RawSrc rs, uint32_t *__restrict__ dst, NttConst C,
               uint32_t L, uint64_t rows) {
   constexpr int N = 1 << LOGN;
@@ -234,7 +221,7 @@ __global__ void __launch_bounds__((1 << LOGN) / 16)
 }
 
 template <int LOGN>
-__global__ void __launch_bounds__((1 << LOGN) / 16)
+__global__ void __launch_bounds__((1 << LOGN) / 16, 16384 >> LOGN)  // >= 1024 threads per SM
     k_ntt_inv(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst, NttConst C, uint32_t L, uint64_t rows) {
   constexpr int N = 1 << LOGN;
   extern __shared__ uint32_t sm[];
@@ -270,56 +257,50 @@ __global__ void __launch_bounds__((1 << LOGN) / 16)
   }
 }
 
-// One row of the pair kernel below: the forward passes of row `gin`, the last
-// one into the pair destination.  Not inlined, so that the two rows of a block
-// run one after the other instead of being interleaved (which needs twice the
-// registers).
-template <int LOGN>
-__device__ __noinline__ void pair_row(uint32_t *sm, const uint32_t *__restrict__ gin, const uint32_t *__restrict__ w,
-                                      const uint32_t *__restrict__ wsh, uint32_t q, const SlotDst *sd) {
-  const RawSrc rs = {};
-  uint32_t *gout = nullptr;
-  if constexpr (LOGN == 11) {
-    ntt_pass<11, 4, 7, true, SRC_U32, DST_SMEM>(sm, gin, rs, 0, gout, w, wsh, q, 0, 0);
-    __syncthreads();
-    ntt_pass<11, 4, 3, true, SRC_SMEM, DST_SMEM>(sm, gin, rs, 0, gout, w, wsh, q, 0, 0);
-    __syncthreads();
-    ntt_pass<11, 3, 0, true, SRC_SMEM, DST_PAIR>(sm, gin, rs, 0, gout, w, wsh, q, 0, 0, sd);
-  } else if constexpr (LOGN == 12) {
-    ntt_pass<12, 4, 8, true, SRC_U32, DST_SMEM>(sm, gin, rs, 0, gout, w, wsh, q, 0, 0);
-    __syncthreads();
-    ntt_pass<12, 4, 4, true, SRC_SMEM, DST_SMEM>(sm, gin, rs, 0, gout, w, wsh, q, 0, 0);
-    __syncthreads();
-    ntt_pass<12, 4, 0, true, SRC_SMEM, DST_PAIR>(sm, gin, rs, 0, gout, w, wsh, q, 0, 0, sd);
-  } else {
-    ntt_pass<13, 4, 9, true, SRC_U32, DST_SMEM>(sm, gin, rs, 0, gout, w, wsh, q, 0, 0);
-    __syncthreads();
-    ntt_pass<13, 4, 5, true, SRC_SMEM, DST_SMEM>(sm, gin, rs, 0, gout, w, wsh, q, 0, 0);
-    __syncthreads();
-    ntt_pass<13, 4, 1, true, SRC_SMEM, DST_SMEM>(sm, gin, rs, 0, gout, w, wsh, q, 0, 0);
-    __syncthreads();
-    ntt_pass<13, 1, 0, true, SRC_SMEM, DST_PAIR>(sm, gin, rs, 0, gout, w, wsh, q, 0, 0, sd);
-  }
-}
-
 // Forward NTT of the a- and b-polynomial of one ciphertext (rows (i, comp 0) and
 // (i, comp 1) of prime j of a batch-1 query chunk), written straight into the
 // slot-major layout [L*n][Kc][2] that the batch-1 scan reads: the transpose of
-// Sec. 4.2 fused into the NTT's last pass.  Block = i * L + j.
+// Sec. 4.2 fused into the NTT.  Block = i * L + j, 2 x n/16 threads: each half
+// transforms one row in its own shared buffer, then all threads write the pairs.
 template <int LOGN>
-__global__ void __launch_bounds__((1 << LOGN) / 16)
+__global__ void __launch_bounds__((1 << LOGN) / 8)
     k_ntt_fwd_pair_slots(const uint32_t *__restrict__ src, uint64_t row0, NttConst C, uint32_t L, uint32_t Kc,
                          uint32_t *__restrict__ slots) {
-  constexpr int N = 1 << LOGN, PADN = N + N / 16;
+  constexpr int N = 1 << LOGN, PADN = N + N / 16, T = N / 16;
   extern __shared__ uint32_t sm[];
   const uint32_t i = blockIdx.x / L, j = blockIdx.x % L;
-  SlotDst sd = {slots, sm + PADN, Kc, i, j << LOGN, 0};
-  for (int comp = 0; comp < 2; ++comp) {
-    sd.second = comp;
-    pair_row<LOGN>(sm, src + (row0 + (uint64_t)i * 2 * L + (uint64_t)comp * L + j) * N, C.t[j].fwd, C.t[j].fwd_sh,
-                   C.q[j], &sd);
-    __syncthreads();  // the second row reuses sm; its last pass reads the first row's sm2
+  const uint32_t half = threadIdx.x / T, tid = threadIdx.x % T;
+  uint32_t *smh = sm + half * PADN;
+  const uint32_t q = C.q[j];
+  const uint32_t *w = C.t[j].fwd, *wsh = C.t[j].fwd_sh;
+  const uint32_t *gin = src + (row0 + (uint64_t)i * 2 * L + (uint64_t)half * L + j) * N;
+  const RawSrc rs = {};
+  uint32_t *gout = nullptr;
+  if constexpr (LOGN == 11) {
+    ntt_pass<11, 4, 7, true, SRC_U32, DST_SMEM>(smh, gin, rs, 0, gout, w, wsh, q, 0, 0, nullptr, tid);
+    __syncthreads();
+    ntt_pass<11, 4, 3, true, SRC_SMEM, DST_SMEM>(smh, gin, rs, 0, gout, w, wsh, q, 0, 0, nullptr, tid);
+    __syncthreads();
+    ntt_pass<11, 3, 0, true, SRC_SMEM, DST_PAIR>(smh, gin, rs, 0, gout, w, wsh, q, 0, 0, nullptr, tid);
+  } else if constexpr (LOGN == 12) {
+    ntt_pass<12, 4, 8, true, SRC_U32, DST_SMEM>(smh, gin, rs, 0, gout, w, wsh, q, 0, 0, nullptr, tid);
+    __syncthreads();
+    ntt_pass<12, 4, 4, true, SRC_SMEM, DST_SMEM>(smh, gin, rs, 0, gout, w, wsh, q, 0, 0, nullptr, tid);
+    __syncthreads();
+    ntt_pass<12, 4, 0, true, SRC_SMEM, DST_PAIR>(smh, gin, rs, 0, gout, w, wsh, q, 0, 0, nullptr, tid);
+  } else {
+    ntt_pass<13, 4, 9, true, SRC_U32, DST_SMEM>(smh, gin, rs, 0, gout, w, wsh, q, 0, 0, nullptr, tid);
+    __syncthreads();
+    ntt_pass<13, 4, 5, true, SRC_SMEM, DST_SMEM>(smh, gin, rs, 0, gout, w, wsh, q, 0, 0, nullptr, tid);
+    __syncthreads();
+    ntt_pass<13, 4, 1, true, SRC_SMEM, DST_SMEM>(smh, gin, rs, 0, gout, w, wsh, q, 0, 0, nullptr, tid);
+    __syncthreads();
+    ntt_pass<13, 1, 0, true, SRC_SMEM, DST_PAIR>(smh, gin, rs, 0, gout, w, wsh, q, 0, 0, nullptr, tid);
   }
+  __syncthreads();
+  uint32_t *dst = slots + ((uint64_t)j * N * Kc + i) * 2;
+  for (uint32_t k = threadIdx.x; k < (uint32_t)N; k += 2 * T)
+    *reinterpret_cast<uint2 *>(dst + (uint64_t)k * Kc * 2) = make_uint2(sm[padx(k)], sm[PADN + padx(k)]);
 }
 
 constexpr uint64_t kMaxGrid = 1u << 30;
@@ -391,7 +372,7 @@ cudaError_t launch_ntt_fwd_raw(const ParamCtx &c, const uint8_t *raw, int col_ma
 template <int LOGN>
 cudaError_t pair_launch(const ParamCtx &c, const uint32_t *src, uint64_t row0, uint32_t Kc, uint32_t *slots,
                         cudaStream_t s) {
-  const int T = (1 << LOGN) / 16;
+  const int T = (1 << LOGN) / 8;  // two rows in parallel
   const int smem = 2 * ((1 << LOGN) + (1 << LOGN) / 16) * (int)sizeof(uint32_t);
   cudaError_t e = cudaFuncSetAttribute(k_ntt_fwd_pair_slots<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;

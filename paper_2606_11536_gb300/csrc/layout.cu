@@ -112,6 +112,75 @@ __global__ void __launch_bounds__(256) k_slots_to_responses(const uint32_t *__re
   }
 }
 
+// 64 x 64 tiles with 16-byte global accesses on both sides (the batched path's
+// transposes).  Shared tile rows are padded to 65 words.
+constexpr int VT = 64;
+
+// qhat chunk -> qs[s][f], f = i*Mp + m, m = 2b + comp; needs Kc*Mp % 4 == 0.
+__global__ void __launch_bounds__(256) k_query_to_slots_v(const uint32_t *__restrict__ qhat, uint32_t B, uint32_t Kc,
+                                                          uint32_t L, uint32_t logn, uint32_t Mp,
+                                                          uint32_t *__restrict__ qs) {
+  __shared__ uint32_t tile[VT][VT + 1];  // [f][k]
+  const uint32_t n = 1u << logn;
+  const uint64_t F = (uint64_t)Kc * Mp;
+  const uint64_t f0 = (uint64_t)blockIdx.x * VT;
+  const uint32_t s0 = blockIdx.y * VT;
+  const uint32_t j = s0 >> logn, k0 = s0 & (n - 1);
+  const uint32_t t = threadIdx.x, lane16 = t & 15, row = t >> 4;  // 16 rows of 16 lanes
+  // read: row f, columns k0 + 4*lane16 .. +3
+  for (uint32_t r = row; r < VT; r += 16) {
+    const uint64_t f = f0 + r;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (f < F) {
+      const uint32_t i = (uint32_t)(f / Mp), m = (uint32_t)(f % Mp);
+      if (m < 2 * B) {
+        const uint64_t src = ((((uint64_t)(m >> 1) * Kc + i) * 2 + (m & 1)) * L + j) * n + k0 + 4 * lane16;
+        v = *reinterpret_cast<const uint4 *>(qhat + src);
+      }
+    }
+    tile[r][4 * lane16] = v.x, tile[r][4 * lane16 + 1] = v.y, tile[r][4 * lane16 + 2] = v.z,
+    tile[r][4 * lane16 + 3] = v.w;
+  }
+  __syncthreads();
+  // write: slot s0 + kk, f0 + 4*lane16 .. +3
+  for (uint32_t kk = row; kk < VT; kk += 16) {
+    const uint64_t f = f0 + 4 * lane16;
+    if (f >= F) continue;
+    const uint4 v = make_uint4(tile[4 * lane16][kk], tile[4 * lane16 + 1][kk], tile[4 * lane16 + 2][kk],
+                               tile[4 * lane16 + 3][kk]);
+    *reinterpret_cast<uint4 *>(qs + (uint64_t)(s0 + kk) * F + f) = v;
+  }
+}
+
+// out[s][f], f = m*D2 + c -> resp[b][c][comp][j][k]; needs M*D2 % 4 == 0.
+__global__ void __launch_bounds__(256) k_slots_to_responses_v(const uint32_t *__restrict__ out, uint32_t M,
+                                                              uint32_t D2, uint32_t L, uint32_t logn,
+                                                              uint32_t *__restrict__ resp) {
+  __shared__ uint32_t tile[VT][VT + 1];  // [k][f]
+  const uint32_t n = 1u << logn;
+  const uint64_t F = (uint64_t)M * D2;
+  const uint64_t f0 = (uint64_t)blockIdx.x * VT;
+  const uint32_t s0 = blockIdx.y * VT;
+  const uint32_t j = s0 >> logn, k0 = s0 & (n - 1);
+  const uint32_t t = threadIdx.x, lane16 = t & 15, row = t >> 4;
+  for (uint32_t kk = row; kk < VT; kk += 16) {
+    const uint64_t f = f0 + 4 * lane16;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (f < F) v = *reinterpret_cast<const uint4 *>(out + (uint64_t)(s0 + kk) * F + f);
+    tile[kk][4 * lane16] = v.x, tile[kk][4 * lane16 + 1] = v.y, tile[kk][4 * lane16 + 2] = v.z,
+    tile[kk][4 * lane16 + 3] = v.w;
+  }
+  __syncthreads();
+  for (uint32_t r = row; r < VT; r += 16) {
+    const uint64_t f = f0 + r;
+    if (f >= F) continue;
+    const uint32_t m = (uint32_t)(f / D2), c = (uint32_t)(f % D2);
+    const uint64_t dst = ((((uint64_t)(m >> 1) * D2 + c) * 2 + (m & 1)) * L + j) * n + k0 + 4 * lane16;
+    *reinterpret_cast<uint4 *>(resp + dst) = make_uint4(tile[4 * lane16][r], tile[4 * lane16 + 1][r],
+                                                        tile[4 * lane16 + 2][r], tile[4 * lane16 + 3][r]);
+  }
+}
+
 // NTT-form DB polys [np][L][n] -> resident layout.  Plain: polys are row-major ids
 // poly0 + p = i*D2 + c.  Tile = 32 polys x 32 slots of one prime.
 __global__ void __launch_bounds__(256) k_db_scatter_plain(const uint32_t *__restrict__ polys, uint64_t poly0,
@@ -188,6 +257,11 @@ __global__ void k_db_read_poly(const void *__restrict__ res, int layout, uint64_
 cudaError_t launch_query_to_slots(const ParamCtx &c, const uint32_t *qhat, uint32_t B, uint32_t Kc, uint32_t Mp,
                                   uint32_t *qs, cudaStream_t s) {
   const uint64_t F = (uint64_t)Kc * Mp;
+  if (F % 4 == 0) {
+    dim3 grid((unsigned)((F + VT - 1) / VT), (c.p.L << c.logn) / VT);
+    k_query_to_slots_v<<<grid, 256, 0, s>>>(qhat, B, Kc, c.p.L, c.logn, Mp, qs);
+    return cudaGetLastError();
+  }
   dim3 grid((unsigned)((F + TF - 1) / TF), (c.p.L << c.logn) / TK);
   k_query_to_slots<<<grid, 256, 0, s>>>(qhat, B, Kc, c.p.L, c.logn, Mp, qs);
   return cudaGetLastError();
@@ -203,6 +277,11 @@ cudaError_t launch_query_to_limbs(const ParamCtx &c, const uint32_t *qhat, uint3
 cudaError_t launch_slots_to_responses(const ParamCtx &c, const uint32_t *out, uint32_t B, uint32_t D2,
                                       uint32_t *resp, cudaStream_t s) {
   const uint64_t F = (uint64_t)2 * B * D2;
+  if (F % 4 == 0) {
+    dim3 grid((unsigned)((F + VT - 1) / VT), (c.p.L << c.logn) / VT);
+    k_slots_to_responses_v<<<grid, 256, 0, s>>>(out, 2 * B, D2, c.p.L, c.logn, resp);
+    return cudaGetLastError();
+  }
   dim3 grid((unsigned)((F + TF - 1) / TF), (c.p.L << c.logn) / TK);
   k_slots_to_responses<<<grid, 256, 0, s>>>(out, 2 * B, D2, c.p.L, c.logn, resp);
   return cudaGetLastError();

@@ -76,6 +76,9 @@ def lib():
             "orc_bfv_noise": (None, [PP, I8P, U32P, U32P, I64P]),
             "orc_bfv_phase": (None, [PP, I8P, U32P, U64P]),
             "orc_freivalds": (C.c_longlong, [PP, U8P, U32P, C.c_uint32, U32P, U32P, C.c_int]),
+            "orc_modswitch": (None, [PP, U32P, C.c_uint64, U32P]),
+            "orc_bfv_phase_q0": (None, [PP, I8P, U32P, U64P]),
+            "orc_bfv_decrypt_q0": (None, [PP, I8P, U32P, U32P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -265,6 +268,32 @@ def bfv_phase(P: OrcParams, s, ct) -> list:
     out = np.empty(2 * P.n, dtype=np.uint64)
     lib().orc_bfv_phase(C.byref(P), np.ascontiguousarray(s, dtype=np.int8), _u32(ct).reshape(-1), out)
     return [int(out[2 * t]) | (int(out[2 * t + 1]) << 64) for t in range(P.n)]
+
+
+def modswitch(P: OrcParams, polys) -> np.ndarray:
+    """Modulus switching to q_0: polys [..., L, n] coefficient form -> [..., n],
+    each coefficient round(x q_0 / q) mod q_0."""
+    a = _u32(polys)
+    lead = a.shape[:-2]
+    assert a.shape[-2:] == (P.L, P.n)
+    count = int(np.prod(lead)) if lead else 1
+    out = np.empty(lead + (P.n,), dtype=np.uint32)
+    lib().orc_modswitch(C.byref(P), a.reshape(-1), count, out.reshape(-1))
+    return out
+
+
+def bfv_phase_q0(P: OrcParams, s, ct) -> np.ndarray:
+    """Phase a*s + b mod q_0 of a switched ciphertext [2][n]."""
+    out = np.empty(P.n, dtype=np.uint64)
+    lib().orc_bfv_phase_q0(C.byref(P), np.ascontiguousarray(s, dtype=np.int8), _u32(ct).reshape(-1), out)
+    return out
+
+
+def bfv_decrypt_q0(P: OrcParams, s, ct) -> np.ndarray:
+    """Decryption of a switched ciphertext [2][n] over q_0."""
+    m = np.empty(P.n, dtype=np.uint32)
+    lib().orc_bfv_decrypt_q0(C.byref(P), np.ascontiguousarray(s, dtype=np.int8), _u32(ct).reshape(-1), m)
+    return m
 
 
 def encrypt_query(P: OrcParams, s, a, e, i_star: int) -> np.ndarray:

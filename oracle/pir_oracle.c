@@ -14,6 +14,8 @@
  *   - polynomial ring R_q = Z_q[X]/(X^n + 1), RNS rows per prime      (Sec. 2.3, App. A.2)
  *   - negacyclic NTT / inverse NTT, one row per prime                 (Sec. 2.3)
  *   - RLWE encryption / decryption with Delta = floor(q/p)            (App. A.2)
+ *   - modulus switching q -> q_0: round(x q_0 / q) mod q_0, and decryption over
+ *     the single prime q_0 afterwards                                 (App. A, Sec. 4.3)
  *   - first-dimension folding: out_c = sum_i DB[i][c] * ct_i in R_q^2 (Sec. 3.2, Sec. 4 "INT32
  *     modular GEMM", Sec. 4.2): in the NTT domain, for every prime q_j and slot k,
  *     out[b][c][k] = sum_i DB[i][c][k] * Q[b][i][k]  (mod q_j).
@@ -24,12 +26,16 @@
  *   - NTT(a)[k] = sum_t a_t psi^((2 brv(k) + 1) t)  (bit-reversed evaluation order);
  *   - a raw DB is a little-endian bit stream of log2(p)-bit coefficients, poly after
  *     poly, poly (i, c) at position i*D2 + c;
- *   - each query ciphertext contributes its a- and b-polynomial as two GEMM rows.
+ *   - each query ciphertext contributes its a- and b-polynomial as two GEMM rows;
+ *   - modulus switching keeps q_0, the largest prime (#RNS = 1, about 2^30), and
+ *     rounds to nearest.
  *
  * Parity: pinned.  The tests check this file against primality by an independent
  * library, the defining congruences, the NTT evaluated by its definition, schoolbook
  * negacyclic multiplication, the convolution theorem, and the BFV decryption
- * invariant (decrypting the answer returns exactly the requested record).
+ * invariant (decrypting the answer returns exactly the requested record); modulus
+ * switching against values built as t Q' + r, the rounding-error bound of App. A
+ * and decryption after the switch.
  */
 #include <pthread.h>
 #include <stdint.h>
@@ -702,6 +708,71 @@ void orc_bfv_phase(const orc_params *P, const int8_t *s, const u32 *ct, u64 *phi
   for (u32 t = 0; t < P->n; t++) {
     phi_lo_hi[2 * t] = (u64)phi[t];
     phi_lo_hi[2 * t + 1] = (u64)(phi[t] >> 64);
+  }
+  free(phi);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Modulus switching down to the single prime q_0                            */
+/* ------------------------------------------------------------------------- */
+
+/* The integer x in [0, q) with x = res[j * stride] (mod q_j) for every j: Chinese
+ * remaindering, built up one prime at a time (x stays below q_0 ... q_j). */
+static u128 crt_lift(const orc_params *P, const u32 *res, u64 stride) {
+  u128 x = res[0], M = P->q[0];
+  for (u32 j = 1; j < P->L; j++) {
+    const u64 q = P->q[j];
+    const u64 h = mulmod(submod(res[(u64)j * stride], (u64)(x % q), q), invmod_prime((u64)(M % q), q), q);
+    x += (u128)h * M;
+    M *= q;
+  }
+  return x;
+}
+
+/* Modulus switching of RLWE ciphertext polynomials (App. A, "Error analysis of
+ * RLWE modulus switching"; Sec. 4.3 fuses it with the inverse NTT): every
+ * coefficient x in [0, q) goes to
+ *     y = round(x * q_0 / q) mod q_0,
+ * so the ciphertext modulus drops from q = q_0 q_1 ... q_{L-1} to the single prime
+ * q_0 (#RNS = 1).  With Q' = q / q_0 = q_1 ... q_{L-1}, x q_0 / q = x / Q', and
+ * round(x / Q') = floor((2x + Q') / (2Q')): Q' is odd, so no value sits exactly
+ * half way.  polys [count][L][n] in coefficient form; out [count][n]. */
+void orc_modswitch(const orc_params *P, const u32 *polys, u64 count, u32 *out) {
+  const u32 n = P->n, L = P->L;
+  u128 Qd = 1;
+  for (u32 j = 1; j < L; j++) Qd *= P->q[j];
+  for (u64 c = 0; c < count; c++)
+    for (u32 t = 0; t < n; t++) {
+      const u128 x = crt_lift(P, polys + c * L * n + t, n);
+      const u128 r = (2 * x + Qd) / (2 * Qd);
+      out[c * n + t] = (u32)(r % P->q[0]);
+    }
+}
+
+/* Phase phi = a*s + b (mod q_0) of a ciphertext [2][n] over the single prime q_0
+ * (what modulus switching leaves), each coefficient in [0, q_0). */
+void orc_bfv_phase_q0(const orc_params *P, const int8_t *s, const u32 *ct, u64 *phi) {
+  const u32 n = P->n;
+  const u64 q = P->q[0];
+  u32 *sj = (u32 *)calloc(n, sizeof(u32));
+  u32 *as = (u32 *)malloc(sizeof(u32) * n);
+  for (u32 t = 0; t < n; t++) sj[t] = (u32)((s[t] + (i128)q) % q);
+  ring_mul(ct, sj, as, n, q, P->psi[0]);
+  for (u32 t = 0; t < n; t++) phi[t] = addmod(as[t], ct[n + t], q);
+  free(sj);
+  free(as);
+}
+
+/* Decrypt a ciphertext [2][n] over q_0: m = round(p * phi / q_0) mod p (App. A.2,
+ * the scale after switching being about q_0 / p). */
+void orc_bfv_decrypt_q0(const orc_params *P, const int8_t *s, const u32 *ct, u32 *m_out) {
+  const u32 n = P->n;
+  const u64 q = P->q[0], pmask = (1ull << P->log2p) - 1;
+  u64 *phi = (u64 *)malloc(sizeof(u64) * n);
+  orc_bfv_phase_q0(P, s, ct, phi);
+  for (u32 t = 0; t < n; t++) {
+    const u128 num = ((u128)phi[t] << (P->log2p + 1)) + q; /* 2 p phi + q_0 */
+    m_out[t] = (u32)((u64)(num / (2 * (u128)q)) & pmask);
   }
   free(phi);
 }

@@ -179,8 +179,9 @@ class OracleRunner:
     polynomials are prepared once beforehand (as the server's DB is).  A step's
     time is scaled by columns to the full answer."""
 
-    def __init__(self, n, log2p, D1, D2, B, raw, ncols, nthreads):
+    def __init__(self, n, log2p, D1, D2, B, raw, ncols, nthreads, modswitch=False):
         from oracle import oracle as O
+        self.modswitch = modswitch
         self.O = O
         self.P = O.make_params(n, log2p, D1, D2, L_PRIMES)
         self.n, self.D1, self.D2, self.B = n, D1, D2, B
@@ -196,14 +197,16 @@ class OracleRunner:
         t0 = time.perf_counter()
         qhat = self.O.ntt_fwd_rns(self.P, Q, self.nthreads)
         t1 = time.perf_counter()
-        self.O.answer_encoded(self.P, self.dbhat, qhat, self.nthreads)
+        R = self.O.answer_encoded(self.P, self.dbhat, qhat, self.nthreads)
+        if self.modswitch:
+            self.O.modswitch(self.P, R)
         t2 = time.perf_counter()
         return (t1 - t0) + (t2 - t1) * self.D2 / self.ncols
 
     def describe(self):
-        return ("oracle online answer, batch %d: query NTT of the whole batch timed, fold + inverse NTT timed on %d "
+        return ("oracle online answer, batch %d: query NTT of the whole batch timed, fold + inverse NTT%s timed on %d "
                 "of %d columns and scaled by columns; those DB columns NTT-encoded beforehand"
-                % (self.B, self.ncols, self.D2))
+                % (self.B, " + modulus switching" if self.modswitch else "", self.ncols, self.D2))
 
 
 def reference_arm(args, wl):
@@ -217,7 +220,7 @@ def reference_arm(args, wl):
     raw = synth.raw_db(0, raw_bytes)
     nthreads = os.cpu_count() or 1
     ncols = max(1, min(D2, args.ref_cols))
-    runner = OracleRunner(n, log2p, D1, D2, B, raw, ncols, nthreads)
+    runner = OracleRunner(n, log2p, D1, D2, B, raw, ncols, nthreads, modswitch=args.modswitch)
     times = []
     for step in range(args.warmup + args.steps):
         full_s = runner.step(100 + step)
@@ -231,7 +234,7 @@ def reference_arm(args, wl):
         "warmup": args.warmup, "ms_per_step": mean_s * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": wl, "description": desc, "batch": B, "n": n, "log2p": log2p, "D1": D1, "D2": D2,
-                   "L": L_PRIMES},
+                   "L": L_PRIMES, "modswitch": bool(args.modswitch)},
         "cpu_baseline": {"value": value, "unit": "GB/s", "cores": nthreads, "kind": "oracle", "sample": sample_desc},
         "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -273,7 +276,8 @@ def our_arm(args, wl):
     # query sets generated on the device; several rotate when they are small, so no
     # step reads inputs the previous step left in L2
     qwords = B * D1 * 2 * L_PRIMES * n
-    rwords = B * D2 * 2 * L_PRIMES * n
+    msw = g.PIR_ANSWER_MODSWITCH if args.modswitch else 0
+    rwords = B * D2 * 2 * (1 if msw else L_PRIMES) * n  # switched responses keep one prime
     nbuf = 4 if qwords * 4 <= (4 << 30) else 1
     qbufs = [synth.uniform_residues_torch(1000 + 17 * rank + t, synth.STREAM_UNIFORM, B * D1 * 2, n, p.qs,
                                           device=dev).view(-1) for t in range(nbuf)]
@@ -281,7 +285,7 @@ def our_arm(args, wl):
     stream = torch.cuda.current_stream()
 
     def step(t, flags=0):
-        g.pir_answer_ex(db, qbufs[t % nbuf], B, resp, stream=stream, flags=flags, tile=args.tile,
+        g.pir_answer_ex(db, qbufs[t % nbuf], B, resp, stream=stream, flags=flags | msw, tile=args.tile,
                         k_chunk=args.k_chunk)
 
     for t in range(args.warmup):
@@ -360,11 +364,11 @@ def our_arm(args, wl):
         qh.copy_(qbufs[0].cpu())
         e2e_steps = max(3, min(args.steps, 50))
         for _ in range(2):
-            g.pir_answer(db, qh, B, rh, stream=stream)
+            g.pir_answer_ex(db, qh, B, rh, stream=stream, flags=msw)
         barrier()
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
-            g.pir_answer(db, qh, B, rh, stream=stream)
+            g.pir_answer_ex(db, qh, B, rh, stream=stream, flags=msw)
         t1 = time.perf_counter()
         e2e_ms, e2e_q = reduce_timing((t1 - t0) * 1e3, float(B * e2e_steps), device=dev if world > 1 else None)
         e2e = {"value": raw_bytes * e2e_q / (e2e_ms / 1e3) / 1e9, "unit": "GB/s",
@@ -375,7 +379,7 @@ def our_arm(args, wl):
     if rank == 0 and world == 1 and not args.no_cpu_baseline and raw is not None:
         nthreads = os.cpu_count() or 1
         ncols = max(1, min(D2, args.ref_cols))
-        runner = OracleRunner(n, log2p, D1, D2, B, raw, ncols, nthreads)
+        runner = OracleRunner(n, log2p, D1, D2, B, raw, ncols, nthreads, modswitch=args.modswitch)
         runner.step(7)  # warm
         full_s = min(runner.step(8), runner.step(9))
         cpu = {"value": raw_bytes * B / full_s / 1e9, "unit": "GB/s", "cores": nthreads, "kind": "oracle",
@@ -388,7 +392,8 @@ def our_arm(args, wl):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": wl, "description": desc, "batch": B, "n": n, "log2p": log2p, "D1": D1, "D2": D2,
-                       "L": L_PRIMES, "layout": args.layout, "parallelism": "replicas x%d" % world,
+                       "L": L_PRIMES, "layout": args.layout, "modswitch": bool(msw),
+                       "parallelism": "replicas x%d" % world,
                        "l2": "inputs larger than L2: the %.1f GiB NTT-form DB is streamed every step; %d query "
                              "buffers rotate" % (binding.resident_db_bytes(p) / 2 ** 30, nbuf)},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
@@ -516,6 +521,8 @@ def main(argv=None):
     ap.add_argument("--k-chunk", type=int, default=0, help="fold D1 in chunks of this many ciphertexts")
     ap.add_argument("--ref-cols", type=int, default=64, help="columns in the oracle's timed sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--modswitch", action="store_true",
+                    help="switch the responses to the single prime q_0 inside the inverse NTT")
     ap.add_argument("--ntt-sweep", action="store_true", help="time the standalone NTT sweep instead")
     ap.add_argument("--serving", action="store_true", help="run the serving benchmark instead")
     ap.add_argument("--serving-rates", type=float, nargs="+", default=[100, 300, 1000, 3000, 5000])

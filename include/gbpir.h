@@ -117,8 +117,8 @@ typedef struct {
                         ciphertexts (bounds the scratch memory to one chunk)        */
   uint32_t tile;     /* 0 = built-in choice; else a GEMM tile id (pir_gemm_tiles)  */
   uint32_t flags;    /* PIR_ANSWER_STAGE_TIMES: record CUDA events around each stage on
-                        `stream`, read with pir_stage_times; PIR_ANSWER_TEST_STALL:
-                        see below.  Other bits must be 0. */
+                        `stream`, read with pir_stage_times; PIR_ANSWER_TEST_STALL,
+                        PIR_ANSWER_MODSWITCH: see below.  Other bits must be 0. */
 } pir_answer_opts_t;
 
 #define PIR_ANSWER_STAGE_TIMES 1u
@@ -127,6 +127,11 @@ typedef struct {
  * error word and return (the answer is then invalid; pir_check_device reports
  * PIR_ERR_TIMEOUT).  Needs a shape the TMA scan holds (2B <= 8, D2 <= 512). */
 #define PIR_ANSWER_TEST_STALL 2u
+/* Modulus switching of the responses to the single prime q_0, fused into the
+ * inverse NTT (Sec. 4.3; App. A, error analysis of RLWE modulus switching): the
+ * responses are then [B][D2][2][n] uint32 over q_0, coefficient form, canonical
+ * (half the bytes at L = 2), as ntt_inv_modswitch below computes them. */
+#define PIR_ANSWER_MODSWITCH 4u
 
 /* Stages of one answer, in order: forward NTT of the queries, query transpose to
  * the slot-major layout, modular GEMM (with its reduction epilogue), result
@@ -140,8 +145,9 @@ pir_status_t pir_answer_ex(pir_db_t db, const uint32_t *queries, uint32_t B, uin
  * allocation and release as graph nodes) and replayed with one launch: the
  * batched, graph-captured launch the scan is served with.  The graph is bound to
  * the device buffers given here (queries [B][D1][2][L][n], responses
- * [B][D2][2][L][n]); every pir_graph_launch answers whatever the query buffer
- * holds at that point in `stream`'s order.  opts as for pir_answer_ex, except that
+ * [B][D2][2][L][n], or [B][D2][2][n] with PIR_ANSWER_MODSWITCH); every
+ * pir_graph_launch answers whatever the query buffer holds at that point in
+ * `stream`'s order.  opts as for pir_answer_ex, except that
  * PIR_ANSWER_STAGE_TIMES and PIR_ANSWER_TEST_STALL are refused (PIR_ERR_ARG).
  * The caller keeps ownership of the buffers and must keep them (and the DB) alive
  * until pir_graph_destroy.  Errors: PIR_ERR_HANDLE, PIR_ERR_ARG, PIR_ERR_CUDA. */
@@ -187,6 +193,19 @@ pir_status_t pir_answer_noalloc(pir_db_t db, const uint32_t *queries, uint32_t B
  * Errors: PIR_ERR_ARG (NULL, misaligned, invalid params), PIR_ERR_CUDA. */
 pir_status_t ntt_fwd(const pir_params_t *params, uint32_t *polys, size_t count, void *stream);
 pir_status_t ntt_inv(const pir_params_t *params, uint32_t *polys, size_t count, void *stream);
+
+/* Inverse NTT with modulus switching fused into it (Sec. 4.3 fuses the modulus
+ * reduction into the inverse NTT; App. A, "Error analysis of RLWE modulus
+ * switching", defines the switch from q = q_0 ... q_{L-1} to one prime).
+ *   in:  [count][L][n] uint32, NTT form over q, canonical; device memory, read only.
+ *   out: [count][n] uint32, coefficient form over q_0 (the first prime of params),
+ *        canonical; device memory, written.  out[c][t] = round(x q_0 / q) mod q_0,
+ *        x in [0, q) being the CRT lift of coefficient t of ntt_inv(in[c]).
+ * Both buffers 16-byte aligned and disjoint; asynchronous on stream.  With L = 1 the
+ * result equals ntt_inv.  Errors: PIR_ERR_ARG (NULL, misaligned or overlapping
+ * buffers, invalid params), PIR_ERR_CUDA. */
+pir_status_t ntt_inv_modswitch(const pir_params_t *params, const uint32_t *in, size_t count, uint32_t *out,
+                               void *stream);
 
 /* Release a DB handle and its device memory (synchronizes the device first). */
 pir_status_t pir_free_db(pir_db_t db);

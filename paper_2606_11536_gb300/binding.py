@@ -76,6 +76,7 @@ def lib():
             "pir_answer_ex": (i32, [vp, vp, u32, vp, i32, vp, C.POINTER(pir_answer_opts_t)]),
             "ntt_fwd": (i32, [P, vp, sz, vp]),
             "ntt_inv": (i32, [P, vp, sz, vp]),
+            "ntt_inv_modswitch": (i32, [P, vp, sz, vp, vp]),
             "pir_free_db": (i32, [vp]),
             "pir_db_bytes": (i32, [vp, C.POINTER(sz)]),
             "pir_db_info": (i32, [vp, P, C.POINTER(i32)]),
@@ -211,6 +212,18 @@ def ntt_inv(params: pir_params_t, polys, count: int | None = None, stream=None):
     return polys
 
 
+def ntt_inv_modswitch(params: pir_params_t, polys, out, count: int | None = None, stream=None):
+    """Inverse NTT of polys [count][L][n] (NTT form) with modulus switching to q_0
+    fused in; writes out [count][n] over q_0."""
+    ip, idev, nbytes = _ptr(polys)
+    op, odev, _ = _ptr(out)
+    if not (idev and odev):
+        raise ValueError("ntt_inv_modswitch works on device memory")
+    cnt = nbytes // (4 * params.L * params.n) if count is None else count
+    _check(lib().ntt_inv_modswitch(C.byref(params), ip, cnt, op, _stream_ptr(stream)), "ntt_inv_modswitch")
+    return out
+
+
 def pir_free_db(db: Db):
     _check(lib().pir_free_db(C.c_void_p(db.handle)), "pir_free_db")
     db.handle = None
@@ -246,6 +259,7 @@ def pir_gemm_tiles(layout: int) -> int:
 
 PIR_ANSWER_STAGE_TIMES = 1
 PIR_ANSWER_TEST_STALL = 2
+PIR_ANSWER_MODSWITCH = 4
 PIR_STAGES = 5
 STAGE_NAMES = ("query_ntt", "query_transpose", "gemm", "result_transpose", "intt")
 
@@ -267,12 +281,12 @@ class Graph:
         self._keep = (queries, responses)  # the graph reads / writes these buffers
 
 
-def pir_graph_create(db: Db, queries, B: int, responses, k_chunk: int = 0, tile: int = 0) -> Graph:
+def pir_graph_create(db: Db, queries, B: int, responses, k_chunk: int = 0, tile: int = 0, flags: int = 0) -> Graph:
     qp, qdev, _ = _ptr(queries)
     rp, rdev, _ = _ptr(responses)
     if not (qdev and rdev):
         raise ValueError("a graph binds device buffers")
-    o = pir_answer_opts_t(k_chunk, tile, 0)
+    o = pir_answer_opts_t(k_chunk, tile, flags)
     h = C.c_void_p()
     _check(lib().pir_graph_create(C.c_void_p(db.handle), qp, B, rp, C.byref(o), C.byref(h)), "pir_graph_create")
     return Graph(h.value, db, queries, responses)
@@ -327,5 +341,6 @@ def query_bytes(p, B: int) -> int:
     return B * p.D1 * ct_bytes(p.n, p.L)
 
 
-def response_bytes(p, B: int) -> int:
-    return B * p.D2 * ct_bytes(p.n, p.L)
+def response_bytes(p, B: int, modswitch: bool = False) -> int:
+    """Response buffer bytes; with modulus switching the responses keep one prime."""
+    return B * p.D2 * ct_bytes(p.n, 1 if modswitch else p.L)

@@ -204,7 +204,11 @@ pir_status_t answer_device(pir_db *db, const uint32_t *queries, uint32_t B, uint
   }
   const uint64_t nslots = (uint64_t)L * n;
   const uint32_t tile_count = db->layout == PIR_LAYOUT_PLAIN ? gemm_plain_tiles() : gemm_limb_tiles();
-  if (o.tile > tile_count || (o.flags & ~(PIR_ANSWER_STAGE_TIMES | PIR_ANSWER_TEST_STALL)) != 0) return PIR_ERR_ARG;
+  if (o.tile > tile_count || (o.flags & ~(PIR_ANSWER_STAGE_TIMES | PIR_ANSWER_TEST_STALL | PIR_ANSWER_MODSWITCH)) != 0)
+    return PIR_ERR_ARG;
+  // With modulus switching the inverse NTT reads the full-modulus responses from
+  // scratch and writes [B][D2][2][n] over q_0 to `responses`.
+  const bool msw = (o.flags & PIR_ANSWER_MODSWITCH) != 0;
   const int stall = (o.flags & PIR_ANSWER_TEST_STALL) != 0;
   if (stall && (db->layout != PIR_LAYOUT_PLAIN || !scan_tma_supports(2 * B, D2) || (o.tile != 0 && o.tile != 7)))
     return PIR_ERR_ARG;
@@ -214,18 +218,32 @@ pir_status_t answer_device(pir_db *db, const uint32_t *queries, uint32_t B, uint
   const size_t qs_bytes = limb ? nslots * 4 * Mp * Kc : nslots * Kc * Mp * 4;
   const size_t out_bytes = nslots * M * D2 * 4;
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
-  Scratch scratch(s);
-  CK(scratch.alloc(up(qhat_bytes) + up(qs_bytes) + up(out_bytes)));
-  char *base = static_cast<char *>(scratch.ptr);
-  uint32_t *qhat = reinterpret_cast<uint32_t *>(base);
-  void *qs = base + up(qhat_bytes);
-  uint32_t *out = reinterpret_cast<uint32_t *>(base + up(qhat_bytes) + up(qs_bytes));
-
-  StageTimer tm((o.flags & PIR_ANSWER_STAGE_TIMES) != 0, s);
   // Batch 1 on the TMA scan: the forward NTT writes the slot layout itself (pairs of
   // a/b residues, Mp = 2) and the scan writes the response layout itself, so neither
   // transpose runs.
   const bool fused = !limb && B == 1 && (o.tile == 0 || o.tile == 7) && scan_tma_supports(M, D2) && Kc % 2 == 0;
+  // full-modulus responses before switching: the unused result area on the fused
+  // path (the same size at B = 1), an area of their own otherwise
+  StageTimer tm((o.flags & PIR_ANSWER_STAGE_TIMES) != 0, s);
+  const size_t full_bytes = (msw && !fused) ? (size_t)B * D2 * 2 * L * n * 4 : 0;
+  Scratch scratch(s);
+  CK(scratch.alloc(up(qhat_bytes) + up(qs_bytes) + up(out_bytes) + up(full_bytes)));
+  char *base = static_cast<char *>(scratch.ptr);
+  uint32_t *qhat = reinterpret_cast<uint32_t *>(base);
+  void *qs = base + up(qhat_bytes);
+  uint32_t *out = reinterpret_cast<uint32_t *>(base + up(qhat_bytes) + up(qs_bytes));
+  uint32_t *full = !msw ? responses
+                        : fused ? out : reinterpret_cast<uint32_t *>(base + up(qhat_bytes) + up(qs_bytes) + up(out_bytes));
+  auto finish = [&]() -> pir_status_t {  // inverse NTT (with the switch when asked)
+    tm.begin();
+    if (msw)
+      CK(launch_ntt_inv_switch(c, full, responses, (uint64_t)B * D2 * 2, s));
+    else
+      CK(launch_ntt_inv(c, responses, responses, (uint64_t)B * D2 * 2 * L, s));
+    tm.end(4, 1);
+    return PIR_OK;
+  };
+
   if (fused) {
     uint32_t *qs2 = reinterpret_cast<uint32_t *>(base);  // [L*n][Kc][2] fits the qhat area
     for (uint32_t i0 = 0; i0 < D1; i0 += Kc) {
@@ -234,14 +252,11 @@ pir_status_t answer_device(pir_db *db, const uint32_t *queries, uint32_t B, uint
       CK(launch_ntt_fwd_pair_slots(c, queries, D1, i0, kc, qs2, s));
       tm.end(0, 1);
       tm.begin();
-      CK(launch_scan_tma(c, static_cast<const uint32_t *>(db->resident), D1, D2, qs2, M, 2, i0, kc, responses, i0 > 0,
+      CK(launch_scan_tma(c, static_cast<const uint32_t *>(db->resident), D1, D2, qs2, M, 2, i0, kc, full, i0 > 0,
                          stall, 1, s));
       tm.end(2, 1);
     }
-    tm.begin();
-    CK(launch_ntt_inv(c, responses, responses, (uint64_t)B * D2 * 2 * L, s));
-    tm.end(4, 1);
-    return PIR_OK;
+    return finish();
   }
   for (uint32_t i0 = 0; i0 < D1; i0 += Kc) {
     const uint32_t kc = D1 - i0 < Kc ? D1 - i0 : Kc;
@@ -270,12 +285,9 @@ pir_status_t answer_device(pir_db *db, const uint32_t *queries, uint32_t B, uint
     }
   }
   tm.begin();
-  CK(launch_slots_to_responses(c, out, B, D2, responses, s));
+  CK(launch_slots_to_responses(c, out, B, D2, full, s));
   tm.end(3, 1);
-  tm.begin();
-  CK(launch_ntt_inv(c, responses, responses, (uint64_t)B * D2 * 2 * L, s));
-  tm.end(4, 1);
-  return PIR_OK;
+  return finish();
 }
 
 }  // namespace
@@ -451,7 +463,7 @@ pir_status_t pir_answer_ex(pir_db_t db, const uint32_t *queries, uint32_t B, uin
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const pir_params_t &p = db->p;
   const size_t qbytes = (size_t)B * p.D1 * 2 * p.L * p.n * 4;
-  const size_t rbytes = (size_t)B * p.D2 * 2 * p.L * p.n * 4;
+  const size_t rbytes = (size_t)B * p.D2 * 2 * ((o.flags & PIR_ANSWER_MODSWITCH) ? 1 : p.L) * p.n * 4;
   if (on_device) {
     if (!aligned16(queries) || !aligned16(responses)) return PIR_ERR_ARG;
     return answer_device(db, queries, B, responses, s, o);
@@ -491,6 +503,22 @@ static pir_status_t ntt_common(const pir_params_t *params, uint32_t *polys, size
   return PIR_OK;
 }
 
+pir_status_t ntt_inv_modswitch(const pir_params_t *params, const uint32_t *in, size_t count, uint32_t *out,
+                               void *stream) {
+  if (!params || (count && (!in || !out))) return PIR_ERR_ARG;
+  if (count == 0) return validate_params(params);
+  if (!aligned16(in) || !aligned16(out)) return PIR_ERR_ARG;
+  const uintptr_t ib = (uintptr_t)in, ob = (uintptr_t)out;
+  const uint64_t in_bytes = (uint64_t)count * params->L * params->n * 4, out_bytes = (uint64_t)count * params->n * 4;
+  if (ib < ob + out_bytes && ob < ib + in_bytes) return PIR_ERR_ARG;  // the kernel reads rows after others are written
+  const ParamCtx *ctx = nullptr;
+  pir_status_t st = get_param_ctx(params, &ctx);
+  if (st != PIR_OK) return st;
+  CK(launch_ntt_inv_switch(*ctx, in, out, count, static_cast<cudaStream_t>(stream)));
+  count_launches(1);
+  return PIR_OK;
+}
+
 pir_status_t ntt_fwd(const pir_params_t *params, uint32_t *polys, size_t count, void *stream) {
   return ntt_common(params, polys, count, stream, true);
 }
@@ -505,7 +533,7 @@ pir_status_t pir_graph_create(pir_db_t db, const uint32_t *queries, uint32_t B, 
   if (!out || !queries || !responses || B == 0 || !aligned16(queries) || !aligned16(responses)) return PIR_ERR_ARG;
   pir_answer_opts_t o = {};
   if (opts) o = *opts;
-  if (o.flags != 0) return PIR_ERR_ARG;
+  if ((o.flags & ~PIR_ANSWER_MODSWITCH) != 0) return PIR_ERR_ARG;
   *out = nullptr;
   uint32_t *w = nullptr;
   CK(device_error_word(&w));  // lazily allocated state must exist before the capture

@@ -34,6 +34,18 @@ struct ModConst {
   uint64_t k63[PIR_MAX_L];  // q * floor(2^63 / q): the largest multiple of q <= 2^63
 };
 
+// Modulus switching from q = q_0 q_1 ... q_{L-1} down to q_0 (App. A; fused into
+// the inverse NTT as in Sec. 4.3): y = round(x / Q') mod q_0, Q' = q_1 ... q_{L-1}.
+// x mod Q' is formed in mixed radix over q_1 .. q_{L-1} (Garner):
+// x mod Q' = a_1 + a_2 q_1 + a_3 q_1 q_2, digits a_k in [0, q_k).
+struct SwitchConst {
+  uint32_t c[PIR_MAX_L][PIR_MAX_L];     // c[k][i] = q_i^-1 mod q_k, 1 <= i < k < L
+  uint32_t c_sh[PIR_MAX_L][PIR_MAX_L];  // Shoup companions (mod q_k)
+  uint32_t w[PIR_MAX_L], w_sh[PIR_MAX_L];  // w[k] = q_1 ... q_{k-1} mod q_0 (w[1] = 1)
+  uint32_t h[PIR_MAX_L];                   // mixed-radix digits of (Q' - 1) / 2
+  uint32_t qinv, qinv_sh;                  // Q'^-1 mod q_0
+};
+
 // Host-side: the ring (n, L, primes, roots) plus device tables, cached per device
 // and ring.  p.D1 / p.D2 are zero here: database shapes are passed per call.
 struct ParamCtx {
@@ -41,6 +53,7 @@ struct ParamCtx {
   uint32_t logn;
   NttConst ntt;
   ModConst mod;
+  SwitchConst sw;
 };
 
 // params.cu
@@ -70,6 +83,10 @@ cudaError_t launch_ntt_fwd(const ParamCtx &c, const uint32_t *src, uint32_t *dst
 cudaError_t launch_ntt_fwd_rows(const ParamCtx &c, const uint32_t *src, uint64_t off, uint64_t G, uint64_t S,
                                 uint32_t *dst, uint64_t rows, cudaStream_t s);
 cudaError_t launch_ntt_inv(const ParamCtx &c, const uint32_t *src, uint32_t *dst, uint64_t rows, cudaStream_t s);
+// Inverse NTT of `count` RNS polynomials src [count][L][n] with modulus switching to
+// q_0 fused in: dst [count][n] over q_0.  src and dst must not overlap.
+cudaError_t launch_ntt_inv_switch(const ParamCtx &c, const uint32_t *src, uint32_t *dst, uint64_t count,
+                                  cudaStream_t s);
 // Batch-1 queries [1][D1][2][L][n]: forward NTT of ciphertexts i0 .. i0+Kc-1 written
 // directly as the plain slot layout [L*n][Kc][2] (Mp = 2).
 cudaError_t launch_ntt_fwd_pair_slots(const ParamCtx &c, const uint32_t *queries, uint32_t D1, uint32_t i0, uint32_t Kc,

@@ -257,6 +257,108 @@ __global__ void __launch_bounds__((1 << LOGN) / 16, 16384 >> LOGN)  // >= 1024 t
   }
 }
 
+// One coefficient switched to q_0 from its L canonical residues in shared memory
+// (row j at sm + j * padn, position pt): Garner digits a_k of x mod Q', that value
+// mod q_0 and its comparison with (Q' - 1) / 2 (digit by digit from the top), then
+// y = (x_0 - (x mod Q')) Q'^-1 + [x mod Q' > (Q' - 1) / 2]  (mod q_0),
+// which is round(x / Q') mod q_0: x = Q' floor(x / Q') + (x mod Q').  Every residue
+// is below 2^30 < 2 q_k, so one conditional subtraction brings it under any q_k.
+__device__ __forceinline__ uint32_t switch_coeff(const uint32_t *sm, uint32_t padn, uint32_t pt, const NttConst &C,
+                                                 const SwitchConst &W, uint32_t L) {
+  const uint32_t q0 = C.q[0];
+  uint32_t a[PIR_MAX_L];
+  uint32_t xm = 0;
+#pragma unroll
+  for (int k = 1; k < PIR_MAX_L; ++k) {
+    a[k] = 0;
+    if ((uint32_t)k < L) {
+      const uint32_t qk = C.q[k];
+      uint32_t t = sm[k * padn + pt];
+#pragma unroll
+      for (int i = 1; i < k; ++i) {
+        const uint32_t ai = a[i] >= qk ? a[i] - qk : a[i];
+        t = shoup_mul(t + qk - ai, W.c[k][i], W.c_sh[k][i], qk);
+        t = t >= qk ? t - qk : t;
+      }
+      a[k] = t;
+      const uint32_t ak = t >= q0 ? t - q0 : t;
+      uint32_t pr = shoup_mul(ak, W.w[k], W.w_sh[k], q0);
+      pr = pr >= q0 ? pr - q0 : pr;
+      xm += pr;
+      xm = xm >= q0 ? xm - q0 : xm;
+    }
+  }
+  bool up = false, eq = true;
+#pragma unroll
+  for (int k = PIR_MAX_L - 1; k >= 1; --k)
+    if ((uint32_t)k < L && eq && a[k] != W.h[k]) {
+      up = a[k] > W.h[k];
+      eq = false;
+    }
+  uint32_t y = shoup_mul(sm[pt] + q0 - xm, W.qinv, W.qinv_sh, q0);
+  y = y >= q0 ? y - q0 : y;
+  y += up ? 1u : 0u;
+  return y >= q0 ? y - q0 : y;
+}
+
+// Inverse NTT with modulus switching fused into its epilogue (Sec. 4.3 fuses the
+// modulus reduction into the inverse NTT; App. A defines the switch): block c
+// takes the L residue rows src + (c L + j) n of one polynomial (NTT form) and
+// writes dst + c n, its coefficients over the single prime q_0.  2 x n/16 threads:
+// half h inverts rows h, h + 2, ... into their own shared buffers (canonical), then
+// all threads switch the coefficients, four per 16-byte store.
+template <int LOGN>
+__global__ void __launch_bounds__((1 << LOGN) / 8)
+    k_ntt_inv_switch(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst, NttConst C, SwitchConst W,
+                     uint32_t L) {
+  constexpr int N = 1 << LOGN, PADN = N + N / 16, T = N / 16;
+  extern __shared__ uint32_t sm[];
+  const uint32_t half = threadIdx.x / T, tid = threadIdx.x % T;
+  const RawSrc rs = {};
+  uint32_t *gout = nullptr;
+  for (uint32_t r = 0; r < (L + 1) / 2; ++r) {
+    const uint32_t j = 2 * r + half;
+    const bool act = j < L;  // the barriers below are reached by both halves
+    const uint32_t jj = act ? j : 0;
+    uint32_t *smh = sm + jj * PADN;
+    const uint32_t q = C.q[jj], ni = C.ninv[jj], nis = C.ninv_sh[jj];
+    const uint32_t *w = C.t[jj].inv, *wsh = C.t[jj].inv_sh;
+    const uint32_t *gin = src + ((uint64_t)blockIdx.x * L + jj) * N;
+    if constexpr (LOGN == 11) {
+      if (act) ntt_pass<11, 4, 0, false, SRC_U32, DST_SMEM>(smh, gin, rs, 0, gout, w, wsh, q, ni, nis, nullptr, tid);
+      __syncthreads();
+      if (act) ntt_pass<11, 4, 4, false, SRC_SMEM, DST_SMEM>(smh, gin, rs, 0, gout, w, wsh, q, ni, nis, nullptr, tid);
+      __syncthreads();
+      if (act) ntt_pass<11, 3, 8, false, SRC_SMEM, DST_PAIR>(smh, gin, rs, 0, gout, w, wsh, q, ni, nis, nullptr, tid);
+    } else if constexpr (LOGN == 12) {
+      if (act) ntt_pass<12, 4, 0, false, SRC_U32, DST_SMEM>(smh, gin, rs, 0, gout, w, wsh, q, ni, nis, nullptr, tid);
+      __syncthreads();
+      if (act) ntt_pass<12, 4, 4, false, SRC_SMEM, DST_SMEM>(smh, gin, rs, 0, gout, w, wsh, q, ni, nis, nullptr, tid);
+      __syncthreads();
+      if (act) ntt_pass<12, 4, 8, false, SRC_SMEM, DST_PAIR>(smh, gin, rs, 0, gout, w, wsh, q, ni, nis, nullptr, tid);
+    } else {
+      if (act) ntt_pass<13, 4, 0, false, SRC_U32, DST_SMEM>(smh, gin, rs, 0, gout, w, wsh, q, ni, nis, nullptr, tid);
+      __syncthreads();
+      if (act) ntt_pass<13, 4, 4, false, SRC_SMEM, DST_SMEM>(smh, gin, rs, 0, gout, w, wsh, q, ni, nis, nullptr, tid);
+      __syncthreads();
+      if (act) ntt_pass<13, 4, 8, false, SRC_SMEM, DST_SMEM>(smh, gin, rs, 0, gout, w, wsh, q, ni, nis, nullptr, tid);
+      __syncthreads();
+      if (act) ntt_pass<13, 1, 12, false, SRC_SMEM, DST_PAIR>(smh, gin, rs, 0, gout, w, wsh, q, ni, nis, nullptr, tid);
+    }
+    __syncthreads();
+  }
+  uint32_t *out = dst + (uint64_t)blockIdx.x * N;
+  for (uint32_t g = threadIdx.x; g < (uint32_t)N / 4; g += blockDim.x) {
+    const uint32_t pt = padx(4 * g);  // four consecutive positions stay consecutive
+    uint4 y;
+    y.x = switch_coeff(sm, PADN, pt + 0, C, W, L);
+    y.y = switch_coeff(sm, PADN, pt + 1, C, W, L);
+    y.z = switch_coeff(sm, PADN, pt + 2, C, W, L);
+    y.w = switch_coeff(sm, PADN, pt + 3, C, W, L);
+    *reinterpret_cast<uint4 *>(out + 4 * g) = y;
+  }
+}
+
 // Forward NTT of the a- and b-polynomial of one ciphertext (rows (i, comp 0) and
 // (i, comp 1) of prime j of a batch-1 query chunk), written straight into the
 // slot-major layout [L*n][Kc][2] that the batch-1 scan reads: the transpose of
@@ -389,6 +491,32 @@ cudaError_t launch_ntt_fwd_pair_slots(const ParamCtx &c, const uint32_t *queries
     case 11: return pair_launch<11>(c, queries, row0, Kc, slots, s);
     case 12: return pair_launch<12>(c, queries, row0, Kc, slots, s);
     case 13: return pair_launch<13>(c, queries, row0, Kc, slots, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int LOGN>
+cudaError_t switch_launch(const ParamCtx &c, const uint32_t *src, uint32_t *dst, uint64_t count, cudaStream_t s) {
+  constexpr int N = 1 << LOGN, PADN = N + N / 16;
+  const uint32_t L = c.p.L;
+  const int smem = (int)(L * PADN * sizeof(uint32_t));
+  cudaError_t e = cudaFuncSetAttribute(k_ntt_inv_switch<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  for (uint64_t first = 0; first < count; first += kMaxGrid) {
+    const uint64_t nb = count - first < kMaxGrid ? count - first : kMaxGrid;
+    k_ntt_inv_switch<LOGN><<<(unsigned)nb, N / 8, smem, s>>>(src + first * L * N, dst + first * N, c.ntt, c.sw, L);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_ntt_inv_switch(const ParamCtx &c, const uint32_t *src, uint32_t *dst, uint64_t count,
+                                  cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  switch (c.logn) {
+    case 11: return switch_launch<11>(c, src, dst, count, s);
+    case 12: return switch_launch<12>(c, src, dst, count, s);
+    case 13: return switch_launch<13>(c, src, dst, count, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -178,6 +178,31 @@ pir_status_t get_param_ctx(const pir_params_t *p, const ParamCtx **out) {
     ctx->mod.mu[j] = (uint64_t)(~0ull / q);  // floor((2^64 - 1) / q) = floor(2^64 / q) for q not a power of 2
     ctx->mod.k63[j] = ((1ull << 63) / q) * q;
   }
+  {  // modulus switching to q_0
+    SwitchConst &sw = ctx->sw;
+    const uint32_t q0 = p->q[0];
+    for (uint32_t k = 1; k < p->L; ++k)
+      for (uint32_t i = 1; i < k; ++i) {
+        const uint32_t qk = p->q[k];
+        sw.c[k][i] = (uint32_t)pow_mod32(p->q[i] % qk, qk - 2, qk);
+        sw.c_sh[k][i] = shoup(sw.c[k][i], qk);
+      }
+    uint64_t wk = 1;                // q_1 ... q_{k-1} mod q_0
+    unsigned __int128 Qd = 1;       // Q' = q_1 ... q_{L-1} (< 2^90)
+    for (uint32_t k = 1; k < p->L; ++k) {
+      sw.w[k] = (uint32_t)wk;
+      sw.w_sh[k] = shoup(sw.w[k], q0);
+      wk = wk * p->q[k] % q0;
+      Qd *= p->q[k];
+    }
+    sw.qinv = (uint32_t)pow_mod32(wk, q0 - 2, q0);  // wk = Q' mod q_0 (nonzero: distinct primes)
+    sw.qinv_sh = shoup(sw.qinv, q0);
+    unsigned __int128 H = (Qd - 1) / 2;
+    for (uint32_t k = 1; k < p->L; ++k) {
+      sw.h[k] = (uint32_t)(H % p->q[k]);
+      H /= p->q[k];
+    }
+  }
   uint32_t *dtab = nullptr;
   e = cudaMalloc(&dtab, host.size() * sizeof(uint32_t));
   if (e != cudaSuccess) {

@@ -13,18 +13,12 @@ namespace gbpir {
 // ---------------------------------------------------------------------------
 // Per-prime NTT constants handed to kernels by value.
 // ---------------------------------------------------------------------------
-struct PrimeTables {
-  const uint32_t *fwd;     // [n] psi^brv(i)
-  const uint32_t *fwd_sh;  // [n] floor(psi^brv(i) * 2^32 / q)   (Shoup companion)
-  const uint32_t *inv;     // [n] psi^-brv(i)
-  const uint32_t *inv_sh;  // [n] Shoup companions
-};
-
 struct NttConst {
   uint32_t q[PIR_MAX_L];
-  uint32_t ninv[PIR_MAX_L];     // n^-1 mod q
-  uint32_t ninv_sh[PIR_MAX_L];  // Shoup companion of n^-1
-  PrimeTables t[PIR_MAX_L];
+  uint32_t ninv[PIR_MAX_L];        // n^-1 mod q
+  uint32_t ninv_sh[PIR_MAX_L];     // Shoup companion of n^-1
+  const uint2 *fwd[PIR_MAX_L];     // [n] {psi^brv(i), floor(psi^brv(i) * 2^32 / q)}: twiddle, Shoup companion
+  const uint2 *inv[PIR_MAX_L];     // [n] {psi^-brv(i), its Shoup companion}
 };
 
 // Reduction constants of the modular GEMM epilogues.

@@ -22,6 +22,21 @@ namespace {
 
 __device__ __forceinline__ uint32_t padx(uint32_t i) { return i + (i >> 4); }
 
+// x - m if x >= m, else x (x < 2m <= 2^32): as unsigned values x - m wraps above x
+// exactly when x < m, so the minimum picks the right one in two integer operations.
+__device__ __forceinline__ uint32_t csub(uint32_t x, uint32_t m) { return min(x, x - m); }
+
+// Element j < L of a per-prime parameter array, by compare and select: indexing a
+// kernel parameter array with a run-time j makes the compiler copy the whole
+// parameter block to local memory first.
+template <typename T>
+__device__ __forceinline__ T pick(const T (&a)[PIR_MAX_L], uint32_t j) {
+  T r = a[0];
+#pragma unroll
+  for (uint32_t i = 1; i < PIR_MAX_L; ++i) r = j == i ? a[i] : r;
+  return r;
+}
+
 // Source kinds of the first pass.
 enum { SRC_SMEM = 0, SRC_U32 = 1, SRC_RAW = 2 };
 
@@ -64,59 +79,106 @@ __device__ __forceinline__ uint32_t raw_coeff(const RawSrc &rs, uint64_t poly, u
   return (uint32_t)((w >> (bit0 & 7)) & ((1ull << rs.log2p) - 1));
 }
 
-// Forward stages on one radix-2^RB unit: bits BLO+RB-1 down to BLO of the element
-// index.  The pair (x, x + 2^b) of stage bit b belongs to block g = index >> (b+1)
-// and uses twiddle psi^brv(m + g) with m = n >> (b+1).
-template <int RB, int BLO, int LOGN>
-__device__ __forceinline__ void fwd_stages(uint32_t (&v)[1 << RB], uint32_t hi, const uint32_t *__restrict__ w,
-                                           const uint32_t *__restrict__ wsh, uint32_t q) {
-  const uint32_t q2 = 2 * q;
+// Twiddle pairs {w, Shoup companion} used by one stage of one radix-2^RB unit.
+// Stage bit b pairs (x, x + 2^b); the pair belongs to block g = index >> (b+1) and
+// uses twiddle m + g, m = n >> (b+1).  Within a unit the blocks of stage LB are the
+// 2^(RB-1-LB) consecutive entries from m + (hi << (RB-1-LB)), a run aligned to its
+// own length, so they arrive in 16-byte loads (8 bytes for a single pair).
+template <int CNT>
+struct Pairs {  // CNT twiddle pairs held as whole 16-byte vectors (8 bytes when CNT = 1)
+  uint4 v[(CNT + 1) / 2];
+  __device__ __forceinline__ void load(const uint2 *__restrict__ src) {
+    if constexpr (CNT == 1) {
+      const uint2 x = __ldg(src);
+      v[0] = make_uint4(x.x, x.y, 0u, 0u);
+    } else {
 #pragma unroll
-  for (int lb = RB - 1; lb >= 0; --lb) {
-    const uint32_t m = 1u << (LOGN - 1 - (BLO + lb));
-#pragma unroll
-    for (int e = 0; e < (1 << RB); ++e) {
-      if (e & (1 << lb)) continue;
-      const uint32_t g = (hi << (RB - 1 - lb)) | (uint32_t)(e >> (lb + 1));
-      const uint32_t tw = __ldg(w + m + g), tws = __ldg(wsh + m + g);
-      uint32_t x = v[e];
-      const uint32_t y = v[e | (1 << lb)];
-      x = x >= q2 ? x - q2 : x;              // [0, 2q)
-      const uint32_t t = shoup_mul(y, tw, tws, q);  // [0, 2q)
-      v[e] = x + t;                          // [0, 4q)
-      v[e | (1 << lb)] = x - t + q2;         // (0, 4q)
+      for (int i = 0; i < CNT / 2; ++i) v[i] = __ldg(reinterpret_cast<const uint4 *>(src) + i);
     }
+  }
+  template <int I>
+  __device__ __forceinline__ uint32_t w() const { return (I & 1) ? v[I / 2].z : v[I / 2].x; }
+  template <int I>
+  __device__ __forceinline__ uint32_t ws() const { return (I & 1) ? v[I / 2].w : v[I / 2].y; }
+};
+
+// One forward (Cooley-Tukey) butterfly of stage LB on elements E and E + 2^LB.
+template <int RB, int LB, int E, int CNT>
+__device__ __forceinline__ void fwd_bfly(uint32_t (&v)[1 << RB], const Pairs<CNT> &p, uint32_t q) {
+  if constexpr (E < (1 << RB)) {
+    if constexpr ((E & (1 << LB)) == 0) {
+      const uint32_t q2 = 2 * q;
+      uint32_t x = v[E];
+      const uint32_t y = v[E | (1 << LB)];
+      x = csub(x, q2);                                                              // [0, 2q)
+      const uint32_t t = shoup_mul(y, p.template w<(E >> (LB + 1))>(), p.template ws<(E >> (LB + 1))>(), q);  // [0, 2q)
+      v[E] = x + t;                                                                 // [0, 4q)
+      v[E | (1 << LB)] = x - t + q2;                                                // (0, 4q)
+    }
+    fwd_bfly<RB, LB, E + 1, CNT>(v, p, q);
   }
 }
 
-// Inverse stages (Gentleman-Sande), bits BLO up to BLO+RB-1; values in [0, 2q).
-template <int RB, int BLO, int LOGN>
-__device__ __forceinline__ void inv_stages(uint32_t (&v)[1 << RB], uint32_t hi, const uint32_t *__restrict__ w,
-                                           const uint32_t *__restrict__ wsh, uint32_t q) {
-  const uint32_t q2 = 2 * q;
-#pragma unroll
-  for (int lb = 0; lb < RB; ++lb) {
-    const uint32_t m = 1u << (LOGN - 1 - (BLO + lb));
-#pragma unroll
-    for (int e = 0; e < (1 << RB); ++e) {
-      if (e & (1 << lb)) continue;
-      const uint32_t g = (hi << (RB - 1 - lb)) | (uint32_t)(e >> (lb + 1));
-      const uint32_t tw = __ldg(w + m + g), tws = __ldg(wsh + m + g);
-      const uint32_t x = v[e], y = v[e | (1 << lb)];
+// One forward stage on the unit's bit BLO + LB.
+template <int RB, int BLO, int LOGN, int LB>
+__device__ __forceinline__ void fwd_stage(uint32_t (&v)[1 << RB], uint32_t hi, const uint2 *__restrict__ tw,
+                                          uint32_t q) {
+  constexpr int CNT = 1 << (RB - 1 - LB);
+  constexpr uint32_t m = 1u << (LOGN - 1 - (BLO + LB));
+  Pairs<CNT> p;
+  p.load(tw + m + (hi << (RB - 1 - LB)));
+  fwd_bfly<RB, LB, 0, CNT>(v, p, q);
+}
+
+// Forward stages on one unit: bits BLO+RB-1 down to BLO of the element index.
+template <int RB, int BLO, int LOGN, int LB = RB - 1>
+__device__ __forceinline__ void fwd_stages(uint32_t (&v)[1 << RB], uint32_t hi, const uint2 *__restrict__ tw,
+                                           uint32_t q) {
+  fwd_stage<RB, BLO, LOGN, LB>(v, hi, tw, q);
+  if constexpr (LB > 0) fwd_stages<RB, BLO, LOGN, LB - 1>(v, hi, tw, q);
+}
+
+// One inverse (Gentleman-Sande) butterfly of stage LB; values in [0, 2q).
+template <int RB, int LB, int E, int CNT>
+__device__ __forceinline__ void inv_bfly(uint32_t (&v)[1 << RB], const Pairs<CNT> &p, uint32_t q) {
+  if constexpr (E < (1 << RB)) {
+    if constexpr ((E & (1 << LB)) == 0) {
+      const uint32_t q2 = 2 * q;
+      const uint32_t x = v[E], y = v[E | (1 << LB)];
       uint32_t s = x + y;
-      s = s >= q2 ? s - q2 : s;
-      v[e] = s;
-      v[e | (1 << lb)] = shoup_mul(x - y + q2, tw, tws, q);
+      s = csub(s, q2);
+      v[E] = s;
+      v[E | (1 << LB)] = shoup_mul(x - y + q2, p.template w<(E >> (LB + 1))>(), p.template ws<(E >> (LB + 1))>(), q);
     }
+    inv_bfly<RB, LB, E + 1, CNT>(v, p, q);
   }
+}
+
+// One inverse stage on bit BLO + LB.
+template <int RB, int BLO, int LOGN, int LB>
+__device__ __forceinline__ void inv_stage(uint32_t (&v)[1 << RB], uint32_t hi, const uint2 *__restrict__ tw,
+                                          uint32_t q) {
+  constexpr int CNT = 1 << (RB - 1 - LB);
+  constexpr uint32_t m = 1u << (LOGN - 1 - (BLO + LB));
+  Pairs<CNT> p;
+  p.load(tw + m + (hi << (RB - 1 - LB)));
+  inv_bfly<RB, LB, 0, CNT>(v, p, q);
+}
+
+// Inverse stages on one unit: bits BLO up to BLO+RB-1.
+template <int RB, int BLO, int LOGN, int LB = 0>
+__device__ __forceinline__ void inv_stages(uint32_t (&v)[1 << RB], uint32_t hi, const uint2 *__restrict__ tw,
+                                           uint32_t q) {
+  inv_stage<RB, BLO, LOGN, LB>(v, hi, tw, q);
+  if constexpr (LB < RB - 1) inv_stages<RB, BLO, LOGN, LB + 1>(v, hi, tw, q);
 }
 
 // One radix-2^RB pass over the whole row: unit u holds the 2^RB elements whose
 // index has bits [BLO, BLO+RB) free and the rest fixed by u.
 template <int LOGN, int RB, int BLO, bool FWD, int SRC, int DST>
 __device__ __forceinline__ void ntt_pass(uint32_t *sm, const uint32_t *__restrict__ gin, const RawSrc &rs,
-                                         uint64_t poly, uint32_t *__restrict__ gout, const uint32_t *__restrict__ w,
-                                         const uint32_t *__restrict__ wsh, uint32_t q, uint32_t ninv,
+                                         uint64_t poly, uint32_t *__restrict__ gout, const uint2 *__restrict__ tw,
+                                         uint32_t q, uint32_t ninv,
                                          uint32_t ninv_sh, const SlotDst *sd = nullptr,
                                          uint32_t tid = threadIdx.x) {
   constexpr int N = 1 << LOGN, T = N / 16, UNITS = N >> RB, PER = UNITS / T;
@@ -146,19 +208,19 @@ __device__ __forceinline__ void ntt_pass(uint32_t *sm, const uint32_t *__restric
       }
     }
     if constexpr (FWD)
-      fwd_stages<RB, BLO, LOGN>(v, hi, w, wsh, q);
+      fwd_stages<RB, BLO, LOGN>(v, hi, tw, q);
     else
-      inv_stages<RB, BLO, LOGN>(v, hi, w, wsh, q);
+      inv_stages<RB, BLO, LOGN>(v, hi, tw, q);
     if constexpr (DST != DST_SMEM) {
 #pragma unroll
       for (int e = 0; e < (1 << RB); ++e) {
         uint32_t x = v[e];
         if constexpr (FWD) {
-          x = x >= 2 * q ? x - 2 * q : x;
-          x = x >= q ? x - q : x;
+          x = csub(x, 2 * q);
+          x = csub(x, q);
         } else {
           x = shoup_mul(x, ninv, ninv_sh, q);
-          x = x >= q ? x - q : x;
+          x = csub(x, q);
         }
         v[e] = x;
       }
@@ -190,31 +252,31 @@ __global__ void __launch_bounds__((1 << LOGN) / 16, 16384 >> LOGN)  // >= 1024 t
   extern __shared__ uint32_t sm[];
   for (uint64_t row = blockIdx.x; row < rows; row += gridDim.x) {
     const uint32_t j = (uint32_t)(row % L);
-    const uint32_t q = C.q[j];
-    const uint32_t *w = C.t[j].fwd, *wsh = C.t[j].fwd_sh;
+    const uint32_t q = pick(C.q, j);
+    const uint2 *tw = pick(C.fwd, j);
     const uint32_t *gin = src ? src + rm(row) * N : nullptr;
     uint32_t *gout = dst + row * N;
     const uint64_t poly = SRC == SRC_RAW ? rs.poly(row / L) : 0;
     if constexpr (LOGN == 11) {
-      ntt_pass<11, 4, 7, true, SRC, DST_SMEM>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
+      ntt_pass<11, 4, 7, true, SRC, DST_SMEM>(sm, gin, rs, poly, gout, tw, q, 0, 0);
       __syncthreads();
-      ntt_pass<11, 4, 3, true, SRC_SMEM, DST_SMEM>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
+      ntt_pass<11, 4, 3, true, SRC_SMEM, DST_SMEM>(sm, gin, rs, poly, gout, tw, q, 0, 0);
       __syncthreads();
-      ntt_pass<11, 3, 0, true, SRC_SMEM, DST_GLOBAL>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
+      ntt_pass<11, 3, 0, true, SRC_SMEM, DST_GLOBAL>(sm, gin, rs, poly, gout, tw, q, 0, 0);
     } else if constexpr (LOGN == 12) {
-      ntt_pass<12, 4, 8, true, SRC, DST_SMEM>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
+      ntt_pass<12, 4, 8, true, SRC, DST_SMEM>(sm, gin, rs, poly, gout, tw, q, 0, 0);
       __syncthreads();
-      ntt_pass<12, 4, 4, true, SRC_SMEM, DST_SMEM>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
+      ntt_pass<12, 4, 4, true, SRC_SMEM, DST_SMEM>(sm, gin, rs, poly, gout, tw, q, 0, 0);
       __syncthreads();
-      ntt_pass<12, 4, 0, true, SRC_SMEM, DST_GLOBAL>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
+      ntt_pass<12, 4, 0, true, SRC_SMEM, DST_GLOBAL>(sm, gin, rs, poly, gout, tw, q, 0, 0);
     } else {
-      ntt_pass<13, 4, 9, true, SRC, DST_SMEM>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
+      ntt_pass<13, 4, 9, true, SRC, DST_SMEM>(sm, gin, rs, poly, gout, tw, q, 0, 0);
       __syncthreads();
-      ntt_pass<13, 4, 5, true, SRC_SMEM, DST_SMEM>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
+      ntt_pass<13, 4, 5, true, SRC_SMEM, DST_SMEM>(sm, gin, rs, poly, gout, tw, q, 0, 0);
       __syncthreads();
-      ntt_pass<13, 4, 1, true, SRC_SMEM, DST_SMEM>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
+      ntt_pass<13, 4, 1, true, SRC_SMEM, DST_SMEM>(sm, gin, rs, poly, gout, tw, q, 0, 0);
       __syncthreads();
-      ntt_pass<13, 1, 0, true, SRC_SMEM, DST_GLOBAL>(sm, gin, rs, poly, gout, w, wsh, q, 0, 0);
+      ntt_pass<13, 1, 0, true, SRC_SMEM, DST_GLOBAL>(sm, gin, rs, poly, gout, tw, q, 0, 0);
     }
     __syncthreads();  // the next row reuses shared memory
   }
@@ -228,30 +290,30 @@ __global__ void __launch_bounds__((1 << LOGN) / 16, 16384 >> LOGN)  // >= 1024 t
   const RawSrc rs = {};
   for (uint64_t row = blockIdx.x; row < rows; row += gridDim.x) {
     const uint32_t j = (uint32_t)(row % L);
-    const uint32_t q = C.q[j], ni = C.ninv[j], nis = C.ninv_sh[j];
-    const uint32_t *w = C.t[j].inv, *wsh = C.t[j].inv_sh;
+    const uint32_t q = pick(C.q, j), ni = pick(C.ninv, j), nis = pick(C.ninv_sh, j);
+    const uint2 *tw = pick(C.inv, j);
     const uint32_t *gin = src + row * N;
     uint32_t *gout = dst + row * N;
     if constexpr (LOGN == 11) {
-      ntt_pass<11, 4, 0, false, SRC_U32, DST_SMEM>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
+      ntt_pass<11, 4, 0, false, SRC_U32, DST_SMEM>(sm, gin, rs, 0, gout, tw, q, ni, nis);
       __syncthreads();
-      ntt_pass<11, 4, 4, false, SRC_SMEM, DST_SMEM>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
+      ntt_pass<11, 4, 4, false, SRC_SMEM, DST_SMEM>(sm, gin, rs, 0, gout, tw, q, ni, nis);
       __syncthreads();
-      ntt_pass<11, 3, 8, false, SRC_SMEM, DST_GLOBAL>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
+      ntt_pass<11, 3, 8, false, SRC_SMEM, DST_GLOBAL>(sm, gin, rs, 0, gout, tw, q, ni, nis);
     } else if constexpr (LOGN == 12) {
-      ntt_pass<12, 4, 0, false, SRC_U32, DST_SMEM>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
+      ntt_pass<12, 4, 0, false, SRC_U32, DST_SMEM>(sm, gin, rs, 0, gout, tw, q, ni, nis);
       __syncthreads();
-      ntt_pass<12, 4, 4, false, SRC_SMEM, DST_SMEM>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
+      ntt_pass<12, 4, 4, false, SRC_SMEM, DST_SMEM>(sm, gin, rs, 0, gout, tw, q, ni, nis);
       __syncthreads();
-      ntt_pass<12, 4, 8, false, SRC_SMEM, DST_GLOBAL>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
+      ntt_pass<12, 4, 8, false, SRC_SMEM, DST_GLOBAL>(sm, gin, rs, 0, gout, tw, q, ni, nis);
     } else {
-      ntt_pass<13, 4, 0, false, SRC_U32, DST_SMEM>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
+      ntt_pass<13, 4, 0, false, SRC_U32, DST_SMEM>(sm, gin, rs, 0, gout, tw, q, ni, nis);
       __syncthreads();
-      ntt_pass<13, 4, 4, false, SRC_SMEM, DST_SMEM>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
+      ntt_pass<13, 4, 4, false, SRC_SMEM, DST_SMEM>(sm, gin, rs, 0, gout, tw, q, ni, nis);
       __syncthreads();
-      ntt_pass<13, 4, 8, false, SRC_SMEM, DST_SMEM>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
+      ntt_pass<13, 4, 8, false, SRC_SMEM, DST_SMEM>(sm, gin, rs, 0, gout, tw, q, ni, nis);
       __syncthreads();
-      ntt_pass<13, 1, 12, false, SRC_SMEM, DST_GLOBAL>(sm, gin, rs, 0, gout, w, wsh, q, ni, nis);
+      ntt_pass<13, 1, 12, false, SRC_SMEM, DST_GLOBAL>(sm, gin, rs, 0, gout, tw, q, ni, nis);
     }
     __syncthreads();
   }
@@ -308,7 +370,7 @@ __device__ __forceinline__ uint32_t switch_coeff(const uint32_t *sm, uint32_t pa
 // half h inverts rows h, h + 2, ... into their own shared buffers (canonical), then
 // all threads switch the coefficients, four per 16-byte store.
 template <int LOGN>
-__global__ void __launch_bounds__((1 << LOGN) / 8)
+__global__ void __launch_bounds__((1 << LOGN) / 8, 8192 >> LOGN)  // <= 64 registers: 1024 threads per SM
     k_ntt_inv_switch(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst, NttConst C, SwitchConst W,
                      uint32_t L) {
   constexpr int N = 1 << LOGN, PADN = N + N / 16, T = N / 16;
@@ -321,29 +383,29 @@ __global__ void __launch_bounds__((1 << LOGN) / 8)
     const bool act = j < L;  // the barriers below are reached by both halves
     const uint32_t jj = act ? j : 0;
     uint32_t *smh = sm + jj * PADN;
-    const uint32_t q = C.q[jj], ni = C.ninv[jj], nis = C.ninv_sh[jj];
-    const uint32_t *w = C.t[jj].inv, *wsh = C.t[jj].inv_sh;
+    const uint32_t q = pick(C.q, jj), ni = pick(C.ninv, jj), nis = pick(C.ninv_sh, jj);
+    const uint2 *tw = pick(C.inv, jj);
     const uint32_t *gin = src + ((uint64_t)blockIdx.x * L + jj) * N;
     if constexpr (LOGN == 11) {
-      if (act) ntt_pass<11, 4, 0, false, SRC_U32, DST_SMEM>(smh, gin, rs, 0, gout, w, wsh, q, ni, nis, nullptr, tid);
+      if (act) ntt_pass<11, 4, 0, false, SRC_U32, DST_SMEM>(smh, gin, rs, 0, gout, tw, q, ni, nis, nullptr, tid);
       __syncthreads();
-      if (act) ntt_pass<11, 4, 4, false, SRC_SMEM, DST_SMEM>(smh, gin, rs, 0, gout, w, wsh, q, ni, nis, nullptr, tid);
+      if (act) ntt_pass<11, 4, 4, false, SRC_SMEM, DST_SMEM>(smh, gin, rs, 0, gout, tw, q, ni, nis, nullptr, tid);
       __syncthreads();
-      if (act) ntt_pass<11, 3, 8, false, SRC_SMEM, DST_PAIR>(smh, gin, rs, 0, gout, w, wsh, q, ni, nis, nullptr, tid);
+      if (act) ntt_pass<11, 3, 8, false, SRC_SMEM, DST_PAIR>(smh, gin, rs, 0, gout, tw, q, ni, nis, nullptr, tid);
     } else if constexpr (LOGN == 12) {
-      if (act) ntt_pass<12, 4, 0, false, SRC_U32, DST_SMEM>(smh, gin, rs, 0, gout, w, wsh, q, ni, nis, nullptr, tid);
+      if (act) ntt_pass<12, 4, 0, false, SRC_U32, DST_SMEM>(smh, gin, rs, 0, gout, tw, q, ni, nis, nullptr, tid);
       __syncthreads();
-      if (act) ntt_pass<12, 4, 4, false, SRC_SMEM, DST_SMEM>(smh, gin, rs, 0, gout, w, wsh, q, ni, nis, nullptr, tid);
+      if (act) ntt_pass<12, 4, 4, false, SRC_SMEM, DST_SMEM>(smh, gin, rs, 0, gout, tw, q, ni, nis, nullptr, tid);
       __syncthreads();
-      if (act) ntt_pass<12, 4, 8, false, SRC_SMEM, DST_PAIR>(smh, gin, rs, 0, gout, w, wsh, q, ni, nis, nullptr, tid);
+      if (act) ntt_pass<12, 4, 8, false, SRC_SMEM, DST_PAIR>(smh, gin, rs, 0, gout, tw, q, ni, nis, nullptr, tid);
     } else {
-      if (act) ntt_pass<13, 4, 0, false, SRC_U32, DST_SMEM>(smh, gin, rs, 0, gout, w, wsh, q, ni, nis, nullptr, tid);
+      if (act) ntt_pass<13, 4, 0, false, SRC_U32, DST_SMEM>(smh, gin, rs, 0, gout, tw, q, ni, nis, nullptr, tid);
       __syncthreads();
-      if (act) ntt_pass<13, 4, 4, false, SRC_SMEM, DST_SMEM>(smh, gin, rs, 0, gout, w, wsh, q, ni, nis, nullptr, tid);
+      if (act) ntt_pass<13, 4, 4, false, SRC_SMEM, DST_SMEM>(smh, gin, rs, 0, gout, tw, q, ni, nis, nullptr, tid);
       __syncthreads();
-      if (act) ntt_pass<13, 4, 8, false, SRC_SMEM, DST_SMEM>(smh, gin, rs, 0, gout, w, wsh, q, ni, nis, nullptr, tid);
+      if (act) ntt_pass<13, 4, 8, false, SRC_SMEM, DST_SMEM>(smh, gin, rs, 0, gout, tw, q, ni, nis, nullptr, tid);
       __syncthreads();
-      if (act) ntt_pass<13, 1, 12, false, SRC_SMEM, DST_PAIR>(smh, gin, rs, 0, gout, w, wsh, q, ni, nis, nullptr, tid);
+      if (act) ntt_pass<13, 1, 12, false, SRC_SMEM, DST_PAIR>(smh, gin, rs, 0, gout, tw, q, ni, nis, nullptr, tid);
     }
     __syncthreads();
   }
@@ -373,31 +435,31 @@ __global__ void __launch_bounds__((1 << LOGN) / 8)
   const uint32_t i = blockIdx.x / L, j = blockIdx.x % L;
   const uint32_t half = threadIdx.x / T, tid = threadIdx.x % T;
   uint32_t *smh = sm + half * PADN;
-  const uint32_t q = C.q[j];
-  const uint32_t *w = C.t[j].fwd, *wsh = C.t[j].fwd_sh;
+  const uint32_t q = pick(C.q, j);
+  const uint2 *tw = pick(C.fwd, j);
   const uint32_t *gin = src + (row0 + (uint64_t)i * 2 * L + (uint64_t)half * L + j) * N;
   const RawSrc rs = {};
   uint32_t *gout = nullptr;
   if constexpr (LOGN == 11) {
-    ntt_pass<11, 4, 7, true, SRC_U32, DST_SMEM>(smh, gin, rs, 0, gout, w, wsh, q, 0, 0, nullptr, tid);
+    ntt_pass<11, 4, 7, true, SRC_U32, DST_SMEM>(smh, gin, rs, 0, gout, tw, q, 0, 0, nullptr, tid);
     __syncthreads();
-    ntt_pass<11, 4, 3, true, SRC_SMEM, DST_SMEM>(smh, gin, rs, 0, gout, w, wsh, q, 0, 0, nullptr, tid);
+    ntt_pass<11, 4, 3, true, SRC_SMEM, DST_SMEM>(smh, gin, rs, 0, gout, tw, q, 0, 0, nullptr, tid);
     __syncthreads();
-    ntt_pass<11, 3, 0, true, SRC_SMEM, DST_PAIR>(smh, gin, rs, 0, gout, w, wsh, q, 0, 0, nullptr, tid);
+    ntt_pass<11, 3, 0, true, SRC_SMEM, DST_PAIR>(smh, gin, rs, 0, gout, tw, q, 0, 0, nullptr, tid);
   } else if constexpr (LOGN == 12) {
-    ntt_pass<12, 4, 8, true, SRC_U32, DST_SMEM>(smh, gin, rs, 0, gout, w, wsh, q, 0, 0, nullptr, tid);
+    ntt_pass<12, 4, 8, true, SRC_U32, DST_SMEM>(smh, gin, rs, 0, gout, tw, q, 0, 0, nullptr, tid);
     __syncthreads();
-    ntt_pass<12, 4, 4, true, SRC_SMEM, DST_SMEM>(smh, gin, rs, 0, gout, w, wsh, q, 0, 0, nullptr, tid);
+    ntt_pass<12, 4, 4, true, SRC_SMEM, DST_SMEM>(smh, gin, rs, 0, gout, tw, q, 0, 0, nullptr, tid);
     __syncthreads();
-    ntt_pass<12, 4, 0, true, SRC_SMEM, DST_PAIR>(smh, gin, rs, 0, gout, w, wsh, q, 0, 0, nullptr, tid);
+    ntt_pass<12, 4, 0, true, SRC_SMEM, DST_PAIR>(smh, gin, rs, 0, gout, tw, q, 0, 0, nullptr, tid);
   } else {
-    ntt_pass<13, 4, 9, true, SRC_U32, DST_SMEM>(smh, gin, rs, 0, gout, w, wsh, q, 0, 0, nullptr, tid);
+    ntt_pass<13, 4, 9, true, SRC_U32, DST_SMEM>(smh, gin, rs, 0, gout, tw, q, 0, 0, nullptr, tid);
     __syncthreads();
-    ntt_pass<13, 4, 5, true, SRC_SMEM, DST_SMEM>(smh, gin, rs, 0, gout, w, wsh, q, 0, 0, nullptr, tid);
+    ntt_pass<13, 4, 5, true, SRC_SMEM, DST_SMEM>(smh, gin, rs, 0, gout, tw, q, 0, 0, nullptr, tid);
     __syncthreads();
-    ntt_pass<13, 4, 1, true, SRC_SMEM, DST_SMEM>(smh, gin, rs, 0, gout, w, wsh, q, 0, 0, nullptr, tid);
+    ntt_pass<13, 4, 1, true, SRC_SMEM, DST_SMEM>(smh, gin, rs, 0, gout, tw, q, 0, 0, nullptr, tid);
     __syncthreads();
-    ntt_pass<13, 1, 0, true, SRC_SMEM, DST_PAIR>(smh, gin, rs, 0, gout, w, wsh, q, 0, 0, nullptr, tid);
+    ntt_pass<13, 1, 0, true, SRC_SMEM, DST_PAIR>(smh, gin, rs, 0, gout, tw, q, 0, 0, nullptr, tid);
   }
   __syncthreads();
   uint32_t *dst = slots + ((uint64_t)j * N * Kc + i) * 2;

@@ -163,13 +163,13 @@ pir_status_t get_param_ctx(const pir_params_t *p, const ParamCtx **out) {
     const uint32_t q = p->q[j];
     const uint32_t psi = p->psi[j];
     const uint32_t psi_inv = (uint32_t)pow_mod32(psi, q - 2, q);
-    uint32_t *f = &host[(size_t)(4 * j + 0) * n], *fs = &host[(size_t)(4 * j + 1) * n];
-    uint32_t *iv = &host[(size_t)(4 * j + 2) * n], *is = &host[(size_t)(4 * j + 3) * n];
+    // per prime: forward pairs [n][2], then inverse pairs [n][2]
+    uint32_t *f = &host[(size_t)(4 * j + 0) * n], *iv = &host[(size_t)(4 * j + 2) * n];
     for (uint32_t i = 0; i < n; ++i) {
-      f[i] = (uint32_t)pow_mod32(psi, brv(i, lg), q);
-      fs[i] = shoup(f[i], q);
-      iv[i] = (uint32_t)pow_mod32(psi_inv, brv(i, lg), q);
-      is[i] = shoup(iv[i], q);
+      f[2 * i] = (uint32_t)pow_mod32(psi, brv(i, lg), q);
+      f[2 * i + 1] = shoup(f[2 * i], q);
+      iv[2 * i] = (uint32_t)pow_mod32(psi_inv, brv(i, lg), q);
+      iv[2 * i + 1] = shoup(iv[2 * i], q);
     }
     ctx->ntt.q[j] = q;
     ctx->ntt.ninv[j] = (uint32_t)pow_mod32(n, q - 2, q);
@@ -216,10 +216,8 @@ pir_status_t get_param_ctx(const pir_params_t *p, const ParamCtx **out) {
     return cuda_status(e);
   }
   for (uint32_t j = 0; j < p->L; ++j) {
-    ctx->ntt.t[j].fwd = dtab + (size_t)(4 * j + 0) * n;
-    ctx->ntt.t[j].fwd_sh = dtab + (size_t)(4 * j + 1) * n;
-    ctx->ntt.t[j].inv = dtab + (size_t)(4 * j + 2) * n;
-    ctx->ntt.t[j].inv_sh = dtab + (size_t)(4 * j + 3) * n;
+    ctx->ntt.fwd[j] = reinterpret_cast<const uint2 *>(dtab + (size_t)(4 * j + 0) * n);
+    ctx->ntt.inv[j] = reinterpret_cast<const uint2 *>(dtab + (size_t)(4 * j + 2) * n);
   }
   g_cache[k] = ctx;
   *out = ctx;

@@ -128,7 +128,7 @@ typedef struct {
  * PIR_ERR_TIMEOUT).  Needs a shape the TMA scan holds (2B <= 8, D2 <= 512). */
 #define PIR_ANSWER_TEST_STALL 2u
 /* Modulus switching of the responses to the single prime q_0, fused into the
- * inverse NTT (Sec. 4.3; App. A, error analysis of RLWE modulus switching): the
+ * inverse NTT (Sec. 4.3; App. D.5, error analysis of RLWE modulus switching): the
  * responses are then [B][D2][2][n] uint32 over q_0, coefficient form, canonical
  * (half the bytes at L = 2), as ntt_inv_modswitch below computes them. */
 #define PIR_ANSWER_MODSWITCH 4u
@@ -195,7 +195,7 @@ pir_status_t ntt_fwd(const pir_params_t *params, uint32_t *polys, size_t count, 
 pir_status_t ntt_inv(const pir_params_t *params, uint32_t *polys, size_t count, void *stream);
 
 /* Inverse NTT with modulus switching fused into it (Sec. 4.3 fuses the modulus
- * reduction into the inverse NTT; App. A, "Error analysis of RLWE modulus
+ * reduction into the inverse NTT; App. D.5, "Error analysis of RLWE modulus
  * switching", defines the switch from q = q_0 ... q_{L-1} to one prime).
  *   in:  [count][L][n] uint32, NTT form over q, canonical; device memory, read only.
  *   out: [count][n] uint32, coefficient form over q_0 (the first prime of params),

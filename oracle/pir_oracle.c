@@ -15,7 +15,7 @@
  *   - negacyclic NTT / inverse NTT, one row per prime                 (Sec. 2.3)
  *   - RLWE encryption / decryption with Delta = floor(q/p)            (App. A.2)
  *   - modulus switching q -> q_0: round(x q_0 / q) mod q_0, and decryption over
- *     the single prime q_0 afterwards                                 (App. A, Sec. 4.3)
+ *     the single prime q_0 afterwards                                 (App. D.5, Sec. 4.3)
  *   - first-dimension folding: out_c = sum_i DB[i][c] * ct_i in R_q^2 (Sec. 3.2, Sec. 4 "INT32
  *     modular GEMM", Sec. 4.2): in the NTT domain, for every prime q_j and slot k,
  *     out[b][c][k] = sum_i DB[i][c][k] * Q[b][i][k]  (mod q_j).
@@ -34,7 +34,7 @@
  * library, the defining congruences, the NTT evaluated by its definition, schoolbook
  * negacyclic multiplication, the convolution theorem, and the BFV decryption
  * invariant (decrypting the answer returns exactly the requested record); modulus
- * switching against values built as t Q' + r, the rounding-error bound of App. A
+ * switching against values built as t Q' + r, the rounding-error bound of App. D.5
  * and decryption after the switch.
  */
 #include <pthread.h>
@@ -729,7 +729,7 @@ static u128 crt_lift(const orc_params *P, const u32 *res, u64 stride) {
   return x;
 }
 
-/* Modulus switching of RLWE ciphertext polynomials (App. A, "Error analysis of
+/* Modulus switching of RLWE ciphertext polynomials (App. D.5, "Error analysis of
  * RLWE modulus switching"; Sec. 4.3 fuses it with the inverse NTT): every
  * coefficient x in [0, q) goes to
  *     y = round(x * q_0 / q) mod q_0,

@@ -28,7 +28,7 @@ struct ModConst {
   uint64_t k63[PIR_MAX_L];  // q * floor(2^63 / q): the largest multiple of q <= 2^63
 };
 
-// Modulus switching from q = q_0 q_1 ... q_{L-1} down to q_0 (App. A; fused into
+// Modulus switching from q = q_0 q_1 ... q_{L-1} down to q_0 (App. D.5; fused into
 // the inverse NTT as in Sec. 4.3): y = round(x / Q') mod q_0, Q' = q_1 ... q_{L-1}.
 // x mod Q' is formed in mixed radix over q_1 .. q_{L-1} (Garner):
 // x mod Q' = a_1 + a_2 q_1 + a_3 q_1 q_2, digits a_k in [0, q_k).

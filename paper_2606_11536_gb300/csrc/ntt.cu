@@ -364,7 +364,7 @@ __device__ __forceinline__ uint32_t switch_coeff(const uint32_t *sm, uint32_t pa
 }
 
 // Inverse NTT with modulus switching fused into its epilogue (Sec. 4.3 fuses the
-// modulus reduction into the inverse NTT; App. A defines the switch): block c
+// modulus reduction into the inverse NTT; App. D.5 defines the switch): block c
 // takes the L residue rows src + (c L + j) n of one polynomial (NTT form) and
 // writes dst + c n, its coefficients over the single prime q_0.  2 x n/16 threads:
 // half h inverts rows h, h + 2, ... into their own shared buffers (canonical), then

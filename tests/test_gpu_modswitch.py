@@ -1,4 +1,4 @@
-"""GPU parity of modulus switching fused into the inverse NTT (Sec. 4.3; App. A):
+"""GPU parity of modulus switching fused into the inverse NTT (Sec. 4.3; App. D.5):
 ntt_inv_modswitch against the oracle's inverse NTT followed by its switch, bit for
 bit, for every ring size and L = 1..4, on random residues and on coefficients built
 as t Q' + r around the rounding boundary; and pir_answer with PIR_ANSWER_MODSWITCH

@@ -1,7 +1,7 @@
-"""Pins for the oracle's modulus switching to q_0 (App. A, error analysis of RLWE
+"""Pins for the oracle's modulus switching to q_0 (App. D.5, error analysis of RLWE
 modulus switching): coefficients built as x = t Q' + r, whose rounded quotient is
 t or t + 1 by construction; the identity when nothing is dropped; the rounding
-error of a switched ciphertext against the bound of App. A (each coefficient
+error of a switched ciphertext against the bound of App. D.5 (each coefficient
 rounded to within 1/2, so |E| <= (1 + ||s||_1) / 2 in the new units); and
 decryption after switching, for fresh encryptions and for a whole PIR answer."""
 import numpy as np
@@ -75,7 +75,7 @@ def test_rounding_error_bound_and_decryption(orc, n, log2p):
             d = d - q * q0 if d > (q * q0) // 2 else d
             worst = max(worst, abs(d))
         assert 2 * worst <= q * (1 + s1)
-        # and far inside it, as the App. A tail bound predicts for i.i.d. roundings
+        # and far inside it, as the App. D.5 tail bound predicts for i.i.d. roundings
         assert worst < q * 8 * np.sqrt(n + 1)
 
 

@@ -79,6 +79,11 @@ def lib():
             "orc_modswitch": (None, [PP, U32P, C.c_uint64, U32P]),
             "orc_bfv_phase_q0": (None, [PP, I8P, U32P, U64P]),
             "orc_bfv_decrypt_q0": (None, [PP, I8P, U32P, U32P]),
+            "orc_automorphism": (None, [U32P, U32P, C.c_uint32, C.c_uint64, C.c_uint32]),
+            "orc_gadget_bits": (C.c_uint32, [PP, C.c_uint32]),
+            "orc_ksk_gen": (None, [PP, I8P, C.c_uint32, C.c_uint32, U32P, I8P, U32P]),
+            "orc_subs": (None, [PP, U32P, C.c_uint32, U32P, C.c_uint32, U32P]),
+            "orc_expand": (None, [PP, U32P, C.c_uint32, C.c_uint32, U32P, C.c_uint32, U32P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -294,6 +299,67 @@ def bfv_decrypt_q0(P: OrcParams, s, ct) -> np.ndarray:
     m = np.empty(P.n, dtype=np.uint32)
     lib().orc_bfv_decrypt_q0(C.byref(P), np.ascontiguousarray(s, dtype=np.int8), _u32(ct).reshape(-1), m)
     return m
+
+
+# --- query expansion -------------------------------------------------------
+
+def automorphism(a, q: int, g: int) -> np.ndarray:
+    """a(X) -> a(X^g) mod (X^n + 1, q), g odd."""
+    a = _u32(a)
+    out = np.empty_like(a)
+    lib().orc_automorphism(a, out, a.size, q, g)
+    return out
+
+
+def gadget_bits(P: OrcParams, ell: int) -> int:
+    """w with gadget base t = 2^w = 2^ceil(log2 q / ell)."""
+    return int(lib().orc_gadget_bits(C.byref(P), ell))
+
+
+def expansion_galois(n: int, levels: int):
+    """The substitution exponents g_j = n / 2^j + 1 of the expansion levels."""
+    return [n // (1 << j) + 1 for j in range(levels)]
+
+
+def ksk_gen(P: OrcParams, s, g: int, ell: int, a, e) -> np.ndarray:
+    """Key-switching key tau_g(s) -> s: [ell][2][L][n].  a [ell][L][n], e [ell][n]."""
+    out = np.empty((ell, 2, P.L, P.n), dtype=np.uint32)
+    lib().orc_ksk_gen(C.byref(P), np.ascontiguousarray(s, dtype=np.int8), g, ell, _u32(a).reshape(-1),
+                      np.ascontiguousarray(e, dtype=np.int8).reshape(-1), out.reshape(-1))
+    return out
+
+
+def expansion_keys(P: OrcParams, s, levels: int, ell: int, seed: int) -> np.ndarray:
+    """All expansion keys [levels][ell][2][L][n] from seeded client draws (masks from
+    STREAM_KEY_A, errors from STREAM_KEY_ERROR)."""
+    from paper_2606_11536_gb300 import synth
+    keys = np.empty((levels, ell, 2, P.L, P.n), dtype=np.uint32)
+    for j, g in enumerate(expansion_galois(P.n, levels)):
+        a = synth.uniform_residues(seed, synth.STREAM_KEY_A, ell, P.n, P.qs, start=j * ell)
+        e = synth.gaussian_error(seed, ell * P.n, start=j * ell * P.n, stream=synth.STREAM_KEY_ERROR).reshape(ell, P.n)
+        keys[j] = ksk_gen(P, s, g, ell, a, e)
+    return keys
+
+
+def subs(P: OrcParams, ct, g: int, ksk, ell: int) -> np.ndarray:
+    out = np.empty((2, P.L, P.n), dtype=np.uint32)
+    lib().orc_subs(C.byref(P), _u32(ct).reshape(-1), g, _u32(ksk).reshape(-1), ell, out.reshape(-1))
+    return out
+
+
+def expand(P: OrcParams, ct, levels: int, ell: int, keys, count: int) -> np.ndarray:
+    """Expansion of one packed ciphertext [2][L][n] into count ciphertexts [count][2][L][n]."""
+    out = np.empty((count, 2, P.L, P.n), dtype=np.uint32)
+    lib().orc_expand(C.byref(P), _u32(ct).reshape(-1), levels, ell, _u32(keys).reshape(-1), count, out.reshape(-1))
+    return out
+
+
+def encrypt_packed_query(P: OrcParams, s, a, e, i_star: int) -> np.ndarray:
+    """The packed first-dimension query: one ciphertext of m = X^i* (App. C.2),
+    which expands to the D1 ciphertexts Enc([i == i*]).  a [L][n], e [n]."""
+    m = np.zeros(P.n, dtype=np.uint32)
+    m[i_star] = 1
+    return bfv_encrypt(P, s, a, e, m)
 
 
 def encrypt_query(P: OrcParams, s, a, e, i_star: int) -> np.ndarray:

@@ -16,6 +16,9 @@
  *   - RLWE encryption / decryption with Delta = floor(q/p)            (App. A.2)
  *   - modulus switching q -> q_0: round(x q_0 / q) mod q_0, and decryption over
  *     the single prime q_0 afterwards                                 (App. D.5, Sec. 4.3)
+ *   - query expansion: substitutions tau_g, key switching with the base-t gadget
+ *     (t = 2^ceil(log2 q / ell)), SealPIR's recursive expansion with the
+ *     2^-levels pre-scaling                                         (Sec. 3.5, App. C.2, D.3)
  *   - first-dimension folding: out_c = sum_i DB[i][c] * ct_i in R_q^2 (Sec. 3.2, Sec. 4 "INT32
  *     modular GEMM", Sec. 4.2): in the NTT domain, for every prime q_j and slot k,
  *     out[b][c][k] = sum_i DB[i][c][k] * Q[b][i][k]  (mod q_j).
@@ -28,14 +31,21 @@
  *     poly, poly (i, c) at position i*D2 + c;
  *   - each query ciphertext contributes its a- and b-polynomial as two GEMM rows;
  *   - modulus switching keeps q_0, the largest prime (#RNS = 1, about 2^30), and
- *     rounds to nearest.
+ *     rounds to nearest;
+ *   - expansion level j substitutes with g = n/2^j + 1 and keeps the SealPIR index
+ *     order (c + Subs(c) at k, c X^-2^j + Subs(.) at k + 2^j); the gadget digits are
+ *     those of the CRT lift of each coefficient in [0, q).
  *
  * Parity: pinned.  The tests check this file against primality by an independent
  * library, the defining congruences, the NTT evaluated by its definition, schoolbook
  * negacyclic multiplication, the convolution theorem, and the BFV decryption
  * invariant (decrypting the answer returns exactly the requested record); modulus
  * switching against values built as t Q' + r, the rounding-error bound of App. D.5
- * and decryption after the switch.
+ * and decryption after the switch; substitution against polynomial evaluation at
+ * the primitive 2n-th roots and the ring-automorphism laws, key switching and
+ * expansion against decryption (every coefficient, with the exact aliasing above
+ * 2^levels) and worst-case noise bounds, and an expanded query that answers and
+ * decrypts.
  */
 #include <pthread.h>
 #include <stdint.h>
@@ -775,4 +785,171 @@ void orc_bfv_decrypt_q0(const orc_params *P, const int8_t *s, const u32 *ct, u32
     m_out[t] = (u32)((u64)(num / (2 * (u128)q)) & pmask);
   }
   free(phi);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Server-side query expansion (Sec. 3.5; App. C.2; decomposition of App. D.3) */
+/* ------------------------------------------------------------------------- */
+
+/* tau_g: a(X) -> a(X^g) in Z_q[X]/(X^n + 1), g odd.  Coefficient t moves to
+ * e = t g mod 2n, negated when e >= n (X^n = -1). */
+void orc_automorphism(const u32 *a, u32 *out, u32 n, u64 q, u32 g) {
+  for (u32 t = 0; t < n; t++) {
+    const u64 e = (u64)t * g % (2ull * n);
+    if (e < n)
+      out[e] = a[t];
+    else
+      out[e - n] = (u32)((q - a[t]) % q);
+  }
+}
+
+/* out = a X^-k in Z_q[X]/(X^n + 1), 0 <= k < n: coefficient t goes to t - k, or to
+ * t - k + n negated (X^(t-k) = -X^(t-k+n)). */
+static void monomial_div(const u32 *a, u32 *out, u32 n, u64 q, u32 k) {
+  for (u32 t = 0; t < n; t++) {
+    if (t >= k)
+      out[t - k] = a[t];
+    else
+      out[t + n - k] = (u32)((q - a[t]) % q);
+  }
+}
+
+/* Gadget of the expansion keys (App. D.3): base t = 2^w with w = ceil(log2 q / ell),
+ * ell digits; x in [0, q) is sum_k d_k t^k with d_k = (x >> (w k)) mod t. */
+u32 orc_gadget_bits(const orc_params *P, u32 ell) {
+  const u128 q = full_modulus(P);
+  u32 bits = 0;
+  while (bits < 128 && ((u128)1 << bits) < q) bits++; /* ceil(log2 q) */
+  return (bits + ell - 1) / ell;
+}
+
+/* Key-switching key from s' = tau_g(s) to s: for k < ell, ksk[k] = (a_k, b_k) with
+ * a_k s + b_k = t^k s' + e_k (mod q), i.e. b_k = t^k s' + e_k - a_k s.  a [ell][L][n]
+ * (uniform residues) and e [ell][n] are the caller's draws; ksk [ell][2][L][n],
+ * coefficient form. */
+void orc_ksk_gen(const orc_params *P, const int8_t *s, u32 g, u32 ell, const u32 *a, const int8_t *e, u32 *ksk) {
+  const u32 n = P->n, L = P->L, w = orc_gadget_bits(P, ell);
+  u32 *sj = (u32 *)calloc(n, sizeof(u32));
+  u32 *sg = (u32 *)calloc(n, sizeof(u32));
+  u32 *as = (u32 *)calloc(n, sizeof(u32));
+  for (u32 k = 0; k < ell; k++)
+    for (u32 j = 0; j < L; j++) {
+      const u64 q = P->q[j];
+      const u64 tk = (u64)(((u128)1 << (w * k)) % q); /* t^k mod q_j (w k < 128) */
+      for (u32 t = 0; t < n; t++) sj[t] = (u32)((s[t] + (i128)q) % q);
+      orc_automorphism(sj, sg, n, q, g);
+      const u32 *ak = a + ((u64)k * L + j) * n;
+      ring_mul(ak, sj, as, n, q, P->psi[j]);
+      u32 *ka = ksk + (((u64)k * 2 + 0) * L + j) * n;
+      u32 *kb = ksk + (((u64)k * 2 + 1) * L + j) * n;
+      for (u32 t = 0; t < n; t++) {
+        const u64 et = (u64)((e[(u64)k * n + t] + (i128)q) % q);
+        ka[t] = ak[t];
+        kb[t] = (u32)submod(addmod(mulmod(tk, sg[t], q), et, q), as[t], q);
+      }
+    }
+  free(sj);
+  free(sg);
+  free(as);
+}
+
+/* Key switching of ct [2][L][n] (coefficient form, under s') to s: the a-part is
+ * written in the gadget, a = sum_k d_k t^k with digit polynomials d_k of the CRT
+ * lift of every coefficient, and the result is (sum_k d_k a_k, b + sum_k d_k b_k). */
+static void key_switch(const orc_params *P, const u32 *ct, const u32 *ksk, u32 ell, u32 *out) {
+  const u32 n = P->n, L = P->L, w = orc_gadget_bits(P, ell);
+  u32 *d = (u32 *)calloc((size_t)ell * n, sizeof(u32));
+  u32 *prod = (u32 *)calloc(n, sizeof(u32));
+  const u128 mask = ((u128)1 << w) - 1;
+  for (u32 t = 0; t < n; t++) {
+    const u128 x = crt_lift(P, ct + t, n); /* a-part rows [L][n] */
+    for (u32 k = 0; k < ell; k++) d[(u64)k * n + t] = (u32)((x >> (w * k)) & mask);
+  }
+  for (u32 j = 0; j < L; j++) {
+    const u64 q = P->q[j];
+    u32 *oa = out + (u64)j * n, *ob = out + ((u64)L + j) * n;
+    for (u32 t = 0; t < n; t++) {
+      oa[t] = 0;
+      ob[t] = ct[((u64)L + j) * n + t];
+    }
+    for (u32 k = 0; k < ell; k++) {
+      u32 *dk = (u32 *)calloc(n, sizeof(u32));
+      for (u32 t = 0; t < n; t++) dk[t] = (u32)(d[(u64)k * n + t] % q);
+      ring_mul(dk, ksk + (((u64)k * 2 + 0) * L + j) * n, prod, n, q, P->psi[j]);
+      for (u32 t = 0; t < n; t++) oa[t] = (u32)addmod(oa[t], prod[t], q);
+      ring_mul(dk, ksk + (((u64)k * 2 + 1) * L + j) * n, prod, n, q, P->psi[j]);
+      for (u32 t = 0; t < n; t++) ob[t] = (u32)addmod(ob[t], prod[t], q);
+      free(dk);
+    }
+  }
+  free(d);
+  free(prod);
+}
+
+/* Subs(ct, g): tau_g on both components (the result decrypts under tau_g(s)), then
+ * key switching back to s with that substitution's key.  ct, out [2][L][n]. */
+void orc_subs(const orc_params *P, const u32 *ct, u32 g, const u32 *ksk, u32 ell, u32 *out) {
+  const u32 n = P->n, L = P->L;
+  u32 *tmp = (u32 *)calloc((size_t)2 * L * n, sizeof(u32));
+  for (u32 c = 0; c < 2; c++)
+    for (u32 j = 0; j < L; j++)
+      orc_automorphism(ct + ((u64)c * L + j) * n, tmp + ((u64)c * L + j) * n, n, P->q[j], g);
+  key_switch(P, tmp, ksk, ell, out);
+  free(tmp);
+}
+
+/* Query expansion, SealPIR's recursion as App. C.2 applies it.  ct [2][L][n]
+ * encrypts sum_i m_i X^i (i < 2^levels <= n).  It is first multiplied by
+ * 2^-levels mod q.  Level j = 0 .. levels-1 maps each of the 2^j ciphertexts c_k to
+ *     c_k + Subs(c_k, n/2^j + 1)                at index k,
+ *     c'  + Subs(c',  n/2^j + 1), c' = c_k X^-2^j   at index k + 2^j,
+ * so that ciphertext i finally encrypts m_i as a constant polynomial.  ksk
+ * [levels][ell][2][L][n] holds level j's key (g = n/2^j + 1) at index j.  out
+ * [count][2][L][n] receives ciphertexts 0 .. count-1 (count <= 2^levels). */
+void orc_expand(const orc_params *P, const u32 *ct, u32 levels, u32 ell, const u32 *ksk, u32 count, u32 *out) {
+  const u32 n = P->n, L = P->L;
+  const u64 csz = (u64)2 * L * n;
+  const u64 total = 1ull << levels;
+  u32 *cur = (u32 *)calloc(total * csz, sizeof(u32));
+  u32 *nxt = (u32 *)calloc(total * csz, sizeof(u32));
+  u32 *c1 = (u32 *)calloc(csz, sizeof(u32));
+  u32 *sb = (u32 *)calloc(csz, sizeof(u32));
+  for (u32 j = 0; j < L; j++) {
+    const u64 q = P->q[j];
+    const u64 inv = invmod_prime(orc_powmod(2, levels, q), q);
+    for (u32 c = 0; c < 2; c++)
+      for (u32 t = 0; t < n; t++) {
+        const u64 i = ((u64)c * L + j) * n + t;
+        cur[i] = (u32)mulmod(ct[i], inv, q);
+      }
+  }
+  for (u32 lev = 0; lev < levels; lev++) {
+    const u64 C = 1ull << lev;
+    const u32 g = (n >> lev) + 1;
+    const u32 *key = ksk + (u64)lev * ell * csz;
+    for (u64 k = 0; k < C; k++) {
+      const u32 *c0 = cur + k * csz;
+      for (u32 c = 0; c < 2; c++)
+        for (u32 j = 0; j < L; j++)
+          monomial_div(c0 + ((u64)c * L + j) * n, c1 + ((u64)c * L + j) * n, n, P->q[j], (u32)C);
+      for (u32 br = 0; br < 2; br++) {
+        const u32 *src = br ? c1 : c0;
+        u32 *dst = nxt + (k + br * C) * csz;
+        orc_subs(P, src, g, key, ell, sb);
+        for (u32 c = 0; c < 2; c++)
+          for (u32 j = 0; j < L; j++) {
+            const u64 q = P->q[j], o = ((u64)c * L + j) * n;
+            for (u32 t = 0; t < n; t++) dst[o + t] = (u32)addmod(src[o + t], sb[o + t], q);
+          }
+      }
+    }
+    u32 *sw = cur;
+    cur = nxt;
+    nxt = sw;
+  }
+  memcpy(out, cur, sizeof(u32) * count * csz);
+  free(cur);
+  free(nxt);
+  free(c1);
+  free(sb);
 }

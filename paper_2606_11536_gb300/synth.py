@@ -32,6 +32,8 @@ STREAM_A = 4
 STREAM_ERROR = 5
 STREAM_FREIVALDS = 6
 STREAM_UNIFORM = 7
+STREAM_KEY_A = 8      # expansion-key masks
+STREAM_KEY_ERROR = 9  # expansion-key errors
 
 _MASK64 = (1 << 64) - 1
 
@@ -104,11 +106,12 @@ def _gaussian_thresholds(sigma: float, bound: int) -> np.ndarray:
     return np.array(th, dtype=np.uint64)
 
 
-def gaussian_error(seed: int, count: int, start: int = 0, sigma: float = 3.2, bound: int = 19) -> np.ndarray:
+def gaussian_error(seed: int, count: int, start: int = 0, sigma: float = 3.2, bound: int = 19,
+                   stream: int = STREAM_ERROR) -> np.ndarray:
     """Discrete Gaussian draws with standard deviation sigma, clipped to |e| <= bound
     (App. A.1: sigma = 3.2, |e| < 6 sigma), by inversion of the cumulative table."""
     th = _gaussian_thresholds(sigma, bound)
-    u = u64(seed, STREAM_ERROR, start, count)
+    u = u64(seed, stream, start, count)
     k = np.searchsorted(th, u, side="right")
     k = np.minimum(k, 2 * bound)
     return (k.astype(np.int16) - bound).astype(np.int8)

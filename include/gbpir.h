@@ -207,6 +207,50 @@ pir_status_t ntt_inv(const pir_params_t *params, uint32_t *polys, size_t count, 
 pir_status_t ntt_inv_modswitch(const pir_params_t *params, const uint32_t *in, size_t count, uint32_t *out,
                                void *stream);
 
+/* Server-side query expansion (Sec. 3.5, "ExpPack" expansion; App. C.2, SealPIR's
+ * recursive expansion after pre-scaling by 2^-levels; App. D.3, expansion keys with
+ * ell gadget digits of base t = 2^ceil(log2 q / ell)).  A client sends one packed
+ * ciphertext per query, an encryption of m = sum_i m_i X^i, instead of D1
+ * ciphertexts; the server expands it into D1 ciphertexts that each encrypt m_i as
+ * a constant polynomial (a one-hot first-dimension query packs m = X^i*).
+ *
+ * pir_expander_create loads a client's expansion keys: keys[levels][ell][2][L][n]
+ * uint32, coefficient form, canonical; key j switches from tau_g(s) to s for
+ * g = n / 2^j + 1 (App. C.2's level j), key digit k is an encryption of t^k tau_g(s)
+ * (a_k s + b_k = t^k tau_g(s) + e_k).  Host or device memory (keys_on_device); the
+ * call copies them, turns them to NTT form and synchronizes `stream`.  levels is
+ * the expansion depth (2^levels <= n; a DB needs 2^levels >= D1); ell the digit
+ * count, with t = 2^w, w = ceil(ceil(log2 q) / ell) <= 30.  The handle owns device
+ * memory until pir_expander_free.
+ * Errors: PIR_ERR_ARG (NULL, invalid params, levels or ell out of range), PIR_ERR_OOM,
+ * PIR_ERR_CUDA. */
+typedef struct pir_expander *pir_expander_t;
+pir_status_t pir_expander_create(const pir_params_t *params, uint32_t levels, uint32_t ell, const uint32_t *keys,
+                                 int keys_on_device, void *stream, pir_expander_t *out);
+pir_status_t pir_expander_free(pir_expander_t expander);
+
+/* Expand B packed ciphertexts, packed [B][2][L][n] (coefficient form, canonical,
+ * device memory), into out [B][count][2][L][n] (coefficient form, canonical, device
+ * memory; count <= 2^levels): out[b][i] encrypts coefficient i of query b's packed
+ * message.  Asynchronous on stream; scratch from the stream-ordered allocator.
+ * Errors: PIR_ERR_HANDLE, PIR_ERR_ARG (NULL or misaligned buffers, B = 0, count out
+ * of range), PIR_ERR_OOM, PIR_ERR_CUDA. */
+pir_status_t pir_expand(pir_expander_t expander, const uint32_t *packed, uint32_t B, uint32_t count, uint32_t *out,
+                        void *stream);
+
+/* pir_answer for packed queries: expands packed [B][2][L][n] into the D1 query
+ * ciphertexts of every query (in NTT form, on the device) and answers them; the
+ * responses are those pir_answer_ex gives for the expanded queries, [B][D2][2][L][n]
+ * (or [B][D2][2][n] with PIR_ANSWER_MODSWITCH).  on_device as for pir_answer.  opts
+ * as for pir_answer_ex, except that k_chunk must be 0 or >= D1 (the expanded queries
+ * are whole) and PIR_ANSWER_TEST_STALL is refused; with PIR_ANSWER_STAGE_TIMES the
+ * expansion counts as stage 0.  The expander's ring must be the DB's.
+ * Errors: PIR_ERR_HANDLE, PIR_ERR_ARG (mismatched ring, 2^levels < D1, bad buffers or
+ * options), PIR_ERR_UNSUPPORTED (limb layout with D1 not a multiple of 32 or above
+ * 8192), PIR_ERR_OOM, PIR_ERR_CUDA. */
+pir_status_t pir_answer_packed(pir_db_t db, pir_expander_t expander, const uint32_t *packed, uint32_t B,
+                               uint32_t *responses, int on_device, void *stream, const pir_answer_opts_t *opts);
+
 /* Release a DB handle and its device memory (synchronizes the device first). */
 pir_status_t pir_free_db(pir_db_t db);
 

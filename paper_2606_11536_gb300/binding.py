@@ -92,6 +92,10 @@ def lib():
             "pir_graph_destroy": (i32, [vp]),
             "pir_autotune": (i32, [vp, u32, vp, u32, C.POINTER(pir_answer_opts_t)]),
             "pir_answer_noalloc": (i32, [vp, vp, u32, vp, vp]),
+            "pir_expander_create": (i32, [P, u32, u32, vp, i32, vp, C.POINTER(vp)]),
+            "pir_expander_free": (i32, [vp]),
+            "pir_expand": (i32, [vp, vp, u32, u32, vp, vp]),
+            "pir_answer_packed": (i32, [vp, vp, vp, u32, vp, i32, vp, C.POINTER(pir_answer_opts_t)]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(L, name)
@@ -222,6 +226,50 @@ def ntt_inv_modswitch(params: pir_params_t, polys, out, count: int | None = None
     cnt = nbytes // (4 * params.L * params.n) if count is None else count
     _check(lib().ntt_inv_modswitch(C.byref(params), ip, cnt, op, _stream_ptr(stream)), "ntt_inv_modswitch")
     return out
+
+
+class Expander:
+    """A client's expansion keys loaded on the device (pir_expander_t)."""
+
+    def __init__(self, handle: int, params: pir_params_t, levels: int, ell: int):
+        self.handle, self.params, self.levels, self.ell = handle, params, levels, ell
+
+
+def pir_expander_create(params: pir_params_t, levels: int, ell: int, keys, stream=None) -> Expander:
+    """keys [levels][ell][2][L][n] (coefficient form), host array or device tensor."""
+    kp, kdev, _ = _ptr(keys)
+    h = C.c_void_p()
+    _check(lib().pir_expander_create(C.byref(params), levels, ell, kp, int(kdev), _stream_ptr(stream), C.byref(h)),
+           "pir_expander_create")
+    return Expander(h.value, params, levels, ell)
+
+
+def pir_expander_free(ex: Expander):
+    _check(lib().pir_expander_free(C.c_void_p(ex.handle)), "pir_expander_free")
+    ex.handle = None
+
+
+def pir_expand(ex: Expander, packed, B: int, count: int, out, stream=None):
+    """Expand packed [B][2][L][n] into out [B][count][2][L][n] (device buffers)."""
+    pp, pdev, _ = _ptr(packed)
+    op, odev, _ = _ptr(out)
+    if not (pdev and odev):
+        raise ValueError("pir_expand works on device buffers")
+    _check(lib().pir_expand(C.c_void_p(ex.handle), pp, B, count, op, _stream_ptr(stream)), "pir_expand")
+    return out
+
+
+def pir_answer_packed(db: Db, ex: Expander, packed, B: int, responses, stream=None, k_chunk: int = 0, tile: int = 0,
+                      flags: int = 0):
+    """pir_answer for packed queries [B][2][L][n]: expansion, then the scan."""
+    pp, pdev, _ = _ptr(packed)
+    rp, rdev, _ = _ptr(responses)
+    if pdev != rdev:
+        raise ValueError("packed queries and responses must both be host or both be device buffers")
+    o = pir_answer_opts_t(k_chunk, tile, flags)
+    _check(lib().pir_answer_packed(C.c_void_p(db.handle), C.c_void_p(ex.handle), pp, B, rp, int(pdev),
+                                   _stream_ptr(stream), C.byref(o)), "pir_answer_packed")
+    return responses
 
 
 def pir_free_db(db: Db):

@@ -171,8 +171,10 @@ struct StageTimer {
 };
 
 // The device-buffer answer (stream ordered).
+// qhat_ready: when set, the queries are already in NTT form for the whole of D1
+// ([B][D1][2][L][n], e.g. from query expansion): no forward NTT, no K-chunking.
 pir_status_t answer_device(pir_db *db, const uint32_t *queries, uint32_t B, uint32_t *responses, cudaStream_t s,
-                           const pir_answer_opts_t &o) {
+                           const pir_answer_opts_t &o, const uint32_t *qhat_ready = nullptr) {
   const ParamCtx &c = *db->ctx;
   const pir_params_t &p = db->p;
   const uint32_t n = p.n, L = p.L, D1 = p.D1, D2 = p.D2;
@@ -180,8 +182,8 @@ pir_status_t answer_device(pir_db *db, const uint32_t *queries, uint32_t B, uint
   const uint32_t M = 2 * B;
   // plain rows pad to 4 (128-bit loads); limb rows pad to 16 (m16 tensor tiles)
   const uint32_t Mp = limb ? (M + 15u) & ~15u : round4(M);
-  uint32_t Kc = (o.k_chunk == 0 || o.k_chunk >= D1) ? D1 : o.k_chunk;
-  if (o.k_chunk == 0) {
+  uint32_t Kc = (o.k_chunk == 0 || o.k_chunk >= D1 || qhat_ready) ? D1 : o.k_chunk;
+  if (o.k_chunk == 0 && !qhat_ready) {
     // Stream-wise buffering (Sec. 4.4): when the scratch for all of D1 would not fit
     // half of the free device memory, fold D1 in as many equal chunks as needed.
     size_t free_b = 0, total_b = 0;
@@ -201,6 +203,7 @@ pir_status_t answer_device(pir_db *db, const uint32_t *queries, uint32_t B, uint
     if (Kc > 8192) Kc = 8192;
     Kc &= ~31u;
     if (Kc == 0) Kc = 32;
+    if (qhat_ready && Kc != D1) return PIR_ERR_UNSUPPORTED;
   }
   const uint64_t nslots = (uint64_t)L * n;
   const uint32_t tile_count = db->layout == PIR_LAYOUT_PLAIN ? gemm_plain_tiles() : gemm_limb_tiles();
@@ -214,14 +217,15 @@ pir_status_t answer_device(pir_db *db, const uint32_t *queries, uint32_t B, uint
     return PIR_ERR_ARG;
 
   // scratch: NTT'd query chunk | slot-major query chunk | slot-major results
-  const size_t qhat_bytes = (size_t)B * Kc * 2 * L * n * 4;
+  const size_t qhat_bytes = qhat_ready ? 0 : (size_t)B * Kc * 2 * L * n * 4;
   const size_t qs_bytes = limb ? nslots * 4 * Mp * Kc : nslots * Kc * Mp * 4;
   const size_t out_bytes = nslots * M * D2 * 4;
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
   // Batch 1 on the TMA scan: the forward NTT writes the slot layout itself (pairs of
   // a/b residues, Mp = 2) and the scan writes the response layout itself, so neither
   // transpose runs.
-  const bool fused = !limb && B == 1 && (o.tile == 0 || o.tile == 7) && scan_tma_supports(M, D2) && Kc % 2 == 0;
+  const bool fused =
+      !qhat_ready && !limb && B == 1 && (o.tile == 0 || o.tile == 7) && scan_tma_supports(M, D2) && Kc % 2 == 0;
   // full-modulus responses before switching: the unused result area on the fused
   // path (the same size at B = 1), an area of their own otherwise
   StageTimer tm((o.flags & PIR_ANSWER_STAGE_TIMES) != 0, s);
@@ -229,7 +233,7 @@ pir_status_t answer_device(pir_db *db, const uint32_t *queries, uint32_t B, uint
   Scratch scratch(s);
   CK(scratch.alloc(up(qhat_bytes) + up(qs_bytes) + up(out_bytes) + up(full_bytes)));
   char *base = static_cast<char *>(scratch.ptr);
-  uint32_t *qhat = reinterpret_cast<uint32_t *>(base);
+  const uint32_t *qhat = qhat_ready ? qhat_ready : reinterpret_cast<uint32_t *>(base);
   void *qs = base + up(qhat_bytes);
   uint32_t *out = reinterpret_cast<uint32_t *>(base + up(qhat_bytes) + up(qs_bytes));
   uint32_t *full = !msw ? responses
@@ -263,9 +267,12 @@ pir_status_t answer_device(pir_db *db, const uint32_t *queries, uint32_t B, uint
     // forward NTT of ciphertexts i0 .. i0+kc-1 of every query: per query b the rows
     // (b*D1 + i0)*2L .. +kc*2L are contiguous.
     const uint64_t G = (uint64_t)kc * 2 * L, S = (uint64_t)D1 * 2 * L;
-    tm.begin();
-    CK(launch_ntt_fwd_rows(c, queries, (uint64_t)i0 * 2 * L, G, S, qhat, (uint64_t)B * G, s));
-    tm.end(0, 1);
+    if (!qhat_ready) {
+      tm.begin();
+      CK(launch_ntt_fwd_rows(c, queries, (uint64_t)i0 * 2 * L, G, S, const_cast<uint32_t *>(qhat), (uint64_t)B * G,
+                             s));
+      tm.end(0, 1);
+    }
     if (db->layout == PIR_LAYOUT_PLAIN) {
       tm.begin();
       CK(launch_query_to_slots(c, qhat, B, kc, Mp, static_cast<uint32_t *>(qs), s));
@@ -481,6 +488,51 @@ pir_status_t pir_answer_ex(pir_db_t db, const uint32_t *queries, uint32_t B, uin
   }
   CK(cudaMemcpyAsync(responses, dr.ptr, rbytes, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  return PIR_OK;
+}
+
+pir_status_t pir_answer_packed(pir_db_t db, pir_expander_t expander, const uint32_t *packed, uint32_t B,
+                               uint32_t *responses, int on_device, void *stream, const pir_answer_opts_t *opts) {
+  if (!live(db)) return PIR_ERR_HANDLE;
+  const pir_expander_impl *ex = nullptr;
+  if (!expander_view(expander, &ex)) return PIR_ERR_HANDLE;
+  if (B == 0 || !packed || !responses) return PIR_ERR_ARG;
+  pir_answer_opts_t o = {};
+  if (opts) o = *opts;
+  const pir_params_t &p = db->p;
+  if (!expander_fits(ex, p)) return PIR_ERR_ARG;
+  if ((o.k_chunk != 0 && o.k_chunk < p.D1) || (o.flags & PIR_ANSWER_TEST_STALL)) return PIR_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t pbytes = (size_t)B * 2 * p.L * p.n * 4;
+  const size_t rbytes = (size_t)B * p.D2 * 2 * ((o.flags & PIR_ANSWER_MODSWITCH) ? 1 : p.L) * p.n * 4;
+  Scratch dp(s), dr(s), qh(s);
+  const uint32_t *pk = packed;
+  uint32_t *resp = responses;
+  if (on_device) {
+    if (!aligned16(packed) || !aligned16(responses)) return PIR_ERR_ARG;
+  } else {
+    CK(dp.alloc(pbytes));
+    CK(dr.alloc(rbytes));
+    CK(cudaMemcpyAsync(dp.ptr, packed, pbytes, cudaMemcpyHostToDevice, s));
+    pk = static_cast<const uint32_t *>(dp.ptr);
+    resp = static_cast<uint32_t *>(dr.ptr);
+  }
+  // the D1 expanded ciphertexts of every query, in NTT form
+  CK(qh.alloc((size_t)B * p.D1 * 2 * p.L * p.n * 4));
+  StageTimer tm((o.flags & PIR_ANSWER_STAGE_TIMES) != 0, s);
+  tm.begin();
+  uint64_t launches = 0;
+  pir_status_t st = expand_device(ex, pk, B, p.D1, static_cast<uint32_t *>(qh.ptr), s, &launches);
+  tm.end(0, launches);
+  if (st == PIR_OK) st = answer_device(db, nullptr, B, resp, s, o, static_cast<const uint32_t *>(qh.ptr));
+  if (st != PIR_OK) {
+    if (!on_device) cudaStreamSynchronize(s);
+    return st;
+  }
+  if (!on_device) {
+    CK(cudaMemcpyAsync(responses, dr.ptr, rbytes, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
   return PIR_OK;
 }
 

@@ -54,6 +54,15 @@ struct ParamCtx {
 pir_status_t validate_params(const pir_params_t *p);
 pir_status_t get_param_ctx(const pir_params_t *p, const ParamCtx **out);  // cached, device-resident tables
 
+// expand.cu: query expansion.  expand_device writes B x count expanded ciphertexts
+// [B][count][2][L][n] in NTT form from packed [B][2][L][n] (coefficient form) and
+// reports its kernel launches; expander_fits checks ring and depth against a DB.
+struct pir_expander_impl;
+bool expander_view(pir_expander_t h, const pir_expander_impl **out);
+bool expander_fits(const pir_expander_impl *ex, const pir_params_t &p);
+pir_status_t expand_device(const pir_expander_impl *ex, const uint32_t *packed, uint32_t B, uint32_t count,
+                           uint32_t *out, cudaStream_t s, uint64_t *launch_count);
+
 // Read-only view of a live DB handle (api.cu); false for unknown or freed handles.
 struct DbView {
   pir_params_t p;
@@ -77,6 +86,12 @@ cudaError_t launch_ntt_fwd(const ParamCtx &c, const uint32_t *src, uint32_t *dst
 cudaError_t launch_ntt_fwd_rows(const ParamCtx &c, const uint32_t *src, uint64_t off, uint64_t G, uint64_t S,
                                 uint32_t *dst, uint64_t rows, cudaStream_t s);
 cudaError_t launch_ntt_inv(const ParamCtx &c, const uint32_t *src, uint32_t *dst, uint64_t rows, cudaStream_t s);
+// Row-mapped variants: local row r (prime r % L) reads source row
+// off + (r / G) * S + (r % G) * T.
+cudaError_t launch_ntt_inv_rows(const ParamCtx &c, const uint32_t *src, uint64_t off, uint64_t G, uint64_t S,
+                                uint64_t T, uint32_t *dst, uint64_t rows, cudaStream_t s);
+cudaError_t launch_ntt_fwd_rows_t(const ParamCtx &c, const uint32_t *src, uint64_t off, uint64_t G, uint64_t S,
+                                  uint64_t T, uint32_t *dst, uint64_t rows, cudaStream_t s);
 // Inverse NTT of `count` RNS polynomials src [count][L][n] with modulus switching to
 // q_0 fused in: dst [count][n] over q_0.  src and dst must not overlap.
 cudaError_t launch_ntt_inv_switch(const ParamCtx &c, const uint32_t *src, uint32_t *dst, uint64_t count,

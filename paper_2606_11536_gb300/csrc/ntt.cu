@@ -64,9 +64,9 @@ struct RawSrc {
 
 // Source rows of a launch: local row r reads row off + (r / G) * S + r % G, so a
 // chunk of ciphertexts can be taken out of every query of a batch without a copy.
-struct RowMap {
-  uint64_t off, G, S;
-  __device__ __forceinline__ uint64_t operator()(uint64_t r) const { return off + (r / G) * S + r % G; }
+struct RowMap {  // local row r reads source row off + (r / G) * S + (r % G) * T
+  uint64_t off, G, S, T;
+  __device__ __forceinline__ uint64_t operator()(uint64_t r) const { return off + (r / G) * S + (r % G) * T; }
 };
 
 // Coefficient `t` of plaintext polynomial `poly` from the raw bit stream.
@@ -284,7 +284,8 @@ __global__ void __launch_bounds__((1 << LOGN) / 16, 16384 >> LOGN)  // >= 1024 t
 
 template <int LOGN>
 __global__ void __launch_bounds__((1 << LOGN) / 16, 16384 >> LOGN)  // >= 1024 threads per SM
-    k_ntt_inv(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst, NttConst C, uint32_t L, uint64_t rows) {
+    k_ntt_inv(const uint32_t *__restrict__ src, RowMap rm, uint32_t *__restrict__ dst, NttConst C, uint32_t L,
+              uint64_t rows) {
   constexpr int N = 1 << LOGN;
   extern __shared__ uint32_t sm[];
   const RawSrc rs = {};
@@ -292,7 +293,7 @@ __global__ void __launch_bounds__((1 << LOGN) / 16, 16384 >> LOGN)  // >= 1024 t
     const uint32_t j = (uint32_t)(row % L);
     const uint32_t q = pick(C.q, j), ni = pick(C.ninv, j), nis = pick(C.ninv_sh, j);
     const uint2 *tw = pick(C.inv, j);
-    const uint32_t *gin = src + row * N;
+    const uint32_t *gin = src + rm(row) * N;
     uint32_t *gout = dst + row * N;
     if constexpr (LOGN == 11) {
       ntt_pass<11, 4, 0, false, SRC_U32, DST_SMEM>(sm, gin, rs, 0, gout, tw, q, ni, nis);
@@ -483,11 +484,12 @@ cudaError_t fwd_launch(const ParamCtx &c, const uint32_t *src, const RowMap &rm,
 }
 
 template <int LOGN>
-cudaError_t inv_launch(const ParamCtx &c, const uint32_t *src, uint32_t *dst, uint64_t rows, cudaStream_t s) {
+cudaError_t inv_launch(const ParamCtx &c, const uint32_t *src, const RowMap &rm, uint32_t *dst, uint64_t rows,
+                       cudaStream_t s) {
   const int T = (1 << LOGN) / 16;
   const size_t smem = ((1u << LOGN) + (1u << LOGN) / 16) * sizeof(uint32_t);
   const unsigned grid = (unsigned)(rows < kMaxGrid ? rows : kMaxGrid);
-  k_ntt_inv<LOGN><<<grid, T, smem, s>>>(src, dst, c.ntt, c.p.L, rows);
+  k_ntt_inv<LOGN><<<grid, T, smem, s>>>(src, rm, dst, c.ntt, c.p.L, rows);
   return cudaGetLastError();
 }
 
@@ -506,14 +508,14 @@ cudaError_t fwd_any(const ParamCtx &c, const uint32_t *src, const RowMap &rm, co
 
 cudaError_t launch_ntt_fwd(const ParamCtx &c, const uint32_t *src, uint32_t *dst, uint64_t rows, cudaStream_t s) {
   const RawSrc rs = {};
-  const RowMap rm = {0, rows ? rows : 1, 0};
+  const RowMap rm = {0, rows ? rows : 1, 0, 1};
   return fwd_any(c, src, rm, rs, dst, rows, s, false);
 }
 
 cudaError_t launch_ntt_fwd_rows(const ParamCtx &c, const uint32_t *src, uint64_t off, uint64_t G, uint64_t S,
                                 uint32_t *dst, uint64_t rows, cudaStream_t s) {
   const RawSrc rs = {};
-  const RowMap rm = {off, G, S};
+  const RowMap rm = {off, G, S, 1};
   return fwd_any(c, src, rm, rs, dst, rows, s, false);
 }
 
@@ -529,7 +531,7 @@ cudaError_t launch_ntt_fwd_raw(const ParamCtx &c, const uint8_t *raw, int col_ma
     rs.c0 = first;
   else
     rs.poly0 = first;
-  const RowMap rm = {0, 1, 1};
+  const RowMap rm = {0, 1, 1, 1};
   return fwd_any(c, nullptr, rm, rs, dst, npolys * c.p.L, s, true);
 }
 
@@ -585,12 +587,32 @@ cudaError_t launch_ntt_inv_switch(const ParamCtx &c, const uint32_t *src, uint32
 
 cudaError_t launch_ntt_inv(const ParamCtx &c, const uint32_t *src, uint32_t *dst, uint64_t rows, cudaStream_t s) {
   if (rows == 0) return cudaSuccess;
+  const RowMap rm = {0, rows, 0, 1};
   switch (c.logn) {
-    case 11: return inv_launch<11>(c, src, dst, rows, s);
-    case 12: return inv_launch<12>(c, src, dst, rows, s);
-    case 13: return inv_launch<13>(c, src, dst, rows, s);
+    case 11: return inv_launch<11>(c, src, rm, dst, rows, s);
+    case 12: return inv_launch<12>(c, src, rm, dst, rows, s);
+    case 13: return inv_launch<13>(c, src, rm, dst, rows, s);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_ntt_inv_rows(const ParamCtx &c, const uint32_t *src, uint64_t off, uint64_t G, uint64_t S,
+                                uint64_t T, uint32_t *dst, uint64_t rows, cudaStream_t s) {
+  if (rows == 0) return cudaSuccess;
+  const RowMap rm = {off, G, S, T};
+  switch (c.logn) {
+    case 11: return inv_launch<11>(c, src, rm, dst, rows, s);
+    case 12: return inv_launch<12>(c, src, rm, dst, rows, s);
+    case 13: return inv_launch<13>(c, src, rm, dst, rows, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_ntt_fwd_rows_t(const ParamCtx &c, const uint32_t *src, uint64_t off, uint64_t G, uint64_t S,
+                                  uint64_t T, uint32_t *dst, uint64_t rows, cudaStream_t s) {
+  const RawSrc rs = {};
+  const RowMap rm = {off, G, S, T};
+  return fwd_any(c, src, rm, rs, dst, rows, s, false);
 }
 
 }  // namespace gbpir

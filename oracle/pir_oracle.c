@@ -34,7 +34,9 @@
  *     rounds to nearest;
  *   - expansion level j substitutes with g = n/2^j + 1 and keeps the SealPIR index
  *     order (c + Subs(c) at k, c X^-2^j + Subs(.) at k + 2^j); the gadget digits are
- *     those of the CRT lift of each coefficient in [0, q).
+ *     those of the CRT lift in [0, q) of each coefficient of the level's input
+ *     a-part, moved (with their signs) by the same shift and substitution as the
+ *     ciphertext, so a moved digit lies in (-t, t).
  *
  * Parity: pinned.  The tests check this file against primality by an independent
  * library, the defining congruences, the NTT evaluated by its definition, schoolbook
@@ -853,49 +855,77 @@ void orc_ksk_gen(const orc_params *P, const int8_t *s, u32 g, u32 ell, const u32
   free(as);
 }
 
-/* Key switching of ct [2][L][n] (coefficient form, under s') to s: the a-part is
- * written in the gadget, a = sum_k d_k t^k with digit polynomials d_k of the CRT
- * lift of every coefficient, and the result is (sum_k d_k a_k, b + sum_k d_k b_k). */
-static void key_switch(const orc_params *P, const u32 *ct, const u32 *ksk, u32 ell, u32 *out) {
-  const u32 n = P->n, L = P->L, w = orc_gadget_bits(P, ell);
-  u32 *d = (u32 *)calloc((size_t)ell * n, sizeof(u32));
-  u32 *prod = (u32 *)calloc(n, sizeof(u32));
+/* Gadget digits of a polynomial a [L][n] (coefficient form): d [ell][n] with
+ * d_k[t] = (x_t >> (w k)) mod 2^w for the CRT lift x_t in [0, q) of coefficient t,
+ * so that sum_k d_k t^k = a (App. D.3's decomposition). */
+static void gadget_digits(const orc_params *P, const u32 *a, u32 ell, u32 *d) {
+  const u32 n = P->n, w = orc_gadget_bits(P, ell);
   const u128 mask = ((u128)1 << w) - 1;
   for (u32 t = 0; t < n; t++) {
-    const u128 x = crt_lift(P, ct + t, n); /* a-part rows [L][n] */
+    const u128 x = crt_lift(P, a + t, n);
     for (u32 k = 0; k < ell; k++) d[(u64)k * n + t] = (u32)((x >> (w * k)) & mask);
   }
+}
+
+/* The key-switching sums (sum_k e_k K_k.a, b + sum_k e_k K_k.b) for digit
+ * polynomials e_k given as residues [ell][L][n]; b [L][n]; out [2][L][n]. */
+static void key_switch_sum(const orc_params *P, const u32 *e, const u32 *b, const u32 *ksk, u32 ell, u32 *out) {
+  const u32 n = P->n, L = P->L;
+  u32 *prod = (u32 *)calloc(n, sizeof(u32));
   for (u32 j = 0; j < L; j++) {
     const u64 q = P->q[j];
     u32 *oa = out + (u64)j * n, *ob = out + ((u64)L + j) * n;
     for (u32 t = 0; t < n; t++) {
       oa[t] = 0;
-      ob[t] = ct[((u64)L + j) * n + t];
+      ob[t] = b[(u64)j * n + t];
     }
     for (u32 k = 0; k < ell; k++) {
-      u32 *dk = (u32 *)calloc(n, sizeof(u32));
-      for (u32 t = 0; t < n; t++) dk[t] = (u32)(d[(u64)k * n + t] % q);
-      ring_mul(dk, ksk + (((u64)k * 2 + 0) * L + j) * n, prod, n, q, P->psi[j]);
+      const u32 *ek = e + ((u64)k * L + j) * n;
+      ring_mul(ek, ksk + (((u64)k * 2 + 0) * L + j) * n, prod, n, q, P->psi[j]);
       for (u32 t = 0; t < n; t++) oa[t] = (u32)addmod(oa[t], prod[t], q);
-      ring_mul(dk, ksk + (((u64)k * 2 + 1) * L + j) * n, prod, n, q, P->psi[j]);
+      ring_mul(ek, ksk + (((u64)k * 2 + 1) * L + j) * n, prod, n, q, P->psi[j]);
       for (u32 t = 0; t < n; t++) ob[t] = (u32)addmod(ob[t], prod[t], q);
-      free(dk);
     }
   }
-  free(d);
   free(prod);
 }
 
-/* Subs(ct, g): tau_g on both components (the result decrypts under tau_g(s)), then
- * key switching back to s with that substitution's key.  ct, out [2][L][n]. */
-void orc_subs(const orc_params *P, const u32 *ct, u32 g, const u32 *ksk, u32 ell, u32 *out) {
+/* Subs of (a X^-shift, b X^-shift) by g, with the decomposition taken of a itself:
+ * the digit polynomials of a are moved by the same signed permutations as the
+ * ciphertext (X^-shift, then tau_g), which keeps sum_k t^k tau_g(d_k X^-shift) =
+ * tau_g(a X^-shift) since both maps fix the constants t^k; the digits of the moved
+ * ciphertext are thus in (-t, t).  Then the key-switching sums.  ct, out [2][L][n]. */
+static void subs_shifted(const orc_params *P, const u32 *ct, u32 shift, u32 g, const u32 *ksk, u32 ell, u32 *out) {
   const u32 n = P->n, L = P->L;
-  u32 *tmp = (u32 *)calloc((size_t)2 * L * n, sizeof(u32));
-  for (u32 c = 0; c < 2; c++)
-    for (u32 j = 0; j < L; j++)
-      orc_automorphism(ct + ((u64)c * L + j) * n, tmp + ((u64)c * L + j) * n, n, P->q[j], g);
-  key_switch(P, tmp, ksk, ell, out);
+  u32 *d = (u32 *)calloc((size_t)ell * n, sizeof(u32));
+  u32 *e = (u32 *)calloc((size_t)ell * L * n, sizeof(u32));
+  u32 *bs = (u32 *)calloc((size_t)L * n, sizeof(u32));
+  u32 *tmp = (u32 *)calloc(n, sizeof(u32));
+  gadget_digits(P, ct, ell, d);
+  for (u32 j = 0; j < L; j++) {
+    const u64 q = P->q[j];
+    for (u32 k = 0; k < ell; k++) {
+      for (u32 t = 0; t < n; t++) tmp[t] = (u32)(d[(u64)k * n + t] % q);
+      u32 *ek = e + ((u64)k * L + j) * n;
+      monomial_div(tmp, ek, n, q, shift);
+      memcpy(tmp, ek, sizeof(u32) * n);
+      orc_automorphism(tmp, ek, n, q, g);
+    }
+    monomial_div(ct + ((u64)L + j) * n, tmp, n, q, shift);
+    orc_automorphism(tmp, bs + (u64)j * n, n, q, g);
+  }
+  key_switch_sum(P, e, bs, ksk, ell, out);
+  free(d);
+  free(e);
+  free(bs);
   free(tmp);
+}
+
+/* Subs(ct, g): the substitution X -> X^g (the result decrypts under tau_g(s)) with
+ * key switching back to s by that substitution's key; the gadget digits are those
+ * of ct's a-part, substituted along with it.  ct, out [2][L][n]. */
+void orc_subs(const orc_params *P, const u32 *ct, u32 g, const u32 *ksk, u32 ell, u32 *out) {
+  subs_shifted(P, ct, 0, g, ksk, ell, out);
 }
 
 /* Query expansion, SealPIR's recursion as App. C.2 applies it.  ct [2][L][n]
@@ -935,7 +965,8 @@ void orc_expand(const orc_params *P, const u32 *ct, u32 levels, u32 ell, const u
       for (u32 br = 0; br < 2; br++) {
         const u32 *src = br ? c1 : c0;
         u32 *dst = nxt + (k + br * C) * csz;
-        orc_subs(P, src, g, key, ell, sb);
+        /* Subs(c X^-C) with the digits of c's a-part shifted along (see subs_shifted) */
+        subs_shifted(P, c0, br ? (u32)C : 0, g, key, ell, sb);
         for (u32 c = 0; c < 2; c++)
           for (u32 j = 0; j < L; j++) {
             const u64 q = P->q[j], o = ((u64)c * L + j) * n;

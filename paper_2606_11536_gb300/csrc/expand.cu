@@ -12,15 +12,17 @@
 //
 // GPU design: ciphertexts stay in NTT form between levels.  In that form the
 // substitution is a permutation of slots (NTT(tau_g a)[k] = NTT(a)[perm(k)], no
-// arithmetic) and X^-2^j is a pointwise factor.  Only the gadget decomposition needs
-// coefficients, so each level is four launches over all ciphertexts of the level:
+// arithmetic) and X^-2^j is a pointwise factor.  The gadget digits are those of the
+// level's input a-part, moved by the same shift and substitution as the ciphertext
+// (signed digits in (-t, t); sum_k t^k tau_g(d_k X^-C) = tau_g(a X^-C)).  Moved
+// digits are permuted and scaled copies of NTT(d_k), so both branches share one
+// key-switching sum S[s] = sum_k NTT(d_k)[perm(s)] K_k[s]; branch 1 multiplies it by
+// NTT(X^-C)[perm(s)].  Each level is four launches over all its ciphertexts:
 //   1. inverse NTT of the a-parts;
-//   2. decomposition: for both branches, coefficient u of tau_g(a X^-(0 or 2^j)) is
-//      a signed gather of a, lifted to [0, q) by CRT (Garner, 128-bit), split into
-//      ell digits of w bits;
+//   2. decomposition: CRT lift of every coefficient (Garner, 128-bit) into ell
+//      digits of w bits;
 //   3. forward NTT of every digit row under every prime;
-//   4. multiply-accumulate with the key, plus the branch's own ciphertext and its
-//      permuted b-part, reduced once per output residue.
+//   4. the shared sums and both branches' outputs, reduced once per residue.
 #include <cstring>
 #include <mutex>
 #include <set>
@@ -61,113 +63,98 @@ __global__ void k_expand_scale(uint32_t *__restrict__ x, uint64_t words, uint32_
   }
 }
 
-// Digits of both branches.  acoef [cts][L][n] (coefficient form, canonical);
-// dig [cts][2][ell][n].  Thread = (ciphertext, coefficient u).
+// Gadget digits of the a-parts.  acoef [cts][L][n] (coefficient form, canonical);
+// dig [cts][ell][n].  Thread = (ciphertext, coefficient u).
 __global__ void k_expand_decompose(const uint32_t *__restrict__ acoef, uint64_t cts, uint32_t logn, uint32_t L,
-                                   uint32_t C, uint32_t ginv, uint32_t ell, uint32_t w, ExpConst E,
-                                   uint32_t *__restrict__ dig) {
+                                   uint32_t ell, uint32_t w, ExpConst E, uint32_t *__restrict__ dig) {
   const uint32_t n = 1u << logn;
   const uint64_t total = cts << logn;
   for (uint64_t idx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t ct = idx >> logn;
     const uint32_t u = (uint32_t)(idx & (n - 1));
-    // tau_g(y)[u] = +-y[t mod n] with t = u g^-1 mod 2n (negated when t >= n)
-    const uint32_t t = (uint32_t)(((uint64_t)u * ginv) & (2 * n - 1));
-    const uint32_t tt = t & (n - 1);
-    const bool neg_t = t >= n;
-    const uint32_t *a = acoef + ct * L * n;
+    const uint32_t *a = acoef + ct * L * n + u;
+    uint32_t x[PIR_MAX_L];
 #pragma unroll
-    for (uint32_t br = 0; br < 2; ++br) {
-      // branch 1 reads y = a X^-C: y[tt] = a[tt + C], or -a[tt + C - n] past the end
-      uint32_t src = tt;
-      bool neg = neg_t;
-      if (br) {
-        src = tt + C;
-        if (src >= n) src -= n, neg = !neg;
-      }
-      uint32_t x[PIR_MAX_L];
+    for (uint32_t i = 0; i < PIR_MAX_L; ++i) x[i] = i < L ? a[(uint64_t)i * n] : 0;
+    // Garner: x = a_0 + q_0 (a_1 + q_1 (a_2 + q_2 a_3)), a_k in [0, q_k)
 #pragma unroll
-      for (uint32_t i = 0; i < PIR_MAX_L; ++i) {
-        x[i] = 0;
-        if (i < L) {
-          const uint32_t v = a[(uint64_t)i * n + src];
-          const uint32_t q = E.q[i];
-          x[i] = (neg && v) ? q - v : v;
+    for (uint32_t k = 1; k < PIR_MAX_L; ++k) {
+      if (k < L) {
+        const uint32_t qk = E.q[k];
+        uint32_t v = x[k];
+#pragma unroll
+        for (uint32_t i = 0; i < k; ++i) {
+          const uint32_t ai = csub(x[i], qk);
+          v = csub(shoup_mul(v + qk - ai, E.gc[k][i], E.gc_sh[k][i], qk), qk);
         }
+        x[k] = v;
       }
-      // Garner: x = a_0 + q_0 (a_1 + q_1 (a_2 + q_2 a_3)), a_k in [0, q_k)
-#pragma unroll
-      for (uint32_t k = 1; k < PIR_MAX_L; ++k) {
-        if (k < L) {
-          const uint32_t qk = E.q[k];
-          uint32_t v = x[k];
-#pragma unroll
-          for (uint32_t i = 0; i < k; ++i) {
-            const uint32_t ai = csub(x[i], qk);
-            v = csub(shoup_mul(v + qk - ai, E.gc[k][i], E.gc_sh[k][i], qk), qk);
-          }
-          x[k] = v;
-        }
-      }
-      unsigned __int128 X = 0;
-#pragma unroll
-      for (int k = PIR_MAX_L - 1; k >= 0; --k)
-        if ((uint32_t)k < L) X = X * E.q[k] + x[k];
-      const uint32_t mask = (1u << w) - 1;
-      uint32_t *d = dig + ((ct * 2 + br) * ell) * n + u;
-      for (uint32_t k = 0; k < ell; ++k) d[(uint64_t)k * n] = (uint32_t)(X >> (w * k)) & mask;
     }
+    unsigned __int128 X = 0;
+#pragma unroll
+    for (int k = PIR_MAX_L - 1; k >= 0; --k)
+      if ((uint32_t)k < L) X = X * E.q[k] + x[k];
+    const uint32_t mask = (1u << w) - 1;
+    uint32_t *d = dig + ct * ell * n + u;
+    for (uint32_t k = 0; k < ell; ++k) d[(uint64_t)k * n] = (uint32_t)(X >> (w * k)) & mask;
   }
 }
 
-// Multiply-accumulate of one level.  cur [cts][2][L][n] (NTT form, the level's
-// inputs, C per query), dhat [cts][2][ell][L][n], key [ell][2][L][n], mon [L][n]
-// (NTT of X^-C) with Shoup companions, perm [n].  Output ciphertext (query b, index
-// k + br C) goes to out + (b * ostride + k + br C) * 2 L n when k + br C < olimit.
+// Key-switching sums and outputs of one level.  cur [cts][2][L][n] (NTT form, the
+// level's inputs, C per query), dhat [cts][ell][L][n], key [ell][2][L][n], mon [L][n]
+// (NTT of X^-C) with Shoup companions, perm [n].  Thread = (ciphertext, prime, slot s):
+//   S_a = sum_k dhat_k[perm(s)] K_k.a[s],  S_b likewise,
+//   branch 0 -> (a + S_a, b + b[p] + S_b),
+//   branch 1 -> (a m[s] + S_a m[p], b m[s] + (b[p] + S_b) m[p]),   p = perm(s), m = mon.
+// Output ciphertext (query b, index k) goes to out + (b * ostride + k) * 2 L n when
+// k < olimit.
 __global__ void k_expand_mac(const uint32_t *__restrict__ cur, const uint32_t *__restrict__ dhat,
                              const uint32_t *__restrict__ key, const uint32_t *__restrict__ mon,
                              const uint32_t *__restrict__ mon_sh, const uint32_t *__restrict__ perm, uint64_t cts,
                              uint32_t C, uint32_t logn, uint32_t L, uint32_t ell, uint32_t ostride, uint32_t olimit,
                              ExpConst E, uint32_t *__restrict__ out) {
   const uint32_t n = 1u << logn;
-  const uint64_t total = cts * 2 * L * (uint64_t)n;
+  const uint64_t total = cts * L * (uint64_t)n;
   for (uint64_t idx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t s = (uint32_t)(idx & (n - 1));
     const uint32_t i = (uint32_t)((idx >> logn) % L);
-    const uint64_t rest = (idx >> logn) / L;
-    const uint32_t br = (uint32_t)(rest & 1);
-    const uint64_t ct = rest >> 1;
+    const uint64_t ct = (idx >> logn) / L;
     const uint64_t b = ct / C;
-    const uint32_t k = (uint32_t)(ct % C) + br * C;
-    if (k >= olimit) continue;
+    const uint32_t k0 = (uint32_t)(ct % C), k1 = k0 + C;
+    if (k0 >= olimit) continue;
     const uint32_t q = pick4(E.q, i);
     const uint64_t mu = pick4(E.mu, i);
-    const uint32_t *ca = cur + ((ct * 2 + 0) * L + i) * n;
-    const uint32_t *cb = cur + ((ct * 2 + 1) * L + i) * n;
-    const uint32_t ps = __ldg(perm + s);
-    uint32_t a_own = ca[s], b_own = cb[s], b_sub = cb[ps];
-    if (br) {  // the branch's own ciphertext is c X^-C
-      const uint32_t *m = mon + (uint64_t)i * n, *msh = mon_sh + (uint64_t)i * n;
-      a_own = csub(shoup_mul(a_own, __ldg(m + s), __ldg(msh + s), q), q);
-      b_own = csub(shoup_mul(b_own, __ldg(m + s), __ldg(msh + s), q), q);
-      b_sub = csub(shoup_mul(b_sub, __ldg(m + ps), __ldg(msh + ps), q), q);
-    }
-    uint64_t acc_a = a_own, acc_b = (uint64_t)b_own + b_sub;
-    const uint32_t *dh = dhat + ((ct * 2 + br) * ell * L + i) * (uint64_t)n + s;
+    const uint32_t p = __ldg(perm + s);
+    const uint32_t *dh = dhat + (ct * ell * L + i) * (uint64_t)n + p;
     const uint32_t *ka = key + (uint64_t)i * n + s;  // key[d][comp][i][s]
-    const uint64_t kstride = 2ull * L * n;
+    const uint64_t kstride = 2ull * L * n, dstride = (uint64_t)L * n;
     const uint64_t k63 = (((uint64_t)1 << 63) / q) * q;
+    uint64_t acc_a = 0, acc_b = 0;
     for (uint32_t d = 0; d < ell; ++d) {
-      const uint32_t dv = dh[(uint64_t)d * L * n];
+      const uint32_t dv = dh[d * dstride];
       mac_wide(acc_a, dv, __ldg(ka + d * kstride));
-      mac_wide(acc_b, dv, __ldg(ka + d * kstride + (uint64_t)L * n));
+      mac_wide(acc_b, dv, __ldg(ka + d * kstride + dstride));
       if ((d & 7) == 7) acc_a = fold63(acc_a, k63), acc_b = fold63(acc_b, k63);
     }
-    uint32_t *o = out + ((b * ostride + k) * 2 * L + i) * (uint64_t)n + s;
-    o[0] = reduce64(acc_a, q, mu);
-    o[(uint64_t)L * n] = reduce64(acc_b, q, mu);
+    const uint32_t sa = reduce64(acc_a, q, mu), sb = reduce64(acc_b, q, mu);
+    const uint32_t *ca = cur + ((ct * 2 + 0) * L + i) * n;
+    const uint32_t *cb = cur + ((ct * 2 + 1) * L + i) * n;
+    const uint32_t a = ca[s], bs = cb[s], bp = cb[p];
+    const uint32_t tb = csub(bp + sb, q);  // b[p] + S_b
+    uint32_t *o0 = out + ((b * ostride + k0) * 2 * L + i) * (uint64_t)n + s;
+    o0[0] = csub(a + sa, q);
+    o0[dstride] = csub(bs + tb, q);
+    if (k1 < olimit) {
+      const uint32_t *m = mon + (uint64_t)i * n, *msh = mon_sh + (uint64_t)i * n;
+      const uint32_t ms = __ldg(m + s), mss = __ldg(msh + s), mp = __ldg(m + p), mps = __ldg(msh + p);
+      const uint32_t a1 = csub(csub(shoup_mul(a, ms, mss, q), q) + csub(shoup_mul(sa, mp, mps, q), q), q);
+      const uint32_t b1 = csub(csub(shoup_mul(bs, ms, mss, q), q) + csub(shoup_mul(tb, mp, mps, q), q), q);
+      uint32_t *o1 = out + ((b * ostride + k1) * 2 * L + i) * (uint64_t)n + s;
+      o1[0] = a1;
+      o1[dstride] = b1;
+    }
   }
 }
 
@@ -204,7 +191,6 @@ struct pir_expander_impl {
   uint32_t levels, ell, w;
   uint32_t *tables;  // one allocation: keys | mon | mon_sh | perm
   const uint32_t *keys, *mon, *mon_sh, *perm;
-  uint32_t ginv[32];
   ExpConst E;
 };
 
@@ -237,7 +223,7 @@ pir_status_t expand_device(const pir_expander_impl *ex, const uint32_t *packed, 
   const uint64_t full = 1ull << levels;           // ciphertexts per query after the last level
   const uint64_t half = full >> 1 ? full >> 1 : 1;
   // per query: two ciphertext buffers of `full`, a-coefficients, digits and their NTT
-  const uint64_t per_q = (2 * full * ctw + half * L * n + half * 2 * ell * n + half * 2 * ell * L * n) * 4;
+  const uint64_t per_q = (2 * full * ctw + half * L * n + half * ell * n + half * ell * L * n) * 4;
   size_t free_b = 0, total_b = 0;
   uint64_t budget = 1ull << 30;
   if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && free_b / 4 > budget) budget = free_b / 4;
@@ -251,7 +237,7 @@ pir_status_t expand_device(const pir_expander_impl *ex, const uint32_t *packed, 
   uint32_t *nxt = cur + Bc * full * ctw;
   uint32_t *acoef = nxt + Bc * full * ctw;
   uint32_t *dig = acoef + Bc * half * L * n;
-  uint32_t *dhat = dig + Bc * half * 2 * ell * n;
+  uint32_t *dhat = dig + Bc * half * ell * n;
   pir_status_t st = PIR_OK;
   auto ck = [&](cudaError_t err) {
     if (err != cudaSuccess && st == PIR_OK) st = cuda_status(err);
@@ -271,20 +257,19 @@ pir_status_t expand_device(const pir_expander_impl *ex, const uint32_t *packed, 
       const bool last = lev + 1 == levels;
       // 1. a-parts to coefficient form: local row r reads ciphertext r / L, prime r % L
       if (!ck(launch_ntt_inv_rows(c, cur, 0, L, 2ull * L, 1, acoef, cts * L, s))) break;
-      // 2. digits of both branches
-      k_expand_decompose<<<grid_for(cts * n, 256), 256, 0, s>>>(acoef, cts, logn, L, C, ex->ginv[lev], ell, ex->w,
-                                                                ex->E, dig);
+      // 2. gadget digits of the a-parts
+      k_expand_decompose<<<grid_for(cts * n, 256), 256, 0, s>>>(acoef, cts, logn, L, ell, ex->w, ex->E, dig);
       if (!ck(cudaGetLastError())) break;
       // 3. every digit row under every prime: local row r reads digit row r / L
-      if (!ck(launch_ntt_fwd_rows_t(c, dig, 0, L, 1, 0, dhat, cts * 2 * ell * L, s))) break;
+      if (!ck(launch_ntt_fwd_rows_t(c, dig, 0, L, 1, 0, dhat, cts * ell * L, s))) break;
       // 4. key products and sums
       const uint32_t *key = ex->keys + (uint64_t)lev * ell * ctw;
       const uint32_t *mon = ex->mon + (uint64_t)lev * L * n, *msh = ex->mon_sh + (uint64_t)lev * L * n;
       const uint32_t *perm = ex->perm + (uint64_t)lev * n;
       uint32_t *dst = last ? out + (uint64_t)b0 * count * ctw : nxt;
       const uint32_t ostride = last ? count : 2 * C, olimit = last ? count : 2 * C;
-      k_expand_mac<<<grid_for(cts * 2 * L * n, 256), 256, 0, s>>>(cur, dhat, key, mon, msh, perm, cts, C, logn, L,
-                                                                  ell, ostride, olimit, ex->E, dst);
+      k_expand_mac<<<grid_for(cts * L * n, 256), 256, 0, s>>>(cur, dhat, key, mon, msh, perm, cts, C, logn, L, ell,
+                                                              ostride, olimit, ex->E, dst);
       if (!ck(cudaGetLastError())) break;
       launches += 4;
       uint32_t *t = cur;
@@ -366,7 +351,6 @@ pir_status_t pir_expander_create(const pir_params_t *params, uint32_t levels, ui
   }
   for (uint32_t j = 0; j < levels; ++j) {
     const uint64_t g = (n >> j) + 1, two_n = 2ull * n;
-    ex->ginv[j] = (uint32_t)pow_mod64(g, n - 1, two_n);  // the unit group mod 2n has order n
     for (uint32_t k = 0; k < n; ++k) {
       const uint64_t e = (2ull * brv32(k, logn) + 1) * g % two_n;
       hperm[(uint64_t)j * n + k] = brv32((uint32_t)((e - 1) / 2), logn);

@@ -79,6 +79,7 @@ def lib():
             "orc_modswitch": (None, [PP, U32P, C.c_uint64, U32P]),
             "orc_bfv_phase_q0": (None, [PP, I8P, U32P, U64P]),
             "orc_bfv_decrypt_q0": (None, [PP, I8P, U32P, U32P]),
+            "orc_lwe_gemm": (None, [I8P, C.c_uint32, C.c_uint32, U32P, C.c_uint32, U32P]),
             "orc_automorphism": (None, [U32P, U32P, C.c_uint32, C.c_uint64, C.c_uint32]),
             "orc_gadget_bits": (C.c_uint32, [PP, C.c_uint32]),
             "orc_ksk_gen": (None, [PP, I8P, C.c_uint32, C.c_uint32, U32P, I8P, U32P]),
@@ -299,6 +300,20 @@ def bfv_decrypt_q0(P: OrcParams, s, ct) -> np.ndarray:
     m = np.empty(P.n, dtype=np.uint32)
     lib().orc_bfv_decrypt_q0(C.byref(P), np.ascontiguousarray(s, dtype=np.int8), _u32(ct).reshape(-1), m)
     return m
+
+
+# --- scalar-HE (LWE) DB GEMM ------------------------------------------------
+
+def lwe_gemm(A, Q) -> np.ndarray:
+    """out[b][i] = sum_j A[i][j] Q[b][j] mod 2^32; A [D1][D0] int8, Q [B][D0] uint32."""
+    A = np.ascontiguousarray(A, dtype=np.int8)
+    Q = _u32(Q)
+    D1, D0 = A.shape
+    B = Q.shape[0]
+    assert Q.shape == (B, D0)
+    out = np.empty((B, D1), dtype=np.uint32)
+    lib().orc_lwe_gemm(A.reshape(-1), D1, D0, Q.reshape(-1), B, out.reshape(-1))
+    return out
 
 
 # --- query expansion -------------------------------------------------------

@@ -16,6 +16,7 @@
  *   - RLWE encryption / decryption with Delta = floor(q/p)            (App. A.2)
  *   - modulus switching q -> q_0: round(x q_0 / q) mod q_0, and decryption over
  *     the single prime q_0 afterwards                                 (App. D.5, Sec. 4.3)
+ *   - scalar-HE (LWE) DB GEMM: out = DB Q^T mod 2^32 with an INT8 DB         (Sec. 2.5, 4.1, App. A.1)
  *   - query expansion: substitutions tau_g, key switching with the base-t gadget
  *     (t = 2^ceil(log2 q / ell)), SealPIR's recursive expansion with the
  *     2^-levels pre-scaling                                         (Sec. 3.5, App. C.2, D.3)
@@ -59,6 +60,7 @@ typedef uint32_t u32;
 typedef uint64_t u64;
 typedef unsigned __int128 u128;
 typedef __int128 i128;
+typedef int64_t i64;
 
 #define ORC_MAX_L 4
 
@@ -983,4 +985,23 @@ void orc_expand(const orc_params *P, const u32 *ct, u32 levels, u32 ell, const u
   free(nxt);
   free(c1);
   free(sb);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Scalar-HE (LWE) DB GEMM of the online SimplePIR step (Sec. 2.5, Sec. 4.1)  */
+/* ------------------------------------------------------------------------- */
+
+/* out[b][i] = sum_j A[i][j] * Q[b][j]  (mod 2^32): A [D1][D0] INT8 plaintexts (signed),
+ * Q [B][D0] the query ciphertexts' Z_{2^32} entries, out [B][D1].  Every product and
+ * sum is taken exactly in 64-bit arithmetic (D0 <= 2^24) and reduced mod 2^32 once
+ * per output. */
+void orc_lwe_gemm(const int8_t *A, u32 D1, u32 D0, const u32 *Q, u32 B, u32 *out) {
+  for (u32 b = 0; b < B; b++)
+    for (u32 i = 0; i < D1; i++) {
+      i64 acc = 0;
+      const int8_t *a = A + (u64)i * D0;
+      const u32 *q = Q + (u64)b * D0;
+      for (u32 j = 0; j < D0; j++) acc += (i64)a[j] * (i64)q[j]; /* |acc| < 2^7 2^32 2^24 */
+      out[(u64)b * D1 + i] = (u32)((u64)acc & 0xFFFFFFFFull);
+    }
 }

@@ -251,6 +251,26 @@ pir_status_t pir_expand(pir_expander_t expander, const uint32_t *packed, uint32_
 pir_status_t pir_answer_packed(pir_db_t db, pir_expander_t expander, const uint32_t *packed, uint32_t B,
                                uint32_t *responses, int on_device, void *stream, const pir_answer_opts_t *opts);
 
+/* Scalar-HE (LWE) DB GEMM of SimplePIR's online step (Sec. 2.5), built as Sec. 4.1
+ * builds it on the INT8 tensor pipe:
+ *     out[b][i] = sum_j db[i][j] * queries[b][j]   (mod 2^32)
+ *   db:      [D1][D0] int8 (signed plaintexts; the raw DB, no encoding), device.
+ *   queries: [B][D0] uint32 (the query ciphertexts' Z_2^32 entries), device.
+ *   out:     [B][D1] uint32, device, written.
+ * Each query word is split into four byte planes (prmt), each plane multiplied on
+ * the tensor pipe (mma.sync s8 x u8 -> s32, wrapping = mod 2^32) and the planes
+ * recombined by shifts.  path: PIR_LWE_TENSOR, PIR_LWE_SIMT (CUDA-core dp4a on the
+ * same byte planes), or PIR_LWE_AUTO (tensor from 8 queries up).  D0 must be a
+ * multiple of 16 and at most 2^24; buffers 16-byte aligned.  Asynchronous on
+ * stream; the caller owns every buffer.
+ * Errors: PIR_ERR_ARG (NULL or misaligned buffers, zero or unsupported sizes, unknown
+ * path), PIR_ERR_CUDA. */
+#define PIR_LWE_AUTO 0u
+#define PIR_LWE_TENSOR 1u
+#define PIR_LWE_SIMT 2u
+pir_status_t pir_lwe_answer(const int8_t *db, uint32_t D1, uint32_t D0, const uint32_t *queries, uint32_t B,
+                            uint32_t *out, uint32_t path, void *stream);
+
 /* Release a DB handle and its device memory (synchronizes the device first). */
 pir_status_t pir_free_db(pir_db_t db);
 

@@ -92,6 +92,7 @@ def lib():
             "pir_graph_destroy": (i32, [vp]),
             "pir_autotune": (i32, [vp, u32, vp, u32, C.POINTER(pir_answer_opts_t)]),
             "pir_answer_noalloc": (i32, [vp, vp, u32, vp, vp]),
+            "pir_lwe_answer": (i32, [vp, u32, u32, vp, u32, vp, u32, vp]),
             "pir_expander_create": (i32, [P, u32, u32, vp, i32, vp, C.POINTER(vp)]),
             "pir_expander_free": (i32, [vp]),
             "pir_expand": (i32, [vp, vp, u32, u32, vp, vp]),
@@ -225,6 +226,21 @@ def ntt_inv_modswitch(params: pir_params_t, polys, out, count: int | None = None
         raise ValueError("ntt_inv_modswitch works on device memory")
     cnt = nbytes // (4 * params.L * params.n) if count is None else count
     _check(lib().ntt_inv_modswitch(C.byref(params), ip, cnt, op, _stream_ptr(stream)), "ntt_inv_modswitch")
+    return out
+
+
+PIR_LWE_AUTO, PIR_LWE_TENSOR, PIR_LWE_SIMT = 0, 1, 2
+
+
+def pir_lwe_answer(db, D1: int, D0: int, queries, B: int, out, path: int = PIR_LWE_AUTO, stream=None):
+    """Scalar-HE DB GEMM out[b][i] = sum_j db[i][j] queries[b][j] mod 2^32 (device buffers:
+    db [D1][D0] int8, queries [B][D0] uint32, out [B][D1] uint32)."""
+    dp, ddev, _ = _ptr(db)
+    qp, qdev, _ = _ptr(queries)
+    op, odev, _ = _ptr(out)
+    if not (ddev and qdev and odev):
+        raise ValueError("pir_lwe_answer works on device buffers")
+    _check(lib().pir_lwe_answer(dp, D1, D0, qp, B, op, path, _stream_ptr(stream)), "pir_lwe_answer")
     return out
 
 

@@ -473,6 +473,114 @@ def ntt_sweep(args):
     print(json.dumps(line), flush=True)
 
 
+LWE_WORKLOADS = {  # name: (D1, D0, description); the raw INT8 DB is the operand
+    "lwe1g": (1 << 15, 1 << 15, "1 GiB INT8 DB, 32768 x 32768"),
+    "lwe16g": (1 << 17, 1 << 17, "16 GiB INT8 DB, 131072 x 131072"),
+    "lwe64g": (1 << 18, 1 << 18, "64 GiB INT8 DB, 262144 x 262144"),
+}
+
+
+def lwe_bench(args):
+    """Scalar-HE (LWE) DB GEMM of SimplePIR's online step: out = DB Q^T mod 2^32 on
+    the raw INT8 DB (Sec. 2.5, 4.1), B queries per step."""
+    import torch
+    import paper_2606_11536_gb300 as g
+    from paper_2606_11536_gb300 import synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    D1, D0, desc = LWE_WORKLOADS[args.lwe_workload]
+    B = args.batch or 32
+    path = {"auto": g.PIR_LWE_AUTO, "tensor": g.PIR_LWE_TENSOR, "simt": g.PIR_LWE_SIMT}[args.lwe_path]
+    if path == g.PIR_LWE_AUTO:
+        path = g.PIR_LWE_TENSOR if B >= 8 else g.PIR_LWE_SIMT
+    db = synth.raw_db_torch(0, D1 * D0, device=dev).view(torch.int8)  # uniform INT8 plaintexts
+    nbuf = 2
+    # query entries: uniform Z_2^32 words (both halves of each counter-based u64 draw)
+    qs = [synth.u64_torch(40 + t, synth.STREAM_UNIFORM, 0, (B * D0 + 1) // 2, device=dev).view(torch.int32)[:B * D0]
+          .contiguous() for t in range(nbuf)]
+    out = torch.empty(B * D1, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    peak_tops = g.pir_probe_int8_mma(stream)
+
+    def step(t):
+        g.pir_lwe_answer(db, D1, D0, qs[t % nbuf], B, out, path=path, stream=stream)
+
+    for t in range(args.warmup):
+        step(t)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    launches0 = g.pir_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    w0 = time.time()
+    e0.record(stream)
+    for t in range(args.steps):
+        step(t)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    w1 = time.time()
+    launches = g.pir_kernel_launches() - launches0
+    sampler.stop()
+    clocks = sampler.summary(w0, w1)
+    ms = e0.elapsed_time(e1) / args.steps
+    raw = D1 * D0
+    value = raw * B / (ms / 1e3) / 1e9
+    macs = D1 * D0 * B
+    peaks, kind = measured_peaks()
+    if path == g.PIR_LWE_TENSOR:
+        achieved = 2.0 * 4 * macs / (ms / 1e3) / 1e12  # four byte planes per INT8 x INT32 product
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak_tops, "unit": "TOPS (INT8 mma.sync)",
+                    "frac": achieved / peak_tops, "traffic": None, "kernel": "lwe_mma",
+                    "peak_source": "pir_probe_int8_mma on this GPU (MEASURED_PEAKS.json has no INT8 entry)",
+                    "hbm_frac": (raw * -(-B // (16 if B >= 16 else 8)) / (ms / 1e3) / 1e9) / float(peaks["hbm_gbs"])}
+    else:
+        achieved = raw * -(-B // min(B, 4)) / (ms / 1e3) / 1e9  # the DB streams once per group of 4 queries
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                    "frac": achieved / float(peaks["hbm_gbs"]), "traffic": None, "kernel": "lwe_dp4a",
+                    "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % kind}
+    # end to end: queries from pinned host memory, results back to the host
+    qh = torch.empty(B * D0, dtype=torch.int32, pin_memory=True)
+    oh = torch.empty(B * D1, dtype=torch.int32, pin_memory=True)
+    qh.copy_(qs[0].cpu())
+    qd = torch.empty_like(qs[0])
+
+    def e2e_step():
+        qd.copy_(qh, non_blocking=True)
+        g.pir_lwe_answer(db, D1, D0, qd, B, out, path=path, stream=stream)
+        oh.copy_(out, non_blocking=True)
+        stream.synchronize()
+
+    e2e_step()
+    t0 = time.perf_counter()
+    n_e2e = max(3, min(args.steps, 20))
+    for _ in range(n_e2e):
+        e2e_step()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / n_e2e
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import oracle as O
+        rows = 64
+        A = synth.raw_db(0, rows * D0).view(np.int8).reshape(rows, D0)  # the DB's first rows
+        Qh = qh.numpy().view(np.uint32).reshape(B, D0)
+        t0 = time.perf_counter()
+        O.lwe_gemm(A, Qh)
+        cs = time.perf_counter() - t0
+        cpu = {"value": rows * D0 * B / cs / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": "oracle GEMM of the first %d DB rows x %d queries, one core" % (rows, B)}
+    line = {"metric": "scalar-HE DB GEMM GB/s (raw INT8 DB bytes x queries/s)", "value": value, "unit": "GB/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "s8 x u32 mod 2^32", "data": "synthetic",
+            "config": {"workload": args.lwe_workload, "description": desc, "D1": D1, "D0": D0, "batch": B,
+                       "path": "tensor" if path == g.PIR_LWE_TENSOR else "dp4a",
+                       "l2": "inputs larger than L2: the %.0f GiB DB streams every step" % (raw / 2 ** 30)},
+            "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": {"value": raw * B / (e2e_ms / 1e3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": B * D0 * 4,
+                    "d2h_bytes_per_step": B * D1 * 4, "ms_per_step": e2e_ms},
+            "gpu_launches": int(launches), "clocks": clocks, "modmac_per_s": macs / (ms / 1e3)}
+    print(json.dumps(line), flush=True)
+
+
 SERVING_DBS = [  # name, n, log2p, D1, D2
     ("db1g_n2048", 2048, 16, 512, 512),
     ("db1g_n4096", 4096, 16, 512, 256),
@@ -548,6 +656,9 @@ def main(argv=None):
     ap.add_argument("--k-chunk", type=int, default=0, help="fold D1 in chunks of this many ciphertexts")
     ap.add_argument("--ref-cols", type=int, default=64, help="columns in the oracle's timed sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lwe", action="store_true", help="time the scalar-HE (LWE) INT8 x INT32 DB GEMM instead")
+    ap.add_argument("--lwe-workload", default="lwe16g", choices=sorted(LWE_WORKLOADS))
+    ap.add_argument("--lwe-path", default="auto", choices=["auto", "tensor", "simt"])
     ap.add_argument("--packed", action="store_true",
                     help="one packed ciphertext per query, expanded on the GPU (pir_answer_packed)")
     ap.add_argument("--ell", type=int, default=4, help="gadget digits of the expansion keys with --packed")
@@ -565,6 +676,8 @@ def main(argv=None):
         ap.error("--warmup must be at least 3")
     if args.ntt_sweep:
         return ntt_sweep(args)
+    if args.lwe:
+        return lwe_bench(args)
     if args.serving:
         return serving_bench(args)
     if args.impl == "reference":

@@ -271,6 +271,12 @@ pir_status_t pir_answer_packed(pir_db_t db, pir_expander_t expander, const uint3
 pir_status_t pir_lwe_answer(const int8_t *db, uint32_t D1, uint32_t D0, const uint32_t *queries, uint32_t B,
                             uint32_t *out, uint32_t path, void *stream);
 
+/* Measured peak of the INT8 warp-level tensor instruction (mma.sync m16n8k32 s8 x u8
+ * -> s32) on the current device, in tera-operations per second (2 per multiply-add):
+ * the denominator of the scalar-HE GEMM's roofline.  The paper has no counterpart.
+ * Synchronizes `stream`.  Errors: PIR_ERR_ARG (NULL), PIR_ERR_CUDA. */
+pir_status_t pir_probe_int8_mma(void *stream, double *tops);
+
 /* Release a DB handle and its device memory (synchronizes the device first). */
 pir_status_t pir_free_db(pir_db_t db);
 

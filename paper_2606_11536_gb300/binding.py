@@ -93,6 +93,7 @@ def lib():
             "pir_autotune": (i32, [vp, u32, vp, u32, C.POINTER(pir_answer_opts_t)]),
             "pir_answer_noalloc": (i32, [vp, vp, u32, vp, vp]),
             "pir_lwe_answer": (i32, [vp, u32, u32, vp, u32, vp, u32, vp]),
+            "pir_probe_int8_mma": (i32, [vp, C.POINTER(C.c_double)]),
             "pir_expander_create": (i32, [P, u32, u32, vp, i32, vp, C.POINTER(vp)]),
             "pir_expander_free": (i32, [vp]),
             "pir_expand": (i32, [vp, vp, u32, u32, vp, vp]),
@@ -242,6 +243,13 @@ def pir_lwe_answer(db, D1: int, D0: int, queries, B: int, out, path: int = PIR_L
         raise ValueError("pir_lwe_answer works on device buffers")
     _check(lib().pir_lwe_answer(dp, D1, D0, qp, B, op, path, _stream_ptr(stream)), "pir_lwe_answer")
     return out
+
+
+def pir_probe_int8_mma(stream=None) -> float:
+    """Measured INT8 mma.sync peak of this GPU in TOPS."""
+    v = C.c_double()
+    _check(lib().pir_probe_int8_mma(_stream_ptr(stream), C.byref(v)), "pir_probe_int8_mma")
+    return v.value
 
 
 class Expander:

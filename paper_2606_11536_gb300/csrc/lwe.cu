@@ -158,10 +158,12 @@ __global__ void __launch_bounds__(128) k_lwe_mma(const int8_t *__restrict__ A, u
 
 // CUDA-core path: 256 rows per CTA (one per thread) x QB queries.  Per stage the raw
 // query words are staged, then transposed once into planes [QB][KS/4][4] that every
-// thread reads as broadcasts.
+// thread reads as broadcasts.  blockIdx.z takes K stages [z * kper, (z + 1) * kper):
+// with more than one split the partial sums are added into the zeroed output with
+// wrapping atomics, exact in any order because the result is taken mod 2^32.
 template <int QB>
 __global__ void __launch_bounds__(256) k_lwe_dp4a(const int8_t *__restrict__ A, uint32_t D1, uint32_t D0,
-                                                  const uint32_t *__restrict__ Q, uint32_t B,
+                                                  const uint32_t *__restrict__ Q, uint32_t B, uint32_t kper,
                                                   uint32_t *__restrict__ out) {
   constexpr int A_BYTES = 256 * KS, QR_BYTES = QB * KS * 4, STAGE = A_BYTES + QR_BYTES;
   extern __shared__ __align__(128) uint8_t smem[];
@@ -193,8 +195,9 @@ __global__ void __launch_bounds__(256) k_lwe_dp4a(const int8_t *__restrict__ A, 
 #pragma unroll
     for (int p = 0; p < 4; ++p) acc[b][p] = 0;
 
-  const uint32_t nk = (D0 + KS - 1) / KS;
-  load_stage(0, 0);
+  const uint32_t nk_all = (D0 + KS - 1) / KS, kbeg = blockIdx.z * kper;
+  const uint32_t nk = kbeg >= nk_all ? 0 : (nk_all - kbeg < kper ? nk_all - kbeg : kper);
+  if (nk > 0) load_stage(0, kbeg * KS);
   for (uint32_t kt = 0; kt < nk; ++kt) {
     const int buf = kt & 1;
     asm volatile("cp.async.wait_group 0;\n" ::);
@@ -206,7 +209,7 @@ __global__ void __launch_bounds__(256) k_lwe_dp4a(const int8_t *__restrict__ A, 
       byte_planes(w.x, w.y, w.z, w.w, p);
       planes[t] = make_uint4(p[0], p[1], p[2], p[3]);
     }
-    if (kt + 1 < nk) load_stage(buf ^ 1, (kt + 1) * KS);
+    if (kt + 1 < nk) load_stage(buf ^ 1, (kbeg + kt + 1) * KS);
     __syncthreads();
 #pragma unroll 2
     for (uint32_t ch = 0; ch < KS / 16; ++ch) {
@@ -232,7 +235,10 @@ __global__ void __launch_bounds__(256) k_lwe_dp4a(const int8_t *__restrict__ A, 
     uint32_t v = 0;
 #pragma unroll
     for (int p = 0; p < 4; ++p) v += (uint32_t)acc[b][p] << (8 * p);
-    out[(uint64_t)(q0 + b) * D1 + i] = v;
+    if (gridDim.z > 1)
+      atomicAdd(out + (uint64_t)(q0 + b) * D1 + i, v);
+    else
+      out[(uint64_t)(q0 + b) * D1 + i] = v;
   }
 }
 
@@ -251,13 +257,31 @@ cudaError_t mma_launch(const int8_t *A, uint32_t D1, uint32_t D0, const uint32_t
 
 template <int QB>
 cudaError_t dp4a_launch(const int8_t *A, uint32_t D1, uint32_t D0, const uint32_t *Q, uint32_t B, uint32_t *out,
-                        cudaStream_t s) {
+                        cudaStream_t s, uint32_t *launches) {
   constexpr int smem = 2 * (256 * KS + QB * KS * 4) + QB * KS * 4;
   cudaError_t e = cudaFuncSetAttribute(k_lwe_dp4a<QB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   const uint64_t gx = (D1 + 255) / 256, gy = (B + QB - 1) / QB;
   if (gx > 0x7FFFFFFFull || gy > 65535) return cudaErrorInvalidConfiguration;
-  k_lwe_dp4a<QB><<<dim3((unsigned)gx, (unsigned)gy), 256, smem, s>>>(A, D1, D0, Q, B, out);
+  // split K until the grid fills about four waves of resident CTAs
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lwe_dp4a<QB>, 256, smem)) != cudaSuccess) return e;
+  const uint32_t nk = (D0 + KS - 1) / KS;
+  const uint64_t target = 4ull * sms * (per_sm > 0 ? per_sm : 1);
+  uint64_t splits = (target + gx * gy - 1) / (gx * gy);
+  const uint64_t max_splits = nk / 8 > 0 ? nk / 8 : 1;  // at least 8 stages per split
+  if (splits > max_splits) splits = max_splits;
+  if (splits > 64) splits = 64;
+  if (splits < 1) splits = 1;
+  const uint32_t kper = (uint32_t)((nk + splits - 1) / splits);
+  splits = (nk + kper - 1) / kper;
+  if (splits > 1) {
+    if ((e = cudaMemsetAsync(out, 0, (size_t)B * D1 * sizeof(uint32_t), s)) != cudaSuccess) return e;
+  }
+  k_lwe_dp4a<QB><<<dim3((unsigned)gx, (unsigned)gy, (unsigned)splits), 256, smem, s>>>(A, D1, D0, Q, B, kper, out);
+  *launches = 1;
   return cudaGetLastError();
 }
 
@@ -269,10 +293,11 @@ cudaError_t launch_lwe_gemm(const int8_t *A, uint32_t D1, uint32_t D0, const uin
   if (path == PIR_LWE_AUTO) path = B >= 8 ? PIR_LWE_TENSOR : PIR_LWE_SIMT;
   if (path == PIR_LWE_TENSOR) return B >= 16 ? mma_launch<2>(A, D1, D0, Q, B, out, s) : mma_launch<1>(A, D1, D0, Q, B, out, s);
   if (path == PIR_LWE_SIMT) {
-    if (B >= 4) return dp4a_launch<4>(A, D1, D0, Q, B, out, s);
-    if (B == 3) return dp4a_launch<3>(A, D1, D0, Q, B, out, s);
-    if (B == 2) return dp4a_launch<2>(A, D1, D0, Q, B, out, s);
-    return dp4a_launch<1>(A, D1, D0, Q, B, out, s);
+    uint32_t launches = 0;
+    if (B >= 4) return dp4a_launch<4>(A, D1, D0, Q, B, out, s, &launches);
+    if (B == 3) return dp4a_launch<3>(A, D1, D0, Q, B, out, s, &launches);
+    if (B == 2) return dp4a_launch<2>(A, D1, D0, Q, B, out, s, &launches);
+    return dp4a_launch<1>(A, D1, D0, Q, B, out, s, &launches);
   }
   return cudaErrorInvalidValue;
 }

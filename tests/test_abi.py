@@ -105,3 +105,17 @@ def test_config_sizes():
     assert binding.query_bytes(p, 1) == 32 << 20 and binding.response_bytes(p, 1) == 16 << 20
     p = g.pir_make_params(4096, 16, 4096, 512, 2)
     assert binding.raw_db_bytes(p) == 16 << 30 and binding.resident_db_bytes(p) == 64 << 30
+
+
+def test_bench_and_serving_use_exported_names():
+    """Every `g.<name>` the benchmark and the serving layer call exists in the package
+    (they run only on a GPU machine, so a missing export would surface only there)."""
+    import re
+
+    import paper_2606_11536_gb300 as g
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    for rel in ("bench.py", os.path.join("paper_2606_11536_gb300", "serving.py"), "__graft_entry__.py"):
+        src = open(os.path.join(root, rel)).read()
+        names = set(re.findall(r"\bg\.([A-Za-z_][A-Za-z0-9_]*)", src))
+        missing = sorted(n for n in names if not hasattr(g, n))
+        assert not missing, (rel, missing)

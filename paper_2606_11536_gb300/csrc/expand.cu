@@ -109,20 +109,22 @@ __global__ void k_expand_decompose(const uint32_t *__restrict__ acoef, uint64_t 
 //   branch 1 -> (a m[s] + S_a m[p], b m[s] + (b[p] + S_b) m[p]),   p = perm(s), m = mon.
 // Output ciphertext (query b, index k) goes to out + (b * ostride + k) * 2 L n when
 // k < olimit.
+template <uint32_t L>
 __global__ void k_expand_mac(const uint32_t *__restrict__ cur, const uint32_t *__restrict__ dhat,
                              const uint32_t *__restrict__ key, const uint32_t *__restrict__ mon,
                              const uint32_t *__restrict__ mon_sh, const uint32_t *__restrict__ perm, uint64_t cts,
-                             uint32_t C, uint32_t logn, uint32_t L, uint32_t ell, uint32_t ostride, uint32_t olimit,
-                             ExpConst E, uint32_t *__restrict__ out) {
-  const uint32_t n = 1u << logn;
+                             uint32_t lev, uint32_t logn, uint32_t ell, uint32_t ostride, uint32_t olimit, ExpConst E,
+                             uint32_t *__restrict__ out) {
+  const uint32_t n = 1u << logn, C = 1u << lev;
   const uint64_t total = cts * L * (uint64_t)n;
   for (uint64_t idx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t s = (uint32_t)(idx & (n - 1));
-    const uint32_t i = (uint32_t)((idx >> logn) % L);
-    const uint64_t ct = (idx >> logn) / L;
-    const uint64_t b = ct / C;
-    const uint32_t k0 = (uint32_t)(ct % C), k1 = k0 + C;
+    const uint64_t row = idx >> logn;  // ciphertext * L + prime
+    const uint32_t i = (uint32_t)(row % L);
+    const uint64_t ct = row / L;
+    const uint64_t b = ct >> lev;
+    const uint32_t k0 = (uint32_t)(ct & (C - 1)), k1 = k0 + C;
     if (k0 >= olimit) continue;
     const uint32_t q = pick4(E.q, i);
     const uint64_t mu = pick4(E.mu, i);
@@ -268,8 +270,13 @@ pir_status_t expand_device(const pir_expander_impl *ex, const uint32_t *packed, 
       const uint32_t *perm = ex->perm + (uint64_t)lev * n;
       uint32_t *dst = last ? out + (uint64_t)b0 * count * ctw : nxt;
       const uint32_t ostride = last ? count : 2 * C, olimit = last ? count : 2 * C;
-      k_expand_mac<<<grid_for(cts * L * n, 256), 256, 0, s>>>(cur, dhat, key, mon, msh, perm, cts, C, logn, L, ell,
-                                                              ostride, olimit, ex->E, dst);
+      const unsigned gmac = grid_for(cts * L * n, 256);
+      switch (L) {
+        case 1: k_expand_mac<1><<<gmac, 256, 0, s>>>(cur, dhat, key, mon, msh, perm, cts, lev, logn, ell, ostride, olimit, ex->E, dst); break;
+        case 2: k_expand_mac<2><<<gmac, 256, 0, s>>>(cur, dhat, key, mon, msh, perm, cts, lev, logn, ell, ostride, olimit, ex->E, dst); break;
+        case 3: k_expand_mac<3><<<gmac, 256, 0, s>>>(cur, dhat, key, mon, msh, perm, cts, lev, logn, ell, ostride, olimit, ex->E, dst); break;
+        default: k_expand_mac<4><<<gmac, 256, 0, s>>>(cur, dhat, key, mon, msh, perm, cts, lev, logn, ell, ostride, olimit, ex->E, dst); break;
+      }
       if (!ck(cudaGetLastError())) break;
       launches += 4;
       uint32_t *t = cur;

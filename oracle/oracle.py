@@ -80,6 +80,9 @@ def lib():
             "orc_bfv_phase_q0": (None, [PP, I8P, U32P, U64P]),
             "orc_bfv_decrypt_q0": (None, [PP, I8P, U32P, U32P]),
             "orc_lwe_gemm": (None, [I8P, C.c_uint32, C.c_uint32, U32P, C.c_uint32, U32P]),
+            "orc_rgsw_encrypt": (None, [PP, I8P, U32P, C.c_uint32, U32P, I8P, U32P]),
+            "orc_external_product": (None, [PP, U32P, C.c_uint32, U32P, U32P]),
+            "orc_fold": (None, [PP, U32P, C.c_uint32, U32P, C.c_uint32, U32P]),
             "orc_automorphism": (None, [U32P, U32P, C.c_uint32, C.c_uint64, C.c_uint32]),
             "orc_gadget_bits": (C.c_uint32, [PP, C.c_uint32]),
             "orc_ksk_gen": (None, [PP, I8P, C.c_uint32, C.c_uint32, U32P, I8P, U32P]),
@@ -300,6 +303,44 @@ def bfv_decrypt_q0(P: OrcParams, s, ct) -> np.ndarray:
     m = np.empty(P.n, dtype=np.uint32)
     lib().orc_bfv_decrypt_q0(C.byref(P), np.ascontiguousarray(s, dtype=np.int8), _u32(ct).reshape(-1), m)
     return m
+
+
+# --- RGSW external products (remaining dimensions) --------------------------
+
+def rgsw_encrypt(P: OrcParams, s, mu, ell: int, a, e) -> np.ndarray:
+    """RGSW(mu): [2 ell][2][L][n]; mu [n] small non-negative, a [2 ell][L][n], e [2 ell][n]."""
+    out = np.empty((2 * ell, 2, P.L, P.n), dtype=np.uint32)
+    lib().orc_rgsw_encrypt(C.byref(P), np.ascontiguousarray(s, dtype=np.int8), _u32(mu), ell, _u32(a).reshape(-1),
+                           np.ascontiguousarray(e, dtype=np.int8).reshape(-1), out.reshape(-1))
+    return out
+
+
+def rgsw_bits(P: OrcParams, s, bits, ell: int, seed: int) -> np.ndarray:
+    """RGSW encryptions of the constant polynomials bits[l] (one per folding level),
+    [levels][2 ell][2][L][n], from seeded draws (masks STREAM_KEY_A, errors STREAM_KEY_ERROR)."""
+    from paper_2606_11536_gb300 import synth
+    out = np.empty((len(bits), 2 * ell, 2, P.L, P.n), dtype=np.uint32)
+    for l, bit in enumerate(bits):
+        mu = np.zeros(P.n, dtype=np.uint32)
+        mu[0] = int(bit)
+        a = synth.uniform_residues(seed, synth.STREAM_KEY_A, 2 * ell, P.n, P.qs, start=(1000 + l) * 2 * ell)
+        e = synth.gaussian_error(seed, 2 * ell * P.n, start=(1000 + l) * 2 * ell * P.n,
+                                 stream=synth.STREAM_KEY_ERROR).reshape(2 * ell, P.n)
+        out[l] = rgsw_encrypt(P, s, mu, ell, a, e)
+    return out
+
+
+def external_product(P: OrcParams, rgsw, ell: int, ct) -> np.ndarray:
+    out = np.empty((2, P.L, P.n), dtype=np.uint32)
+    lib().orc_external_product(C.byref(P), _u32(rgsw).reshape(-1), ell, _u32(ct).reshape(-1), out.reshape(-1))
+    return out
+
+
+def fold(P: OrcParams, cts, levels: int, rgsw, ell: int) -> np.ndarray:
+    """Fold 2^levels ciphertexts [2^levels][2][L][n] into one with RGSW selection bits."""
+    out = np.empty((2, P.L, P.n), dtype=np.uint32)
+    lib().orc_fold(C.byref(P), _u32(cts).reshape(-1), levels, _u32(rgsw).reshape(-1), ell, out.reshape(-1))
+    return out
 
 
 # --- scalar-HE (LWE) DB GEMM ------------------------------------------------

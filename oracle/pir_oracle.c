@@ -17,6 +17,8 @@
  *   - modulus switching q -> q_0: round(x q_0 / q) mod q_0, and decryption over
  *     the single prime q_0 afterwards                                 (App. D.5, Sec. 4.3)
  *   - scalar-HE (LWE) DB GEMM: out = DB Q^T mod 2^32 with an INT8 DB         (Sec. 2.5, 4.1, App. A.1)
+ *   - RGSW encryption, RGSW-RLWE external product and the folding of the
+ *     remaining dimensions c_2j + RGSW (x) (c_2j+1 - c_2j)         (Sec. 3.2, 3.6, App. D.3)
  *   - query expansion: substitutions tau_g, key switching with the base-t gadget
  *     (t = 2^ceil(log2 q / ell)), SealPIR's recursive expansion with the
  *     2^-levels pre-scaling                                         (Sec. 3.5, App. C.2, D.3)
@@ -1004,4 +1006,103 @@ void orc_lwe_gemm(const int8_t *A, u32 D1, u32 D0, const u32 *Q, u32 B, u32 *out
       for (u32 j = 0; j < D0; j++) acc += (i64)a[j] * (i64)q[j]; /* |acc| < 2^7 2^32 2^24 */
       out[(u64)b * D1 + i] = (u32)((u64)acc & 0xFFFFFFFFull);
     }
+}
+
+/* ------------------------------------------------------------------------- */
+/* RGSW-RLWE external products for the remaining dimensions (Sec. 3.2, 3.6)   */
+/* ------------------------------------------------------------------------- */
+
+/* RGSW encryption of mu (a polynomial with small non-negative coefficients, e.g. a
+ * selection bit) with the ell-digit base-t gadget of App. D.3: 2 ell rows, each an
+ * RLWE encryption of zero (a s + b = e) plus mu t^k in the a-part (row k < ell) or in
+ * the b-part (row ell + k).  a [2 ell][L][n] uniform residues, e [2 ell][n] errors;
+ * out [2 ell][2][L][n], coefficient form. */
+void orc_rgsw_encrypt(const orc_params *P, const int8_t *s, const u32 *mu, u32 ell, const u32 *a, const int8_t *e,
+                      u32 *out) {
+  const u32 n = P->n, L = P->L, w = orc_gadget_bits(P, ell);
+  u32 *sj = (u32 *)calloc(n, sizeof(u32));
+  u32 *as = (u32 *)calloc(n, sizeof(u32));
+  for (u32 r = 0; r < 2 * ell; r++) {
+    const u32 k = r % ell, in_b = r >= ell;
+    for (u32 j = 0; j < L; j++) {
+      const u64 q = P->q[j];
+      const u64 tk = (u64)(((u128)1 << (w * k)) % q);
+      for (u32 t = 0; t < n; t++) sj[t] = (u32)((s[t] + (i128)q) % q);
+      const u32 *ar = a + ((u64)r * L + j) * n;
+      ring_mul(ar, sj, as, n, q, P->psi[j]);
+      u32 *oa = out + (((u64)r * 2 + 0) * L + j) * n, *ob = out + (((u64)r * 2 + 1) * L + j) * n;
+      for (u32 t = 0; t < n; t++) {
+        const u64 et = (u64)((e[(u64)r * n + t] + (i128)q) % q);
+        const u64 mt = mulmod(tk, mu[t] % q, q);
+        const u64 b0 = submod(et, as[t], q); /* a s + b = e */
+        oa[t] = (u32)(in_b ? ar[t] : addmod(ar[t], mt, q));
+        ob[t] = (u32)(in_b ? addmod(b0, mt, q) : b0);
+      }
+    }
+  }
+  free(sj);
+  free(as);
+}
+
+/* External product RGSW(mu) (x) ct: with a = sum_k t^k d_k(a) and b = sum_k t^k d_k(b)
+ * (digits of the CRT lifts of the coefficients), out = sum_k d_k(a) row_k +
+ * sum_k d_k(b) row_(ell+k); its phase is mu (a s + b) plus the rows' errors weighted
+ * by the digits.  rgsw [2 ell][2][L][n], ct and out [2][L][n], coefficient form. */
+void orc_external_product(const orc_params *P, const u32 *rgsw, u32 ell, const u32 *ct, u32 *out) {
+  const u32 n = P->n, L = P->L;
+  u32 *d = (u32 *)calloc((size_t)2 * ell * n, sizeof(u32));
+  u32 *dk = (u32 *)calloc(n, sizeof(u32));
+  u32 *prod = (u32 *)calloc(n, sizeof(u32));
+  gadget_digits(P, ct, ell, d);                              /* digits of a */
+  gadget_digits(P, ct + (u64)L * n, ell, d + (u64)ell * n);  /* digits of b */
+  memset(out, 0, sizeof(u32) * 2 * L * n);
+  for (u32 r = 0; r < 2 * ell; r++)
+    for (u32 c = 0; c < 2; c++)
+      for (u32 j = 0; j < L; j++) {
+        const u64 q = P->q[j];
+        for (u32 t = 0; t < n; t++) dk[t] = (u32)(d[(u64)r * n + t] % q);
+        ring_mul(dk, rgsw + (((u64)r * 2 + c) * L + j) * n, prod, n, q, P->psi[j]);
+        u32 *o = out + ((u64)c * L + j) * n;
+        for (u32 t = 0; t < n; t++) o[t] = (u32)addmod(o[t], prod[t], q);
+      }
+  free(d);
+  free(dk);
+  free(prod);
+}
+
+/* Folding of 2^levels ciphertexts [2^levels][2][L][n] into one (OnionPIR's remaining
+ * dimensions, Sec. 3.2 / 3.6): level l pairs ciphertexts (2j, 2j + 1) and keeps
+ * c_2j + RGSW_l (x) (c_2j+1 - c_2j), which is c_2j+1 when RGSW_l encrypts 1 and c_2j
+ * when it encrypts 0.  rgsw [levels][2 ell][2][L][n]; out [2][L][n]. */
+void orc_fold(const orc_params *P, const u32 *cts, u32 levels, const u32 *rgsw, u32 ell, u32 *out) {
+  const u32 n = P->n, L = P->L;
+  const u64 csz = (u64)2 * L * n;
+  u64 count = 1ull << levels;
+  u32 *cur = (u32 *)calloc(count * csz, sizeof(u32));
+  u32 *diff = (u32 *)calloc(csz, sizeof(u32));
+  u32 *ep = (u32 *)calloc(csz, sizeof(u32));
+  memcpy(cur, cts, sizeof(u32) * count * csz);
+  for (u32 l = 0; l < levels; l++) {
+    const u32 *g = rgsw + (u64)l * 2 * ell * csz;
+    for (u64 j = 0; j < count / 2; j++) {
+      const u32 *c0 = cur + (2 * j) * csz, *c1 = cur + (2 * j + 1) * csz;
+      for (u32 c = 0; c < 2; c++)
+        for (u32 i = 0; i < L; i++) {
+          const u64 q = P->q[i], o = ((u64)c * L + i) * n;
+          for (u32 t = 0; t < n; t++) diff[o + t] = (u32)submod(c1[o + t], c0[o + t], q);
+        }
+      orc_external_product(P, g, ell, diff, ep);
+      u32 *dst = cur + j * csz; /* j <= 2j: c0 was read above */
+      for (u32 c = 0; c < 2; c++)
+        for (u32 i = 0; i < L; i++) {
+          const u64 q = P->q[i], o = ((u64)c * L + i) * n;
+          for (u32 t = 0; t < n; t++) dst[o + t] = (u32)addmod(c0[o + t], ep[o + t], q);
+        }
+    }
+    count /= 2;
+  }
+  memcpy(out, cur, sizeof(u32) * csz);
+  free(cur);
+  free(diff);
+  free(ep);
 }

@@ -251,6 +251,31 @@ pir_status_t pir_expand(pir_expander_t expander, const uint32_t *packed, uint32_
 pir_status_t pir_answer_packed(pir_db_t db, pir_expander_t expander, const uint32_t *packed, uint32_t B,
                                uint32_t *responses, int on_device, void *stream, const pir_answer_opts_t *opts);
 
+/* Folding of the remaining dimensions with RGSW-RLWE external products (Sec. 3.2 and
+ * 3.6: OnionPIR's construction; gadget of App. D.3).  Each level pairs the
+ * ciphertexts (2j, 2j+1) of a query and keeps c_2j + RGSW_l (x) (c_2j+1 - c_2j), where
+ * the external product writes both components of the difference in the gadget (ell
+ * digits of base t = 2^w, w = ceil(ceil(log2 q) / ell) <= 30, of the CRT lift of every
+ * coefficient) and sums digit x row products.  RGSW_l encrypting the bit l of the
+ * wanted index selects that ciphertext.  An RGSW ciphertext is 2 ell RLWE rows: row
+ * k < ell encrypts zero plus mu t^k in its a-part, row ell + k zero plus mu t^k in its
+ * b-part.
+ *   pir_fold: cts [B][2^levels][2][L][n] -> out [B][2][L][n]; rgsw
+ *     [B][levels][2 ell][2][L][n]; all coefficient form, canonical, device memory,
+ *     16-byte aligned; asynchronous on stream.
+ *   pir_answer_folded: the first-dimension answer of pir_answer_ex (queries
+ *     [B][D1][2][L][n]) folded over all log2(D2) remaining levels (D2 a power of two)
+ *     with rgsw [B][log2 D2][2 ell][2][L][n]: responses [B][2][L][n], or [B][2][n] over
+ *     q_0 with PIR_ANSWER_MODSWITCH; one ciphertext per query holding the record.
+ *     on_device and opts as for pir_answer_ex (PIR_ANSWER_TEST_STALL refused; with
+ *     PIR_ANSWER_STAGE_TIMES the folding and the final inverse NTT count as stage 4).
+ * Errors: PIR_ERR_HANDLE, PIR_ERR_ARG (NULL or misaligned buffers, B = 0, ell out of
+ * range or digits above 30 bits, D2 not a power of two), PIR_ERR_OOM, PIR_ERR_CUDA. */
+pir_status_t pir_fold(const pir_params_t *params, const uint32_t *cts, uint32_t B, uint32_t levels, uint32_t ell,
+                      const uint32_t *rgsw, uint32_t *out, void *stream);
+pir_status_t pir_answer_folded(pir_db_t db, const uint32_t *queries, uint32_t B, uint32_t ell, const uint32_t *rgsw,
+                               uint32_t *responses, int on_device, void *stream, const pir_answer_opts_t *opts);
+
 /* Scalar-HE (LWE) DB GEMM of SimplePIR's online step (Sec. 2.5), built as Sec. 4.1
  * builds it on the INT8 tensor pipe:
  *     out[b][i] = sum_j db[i][j] * queries[b][j]   (mod 2^32)

@@ -93,6 +93,8 @@ def lib():
             "pir_autotune": (i32, [vp, u32, vp, u32, C.POINTER(pir_answer_opts_t)]),
             "pir_answer_noalloc": (i32, [vp, vp, u32, vp, vp]),
             "pir_lwe_answer": (i32, [vp, u32, u32, vp, u32, vp, u32, vp]),
+            "pir_fold": (i32, [P, vp, u32, u32, u32, vp, vp, vp]),
+            "pir_answer_folded": (i32, [vp, vp, u32, u32, vp, vp, i32, vp, C.POINTER(pir_answer_opts_t)]),
             "pir_probe_int8_mma": (i32, [vp, C.POINTER(C.c_double)]),
             "pir_expander_create": (i32, [P, u32, u32, vp, i32, vp, C.POINTER(vp)]),
             "pir_expander_free": (i32, [vp]),
@@ -228,6 +230,30 @@ def ntt_inv_modswitch(params: pir_params_t, polys, out, count: int | None = None
     cnt = nbytes // (4 * params.L * params.n) if count is None else count
     _check(lib().ntt_inv_modswitch(C.byref(params), ip, cnt, op, _stream_ptr(stream)), "ntt_inv_modswitch")
     return out
+
+
+def pir_fold(params: pir_params_t, cts, B: int, levels: int, ell: int, rgsw, out, stream=None):
+    """Fold cts [B][2^levels][2][L][n] with rgsw [B][levels][2 ell][2][L][n] into out [B][2][L][n]."""
+    cp, cdev, _ = _ptr(cts)
+    gp, gdev, _ = _ptr(rgsw)
+    op, odev, _ = _ptr(out)
+    if not (cdev and gdev and odev):
+        raise ValueError("pir_fold works on device buffers")
+    _check(lib().pir_fold(C.byref(params), cp, B, levels, ell, gp, op, _stream_ptr(stream)), "pir_fold")
+    return out
+
+
+def pir_answer_folded(db: Db, queries, B: int, ell: int, rgsw, responses, stream=None, tile: int = 0, flags: int = 0):
+    """First-dimension answer folded over the remaining log2(D2) levels: responses [B][2][L][n]."""
+    qp, qdev, _ = _ptr(queries)
+    gp, gdev, _ = _ptr(rgsw)
+    rp, rdev, _ = _ptr(responses)
+    if not (qdev == gdev == rdev):
+        raise ValueError("queries, rgsw and responses must all be host or all be device buffers")
+    o = pir_answer_opts_t(0, tile, flags)
+    _check(lib().pir_answer_folded(C.c_void_p(db.handle), qp, B, ell, gp, rp, int(qdev), _stream_ptr(stream),
+                                   C.byref(o)), "pir_answer_folded")
+    return responses
 
 
 PIR_LWE_AUTO, PIR_LWE_TENSOR, PIR_LWE_SIMT = 0, 1, 2

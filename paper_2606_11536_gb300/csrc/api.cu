@@ -173,8 +173,10 @@ struct StageTimer {
 // The device-buffer answer (stream ordered).
 // qhat_ready: when set, the queries are already in NTT form for the whole of D1
 // ([B][D1][2][L][n], e.g. from query expansion): no forward NTT, no K-chunking.
+// ntt_out: leave the responses in NTT form (no inverse NTT, no modulus switching),
+// for the folding of the remaining dimensions.
 pir_status_t answer_device(pir_db *db, const uint32_t *queries, uint32_t B, uint32_t *responses, cudaStream_t s,
-                           const pir_answer_opts_t &o, const uint32_t *qhat_ready = nullptr) {
+                           const pir_answer_opts_t &o, const uint32_t *qhat_ready = nullptr, bool ntt_out = false) {
   const ParamCtx &c = *db->ctx;
   const pir_params_t &p = db->p;
   const uint32_t n = p.n, L = p.L, D1 = p.D1, D2 = p.D2;
@@ -211,7 +213,7 @@ pir_status_t answer_device(pir_db *db, const uint32_t *queries, uint32_t B, uint
     return PIR_ERR_ARG;
   // With modulus switching the inverse NTT reads the full-modulus responses from
   // scratch and writes [B][D2][2][n] over q_0 to `responses`.
-  const bool msw = (o.flags & PIR_ANSWER_MODSWITCH) != 0;
+  const bool msw = (o.flags & PIR_ANSWER_MODSWITCH) != 0 && !ntt_out;
   const int stall = (o.flags & PIR_ANSWER_TEST_STALL) != 0;
   if (stall && (db->layout != PIR_LAYOUT_PLAIN || !scan_tma_supports(2 * B, D2) || (o.tile != 0 && o.tile != 7)))
     return PIR_ERR_ARG;
@@ -239,6 +241,7 @@ pir_status_t answer_device(pir_db *db, const uint32_t *queries, uint32_t B, uint
   uint32_t *full = !msw ? responses
                         : fused ? out : reinterpret_cast<uint32_t *>(base + up(qhat_bytes) + up(qs_bytes) + up(out_bytes));
   auto finish = [&]() -> pir_status_t {  // inverse NTT (with the switch when asked)
+    if (ntt_out) return PIR_OK;
     tm.begin();
     if (msw)
       CK(launch_ntt_inv_switch(c, full, responses, (uint64_t)B * D2 * 2, s));
@@ -531,6 +534,69 @@ pir_status_t pir_answer_packed(pir_db_t db, pir_expander_t expander, const uint3
   }
   if (!on_device) {
     CK(cudaMemcpyAsync(responses, dr.ptr, rbytes, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  return PIR_OK;
+}
+
+pir_status_t pir_answer_folded(pir_db_t db, const uint32_t *queries, uint32_t B, uint32_t ell, const uint32_t *rgsw,
+                               uint32_t *responses, int on_device, void *stream, const pir_answer_opts_t *opts) {
+  if (!live(db)) return PIR_ERR_HANDLE;
+  if (B == 0 || !queries || !rgsw || !responses || ell == 0 || ell > 16) return PIR_ERR_ARG;
+  pir_answer_opts_t o = {};
+  if (opts) o = *opts;
+  if (o.flags & PIR_ANSWER_TEST_STALL) return PIR_ERR_ARG;
+  const pir_params_t &p = db->p;
+  const ParamCtx &c = *db->ctx;
+  if ((p.D2 & (p.D2 - 1)) != 0 || gadget_bits(p, ell) > 30) return PIR_ERR_ARG;
+  uint32_t levels = 0;
+  while ((1u << levels) < p.D2) ++levels;
+  const bool msw = (o.flags & PIR_ANSWER_MODSWITCH) != 0;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const uint64_t ctw = 2ull * p.L * p.n;
+  const size_t qbytes = (size_t)B * p.D1 * ctw * 4, gbytes = (size_t)B * levels * 2 * ell * ctw * 4;
+  const size_t rbytes = (size_t)B * 2 * (msw ? 1 : p.L) * p.n * 4;
+  Scratch hq(s), hg(s), hr(s), work(s);
+  const uint32_t *q = queries, *g = rgsw;
+  uint32_t *resp = responses;
+  if (on_device) {
+    if (!aligned16(queries) || !aligned16(rgsw) || !aligned16(responses)) return PIR_ERR_ARG;
+  } else {
+    CK(hq.alloc(qbytes));
+    CK(hg.alloc(gbytes));
+    CK(hr.alloc(rbytes));
+    CK(cudaMemcpyAsync(hq.ptr, queries, qbytes, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(hg.ptr, rgsw, gbytes, cudaMemcpyHostToDevice, s));
+    q = static_cast<const uint32_t *>(hq.ptr);
+    g = static_cast<const uint32_t *>(hg.ptr);
+    resp = static_cast<uint32_t *>(hr.ptr);
+  }
+  // NTT-form first-dimension responses | NTT-form RGSW rows | folded ciphertexts
+  const size_t rn = (size_t)B * p.D2 * ctw, gn = (size_t)B * levels * 2 * ell * ctw, fn = (size_t)B * ctw;
+  CK(work.alloc((rn + gn + fn) * 4));
+  uint32_t *R = static_cast<uint32_t *>(work.ptr), *G = R + rn, *F = G + gn;
+  pir_answer_opts_t o1 = o;
+  o1.flags &= ~PIR_ANSWER_MODSWITCH;
+  pir_status_t st = answer_device(db, q, B, R, s, o1, nullptr, true);
+  if (st == PIR_OK) {
+    StageTimer tm((o.flags & PIR_ANSWER_STAGE_TIMES) != 0, s);
+    tm.begin();
+    uint64_t launches = 0;
+    cudaError_t e = launch_ntt_fwd(c, g, G, gn / p.n, s);
+    if (e != cudaSuccess) st = cuda_status(e);
+    if (st == PIR_OK) st = fold_device(c, R, B, levels, ell, G, F, s, &launches);
+    if (st == PIR_OK) {
+      e = msw ? launch_ntt_inv_switch(c, F, resp, (uint64_t)B * 2, s) : launch_ntt_inv(c, F, resp, (uint64_t)B * 2 * p.L, s);
+      if (e != cudaSuccess) st = cuda_status(e);
+    }
+    tm.end(4, launches + 2);
+  }
+  if (st != PIR_OK) {
+    cudaStreamSynchronize(s);
+    return st;
+  }
+  if (!on_device) {
+    CK(cudaMemcpyAsync(responses, hr.ptr, rbytes, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
   }
   return PIR_OK;

@@ -58,10 +58,22 @@ pir_status_t get_param_ctx(const pir_params_t *p, const ParamCtx **out);  // cac
 // [B][count][2][L][n] in NTT form from packed [B][2][L][n] (coefficient form) and
 // reports its kernel launches; expander_fits checks ring and depth against a DB.
 struct pir_expander_impl;
+// Gadget digits (App. D.3): for every polynomial [L][n] (coefficient form, canonical)
+// of coef [polys][L][n], dig [polys][ell][n] holds the w-bit digits of the CRT lift of
+// each coefficient, w = gadget_bits(p, ell) = ceil(ceil(log2 q) / ell).
+uint32_t gadget_bits(const pir_params_t &p, uint32_t ell);
+cudaError_t launch_gadget_digits(const ParamCtx &c, const uint32_t *coef, uint64_t polys, uint32_t ell,
+                                 uint32_t *dig, cudaStream_t s);
 bool expander_view(pir_expander_t h, const pir_expander_impl **out);
 bool expander_fits(const pir_expander_impl *ex, const pir_params_t &p);
 pir_status_t expand_device(const pir_expander_impl *ex, const uint32_t *packed, uint32_t B, uint32_t count,
                            uint32_t *out, cudaStream_t s, uint64_t *launch_count);
+
+// fold.cu: folding of the remaining dimensions with RGSW external products; cur
+// [B][2^levels][2][L][n] and rgsw [B][levels][2 ell][2][L][n] in NTT form, out
+// [B][2][L][n] in NTT form; cur is overwritten.
+pir_status_t fold_device(const ParamCtx &c, uint32_t *cur, uint32_t B, uint32_t levels, uint32_t ell,
+                         const uint32_t *rgsw, uint32_t *out, cudaStream_t s, uint64_t *launch_count);
 
 // Read-only view of a live DB handle (api.cu); false for unknown or freed handles.
 struct DbView {

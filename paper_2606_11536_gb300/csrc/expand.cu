@@ -161,6 +161,27 @@ __global__ void k_expand_mac(const uint32_t *__restrict__ cur, const uint32_t *_
 }
 
 uint64_t mul_mod64(uint64_t a, uint64_t b, uint64_t m) { return (uint64_t)((unsigned __int128)a * b % m); }
+uint64_t pow_mod64(uint64_t b, uint64_t e, uint64_t m);
+uint32_t shoup32(uint32_t w, uint32_t q);
+
+// Reduction and Garner constants of a ring (2^-levels too, for the expansion's pre-scaling).
+ExpConst make_exp_const(const pir_params_t &p, uint32_t levels) {
+  ExpConst E;
+  std::memset(&E, 0, sizeof(E));
+  for (uint32_t k = 0; k < p.L; ++k) {
+    const uint32_t qk = p.q[k];
+    E.q[k] = qk;
+    E.mu[k] = ~0ull / qk;
+    const uint32_t inv = (uint32_t)pow_mod64(pow_mod64(2, levels, qk), qk - 2, qk);
+    E.inv2l[k] = inv;
+    E.inv2l_sh[k] = shoup32(inv, qk);
+    for (uint32_t i = 0; i < k; ++i) {
+      E.gc[k][i] = (uint32_t)pow_mod64(p.q[i] % qk, qk - 2, qk);
+      E.gc_sh[k][i] = shoup32(E.gc[k][i], qk);
+    }
+  }
+  return E;
+}
 uint64_t pow_mod64(uint64_t b, uint64_t e, uint64_t m) {
   uint64_t r = 1 % m;
   b %= m;
@@ -292,6 +313,18 @@ pir_status_t expand_device(const pir_expander_impl *ex, const uint32_t *packed, 
   return st;
 }
 
+uint32_t gadget_bits(const pir_params_t &p, uint32_t ell) { return (modulus_bits(p) + ell - 1) / ell; }
+
+cudaError_t launch_gadget_digits(const ParamCtx &c, const uint32_t *coef, uint64_t polys, uint32_t ell,
+                                 uint32_t *dig, cudaStream_t s) {
+  if (polys == 0) return cudaSuccess;
+  const ExpConst E = make_exp_const(c.p, 0);
+  const uint32_t n = c.p.n;
+  k_expand_decompose<<<grid_for(polys * n, 256), 256, 0, s>>>(coef, polys, c.logn, c.p.L, ell, gadget_bits(c.p, ell), E,
+                                                              dig);
+  return cudaGetLastError();
+}
+
 bool expander_view(pir_expander_t h, const pir_expander_impl **out) {
   if (!ex_live(h)) return false;
   *out = reinterpret_cast<const pir_expander_impl *>(h);
@@ -363,20 +396,7 @@ pir_status_t pir_expander_create(const pir_params_t *params, uint32_t levels, ui
       hperm[(uint64_t)j * n + k] = brv32((uint32_t)((e - 1) / 2), logn);
     }
   }
-  ExpConst &E = ex->E;
-  std::memset(&E, 0, sizeof(E));
-  for (uint32_t k = 0; k < L; ++k) {
-    const uint32_t qk = params->q[k];
-    E.q[k] = qk;
-    E.mu[k] = ~0ull / qk;
-    const uint32_t inv = (uint32_t)pow_mod64(pow_mod64(2, levels, qk), qk - 2, qk);
-    E.inv2l[k] = inv;
-    E.inv2l_sh[k] = shoup32(inv, qk);
-    for (uint32_t i = 0; i < k; ++i) {
-      E.gc[k][i] = (uint32_t)pow_mod64(params->q[i] % qk, qk - 2, qk);
-      E.gc_sh[k][i] = shoup32(E.gc[k][i], qk);
-    }
-  }
+  ex->E = make_exp_const(*params, levels);
   cudaError_t e = cudaMalloc(&ex->tables, words * 4);
   if (e != cudaSuccess) {
     delete ex;

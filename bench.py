@@ -284,6 +284,17 @@ def our_arm(args, wl):
     resp = torch.empty(rwords, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
 
+    if args.packed and args.folded:
+        raise SystemExit("--packed and --folded are separate modes")
+    rg = None
+    if args.folded:
+        # RGSW rows of the log2(D2) remaining levels per query; the external products'
+        # cost does not depend on their values, so timing-only rows are uniform residues
+        flevels = max(0, (D2 - 1).bit_length())
+        rg = synth.uniform_residues_torch(78, synth.STREAM_KEY_A, B * flevels * 2 * args.ell * 2, n, p.qs,
+                                          device=dev).view(-1)
+        rwords = B * 2 * (1 if msw else L_PRIMES) * n
+        resp = torch.empty(rwords, dtype=torch.int32, device=dev)
     ex = None
     if args.packed:
         # packed queries (one ciphertext each) expanded on the GPU; the expansion's
@@ -298,6 +309,10 @@ def our_arm(args, wl):
                                               device=dev).view(-1) for t in range(nbuf)]
 
     def step(t, flags=0):
+        if rg is not None:
+            g.pir_answer_folded(db, qbufs[t % nbuf], B, args.ell, rg, resp, stream=stream, flags=flags | msw,
+                                tile=args.tile)
+            return
         if ex is not None:
             g.pir_answer_packed(db, ex, qbufs[t % nbuf], B, resp, stream=stream, flags=flags | msw,
                                 tile=args.tile)
@@ -380,7 +395,15 @@ def our_arm(args, wl):
         rh = torch.empty(rwords, dtype=torch.int32, pin_memory=True)
         qh.copy_(qbufs[0].cpu())
         e2e_steps = max(3, min(args.steps, 50))
+        rgh = None
+        if rg is not None:
+            rgh = torch.empty(rg.numel(), dtype=torch.int32, pin_memory=True)
+            rgh.copy_(rg.cpu())
+
         def e2e_step():
+            if rg is not None:
+                g.pir_answer_folded(db, qh, B, args.ell, rgh, rh, stream=stream, flags=msw)
+                return
             if ex is not None:
                 g.pir_answer_packed(db, ex, qh, B, rh, stream=stream, flags=msw)
             else:
@@ -394,12 +417,13 @@ def our_arm(args, wl):
         t1 = time.perf_counter()
         e2e_ms, e2e_q = reduce_timing((t1 - t0) * 1e3, float(B * e2e_steps), device=dev if world > 1 else None)
         e2e = {"value": raw_bytes * e2e_q / (e2e_ms / 1e3) / 1e9, "unit": "GB/s",
-               "h2d_bytes_per_step": qwords * 4, "d2h_bytes_per_step": rwords * 4,
+               "h2d_bytes_per_step": qwords * 4 + (rg.numel() * 4 if rg is not None else 0),
+               "d2h_bytes_per_step": rwords * 4,
                "ms_per_step": e2e_ms / e2e_steps}
 
     cpu = None
-    # the oracle baseline times the unpacked answer; with --packed there is none
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and raw is not None and not args.packed:
+    # the oracle baseline times the plain answer; with --packed or --folded there is none
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and raw is not None and not (args.packed or args.folded):
         nthreads = os.cpu_count() or 1
         ncols = max(1, min(D2, args.ref_cols))
         runner = OracleRunner(n, log2p, D1, D2, B, raw, ncols, nthreads, modswitch=args.modswitch)
@@ -418,6 +442,9 @@ def our_arm(args, wl):
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": wl, "description": desc, "batch": B, "n": n, "log2p": log2p, "D1": D1, "D2": D2,
                        "L": L_PRIMES, "layout": args.layout, "modswitch": bool(msw),
+                       "responses": ("folded to one ciphertext per query by %d RGSW external-product levels "
+                                     "(%d gadget digits; timing-only RGSW rows)" % ((D2 - 1).bit_length(), args.ell)
+                                     if args.folded else "D2 ciphertexts each"),
                        "queries": ("packed, expanded on the GPU (levels %d, %d gadget digits; timing-only keys)"
                                    % ((D1 - 1).bit_length(), args.ell) if args.packed else "D1 ciphertexts each"),
                        "parallelism": "replicas x%d" % world,
@@ -661,7 +688,9 @@ def main(argv=None):
     ap.add_argument("--lwe-path", default="auto", choices=["auto", "tensor", "simt"])
     ap.add_argument("--packed", action="store_true",
                     help="one packed ciphertext per query, expanded on the GPU (pir_answer_packed)")
-    ap.add_argument("--ell", type=int, default=4, help="gadget digits of the expansion keys with --packed")
+    ap.add_argument("--folded", action="store_true",
+                    help="fold the D2 responses into one per query with RGSW external products (pir_answer_folded)")
+    ap.add_argument("--ell", type=int, default=4, help="gadget digits of the expansion keys / RGSW rows")
     ap.add_argument("--modswitch", action="store_true",
                     help="switch the responses to the single prime q_0 inside the inverse NTT")
     ap.add_argument("--ntt-sweep", action="store_true", help="time the standalone NTT sweep instead")

@@ -308,16 +308,22 @@ def our_arm(args, wl):
         qbufs = [synth.uniform_residues_torch(2000 + 17 * rank + t, synth.STREAM_UNIFORM, B * 2, n, p.qs,
                                               device=dev).view(-1) for t in range(nbuf)]
 
+    # steps go round-robin over `streams` CUDA streams, each with its own response
+    # buffer, so that one answer's NTT work can run beside another's scan (as the
+    # serving loop runs them); the timed region still spans exactly K whole steps
+    streams = [stream] + [torch.cuda.Stream(device=dev) for _ in range(args.streams - 1)]
+    resps = [resp] + [torch.empty_like(resp) for _ in range(args.streams - 1)]
+
     def step(t, flags=0):
+        st, rs = streams[t % len(streams)], resps[t % len(streams)]
         if rg is not None:
-            g.pir_answer_folded(db, qbufs[t % nbuf], B, args.ell, rg, resp, stream=stream, flags=flags | msw,
+            g.pir_answer_folded(db, qbufs[t % nbuf], B, args.ell, rg, rs, stream=st, flags=flags | msw,
                                 tile=args.tile)
             return
         if ex is not None:
-            g.pir_answer_packed(db, ex, qbufs[t % nbuf], B, resp, stream=stream, flags=flags | msw,
-                                tile=args.tile)
+            g.pir_answer_packed(db, ex, qbufs[t % nbuf], B, rs, stream=st, flags=flags | msw, tile=args.tile)
             return
-        g.pir_answer_ex(db, qbufs[t % nbuf], B, resp, stream=stream, flags=flags | msw, tile=args.tile,
+        g.pir_answer_ex(db, qbufs[t % nbuf], B, rs, stream=st, flags=flags | msw, tile=args.tile,
                         k_chunk=args.k_chunk)
 
     for t in range(args.warmup):
@@ -336,8 +342,12 @@ def our_arm(args, wl):
     ev1 = torch.cuda.Event(enable_timing=True)
     w0 = time.time()
     ev0.record(stream)
+    for st in streams[1:]:
+        st.wait_event(ev0)
     for t in range(args.steps):
         step(t, flags=g.PIR_ANSWER_STAGE_TIMES)
+    for st in streams[1:]:
+        stream.wait_stream(st)
     ev1.record(stream)
     torch.cuda.synchronize()
     w1 = time.time()
@@ -441,7 +451,7 @@ def our_arm(args, wl):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": wl, "description": desc, "batch": B, "n": n, "log2p": log2p, "D1": D1, "D2": D2,
-                       "L": L_PRIMES, "layout": args.layout, "modswitch": bool(msw),
+                       "L": L_PRIMES, "layout": args.layout, "modswitch": bool(msw), "streams": args.streams,
                        "responses": ("folded to one ciphertext per query by %d RGSW external-product levels "
                                      "(%d gadget digits; timing-only RGSW rows)" % ((D2 - 1).bit_length(), args.ell)
                                      if args.folded else "D2 ciphertexts each"),
@@ -688,6 +698,8 @@ def main(argv=None):
     ap.add_argument("--lwe-path", default="auto", choices=["auto", "tensor", "simt"])
     ap.add_argument("--packed", action="store_true",
                     help="one packed ciphertext per query, expanded on the GPU (pir_answer_packed)")
+    ap.add_argument("--streams", type=int, default=1,
+                    help="CUDA streams the steps go round-robin over (answers in flight at once)")
     ap.add_argument("--folded", action="store_true",
                     help="fold the D2 responses into one per query with RGSW external products (pir_answer_folded)")
     ap.add_argument("--ell", type=int, default=4, help="gadget digits of the expansion keys / RGSW rows")

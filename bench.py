@@ -385,12 +385,20 @@ def our_arm(args, wl):
         # INT32 pipe: one 32x32+64-bit multiply-add per modular MAC; peak derived in
         # the design notes from 152 SMs x 32 wide multiply-adds / clock x SM clock
         sm_mhz = clocks["sm_mhz"] or float(peaks.get("sm_max_mhz", 2070.0))
-        alu_peak = 152 * 32 * sm_mhz * 1e6 / 1e12
-        roofline = {"bound": "alu", "achieved": macs / (gemm_ms / 1e3) / 1e12, "peak": alu_peak,
-                    "unit": "T modMAC/s"}
+        if layout == g.PIR_LAYOUT_PLAIN:
+            alu_peak = 152 * 32 * sm_mhz * 1e6 / 1e12
+            roofline = {"bound": "alu", "achieved": macs / (gemm_ms / 1e3) / 1e12, "peak": alu_peak,
+                        "unit": "T modMAC/s", "peak_source": "152 SMs x 32 IMAD.WIDE/clk x sampled SM clock"}
+        else:
+            # limb path: 16 byte products per modular MAC on the INT8 tensor pipe; the peak
+            # is that pipe's rate measured live by the library's probe
+            tops = g.pir_probe_int8_mma(stream)
+            roofline = {"bound": "tensor", "achieved": 2.0 * 16 * macs / (gemm_ms / 1e3) / 1e12, "peak": tops,
+                        "unit": "TOPS (INT8 mma.sync)", "modmac_per_s": macs / (gemm_ms / 1e3),
+                        "peak_source": "pir_probe_int8_mma on this GPU (MEASURED_PEAKS.json has no INT8 entry)"}
     roofline["frac"] = roofline["achieved"] / roofline["peak"]
-    roofline["peak_source"] = "%s (%s)" % (peak_kind, "MEASURED_PEAKS.json hbm_gbs" if roofline["bound"] == "hbm"
-                                           else "152 SMs x 32 IMAD.WIDE/clk x sampled SM clock")
+    if roofline["bound"] == "hbm":
+        roofline["peak_source"] = "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind
     roofline["kernel"] = kernel_tag
     roofline["kernel_ms"] = gemm_ms / launches_per_step
     roofline["launches_per_step"] = launches_per_step

@@ -22,6 +22,20 @@ namespace {
 
 __device__ __forceinline__ uint32_t padx(uint32_t i) { return i + (i >> 4); }
 
+// Padded shared index of element e of a unit whose base index has bits
+// [BLO, BLO + RB) clear: when BLO >= 4, or BLO == 0 (a base aligned to 2^RB, RB <= 4),
+// the padding of base + e 2^BLO is that of base plus a constant, so the address is
+// the unit's padded base plus a compile-time offset.
+template <int BLO>
+__device__ __forceinline__ uint32_t pidx(uint32_t pbase, uint32_t base, int e) {
+  if constexpr (BLO >= 4)
+    return pbase + (uint32_t)e * ((1u << BLO) + (1u << (BLO - 4)));
+  else if constexpr (BLO == 0)
+    return pbase + (uint32_t)e;
+  else
+    return padx(base + ((uint32_t)e << BLO));
+}
+
 // x - m if x >= m, else x (x < 2m <= 2^32): as unsigned values x - m wraps above x
 // exactly when x < m, so the minimum picks the right one in two integer operations.
 __device__ __forceinline__ uint32_t csub(uint32_t x, uint32_t m) { return min(x, x - m); }
@@ -188,6 +202,7 @@ __device__ __forceinline__ void ntt_pass(uint32_t *sm, const uint32_t *__restric
     const uint32_t u = tid + r * T;
     const uint32_t lo = u & ((1u << BLO) - 1), hi = u >> BLO;
     const uint32_t base = (hi << (BLO + RB)) | lo;
+    const uint32_t pbase = padx(base);
     uint32_t v[1 << RB];
     if constexpr (SRC == SRC_U32 && BLO == 0 && RB >= 2) {
 #pragma unroll
@@ -198,9 +213,9 @@ __device__ __forceinline__ void ntt_pass(uint32_t *sm, const uint32_t *__restric
     } else {
 #pragma unroll
       for (int e = 0; e < (1 << RB); ++e) {
-        const uint32_t idx = base | ((uint32_t)e << BLO);
+        const uint32_t idx = base + ((uint32_t)e << BLO);
         if constexpr (SRC == SRC_SMEM)
-          v[e] = sm[padx(idx)];
+          v[e] = sm[pidx<BLO>(pbase, base, e)];
         else if constexpr (SRC == SRC_U32)
           v[e] = __ldg(gin + idx);
         else
@@ -226,7 +241,7 @@ __device__ __forceinline__ void ntt_pass(uint32_t *sm, const uint32_t *__restric
       }
       if constexpr (DST == DST_PAIR) {
 #pragma unroll
-        for (int e = 0; e < (1 << RB); ++e) sm[padx(base | ((uint32_t)e << BLO))] = v[e];
+        for (int e = 0; e < (1 << RB); ++e) sm[pidx<BLO>(pbase, base, e)] = v[e];
       } else if constexpr (BLO == 0 && RB >= 2) {
 #pragma unroll
         for (int e = 0; e < (1 << RB); e += 4)
@@ -235,11 +250,11 @@ __device__ __forceinline__ void ntt_pass(uint32_t *sm, const uint32_t *__restric
         *reinterpret_cast<uint2 *>(gout + base) = make_uint2(v[0], v[1]);
       } else {
 #pragma unroll
-        for (int e = 0; e < (1 << RB); ++e) gout[base | ((uint32_t)e << BLO)] = v[e];
+        for (int e = 0; e < (1 << RB); ++e) gout[base + ((uint32_t)e << BLO)] = v[e];
       }
     } else {
 #pragma unroll
-      for (int e = 0; e < (1 << RB); ++e) sm[padx(base | ((uint32_t)e << BLO))] = v[e];
+      for (int e = 0; e < (1 << RB); ++e) sm[pidx<BLO>(pbase, base, e)] = v[e];
     }
   }
 }

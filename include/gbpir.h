@@ -90,6 +90,8 @@ pir_status_t pir_make_params(uint32_t n, uint32_t log2p, uint32_t D1, uint32_t D
  *   out_handle: receives the handle; the library owns the resident DB until
  *               pir_free_db.  The caller keeps ownership of raw_db.
  * Errors: PIR_ERR_ARG (NULL pointers, raw_bytes mismatch, invalid params),
+ * PIR_ERR_UNSUPPORTED (D2 not a multiple of 4: the kernels move columns four at a
+ * time; the limb layout with D1 not a multiple of 32: its tensor steps take 32 rows),
  * PIR_ERR_ADMISSION (resident bytes exceed the free device memory less a reserve),
  * PIR_ERR_OOM, PIR_ERR_CUDA. */
 pir_status_t pir_setup_db(const pir_params_t *params, const void *raw_db, size_t raw_bytes, int raw_on_device,
@@ -115,7 +117,11 @@ pir_status_t pir_answer(pir_db_t db, const uint32_t *queries, uint32_t B, uint32
 typedef struct {
   uint32_t k_chunk;  /* 0 = whole D1 at once; else fold D1 in chunks of this many
                         ciphertexts (bounds the scratch memory to one chunk)        */
-  uint32_t tile;     /* 0 = built-in choice; else a GEMM tile id (pir_gemm_tiles)  */
+  uint32_t tile;     /* 0 = built-in choice; else a GEMM tile id (pir_gemm_tiles) that
+                        holds the batch: plain 1, 2, 3 and 7 take at most 2, 4, 8 and
+                        8 query rows (2B), 7 also D2 <= 512; limb 2 and 3 need the
+                        rows padded to 16 to be multiples of 32 and 64; otherwise
+                        PIR_ERR_ARG */
   uint32_t flags;    /* PIR_ANSWER_STAGE_TIMES: record CUDA events around each stage on
                         `stream`, read with pir_stage_times; PIR_ANSWER_TEST_STALL,
                         PIR_ANSWER_MODSWITCH: see below.  Other bits must be 0. */

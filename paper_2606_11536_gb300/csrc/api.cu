@@ -211,6 +211,7 @@ pir_status_t answer_device(pir_db *db, const uint32_t *queries, uint32_t B, uint
   const uint32_t tile_count = db->layout == PIR_LAYOUT_PLAIN ? gemm_plain_tiles() : gemm_limb_tiles();
   if (o.tile > tile_count || (o.flags & ~(PIR_ANSWER_STAGE_TIMES | PIR_ANSWER_TEST_STALL | PIR_ANSWER_MODSWITCH)) != 0)
     return PIR_ERR_ARG;
+  if (limb ? !gemm_limb_tile_ok(o.tile, Mp) : !gemm_plain_tile_ok(o.tile, M, D2)) return PIR_ERR_ARG;
   // With modulus switching the inverse NTT reads the full-modulus responses from
   // scratch and writes [B][D2][2][n] over q_0 to `responses`.
   const bool msw = (o.flags & PIR_ANSWER_MODSWITCH) != 0 && !ntt_out;

@@ -153,6 +153,10 @@ cudaError_t launch_gemm_limb(const ParamCtx &c, const uint8_t *db, uint32_t D1, 
                              uint32_t M, uint32_t Mp, uint32_t i0, uint32_t Kc, uint32_t *out, int acc,
                              uint32_t tile, cudaStream_t s);
 uint32_t gemm_limb_tiles();
+// Whether a tile id holds a shape (the plain tiles 1-3 and 7 bound the query rows;
+// the limb tiles need the padded rows to fill whole warp tiles).
+bool gemm_plain_tile_ok(uint32_t tile, uint32_t M, uint32_t D2);
+bool gemm_limb_tile_ok(uint32_t tile, uint32_t Mp);
 
 // ---------------------------------------------------------------------------
 // Device helpers

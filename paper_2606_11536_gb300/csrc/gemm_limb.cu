@@ -191,6 +191,16 @@ cudaError_t limb_launch(const ParamCtx &c, const uint8_t *db, uint32_t D1, uint3
 // 0 picks by the padded row count Mp (a multiple of 16).
 uint32_t gemm_limb_tiles() { return 3; }
 
+bool gemm_limb_tile_ok(uint32_t tile, uint32_t Mp) {
+  switch (tile) {
+    case 0: return true;
+    case 1: return Mp % 16 == 0;
+    case 2: return Mp % 32 == 0;
+    case 3: return Mp % 64 == 0;
+  }
+  return false;
+}
+
 cudaError_t launch_gemm_limb(const ParamCtx &c, const uint8_t *db, uint32_t D1, uint32_t D2, const uint8_t *ql,
                              uint32_t M, uint32_t Mp, uint32_t i0, uint32_t Kc, uint32_t *out, int acc,
                              uint32_t tile, cudaStream_t s) {

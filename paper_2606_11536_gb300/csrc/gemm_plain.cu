@@ -292,6 +292,17 @@ cudaError_t gemm_launch(const ParamCtx &c, const uint32_t *db, uint32_t D1, uint
 // GEMM tile by M.
 uint32_t gemm_plain_tiles() { return 7; }
 
+bool gemm_plain_tile_ok(uint32_t tile, uint32_t M, uint32_t D2) {
+  switch (tile) {
+    case 0: case 4: case 5: case 6: return true;
+    case 1: return M <= 2;
+    case 2: return M <= 4;
+    case 3: return M <= 8;
+    case 7: return scan_tma_supports(M, D2);
+  }
+  return false;
+}
+
 cudaError_t launch_gemm_plain(const ParamCtx &c, const uint32_t *db, uint32_t D1, uint32_t D2, const uint32_t *qs,
                               uint32_t M, uint32_t Mp, uint32_t i0, uint32_t Kc, uint32_t *out, int acc,
                               uint32_t tile, int stall_test, cudaStream_t s) {

@@ -373,9 +373,12 @@ def our_arm(args, wl):
     peaks, peak_kind = measured_peaks()
     src = os.path.join(ROOT, "paper_2606_11536_gb300", "csrc",
                        "gemm_plain.cu" if layout == g.PIR_LAYOUT_PLAIN else "gemm_limb.cu")
-    if layout == g.PIR_LAYOUT_PLAIN and M <= 8:
-        # the built-in choice takes the TMA scan up to 4 query rows and the GEMV above
-        kernel_tag = "scan_tma" if (D2 <= 512 and (args.tile == 7 or (args.tile == 0 and M <= 4))) else "gemv_scan"
+    # the built-in choice takes the TMA scan up to 4 query rows (bound by HBM), the
+    # GEMV tiles 1-3 when asked for (HBM-shaped), and the tiled GEMMs otherwise (ALU)
+    streaming = layout == g.PIR_LAYOUT_PLAIN and M <= 8 and (
+        args.tile in (1, 2, 3, 7) or (args.tile == 0 and M <= 4 and D2 <= 512))
+    if streaming:
+        kernel_tag = "scan_tma" if args.tile in (0, 7) else "gemv_scan"
         alg_bytes = nslots * (D1 * D2 * 4 + D1 * Mp * 4 + M * D2 * 4)
         roofline = {"bound": "hbm", "achieved": alg_bytes / (gemm_ms / 1e3) / 1e9,
                     "peak": float(peaks["hbm_gbs"]), "unit": "GB/s"}

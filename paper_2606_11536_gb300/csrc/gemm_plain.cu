@@ -158,14 +158,18 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool pr
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
 
-template <int TM, int TC, int RM>
+// KS: K rows per stage (a multiple of the 8 products between folds); the narrow tiles
+// for small batches take fewer rows so that their wide column tile fits static
+// shared memory.
+template <int TM, int TC, int RM, int KS = kKS>
 __global__ void __launch_bounds__(256) k_gemm(const uint32_t *__restrict__ db, const uint32_t *__restrict__ qs,
                                               uint32_t M, uint32_t Mp, uint32_t D1, uint32_t D2, uint32_t i0,
                                               uint32_t Kc, uint32_t *__restrict__ out, ModConst mc, uint32_t logn,
                                               int acc_in) {
   static_assert((TM / RM) * (TC / 8) == 256, "thread tile RM x 8 over 256 threads");
-  __shared__ __align__(16) uint32_t As[2][kKS][TM];
-  __shared__ __align__(16) uint32_t Bs[2][kKS][TC];
+  static_assert(KS % kFoldProducts == 0, "folds fall on whole groups of K rows");
+  __shared__ __align__(16) uint32_t As[2][KS][TM];
+  __shared__ __align__(16) uint32_t Bs[2][KS][TC];
   const uint32_t nct = (D2 + TC - 1) / TC, nmt = (Mp + TM - 1) / TM;
   const uint64_t bid = blockIdx.x;
   const uint32_t ct = (uint32_t)(bid % nct);
@@ -182,13 +186,13 @@ __global__ void __launch_bounds__(256) k_gemm(const uint32_t *__restrict__ db, c
 
   // loader mapping: A tile = kKS x TM words = kKS*TM/4 uint4; B tile = kKS*TC/4 uint4
   auto load_tiles = [&](int buf, uint32_t k0) {
-    for (uint32_t t = tid; t < kKS * TM / 4; t += 256) {
+    for (uint32_t t = tid; t < KS * TM / 4; t += 256) {
       const uint32_t r = t / (TM / 4), c4 = (t % (TM / 4)) * 4;
       const bool ok = (k0 + r < Kc) && (m0 + c4 < Mp);
       const uint32_t *g = ok ? qss + (uint64_t)(k0 + r) * Mp + m0 + c4 : qss;
       cp_async16(&As[buf][r][c4], g, ok);
     }
-    for (uint32_t t = tid; t < kKS * TC / 4; t += 256) {
+    for (uint32_t t = tid; t < KS * TC / 4; t += 256) {
       const uint32_t r = t / (TC / 4), c4 = (t % (TC / 4)) * 4;
       const bool ok = (k0 + r < Kc) && (c0 + c4 < D2);
       const uint32_t *g = ok ? dbs + (uint64_t)(k0 + r) * D2 + c0 + c4 : dbs;
@@ -203,24 +207,26 @@ __global__ void __launch_bounds__(256) k_gemm(const uint32_t *__restrict__ db, c
 #pragma unroll
     for (int b = 0; b < 8; ++b) acc[a][b] = 0;
 
-  const uint32_t nk = (Kc + kKS - 1) / kKS;
+  const uint32_t nk = (Kc + KS - 1) / KS;
   load_tiles(0, 0);
   for (uint32_t kt = 0; kt < nk; ++kt) {
     const int buf = kt & 1;
     cp_async_wait0();
     __syncthreads();
-    if (kt + 1 < nk) load_tiles(buf ^ 1, (kt + 1) * kKS);
+    if (kt + 1 < nk) load_tiles(buf ^ 1, (kt + 1) * KS);
 #pragma unroll
-    for (int half = 0; half < 2; ++half) {
+    for (int half = 0; half < KS / kFoldProducts; ++half) {
 #pragma unroll
-      for (int kk = half * 8; kk < half * 8 + 8; ++kk) {
+      for (int kk = half * kFoldProducts; kk < half * kFoldProducts + kFoldProducts; ++kk) {
         uint32_t av[RM];
         if constexpr (RM == 4) {
           const uint4 a = *reinterpret_cast<const uint4 *>(&As[buf][kk][tm * 4]);
           av[0] = a.x, av[1] = a.y, av[2] = a.z, av[3] = a.w;
-        } else {
+        } else if constexpr (RM == 2) {
           const uint2 a = *reinterpret_cast<const uint2 *>(&As[buf][kk][tm * 2]);
           av[0] = a.x, av[1] = a.y;
+        } else {
+          av[0] = As[buf][kk][tm];  // one row per thread: a broadcast within the warp
         }
         const uint4 b0 = *reinterpret_cast<const uint4 *>(&Bs[buf][kk][tc * 4]);
         const uint4 b1 = *reinterpret_cast<const uint4 *>(&Bs[buf][kk][TC / 2 + tc * 4]);
@@ -274,27 +280,27 @@ cudaError_t gemv_launch(const ParamCtx &c, const uint32_t *db, uint32_t D1, uint
   return cudaGetLastError();
 }
 
-template <int TM, int TC, int RM>
+template <int TM, int TC, int RM, int KS = kKS>
 cudaError_t gemm_launch(const ParamCtx &c, const uint32_t *db, uint32_t D1, uint32_t D2, const uint32_t *qs,
                         uint32_t M, uint32_t Mp, uint32_t i0, uint32_t Kc, uint32_t *out, int acc, cudaStream_t s) {
   const uint64_t nslots = (uint64_t)c.p.L << c.logn;
   const uint64_t blocks = nslots * ((D2 + TC - 1) / TC) * ((Mp + TM - 1) / TM);
   if (blocks > 0x7FFFFFFFull) return cudaErrorInvalidConfiguration;
-  k_gemm<TM, TC, RM><<<(unsigned)blocks, 256, 0, s>>>(db, qs, M, Mp, D1, D2, i0, Kc, out, c.mod, c.logn, acc);
+  k_gemm<TM, TC, RM, KS><<<(unsigned)blocks, 256, 0, s>>>(db, qs, M, Mp, D1, D2, i0, Kc, out, c.mod, c.logn, acc);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 // Tile ids: 1 = GEMV MB=2, 2 = GEMV MB=4, 3 = GEMV MB=8, 4 = GEMM 16x256, 5 = GEMM 32x256,
-// 6 = GEMM 64x128, 7 = TMA-staged scan (M <= 8, D2 <= 512; scan_tma.cu).  0 picks the
-// TMA scan when it holds the shape, else the smallest GEMV that holds M, else a
-// GEMM tile by M.
-uint32_t gemm_plain_tiles() { return 7; }
+// 6 = GEMM 64x128, 7 = TMA-staged scan (M <= 8, D2 <= 512; scan_tma.cu), 8 = GEMM 8x256
+// (one query row per thread, for a few queries).  0 picks the TMA scan up to 4 rows,
+// the 8-row GEMM up to 8, else a GEMM tile by M.
+uint32_t gemm_plain_tiles() { return 8; }
 
 bool gemm_plain_tile_ok(uint32_t tile, uint32_t M, uint32_t D2) {
   switch (tile) {
-    case 0: case 4: case 5: case 6: return true;
+    case 0: case 4: case 5: case 6: case 8: return true;
     case 1: return M <= 2;
     case 2: return M <= 4;
     case 3: return M <= 8;
@@ -309,10 +315,11 @@ cudaError_t launch_gemm_plain(const ParamCtx &c, const uint32_t *db, uint32_t D1
   if (tile == 0) {
     // measured on GB300: the TMA scan wins up to 4 query rows; with 6-8 rows its
     // accumulators cap it at one or two CTAs per SM and the GEMV-shaped kernel wins
+    // (5-8 rows: the 8-row GEMM tile measured 15-17% ahead of the GEMV)
     if (M <= 4 && scan_tma_supports(M, D2)) tile = 7;
     else if (M <= 2) tile = 1;
     else if (M <= 4) tile = 2;
-    else if (M <= 8) tile = 3;
+    else if (M <= 8) tile = 8;
     else if (M <= 16) tile = 4;
     else if (M <= 32) tile = 5;
     else tile = 6;
@@ -326,6 +333,7 @@ cudaError_t launch_gemm_plain(const ParamCtx &c, const uint32_t *db, uint32_t D1
     case 4: return gemm_launch<16, 256, 2>(c, db, D1, D2, qs, M, Mp, i0, Kc, out, acc, s);
     case 5: return gemm_launch<32, 256, 4>(c, db, D1, D2, qs, M, Mp, i0, Kc, out, acc, s);
     case 6: return gemm_launch<64, 128, 4>(c, db, D1, D2, qs, M, Mp, i0, Kc, out, acc, s);
+    case 8: return gemm_launch<8, 256, 1>(c, db, D1, D2, qs, M, Mp, i0, Kc, out, acc, s);
   }
   return cudaErrorInvalidValue;
 }

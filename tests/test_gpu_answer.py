@@ -70,7 +70,7 @@ def test_batches_ragged_shapes(orc, B):
         g.pir_free_db(db)
 
 
-@pytest.mark.parametrize("B,tiles", [(1, (1, 2, 3, 4, 5, 6, 7)), (2, (2, 3, 7)), (4, (3, 7))])
+@pytest.mark.parametrize("B,tiles", [(1, (1, 2, 3, 4, 5, 6, 7, 8)), (2, (2, 3, 7, 8)), (4, (3, 7, 8)), (7, (4, 8))])
 def test_small_batches_every_tile(orc, B, tiles):
     p, P, raw, db = instance(orc, 4096, 16, 50, 44, seed=60 + B)
     try:
@@ -78,7 +78,8 @@ def test_small_batches_every_tile(orc, B, tiles):
         ref = orc.answer(P, raw, Q)
         for tile in tiles:
             assert np.array_equal(run(db, P, Q, B, tile=tile), ref), tile
-        assert np.array_equal(run(db, P, Q, B, tile=7, k_chunk=13), ref)
+        if 2 * B <= 8:  # the TMA scan takes at most 8 query rows
+            assert np.array_equal(run(db, P, Q, B, tile=7, k_chunk=13), ref)
     finally:
         g.pir_free_db(db)
 

@@ -30,7 +30,7 @@ def draw(seed):
         tile = int(rng.choice([t for t, ok in ((0, True), (1, True), (2, Mp % 32 == 0), (3, Mp % 64 == 0)) if ok]))
     else:
         tiles = [0] + [t for t, ok in ((1, M <= 2), (2, M <= 4), (3, M <= 8), (4, True), (5, True), (6, True),
-                                       (7, M <= 8 and D2 <= 512)) if ok]
+                                       (7, M <= 8 and D2 <= 512), (8, True)) if ok]
         tile = int(rng.choice(tiles))
     k_chunk = 0 if rng.random() < 0.5 else int(rng.integers(1, D1 + 1))
     if layout and k_chunk:

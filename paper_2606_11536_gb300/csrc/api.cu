@@ -151,6 +151,33 @@ cudaEvent_t take_event() {
 
 thread_local bool t_capturing = false;  // launches inside a graph capture are not launches yet
 
+// Arrival of the query upload in pieces of kc ciphertexts (host-buffer answers): ev[k]
+// is recorded on the copy stream after piece k's copies; a forward NTT over
+// ciphertexts [i0, i0 + cnt) waits on every piece it touches.
+constexpr uint32_t kMaxFeedChunks = 16;
+struct ChunkFeed {
+  uint32_t n = 0, kc = 0;
+  cudaEvent_t ev[kMaxFeedChunks] = {};
+  cudaError_t wait(cudaStream_t s, uint32_t i0, uint32_t cnt) const {
+    if (n == 0 || cnt == 0) return cudaSuccess;
+    const uint32_t last = (i0 + cnt - 1) / kc;
+    for (uint32_t k = i0 / kc; k <= last && k < n; ++k) {
+      cudaError_t e = cudaStreamWaitEvent(s, ev[k], 0);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+};
+thread_local cudaStream_t t_copy_stream = nullptr;
+cudaError_t copy_stream(cudaStream_t *out) {
+  if (!t_copy_stream) {
+    cudaError_t e = cudaStreamCreateWithFlags(&t_copy_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+  }
+  *out = t_copy_stream;
+  return cudaSuccess;
+}
+
 struct StageTimer {
   bool on;
   cudaStream_t s;
@@ -176,7 +203,8 @@ struct StageTimer {
 // ntt_out: leave the responses in NTT form (no inverse NTT, no modulus switching),
 // for the folding of the remaining dimensions.
 pir_status_t answer_device(pir_db *db, const uint32_t *queries, uint32_t B, uint32_t *responses, cudaStream_t s,
-                           const pir_answer_opts_t &o, const uint32_t *qhat_ready = nullptr, bool ntt_out = false) {
+                           const pir_answer_opts_t &o, const uint32_t *qhat_ready = nullptr, bool ntt_out = false,
+                           const ChunkFeed *feed = nullptr) {
   const ParamCtx &c = *db->ctx;
   const pir_params_t &p = db->p;
   const uint32_t n = p.n, L = p.L, D1 = p.D1, D2 = p.D2;
@@ -227,18 +255,23 @@ pir_status_t answer_device(pir_db *db, const uint32_t *queries, uint32_t B, uint
   // Batch 1 on the TMA scan: the forward NTT writes the slot layout itself (pairs of
   // a/b residues, Mp = 2) and the scan writes the response layout itself, so neither
   // transpose runs.
-  const bool fused =
-      !qhat_ready && !limb && B == 1 && (o.tile == 0 || o.tile == 7) && scan_tma_supports(M, D2) && Kc % 2 == 0;
+  // (every chunk, the last included, must hold an even number of ciphertexts)
+  const bool fused = !qhat_ready && !limb && B == 1 && (o.tile == 0 || o.tile == 7) && scan_tma_supports(M, D2) &&
+                     Kc % 2 == 0 && D1 % 2 == 0;
   // full-modulus responses before switching: the unused result area on the fused
   // path (the same size at B = 1), an area of their own otherwise
   StageTimer tm((o.flags & PIR_ANSWER_STAGE_TIMES) != 0, s);
   const size_t full_bytes = (msw && !fused) ? (size_t)B * D2 * 2 * L * n * 4 : 0;
+  // K-chunked fused path: the chunks before the last accumulate slot-major here
+  const size_t slot_bytes = (fused && Kc < D1) ? out_bytes : 0;
   Scratch scratch(s);
-  CK(scratch.alloc(up(qhat_bytes) + up(qs_bytes) + up(out_bytes) + up(full_bytes)));
+  CK(scratch.alloc(up(qhat_bytes) + up(qs_bytes) + up(out_bytes) + up(full_bytes) + up(slot_bytes)));
   char *base = static_cast<char *>(scratch.ptr);
   const uint32_t *qhat = qhat_ready ? qhat_ready : reinterpret_cast<uint32_t *>(base);
   void *qs = base + up(qhat_bytes);
   uint32_t *out = reinterpret_cast<uint32_t *>(base + up(qhat_bytes) + up(qs_bytes));
+  uint32_t *slotbuf = reinterpret_cast<uint32_t *>(base + up(qhat_bytes) + up(qs_bytes) + up(out_bytes) +
+                                                   up(full_bytes));
   uint32_t *full = !msw ? responses
                         : fused ? out : reinterpret_cast<uint32_t *>(base + up(qhat_bytes) + up(qs_bytes) + up(out_bytes));
   auto finish = [&]() -> pir_status_t {  // inverse NTT (with the switch when asked)
@@ -257,17 +290,34 @@ pir_status_t answer_device(pir_db *db, const uint32_t *queries, uint32_t B, uint
     for (uint32_t i0 = 0; i0 < D1; i0 += Kc) {
       const uint32_t kc = D1 - i0 < Kc ? D1 - i0 : Kc;
       tm.begin();
-      CK(launch_ntt_fwd_pair_slots(c, queries, D1, i0, kc, qs2, s));
-      tm.end(0, 1);
+      uint64_t nl = 1;
+      if (feed && feed->n > 1 && Kc == D1) {
+        // one scan pass; the forward NTT follows the upload piece by piece
+        nl = 0;
+        for (uint32_t p0 = 0; p0 < D1; p0 += feed->kc, ++nl) {
+          const uint32_t pc = D1 - p0 < feed->kc ? D1 - p0 : feed->kc;
+          CK(feed->wait(s, p0, pc));
+          CK(launch_ntt_fwd_pair_slots(c, queries, p0, pc, D1, p0, qs2, s));
+        }
+      } else {
+        if (feed) CK(feed->wait(s, i0, kc));
+        CK(launch_ntt_fwd_pair_slots(c, queries, i0, kc, kc, 0, qs2, s));
+      }
+      tm.end(0, nl);
       tm.begin();
-      CK(launch_scan_tma(c, static_cast<const uint32_t *>(db->resident), D1, D2, qs2, M, 2, i0, kc, full, i0 > 0,
-                         stall, 1, s));
+      // single pass: straight to the response layout; several K-chunks: slot-major
+      // accumulation, and the last chunk adds it in while writing the response layout
+      const bool last = i0 + kc >= D1;
+      CK(launch_scan_tma(c, static_cast<const uint32_t *>(db->resident), D1, D2, qs2, M, 2, i0, kc,
+                         last ? full : slotbuf, !last && i0 > 0, stall, last ? 1 : 0, (last && i0 > 0) ? slotbuf : nullptr,
+                         s));
       tm.end(2, 1);
     }
     return finish();
   }
   for (uint32_t i0 = 0; i0 < D1; i0 += Kc) {
     const uint32_t kc = D1 - i0 < Kc ? D1 - i0 : Kc;
+    if (feed) CK(feed->wait(s, i0, kc));
     // forward NTT of ciphertexts i0 .. i0+kc-1 of every query: per query b the rows
     // (b*D1 + i0)*2L .. +kc*2L are contiguous.
     const uint64_t G = (uint64_t)kc * 2 * L, S = (uint64_t)D1 * 2 * L;
@@ -483,16 +533,55 @@ pir_status_t pir_answer_ex(pir_db_t db, const uint32_t *queries, uint32_t B, uin
   Scratch dq(s), dr(s);
   CK(dq.alloc(qbytes));
   CK(dr.alloc(rbytes));
-  CK(cudaMemcpyAsync(dq.ptr, queries, qbytes, cudaMemcpyHostToDevice, s));
-  pir_status_t st =
-      answer_device(db, static_cast<const uint32_t *>(dq.ptr), B, static_cast<uint32_t *>(dr.ptr), s, o);
-  if (st != PIR_OK) {
-    cudaStreamSynchronize(s);
-    return st;
+  // A large upload goes in K-chunk pieces on a copy stream; each chunk's forward NTT
+  // waits only for its own piece, so later pieces arrive while earlier chunks are
+  // being scanned.  Only when the caller leaves the chunking to the library.
+  pir_answer_opts_t o2 = o;
+  ChunkFeed feed;
+  const bool limb = db->layout == PIR_LAYOUT_LIMB;
+  uint32_t Kc = p.D1;
+  if (o.k_chunk == 0 && qbytes >= (8ull << 20) && qbytes <= (4ull << 30) && p.D1 >= 8) {
+    uint32_t kc = (p.D1 + 3) / 4;
+    kc = limb ? (kc + 31) & ~31u : (kc + 1) & ~1u;
+    if (kc < p.D1 && (!limb || kc <= 8192)) Kc = kc;
   }
-  CK(cudaMemcpyAsync(responses, dr.ptr, rbytes, cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  return PIR_OK;
+  cudaStream_t cs = nullptr;
+  if (Kc < p.D1 && copy_stream(&cs) == cudaSuccess) {
+    // batch 1 on the plain layout keeps one scan pass (a K-chunked scan costs more
+    // than the upload it hides) and pipelines only the forward NTT behind the pieces
+    if (B > 1 || limb) o2.k_chunk = Kc;
+    feed.kc = Kc;
+    feed.n = (p.D1 + Kc - 1) / Kc;
+    cudaEvent_t ready = take_event();  // the scratch is allocated in s's order
+    if (!ready) return PIR_ERR_CUDA;
+    CK(cudaEventRecord(ready, s));
+    CK(cudaStreamWaitEvent(cs, ready, 0));
+    t_free_events.push_back(ready);
+    const size_t ct = (size_t)2 * p.L * p.n;  // words per ciphertext
+    for (uint32_t k = 0; k < feed.n; ++k) {
+      const uint32_t i0 = k * Kc, kc = p.D1 - i0 < Kc ? p.D1 - i0 : Kc;
+      for (uint32_t b = 0; b < B; ++b) {
+        const size_t off = ((size_t)b * p.D1 + i0) * ct;
+        CK(cudaMemcpyAsync(static_cast<uint32_t *>(dq.ptr) + off, queries + off, (size_t)kc * ct * 4,
+                           cudaMemcpyHostToDevice, cs));
+      }
+      if (!(feed.ev[k] = take_event())) return PIR_ERR_CUDA;
+      CK(cudaEventRecord(feed.ev[k], cs));
+    }
+  } else {
+    CK(cudaMemcpyAsync(dq.ptr, queries, qbytes, cudaMemcpyHostToDevice, s));
+  }
+  pir_status_t st = answer_device(db, static_cast<const uint32_t *>(dq.ptr), B, static_cast<uint32_t *>(dr.ptr), s,
+                                  o2, nullptr, false, feed.n ? &feed : nullptr);
+  if (st == PIR_OK) {
+    cudaError_t e = cudaMemcpyAsync(responses, dr.ptr, rbytes, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) st = cuda_status(e);
+  }
+  cudaStreamSynchronize(s);
+  if (cs) cudaStreamSynchronize(cs);  // the pieces are all consumed; their events can be reused
+  for (uint32_t k = 0; k < feed.n; ++k)
+    if (feed.ev[k]) t_free_events.push_back(feed.ev[k]);
+  return st;
 }
 
 pir_status_t pir_answer_packed(pir_db_t db, pir_expander_t expander, const uint32_t *packed, uint32_t B,

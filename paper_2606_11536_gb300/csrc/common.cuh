@@ -108,10 +108,10 @@ cudaError_t launch_ntt_fwd_rows_t(const ParamCtx &c, const uint32_t *src, uint64
 // q_0 fused in: dst [count][n] over q_0.  src and dst must not overlap.
 cudaError_t launch_ntt_inv_switch(const ParamCtx &c, const uint32_t *src, uint32_t *dst, uint64_t count,
                                   cudaStream_t s);
-// Batch-1 queries [1][D1][2][L][n]: forward NTT of ciphertexts i0 .. i0+Kc-1 written
-// directly as the plain slot layout [L*n][Kc][2] (Mp = 2).
-cudaError_t launch_ntt_fwd_pair_slots(const ParamCtx &c, const uint32_t *queries, uint32_t D1, uint32_t i0, uint32_t Kc,
-                                      uint32_t *slots, cudaStream_t s);
+// Batch-1 queries [1][D1][2][L][n]: forward NTT of ciphertexts i0 .. i0+kc-1 written
+// directly into the plain slot layout [L*n][stride][2] (Mp = 2), columns col0 .. col0+kc-1.
+cudaError_t launch_ntt_fwd_pair_slots(const ParamCtx &c, const uint32_t *queries, uint32_t i0, uint32_t kc,
+                                      uint32_t stride, uint32_t col0, uint32_t *slots, cudaStream_t s);
 // Forward NTT of DB plaintexts read from the raw bit stream (RNS lift fused: a
 // coefficient < p < q_j is its own residue).  Row-major: polys first .. first+np-1;
 // column-major: local poly p is (i, c) = (p % D1, first + p / D1).  dst is [np][L][n].
@@ -143,9 +143,11 @@ uint32_t gemm_plain_tiles();
 // completes (exercises the bounded-wait error path).
 bool scan_tma_supports(uint32_t M, uint32_t D2);
 // out_poly = 1 writes the response layout [B][D2][2][L][n] (NTT domain) directly.
+// acc_src, when set, is a slot-major partial result [L*n][M][D2] added in before the
+// write (the K-chunks before the last accumulate there with coalesced accesses).
 cudaError_t launch_scan_tma(const ParamCtx &c, const uint32_t *db, uint32_t D1, uint32_t D2, const uint32_t *qs,
                             uint32_t M, uint32_t Mp, uint32_t i0, uint32_t Kc, uint32_t *out, int acc, int stall_test,
-                            int out_poly, cudaStream_t s);
+                            int out_poly, const uint32_t *acc_src, cudaStream_t s);
 
 // gemm_limb.cu: the same contract on the limb layouts (db [s][4][D2][D1] u8,
 // ql [s][4][Mp][Kc] u8), exact through u8 x u8 -> s32 tensor-pipe products.

@@ -326,7 +326,7 @@ cudaError_t launch_gemm_plain(const ParamCtx &c, const uint32_t *db, uint32_t D1
   }
   if (stall_test && tile != 7) return cudaErrorInvalidValue;
   switch (tile) {
-    case 7: return launch_scan_tma(c, db, D1, D2, qs, M, Mp, i0, Kc, out, acc, stall_test, 0, s);
+    case 7: return launch_scan_tma(c, db, D1, D2, qs, M, Mp, i0, Kc, out, acc, stall_test, 0, nullptr, s);
     case 1: return M <= 2 ? gemv_launch<2>(c, db, D1, D2, qs, M, Mp, i0, Kc, out, acc, s) : cudaErrorInvalidValue;
     case 2: return M <= 4 ? gemv_launch<4>(c, db, D1, D2, qs, M, Mp, i0, Kc, out, acc, s) : cudaErrorInvalidValue;
     case 3: return M <= 8 ? gemv_launch<8>(c, db, D1, D2, qs, M, Mp, i0, Kc, out, acc, s) : cudaErrorInvalidValue;

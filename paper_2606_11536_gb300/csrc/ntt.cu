@@ -439,13 +439,13 @@ __global__ void __launch_bounds__((1 << LOGN) / 8, 8192 >> LOGN)  // <= 64 regis
 
 // Forward NTT of the a- and b-polynomial of one ciphertext (rows (i, comp 0) and
 // (i, comp 1) of prime j of a batch-1 query chunk), written straight into the
-// slot-major layout [L*n][Kc][2] that the batch-1 scan reads: the transpose of
+// slot-major layout [L*n][stride][2] that the batch-1 scan reads (column col0 + i): the transpose of
 // Sec. 4.2 fused into the NTT.  Block = i * L + j, 2 x n/16 threads: each half
 // transforms one row in its own shared buffer, then all threads write the pairs.
 template <int LOGN>
 __global__ void __launch_bounds__((1 << LOGN) / 8)
-    k_ntt_fwd_pair_slots(const uint32_t *__restrict__ src, uint64_t row0, NttConst C, uint32_t L, uint32_t Kc,
-                         uint32_t *__restrict__ slots) {
+    k_ntt_fwd_pair_slots(const uint32_t *__restrict__ src, uint64_t row0, NttConst C, uint32_t L, uint32_t stride,
+                         uint32_t col0, uint32_t *__restrict__ slots) {
   constexpr int N = 1 << LOGN, PADN = N + N / 16, T = N / 16;
   extern __shared__ uint32_t sm[];
   const uint32_t i = blockIdx.x / L, j = blockIdx.x % L;
@@ -478,9 +478,9 @@ __global__ void __launch_bounds__((1 << LOGN) / 8)
     ntt_pass<13, 1, 0, true, SRC_SMEM, DST_PAIR>(smh, gin, rs, 0, gout, tw, q, 0, 0, nullptr, tid);
   }
   __syncthreads();
-  uint32_t *dst = slots + ((uint64_t)j * N * Kc + i) * 2;
+  uint32_t *dst = slots + ((uint64_t)j * N * stride + col0 + i) * 2;
   for (uint32_t k = threadIdx.x; k < (uint32_t)N; k += 2 * T)
-    *reinterpret_cast<uint2 *>(dst + (uint64_t)k * Kc * 2) = make_uint2(sm[padx(k)], sm[PADN + padx(k)]);
+    *reinterpret_cast<uint2 *>(dst + (uint64_t)k * stride * 2) = make_uint2(sm[padx(k)], sm[PADN + padx(k)]);
 }
 
 constexpr uint64_t kMaxGrid = 1u << 30;
@@ -551,25 +551,25 @@ cudaError_t launch_ntt_fwd_raw(const ParamCtx &c, const uint8_t *raw, int col_ma
 }
 
 template <int LOGN>
-cudaError_t pair_launch(const ParamCtx &c, const uint32_t *src, uint64_t row0, uint32_t Kc, uint32_t *slots,
-                        cudaStream_t s) {
+cudaError_t pair_launch(const ParamCtx &c, const uint32_t *src, uint64_t row0, uint32_t kc, uint32_t stride,
+                        uint32_t col0, uint32_t *slots, cudaStream_t s) {
   const int T = (1 << LOGN) / 8;  // two rows in parallel
   const int smem = 2 * ((1 << LOGN) + (1 << LOGN) / 16) * (int)sizeof(uint32_t);
   cudaError_t e = cudaFuncSetAttribute(k_ntt_fwd_pair_slots<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  k_ntt_fwd_pair_slots<LOGN><<<Kc * c.p.L, T, smem, s>>>(src, row0, c.ntt, c.p.L, Kc, slots);
+  k_ntt_fwd_pair_slots<LOGN><<<kc * c.p.L, T, smem, s>>>(src, row0, c.ntt, c.p.L, stride, col0, slots);
   return cudaGetLastError();
 }
 
-cudaError_t launch_ntt_fwd_pair_slots(const ParamCtx &c, const uint32_t *queries, uint32_t D1, uint32_t i0, uint32_t Kc,
-                                      uint32_t *slots, cudaStream_t s) {
-  (void)D1;
-  if (Kc == 0) return cudaSuccess;
+cudaError_t launch_ntt_fwd_pair_slots(const ParamCtx &c, const uint32_t *queries, uint32_t i0, uint32_t kc,
+                                      uint32_t stride, uint32_t col0, uint32_t *slots, cudaStream_t s) {
+  if (kc == 0) return cudaSuccess;
+  if (col0 + (uint64_t)kc > stride) return cudaErrorInvalidValue;
   const uint64_t row0 = (uint64_t)i0 * 2 * c.p.L;  // row (b = 0, i0, comp 0, j = 0)
   switch (c.logn) {
-    case 11: return pair_launch<11>(c, queries, row0, Kc, slots, s);
-    case 12: return pair_launch<12>(c, queries, row0, Kc, slots, s);
-    case 13: return pair_launch<13>(c, queries, row0, Kc, slots, s);
+    case 11: return pair_launch<11>(c, queries, row0, kc, stride, col0, slots, s);
+    case 12: return pair_launch<12>(c, queries, row0, kc, stride, col0, slots, s);
+    case 13: return pair_launch<13>(c, queries, row0, kc, stride, col0, slots, s);
   }
   return cudaErrorInvalidValue;
 }

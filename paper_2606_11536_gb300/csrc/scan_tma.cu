@@ -101,6 +101,7 @@ struct ScanArgs {
   int acc_in;
   int stall_test;      // consumers wait on a barrier nobody arrives on (tests the timeout path)
   int out_poly;        // 1: out is the response layout [B][D2][2][L*n] (NTT domain), else [L*n][M][D2]
+  const uint32_t *acc_src;  // optional slot-major partial [L*n][M][D2] added before the write
 };
 
 // Rows per unrolled group and CTAs per SM, by accumulator count (MB rows x T quads):
@@ -275,6 +276,13 @@ __global__ void __launch_bounds__(kThreads, ScanShape<MB, T>::kMinBlocks) k_scan
           r[e] = v;
         }
         if (phs == 0 && qv[t] && (uint32_t)m < a.M) {
+          if (a.acc_src) {  // earlier K-chunks, slot-major: one coalesced 16-byte read
+            const uint4 prev = *reinterpret_cast<const uint4 *>(a.acc_src + ((uint64_t)s * a.M + m) * a.D2 + 4 * quad[t]);
+            r[0] = reduce64((uint64_t)r[0] + prev.x, q, mu);
+            r[1] = reduce64((uint64_t)r[1] + prev.y, q, mu);
+            r[2] = reduce64((uint64_t)r[2] + prev.z, q, mu);
+            r[3] = reduce64((uint64_t)r[3] + prev.w, q, mu);
+          }
           if (a.out_poly) {
             // response layout: element (b, c, comp, j, k) at ((b*D2 + c)*2 + comp)*L*n + s.
             // Consecutive slots go to consecutive CTAs at about the same time, so the
@@ -330,7 +338,7 @@ bool scan_tma_supports(uint32_t M, uint32_t D2) { return M <= 8 && D2 % 4 == 0 &
 
 cudaError_t launch_scan_tma(const ParamCtx &c, const uint32_t *db, uint32_t D1, uint32_t D2, const uint32_t *qs,
                             uint32_t M, uint32_t Mp, uint32_t i0, uint32_t Kc, uint32_t *out, int acc, int stall_test,
-                            int out_poly, cudaStream_t s) {
+                            int out_poly, const uint32_t *acc_src, cudaStream_t s) {
   // query rows are bulk-copied: Mp = 2 needs an even Kc (16-byte chunk starts)
   if (!scan_tma_supports(M, D2) || Kc == 0 || !(Mp % 4 == 0 || (Mp == 2 && M <= 2 && Kc % 2 == 0)))
     return cudaErrorInvalidValue;
@@ -358,6 +366,7 @@ cudaError_t launch_scan_tma(const ParamCtx &c, const uint32_t *db, uint32_t D1, 
   a.acc_in = acc;
   a.stall_test = stall_test;
   a.out_poly = out_poly;
+  a.acc_src = acc_src;
   const uint32_t nq = D2 / 4;
   const int T = nq > 64 ? 2 : 1;  // 8 warps x 8 quads per pass
   const int MB = M <= 2 ? 2 : M <= 4 ? 4 : 8;

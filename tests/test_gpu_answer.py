@@ -206,3 +206,22 @@ def test_limb_full_size_1gib_batch8(orc):
         assert orc.freivalds(P, raw, Q, R, synth.freivalds_vector(4, P.qs, D2)) == 0
     finally:
         g.pir_free_db(db)
+
+
+@pytest.mark.parametrize("D1,B,k_chunk", [(99, 1, 26), (99, 1, 0), (120, 1, 0), (118, 1, 0), (64, 3, 0)])
+def test_host_buffers_pipelined_upload_and_odd_chunks(orc, D1, B, k_chunk):
+    """Host-buffer answers whose upload is split into pieces on a copy stream (queries
+    of 8 MiB and more): batch 1 keeps one scan pass with the forward NTT following the
+    pieces (D1 = 120, 118: equal and ragged pieces), an odd D1 takes the unfused path,
+    batch 3 scans K-chunk by K-chunk; and an odd D1 with an even chunk size."""
+    n = 8192 if D1 >= 100 else 4096
+    p, P, raw, db = instance(orc, n, 16, D1, 8, seed=D1 + B)
+    try:
+        Q = random_queries(P, B, 77 + D1)
+        ref = orc.answer(P, raw, Q)
+        host = np.zeros(ref.shape, dtype=np.uint32)
+        g.pir_answer_ex(db, Q, B, host, k_chunk=k_chunk)
+        assert np.array_equal(host, ref)
+        assert np.array_equal(run(db, P, Q, B, k_chunk=k_chunk), ref)
+    finally:
+        g.pir_free_db(db)

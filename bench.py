@@ -412,10 +412,16 @@ def our_arm(args, wl):
 
     # end to end through the public API with pinned host buffers
     e2e = None
-    if (qwords + rwords) * 4 <= (16 << 30):
+    try:
+        host_ram = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES")
+    except (ValueError, OSError):
+        host_ram = 64 << 30
+    # pinned host buffers up to half of host memory; host batches above 4 GiB
+    # run as a streamed answer inside pir_answer_ex (pieces of at most 1 GiB)
+    if (qwords + rwords) * 4 <= host_ram // 2:
         qh = torch.empty(qwords, dtype=torch.int32, pin_memory=True)
         rh = torch.empty(rwords, dtype=torch.int32, pin_memory=True)
-        qh.copy_(qbufs[0].cpu())
+        qh.copy_(qbufs[0])
         e2e_steps = max(3, min(args.steps, 50))
         rgh = None
         if rg is not None:

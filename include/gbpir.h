@@ -144,8 +144,47 @@ typedef struct {
  * transpose, inverse NTT. */
 #define PIR_STAGES 5
 
+/* pir_answer with options.  With host buffers and k_chunk = 0, queries of 8 MiB to
+ * 4 GiB are uploaded in four pieces on a copy stream, each piece's forward NTT
+ * waiting only for its own copy; larger host batches run as a streamed answer
+ * (pir_answer_begin below) in pieces of at most 1 GiB, so the device holds one
+ * piece at a time. */
 pir_status_t pir_answer_ex(pir_db_t db, const uint32_t *queries, uint32_t B, uint32_t *responses, int on_device,
                            void *stream, const pir_answer_opts_t *opts);
+
+/* Streamed answer: the queries arrive in pieces along D1 (Sec. 4.4, stream-wise
+ * buffering of the first-dimension scan), so a batch whose query ciphertexts do
+ * not fit device memory, or whose upload should overlap the scan, needs only one
+ * piece resident at a time.
+ *   pir_answer_begin: opens a session for B queries against db; kc_max bounds the
+ *     ciphertexts per piece (the device scratch is sized by it).  opts as for
+ *     pir_answer_ex except that k_chunk must be 0 and PIR_ANSWER_TEST_STALL is
+ *     refused.  Work runs on `stream`.
+ *   pir_answer_chunk: ciphertexts i0 .. i0+kc-1 of every query, [B][kc][2][L][n]
+ *     uint32 coefficient form, canonical.  Pieces come in order: i0 is the first
+ *     ciphertext not yet given, 1 <= kc <= kc_max, i0 + kc <= D1; on the limb
+ *     layout kc is a multiple of 32.  Device buffers (on_device = 1) are read in
+ *     `stream`'s order and must stay valid until the work is done.  Host buffers
+ *     are copied on a copy stream through two staging buffers, so the copy of
+ *     one piece overlaps the scan of the previous one; the call returns once its
+ *     copy is complete and the buffer may be reused.
+ *   pir_answer_end: after all D1 ciphertexts, writes the responses as pir_answer_ex
+ *     does ([B][D2][2][L][n], or [B][D2][2][n] over q_0 with PIR_ANSWER_MODSWITCH);
+ *     host buffers are filled when it returns.  Releases the session in every
+ *     case.  pir_answer_abort releases it without a result.
+ * The result equals pir_answer_ex on the whole query buffer.  The DB must outlive
+ * the session.  A failed pir_answer_chunk leaves the session failed: pir_answer_end
+ * then returns that status.
+ * Errors: PIR_ERR_HANDLE (session or DB), PIR_ERR_ARG (B = 0, kc_max = 0, NULL or
+ * misaligned buffers, pieces out of order or out of range, end before D1
+ * ciphertexts), PIR_ERR_OOM, PIR_ERR_CUDA. */
+typedef struct pir_session *pir_session_t;
+pir_status_t pir_answer_begin(pir_db_t db, uint32_t B, uint32_t kc_max, void *stream, const pir_answer_opts_t *opts,
+                              pir_session_t *out);
+pir_status_t pir_answer_chunk(pir_session_t session, const uint32_t *queries, uint32_t i0, uint32_t kc,
+                              int on_device);
+pir_status_t pir_answer_end(pir_session_t session, uint32_t *responses, int on_device);
+pir_status_t pir_answer_abort(pir_session_t session);
 
 /* A whole answer captured once into a CUDA graph (all its kernels, scratch
  * allocation and release as graph nodes) and replayed with one launch: the

@@ -100,6 +100,10 @@ def lib():
             "pir_expander_free": (i32, [vp]),
             "pir_expand": (i32, [vp, vp, u32, u32, vp, vp]),
             "pir_answer_packed": (i32, [vp, vp, vp, u32, vp, i32, vp, C.POINTER(pir_answer_opts_t)]),
+            "pir_answer_begin": (i32, [vp, u32, u32, vp, C.POINTER(pir_answer_opts_t), C.POINTER(vp)]),
+            "pir_answer_chunk": (i32, [vp, vp, u32, u32, i32]),
+            "pir_answer_end": (i32, [vp, vp, i32]),
+            "pir_answer_abort": (i32, [vp]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(L, name)
@@ -388,6 +392,49 @@ def pir_graph_create(db: Db, queries, B: int, responses, k_chunk: int = 0, tile:
     h = C.c_void_p()
     _check(lib().pir_graph_create(C.c_void_p(db.handle), qp, B, rp, C.byref(o), C.byref(h)), "pir_graph_create")
     return Graph(h.value, db, queries, responses)
+
+
+class Session:
+    """A streamed answer (pir_session_t): pieces of the queries along D1."""
+
+    def __init__(self, handle, db, B, kc_max):
+        self.handle = handle
+        self.db = db
+        self.B = B
+        self.kc_max = kc_max
+        self._keep = []  # device pieces are read in stream order: keep them alive
+
+
+def pir_answer_begin(db: Db, B: int, kc_max: int, stream=None, tile: int = 0, flags: int = 0) -> Session:
+    o = pir_answer_opts_t(0, tile, flags)
+    h = C.c_void_p()
+    _check(lib().pir_answer_begin(C.c_void_p(db.handle), B, kc_max, _stream_ptr(stream), C.byref(o), C.byref(h)),
+           "pir_answer_begin")
+    return Session(h.value, db, B, kc_max)
+
+
+def pir_answer_chunk(session: Session, queries, i0: int, kc: int):
+    """Ciphertexts i0 .. i0+kc-1 of every query, [B][kc][2][L][n] (host or device)."""
+    qp, qdev, _ = _ptr(queries)
+    _check(lib().pir_answer_chunk(C.c_void_p(session.handle), qp, i0, kc, int(qdev)), "pir_answer_chunk")
+    if qdev:
+        session._keep.append(queries)
+
+
+def pir_answer_end(session: Session, responses):
+    rp, rdev, _ = _ptr(responses)
+    h, session.handle = session.handle, None
+    try:
+        _check(lib().pir_answer_end(C.c_void_p(h), rp, int(rdev)), "pir_answer_end")
+    finally:
+        session._keep = []
+    return responses
+
+
+def pir_answer_abort(session: Session):
+    h, session.handle = session.handle, None
+    session._keep = []
+    _check(lib().pir_answer_abort(C.c_void_p(h)), "pir_answer_abort")
 
 
 def pir_graph_launch(graph: Graph, stream=None):

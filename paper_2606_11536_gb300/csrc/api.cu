@@ -70,6 +70,22 @@ struct pir_db {
   std::map<uint32_t, pir_answer_opts_t> tuned;  // batch size -> fastest options
 };
 
+// A streamed answer (pir_answer_begin): device scratch for one piece of at most
+// kc_max ciphertexts per query, the slot-major result that the pieces accumulate
+// into, and two staging buffers for pieces given in host memory.
+struct pir_session {
+  uint64_t magic;
+  pir_db *db;
+  cudaStream_t s;
+  uint32_t B, kc_max, next, pieces;
+  pir_answer_opts_t o;
+  pir_status_t failed;
+  void *mem;        // qhat | qs | out
+  void *stage_mem;  // two host-piece staging buffers, allocated with the first host piece
+  size_t qhat_bytes, qs_bytes, stage_bytes;
+  cudaEvent_t arrived[2], consumed[2];
+};
+
 struct pir_graph {
   uint64_t magic;
   pir_db *db;
@@ -85,6 +101,20 @@ constexpr uint64_t kGraphMagic = 0x4742504952475231ull;  // "GBPIRGR1"
 std::mutex g_reg_mu;
 std::set<pir_db *> g_live;
 std::set<pir_graph *> g_graphs;
+std::set<pir_session *> g_sessions;
+constexpr uint64_t kSessionMagic = 0x4742504952535331ull;  // "GBPIRSS1"
+
+bool session_live(pir_session *ses) {
+  std::lock_guard<std::mutex> lock(g_reg_mu);
+  return ses && g_sessions.count(ses) && ses->magic == kSessionMagic;
+}
+// removes the session from the registry; false if it was not live
+bool session_take(pir_session *ses) {
+  std::lock_guard<std::mutex> lock(g_reg_mu);
+  if (!ses || !g_sessions.count(ses)) return false;
+  g_sessions.erase(ses);
+  return true;
+}
 
 bool live(pir_db *db) {
   std::lock_guard<std::mutex> lock(g_reg_mu);
@@ -364,6 +394,192 @@ bool db_view(pir_db_t db, DbView *out) {
 }
 }  // namespace gbpir
 
+namespace {
+
+// Ciphertexts i0 .. i0+kc-1 of every query, query b's at src + b * stride (words):
+// forward NTT, transpose to the GEMM layout, modular GEMM accumulated into the
+// session's slot-major result.  Host pieces go through a staging buffer on the copy
+// stream; the call returns once that copy has completed.
+pir_status_t session_piece(pir_session *ses, const uint32_t *src, uint64_t stride, uint32_t i0, uint32_t kc,
+                           bool on_device) {
+  pir_db *db = ses->db;
+  const ParamCtx &c = *db->ctx;
+  const pir_params_t &p = db->p;
+  const cudaStream_t s = ses->s;
+  const uint32_t B = ses->B, L = p.L, n = p.n, M = 2 * B;
+  const bool limb = db->layout == PIR_LAYOUT_LIMB;
+  const uint32_t Mp = limb ? (M + 15u) & ~15u : round4(M);
+  const uint64_t ct = 2ull * L * n, G = (uint64_t)kc * 2 * L;
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  char *base = static_cast<char *>(ses->mem);
+  uint32_t *qhat = reinterpret_cast<uint32_t *>(base);
+  void *qs = base + up(ses->qhat_bytes);
+  uint32_t *out = reinterpret_cast<uint32_t *>(base + up(ses->qhat_bytes) + up(ses->qs_bytes));
+  const uint32_t slot = ses->pieces & 1;
+  uint64_t row_stride = stride / n;  // rows of n words
+  if (!on_device) {
+    if (!ses->stage_mem) {
+      CK(cudaMallocAsync(&ses->stage_mem, 2 * ses->stage_bytes, s));
+      // the copy stream touches the staging memory only after its allocation
+      CK(cudaEventRecord(ses->consumed[0], s));
+      CK(cudaEventRecord(ses->consumed[1], s));
+    }
+    cudaStream_t cs = nullptr;
+    CK(copy_stream(&cs));
+    uint32_t *stage = reinterpret_cast<uint32_t *>(static_cast<char *>(ses->stage_mem) + slot * ses->stage_bytes);
+    CK(cudaStreamWaitEvent(cs, ses->consumed[slot], 0));  // the piece before last has been read
+    if (stride == kc * ct) {
+      CK(cudaMemcpyAsync(stage, src, (size_t)B * kc * ct * 4, cudaMemcpyHostToDevice, cs));
+    } else {
+      for (uint32_t b = 0; b < B; ++b)
+        CK(cudaMemcpyAsync(stage + b * kc * ct, src + b * stride, kc * ct * 4, cudaMemcpyHostToDevice, cs));
+    }
+    CK(cudaEventRecord(ses->arrived[slot], cs));
+    CK(cudaStreamWaitEvent(s, ses->arrived[slot], 0));
+    src = stage;
+    row_stride = G;
+  }
+  StageTimer tm((ses->o.flags & PIR_ANSWER_STAGE_TIMES) != 0, s);
+  tm.begin();
+  CK(launch_ntt_fwd_rows(c, src, 0, G, row_stride, qhat, (uint64_t)B * G, s));
+  tm.end(0, 1);
+  if (!on_device) CK(cudaEventRecord(ses->consumed[slot], s));
+  if (!limb) {
+    tm.begin();
+    CK(launch_query_to_slots(c, qhat, B, kc, Mp, static_cast<uint32_t *>(qs), s));
+    tm.end(1, 1);
+    tm.begin();
+    CK(launch_gemm_plain(c, static_cast<const uint32_t *>(db->resident), p.D1, p.D2, static_cast<const uint32_t *>(qs),
+                         M, Mp, i0, kc, out, i0 > 0, ses->o.tile, 0, s));
+    tm.end(2, 1);
+  } else {
+    tm.begin();
+    CK(launch_query_to_limbs(c, qhat, B, kc, Mp, static_cast<uint8_t *>(qs), s));
+    tm.end(1, 1);
+    tm.begin();
+    CK(launch_gemm_limb(c, static_cast<const uint8_t *>(db->resident), p.D1, p.D2, static_cast<const uint8_t *>(qs), M,
+                        Mp, i0, kc, out, i0 > 0, ses->o.tile, s));
+    tm.end(2, 1);
+  }
+  if (!on_device) CK(cudaEventSynchronize(ses->arrived[slot]));  // the caller's buffer is free again
+  return PIR_OK;
+}
+
+// The slot-major result to responses: transpose, inverse NTT (with the switch to
+// q_0 when asked), and for host responses the copy out.  Synchronous for host.
+pir_status_t session_finish(pir_session *ses, uint32_t *responses, bool on_device) {
+  pir_db *db = ses->db;
+  const ParamCtx &c = *db->ctx;
+  const pir_params_t &p = db->p;
+  const cudaStream_t s = ses->s;
+  const uint32_t B = ses->B, L = p.L, n = p.n, D2 = p.D2;
+  const bool msw = (ses->o.flags & PIR_ANSWER_MODSWITCH) != 0;
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const uint32_t *out = reinterpret_cast<const uint32_t *>(static_cast<char *>(ses->mem) + up(ses->qhat_bytes) +
+                                                           up(ses->qs_bytes));
+  const size_t full_bytes = (size_t)B * D2 * 2 * L * n * 4, rbytes = (size_t)B * D2 * 2 * (msw ? 1 : L) * n * 4;
+  // full-modulus responses: in `responses` itself unless switched or on the host;
+  // the final responses: device staging for host buffers
+  Scratch scr(s);
+  CK(scr.alloc((msw ? up(full_bytes) : 0) + (on_device ? 0 : up(rbytes))));
+  char *sb = static_cast<char *>(scr.ptr);
+  uint32_t *dst = on_device ? responses : reinterpret_cast<uint32_t *>(sb + (msw ? up(full_bytes) : 0));
+  uint32_t *full = msw ? reinterpret_cast<uint32_t *>(sb) : dst;
+  StageTimer tm((ses->o.flags & PIR_ANSWER_STAGE_TIMES) != 0, s);
+  tm.begin();
+  CK(launch_slots_to_responses(c, out, B, D2, full, s));
+  tm.end(3, 1);
+  tm.begin();
+  if (msw)
+    CK(launch_ntt_inv_switch(c, full, dst, (uint64_t)B * D2 * 2, s));
+  else
+    CK(launch_ntt_inv(c, dst, dst, (uint64_t)B * D2 * 2 * L, s));
+  tm.end(4, 1);
+  if (!on_device) {
+    CK(cudaMemcpyAsync(responses, dst, rbytes, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  return PIR_OK;
+}
+
+void session_release(pir_session *ses) {
+  if (ses->mem) cudaFreeAsync(ses->mem, ses->s);
+  if (ses->stage_mem) cudaFreeAsync(ses->stage_mem, ses->s);  // every copy was waited for on s
+  for (int k = 0; k < 2; ++k) {
+    if (ses->arrived[k]) cudaEventDestroy(ses->arrived[k]);
+    if (ses->consumed[k]) cudaEventDestroy(ses->consumed[k]);
+  }
+  ses->magic = 0;
+  delete ses;
+}
+
+pir_status_t session_open(pir_db *db, uint32_t B, uint32_t kc_max, cudaStream_t s, const pir_answer_opts_t &o,
+                          pir_session **out) {
+  const pir_params_t &p = db->p;
+  const bool limb = db->layout == PIR_LAYOUT_LIMB;
+  if (o.k_chunk != 0 || (o.flags & ~(PIR_ANSWER_STAGE_TIMES | PIR_ANSWER_MODSWITCH)) != 0) return PIR_ERR_ARG;
+  const uint32_t M = 2 * B, Mp = limb ? (M + 15u) & ~15u : round4(M);
+  const uint32_t tile_count = limb ? gemm_limb_tiles() : gemm_plain_tiles();
+  if (o.tile > tile_count) return PIR_ERR_ARG;
+  if (limb ? !gemm_limb_tile_ok(o.tile, Mp) : !gemm_plain_tile_ok(o.tile, M, p.D2)) return PIR_ERR_ARG;
+  if (kc_max > p.D1) kc_max = p.D1;
+  if (limb) {  // byte-limb class sums stay below 2^31 for at most 8192 rows; pieces of 32 rows
+    if (kc_max > 8192) kc_max = 8192;
+    kc_max = kc_max < 32 ? 32 : kc_max & ~31u;
+  }
+  const uint64_t nslots = (uint64_t)p.L * p.n, ct = 2ull * p.L * p.n;
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  pir_session *ses = new pir_session{};
+  ses->magic = kSessionMagic;
+  ses->db = db;
+  ses->s = s;
+  ses->B = B;
+  ses->kc_max = kc_max;
+  ses->o = o;
+  ses->failed = PIR_OK;
+  ses->qhat_bytes = (size_t)B * kc_max * ct * 4;
+  ses->qs_bytes = limb ? nslots * 4 * Mp * kc_max : nslots * kc_max * Mp * 4;
+  ses->stage_bytes = up(ses->qhat_bytes);
+  const size_t out_bytes = nslots * M * p.D2 * 4;
+  void *mem = nullptr;
+  cudaError_t e = cudaMallocAsync(&mem, up(ses->qhat_bytes) + up(ses->qs_bytes) + up(out_bytes), s);
+  if (e == cudaSuccess) ses->mem = mem;
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    if ((e = cudaEventCreateWithFlags(&ses->arrived[k], cudaEventDisableTiming)) == cudaSuccess)
+      e = cudaEventCreateWithFlags(&ses->consumed[k], cudaEventDisableTiming);
+  }
+  if (e != cudaSuccess) {
+    session_release(ses);  // whatever was made
+    return cuda_status(e);
+  }
+  {
+    std::lock_guard<std::mutex> lock(g_reg_mu);
+    g_sessions.insert(ses);
+  }
+  *out = ses;
+  return PIR_OK;
+}
+
+// One piece, checked: in order, within kc_max and D1, whole 32-row blocks on the limb layout.
+pir_status_t session_chunk(pir_session *ses, const uint32_t *src, uint64_t stride, uint32_t i0, uint32_t kc,
+                           bool on_device) {
+  if (ses->failed != PIR_OK) return ses->failed;
+  const pir_params_t &p = ses->db->p;
+  if (!src || kc == 0 || kc > ses->kc_max || i0 != ses->next || (uint64_t)i0 + kc > p.D1) return PIR_ERR_ARG;
+  if (ses->db->layout == PIR_LAYOUT_LIMB && kc % 32 != 0) return PIR_ERR_ARG;
+  if (on_device && !aligned16(src)) return PIR_ERR_ARG;
+  const pir_status_t st = session_piece(ses, src, stride, i0, kc, on_device);
+  if (st != PIR_OK) {
+    ses->failed = st;
+    return st;
+  }
+  ses->next += kc;
+  ses->pieces += 1;
+  return PIR_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char *pir_status_str(pir_status_t st) {
@@ -529,6 +745,26 @@ pir_status_t pir_answer_ex(pir_db_t db, const uint32_t *queries, uint32_t B, uin
     if (!aligned16(queries) || !aligned16(responses)) return PIR_ERR_ARG;
     return answer_device(db, queries, B, responses, s, o);
   }
+  // host batches above 4 GiB: a streamed answer in pieces of at most 1 GiB
+  const uint64_t ct_bytes = 2ull * p.L * p.n * 4;
+  if (o.k_chunk == 0 && qbytes > (4ull << 30) && (o.flags & PIR_ANSWER_TEST_STALL) == 0) {
+    uint64_t kc = (1ull << 30) / ((uint64_t)B * ct_bytes);
+    if (kc == 0) kc = 1;
+    if (db->layout == PIR_LAYOUT_LIMB) kc = kc < 32 ? 32 : (kc > 8192 ? 8192 : kc & ~31ull);
+    if (kc > p.D1) kc = p.D1;
+    pir_session *ses = nullptr;
+    pir_status_t st = session_open(db, B, (uint32_t)kc, s, o, &ses);
+    if (st != PIR_OK) return st;
+    for (uint32_t i0 = 0; i0 < p.D1 && st == PIR_OK; i0 += (uint32_t)kc) {
+      const uint32_t k = p.D1 - i0 < kc ? p.D1 - i0 : (uint32_t)kc;
+      st = session_chunk(ses, queries + (size_t)i0 * (ct_bytes / 4), (uint64_t)p.D1 * (ct_bytes / 4), i0, k, false);
+    }
+    if (st == PIR_OK) st = session_finish(ses, responses, false);
+    session_take(ses);
+    session_release(ses);
+    cudaStreamSynchronize(s);
+    return st;
+  }
   // host buffers: stage through device memory; synchronous
   Scratch dq(s), dr(s);
   CK(dq.alloc(qbytes));
@@ -582,6 +818,43 @@ pir_status_t pir_answer_ex(pir_db_t db, const uint32_t *queries, uint32_t B, uin
   for (uint32_t k = 0; k < feed.n; ++k)
     if (feed.ev[k]) t_free_events.push_back(feed.ev[k]);
   return st;
+}
+
+pir_status_t pir_answer_begin(pir_db_t db, uint32_t B, uint32_t kc_max, void *stream, const pir_answer_opts_t *opts,
+                              pir_session_t *out) {
+  if (!live(db)) return PIR_ERR_HANDLE;
+  if (!out || B == 0 || kc_max == 0) return PIR_ERR_ARG;
+  pir_answer_opts_t o = {};
+  if (opts) o = *opts;
+  return session_open(db, B, kc_max, static_cast<cudaStream_t>(stream), o, out);
+}
+
+pir_status_t pir_answer_chunk(pir_session_t session, const uint32_t *queries, uint32_t i0, uint32_t kc,
+                              int on_device) {
+  if (!session_live(session) || !live(session->db)) return PIR_ERR_HANDLE;
+  const pir_params_t &p = session->db->p;
+  return session_chunk(session, queries, (uint64_t)kc * 2 * p.L * p.n, i0, kc, on_device != 0);
+}
+
+pir_status_t pir_answer_end(pir_session_t session, uint32_t *responses, int on_device) {
+  if (!session_take(session)) return PIR_ERR_HANDLE;
+  pir_status_t st = session->failed;
+  if (st == PIR_OK) {
+    if (!live(session->db))
+      st = PIR_ERR_HANDLE;
+    else if (!responses || session->next != session->db->p.D1 || (on_device && !aligned16(responses)))
+      st = PIR_ERR_ARG;
+    else
+      st = session_finish(session, responses, on_device != 0);
+  }
+  session_release(session);
+  return st;
+}
+
+pir_status_t pir_answer_abort(pir_session_t session) {
+  if (!session_take(session)) return PIR_ERR_HANDLE;
+  session_release(session);
+  return PIR_OK;
 }
 
 pir_status_t pir_answer_packed(pir_db_t db, pir_expander_t expander, const uint32_t *packed, uint32_t B,

@@ -6,7 +6,7 @@ GEMM with its reduction, and the inverse NTT of the responses.  The metric is
 DB-scan throughput in raw DB bytes x queries / s.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--batch B]
-                  [--layout plain|limb] [--impl ours|reference]
+                  [--layout plain|limb|tensor] [--impl ours|reference]
 
 Prints one JSON line (rank 0).  Under torchrun (N > 1) every rank holds its own
 replica of the database and answers its own batches (independent problems, no
@@ -259,7 +259,7 @@ def our_arm(args, wl):
 
     n, log2p, D1, D2, B0, desc = WORKLOADS[wl]
     B = args.batch or B0
-    layout = g.PIR_LAYOUT_LIMB if args.layout == "limb" else g.PIR_LAYOUT_PLAIN
+    layout = {"plain": g.PIR_LAYOUT_PLAIN, "limb": g.PIR_LAYOUT_LIMB, "tensor": g.PIR_LAYOUT_TENSOR}[args.layout]
     p = g.pir_make_params(n, log2p, D1, D2, L_PRIMES)
     raw_bytes = binding.raw_db_bytes(p)
     small = raw_bytes <= (2 << 30)
@@ -372,7 +372,7 @@ def our_arm(args, wl):
     gemm_ms = stage_ms[2] / gemm_launches * launches_per_step  # kernel time per step
     peaks, peak_kind = measured_peaks()
     src = os.path.join(ROOT, "paper_2606_11536_gb300", "csrc",
-                       "gemm_plain.cu" if layout == g.PIR_LAYOUT_PLAIN else "gemm_limb.cu")
+                       {g.PIR_LAYOUT_PLAIN: "gemm_plain.cu", g.PIR_LAYOUT_LIMB: "gemm_limb.cu"}.get(layout, "gemm_tc.cu"))
     # the built-in choice takes the TMA scan up to 4 query rows (bound by HBM), the
     # GEMV tiles 1-3 when asked for (HBM-shaped), and the tiled GEMMs otherwise (ALU)
     streaming = layout == g.PIR_LAYOUT_PLAIN and M <= 8 and (
@@ -382,6 +382,19 @@ def our_arm(args, wl):
         alg_bytes = nslots * (D1 * D2 * 4 + D1 * Mp * 4 + M * D2 * 4)
         roofline = {"bound": "hbm", "achieved": alg_bytes / (gemm_ms / 1e3) / 1e9,
                     "peak": float(peaks["hbm_gbs"]), "unit": "GB/s"}
+    elif layout == g.PIR_LAYOUT_TENSOR:
+        # bf16 tensor cores: 16 digit products per modular MAC (useful rows only, the
+        # padding to 8 rows not counted) against the measured dense bf16 peak; the
+        # kernel runs inside a long step, so the sustained figure
+        kernel_tag = "gemm_tc"
+        Mp8 = (M + 7) // 8 * 8
+        alg_bytes = nslots * (D1 * D2 * 8 + D1 * Mp8 * 8 + M * D2 * 4)
+        macs = nslots * D1 * D2 * M
+        tflops = 2.0 * 16 * macs / (gemm_ms / 1e3) / 1e12
+        roofline = {"bound": "tensor", "achieved": tflops, "peak": float(peaks.get("bf16_tflops_sustained", 1700.0)),
+                    "unit": "TFLOP/s", "modmac_per_s": macs / (gemm_ms / 1e3),
+                    "peak_source": "%s bf16_tflops_sustained (MEASURED_PEAKS.json)" % peak_kind,
+                    "hbm_gbs": alg_bytes / (gemm_ms / 1e3) / 1e9}
     else:
         kernel_tag = "gemm_plain" if layout == g.PIR_LAYOUT_PLAIN else "gemm_limb"
         alg_bytes = nslots * (D1 * D2 * 4 + D1 * Mp * 4 + M * D2 * 4)
@@ -705,7 +718,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--batch", type=int, default=0)
-    ap.add_argument("--layout", default="plain", choices=["plain", "limb"])
+    ap.add_argument("--layout", default="plain", choices=["plain", "limb", "tensor"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tile", type=int, default=0, help="GEMM tile id (0 = built-in choice)")
     ap.add_argument("--k-chunk", type=int, default=0, help="fold D1 in chunks of this many ciphertexts")

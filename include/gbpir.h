@@ -64,8 +64,11 @@ typedef struct {
 
 /* Resident-DB layouts, chosen once at setup (the GEMM path follows the layout). */
 typedef enum {
-  PIR_LAYOUT_PLAIN = 0, /* u32 residues [L*n slots][D1][D2]: CUDA-core u32 x u32 -> u64 path */
-  PIR_LAYOUT_LIMB = 1   /* u8 limb planes [L*n slots][4][D2][D1]: INT8 tensor-pipe path    */
+  PIR_LAYOUT_PLAIN = 0,  /* u32 residues [L*n slots][D1][D2]: CUDA-core u32 x u32 -> u64 path */
+  PIR_LAYOUT_LIMB = 1,   /* u8 limb planes [L*n slots][4][D2][D1]: INT8 tensor-pipe path    */
+  PIR_LAYOUT_TENSOR = 2  /* signed base-256 digits in bf16, 8 bytes per residue, laid out as
+                            tensor-core operand tiles: the tcgen05 bf16 path (needs
+                            D1 % 64 == 0 and D2 % 32 == 0)                                     */
 } pir_layout_t;
 
 typedef struct pir_db *pir_db_t;
@@ -84,14 +87,18 @@ pir_status_t pir_make_params(uint32_t n, uint32_t log2p, uint32_t D1, uint32_t D
  *   raw_db:     D1*D2*n*log2p/8 bytes, a little-endian bit stream of log2p-bit
  *               coefficients, polynomial after polynomial, polynomial (i, c) at
  *               position i*D2 + c.  Host or device memory (raw_on_device).
- *   layout:     PIR_LAYOUT_PLAIN or PIR_LAYOUT_LIMB.
+ *   layout:     PIR_LAYOUT_PLAIN, PIR_LAYOUT_LIMB or PIR_LAYOUT_TENSOR.  The tensor
+ *               layout holds twice the bytes of the others and runs the batched
+ *               answer on the bf16 tensor cores (K-chunks of at most 1024 rows keep
+ *               the f32 sums of digit products exact).
  *   stream:     cudaStream_t for the encode kernels; the call returns after the
  *               DB is resident (it synchronizes the stream).
  *   out_handle: receives the handle; the library owns the resident DB until
  *               pir_free_db.  The caller keeps ownership of raw_db.
  * Errors: PIR_ERR_ARG (NULL pointers, raw_bytes mismatch, invalid params),
  * PIR_ERR_UNSUPPORTED (D2 not a multiple of 4: the kernels move columns four at a
- * time; the limb layout with D1 not a multiple of 32: its tensor steps take 32 rows),
+ * time; the limb layout with D1 not a multiple of 32: its tensor steps take 32 rows;
+ * the tensor layout with D1 not a multiple of 64 or D2 not a multiple of 32),
  * PIR_ERR_ADMISSION (resident bytes exceed the free device memory less a reserve),
  * PIR_ERR_OOM, PIR_ERR_CUDA. */
 pir_status_t pir_setup_db(const pir_params_t *params, const void *raw_db, size_t raw_bytes, int raw_on_device,

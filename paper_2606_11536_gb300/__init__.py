@@ -4,7 +4,7 @@ The CUDA library is loaded on first use (``binding.lib()``); the package imports
 without a GPU so that host logic and the seeded input generator work anywhere.
 """
 from .binding import (  # noqa: F401
-    PIR_LAYOUT_LIMB, PIR_LAYOUT_PLAIN, Db, PirError, ntt_fwd, ntt_inv, pir_answer, pir_answer_ex, pir_db_bytes,
+    PIR_LAYOUT_LIMB, PIR_LAYOUT_PLAIN, PIR_LAYOUT_TENSOR, Db, PirError, ntt_fwd, ntt_inv, pir_answer, pir_answer_ex, pir_db_bytes,
     pir_db_info, pir_db_read_poly, pir_free_db, pir_gemm_tiles, pir_make_params, pir_params_t, pir_setup_db,
     pir_status_str, pir_stage_times, pir_kernel_launches, PIR_ANSWER_STAGE_TIMES,
     PIR_ANSWER_TEST_STALL, pir_check_device, Graph, pir_graph_create, pir_graph_launch, pir_graph_destroy,

@@ -15,6 +15,7 @@ import numpy as np
 PIR_MAX_L = 4
 PIR_LAYOUT_PLAIN = 0
 PIR_LAYOUT_LIMB = 1
+PIR_LAYOUT_TENSOR = 2
 
 STATUS = {
     0: "PIR_OK", 1: "PIR_ERR_ARG", 2: "PIR_ERR_OOM", 3: "PIR_ERR_ADMISSION", 4: "PIR_ERR_CUDA",

@@ -141,10 +141,46 @@ struct Scratch {
   }
 };
 
-size_t resident_bytes(const pir_params_t &p) { return (size_t)4 * p.L * p.n * p.D1 * p.D2; }
+size_t resident_bytes(const pir_params_t &p, int layout) {
+  return (size_t)(layout == PIR_LAYOUT_TENSOR ? 8 : 4) * p.L * p.n * p.D1 * p.D2;
+}
 size_t raw_bytes_of(const pir_params_t &p) { return (size_t)p.D1 * p.D2 * p.n * p.log2p / 8; }
 
 uint32_t round4(uint32_t x) { return (x + 3u) & ~3u; }
+
+// Per-layout rules of the GEMM paths.  Padded query rows: plain 4 (128-bit loads),
+// limb 16 (m16 tensor tiles), tensor 8 (8-row core matrices).
+uint32_t layout_rows(int layout, uint32_t M) {
+  return layout == PIR_LAYOUT_LIMB ? (M + 15u) & ~15u : layout == PIR_LAYOUT_TENSOR ? tc_rows(M) : round4(M);
+}
+// The K-chunk a layout takes: limb 32-row blocks up to 8192 (byte-limb class sums stay
+// below 2^31), tensor 64-row blocks up to 1024 (f32 sums of digit products stay exact).
+uint32_t layout_chunk(int layout, uint32_t Kc) {
+  if (layout == PIR_LAYOUT_LIMB) {
+    if (Kc > 8192) Kc = 8192;
+    Kc &= ~31u;
+    return Kc ? Kc : 32;
+  }
+  if (layout == PIR_LAYOUT_TENSOR) {
+    if (Kc > 1024) Kc = 1024;
+    Kc &= ~63u;
+    return Kc ? Kc : 64;
+  }
+  return Kc ? Kc : 1;
+}
+// bytes of the chunk's GEMM-layout query copy: u32 slots, four u8 limb planes, or
+// four bf16 digits
+size_t layout_qs_bytes(int layout, uint64_t nslots, uint32_t Kc, uint32_t Mp) {
+  return (size_t)nslots * Kc * Mp * (layout == PIR_LAYOUT_TENSOR ? 8 : 4);
+}
+uint32_t layout_tiles(int layout) {
+  return layout == PIR_LAYOUT_PLAIN ? gemm_plain_tiles() : layout == PIR_LAYOUT_LIMB ? gemm_limb_tiles() : 1;
+}
+bool layout_tile_ok(int layout, uint32_t tile, uint32_t M, uint32_t Mp, uint32_t D2) {
+  if (layout == PIR_LAYOUT_PLAIN) return gemm_plain_tile_ok(tile, M, D2);
+  if (layout == PIR_LAYOUT_LIMB) return gemm_limb_tile_ok(tile, Mp);
+  return tile <= 1;
+}
 
 // Keep the pool's memory once freed: repeated answers then reuse it instead of
 // returning it to the driver every call.
@@ -227,6 +263,34 @@ struct StageTimer {
   }
 };
 
+// One K-chunk on the DB's GEMM path: the NTT-form chunk qhat [B][kc][2][L][n] to
+// the layout's query copy qs, then the GEMM accumulated into out [L*n][M][D2].
+pir_status_t chunk_gemm(const pir_db *db, const uint32_t *qhat, uint32_t B, uint32_t Mp, uint32_t i0, uint32_t kc,
+                        void *qs, uint32_t *out, uint32_t tile, int stall, StageTimer &tm, cudaStream_t s) {
+  const ParamCtx &c = *db->ctx;
+  const uint32_t D1 = db->p.D1, D2 = db->p.D2, M = 2 * B;
+  tm.begin();
+  if (db->layout == PIR_LAYOUT_PLAIN)
+    CK(launch_query_to_slots(c, qhat, B, kc, Mp, static_cast<uint32_t *>(qs), s));
+  else if (db->layout == PIR_LAYOUT_LIMB)
+    CK(launch_query_to_limbs(c, qhat, B, kc, Mp, static_cast<uint8_t *>(qs), s));
+  else
+    CK(launch_query_to_tensor(c, qhat, B, kc, Mp, static_cast<uint16_t *>(qs), s));
+  tm.end(1, 1);
+  tm.begin();
+  if (db->layout == PIR_LAYOUT_PLAIN)
+    CK(launch_gemm_plain(c, static_cast<const uint32_t *>(db->resident), D1, D2, static_cast<const uint32_t *>(qs), M,
+                         Mp, i0, kc, out, i0 > 0, tile, stall, s));
+  else if (db->layout == PIR_LAYOUT_LIMB)
+    CK(launch_gemm_limb(c, static_cast<const uint8_t *>(db->resident), D1, D2, static_cast<const uint8_t *>(qs), M, Mp,
+                        i0, kc, out, i0 > 0, tile, s));
+  else
+    CK(launch_gemm_tc(c, static_cast<const uint16_t *>(db->resident), D1, D2, static_cast<const uint16_t *>(qs), M,
+                      Mp, i0, kc, out, i0 > 0, s));
+  tm.end(2, 1);
+  return PIR_OK;
+}
+
 // The device-buffer answer (stream ordered).
 // qhat_ready: when set, the queries are already in NTT form for the whole of D1
 // ([B][D1][2][L][n], e.g. from query expansion): no forward NTT, no K-chunking.
@@ -238,17 +302,16 @@ pir_status_t answer_device(pir_db *db, const uint32_t *queries, uint32_t B, uint
   const ParamCtx &c = *db->ctx;
   const pir_params_t &p = db->p;
   const uint32_t n = p.n, L = p.L, D1 = p.D1, D2 = p.D2;
-  const bool limb = db->layout == PIR_LAYOUT_LIMB;
+  const bool plain = db->layout == PIR_LAYOUT_PLAIN;
   const uint32_t M = 2 * B;
-  // plain rows pad to 4 (128-bit loads); limb rows pad to 16 (m16 tensor tiles)
-  const uint32_t Mp = limb ? (M + 15u) & ~15u : round4(M);
+  const uint32_t Mp = layout_rows(db->layout, M);
   uint32_t Kc = (o.k_chunk == 0 || o.k_chunk >= D1 || qhat_ready) ? D1 : o.k_chunk;
   if (o.k_chunk == 0 && !qhat_ready) {
     // Stream-wise buffering (Sec. 4.4): when the scratch for all of D1 would not fit
     // half of the free device memory, fold D1 in as many equal chunks as needed.
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
-      const size_t per_row = (size_t)B * 2 * L * n * 4 + (size_t)L * n * (M + 15) * 4;  // qhat + slot layout
+      const size_t per_row = (size_t)B * 2 * L * n * 4 + layout_qs_bytes(db->layout, (uint64_t)L * n, 1, Mp);
       const size_t budget = free_b / 2;
       if ((size_t)D1 * per_row > budget && per_row > 0) {
         const size_t rows = budget / per_row;
@@ -258,18 +321,15 @@ pir_status_t answer_device(pir_db *db, const uint32_t *queries, uint32_t B, uint
       }
     }
   }
-  if (limb) {
-    // byte-limb class sums stay below 2^31 for at most 8192 rows; chunks of 32 rows
-    if (Kc > 8192) Kc = 8192;
-    Kc &= ~31u;
-    if (Kc == 0) Kc = 32;
-    if (qhat_ready && Kc != D1) return PIR_ERR_UNSUPPORTED;
+  if (!plain) {
+    Kc = layout_chunk(db->layout, Kc);
+    if (qhat_ready && Kc < D1) return PIR_ERR_UNSUPPORTED;
   }
   const uint64_t nslots = (uint64_t)L * n;
-  const uint32_t tile_count = db->layout == PIR_LAYOUT_PLAIN ? gemm_plain_tiles() : gemm_limb_tiles();
-  if (o.tile > tile_count || (o.flags & ~(PIR_ANSWER_STAGE_TIMES | PIR_ANSWER_TEST_STALL | PIR_ANSWER_MODSWITCH)) != 0)
+  if (o.tile > layout_tiles(db->layout) ||
+      (o.flags & ~(PIR_ANSWER_STAGE_TIMES | PIR_ANSWER_TEST_STALL | PIR_ANSWER_MODSWITCH)) != 0)
     return PIR_ERR_ARG;
-  if (limb ? !gemm_limb_tile_ok(o.tile, Mp) : !gemm_plain_tile_ok(o.tile, M, D2)) return PIR_ERR_ARG;
+  if (!layout_tile_ok(db->layout, o.tile, M, Mp, D2)) return PIR_ERR_ARG;
   // With modulus switching the inverse NTT reads the full-modulus responses from
   // scratch and writes [B][D2][2][n] over q_0 to `responses`.
   const bool msw = (o.flags & PIR_ANSWER_MODSWITCH) != 0 && !ntt_out;
@@ -279,14 +339,14 @@ pir_status_t answer_device(pir_db *db, const uint32_t *queries, uint32_t B, uint
 
   // scratch: NTT'd query chunk | slot-major query chunk | slot-major results
   const size_t qhat_bytes = qhat_ready ? 0 : (size_t)B * Kc * 2 * L * n * 4;
-  const size_t qs_bytes = limb ? nslots * 4 * Mp * Kc : nslots * Kc * Mp * 4;
+  const size_t qs_bytes = layout_qs_bytes(db->layout, nslots, Kc, Mp);
   const size_t out_bytes = nslots * M * D2 * 4;
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
   // Batch 1 on the TMA scan: the forward NTT writes the slot layout itself (pairs of
   // a/b residues, Mp = 2) and the scan writes the response layout itself, so neither
   // transpose runs.
   // (every chunk, the last included, must hold an even number of ciphertexts)
-  const bool fused = !qhat_ready && !limb && B == 1 && (o.tile == 0 || o.tile == 7) && scan_tma_supports(M, D2) &&
+  const bool fused = !qhat_ready && plain && B == 1 && (o.tile == 0 || o.tile == 7) && scan_tma_supports(M, D2) &&
                      Kc % 2 == 0 && D1 % 2 == 0;
   // full-modulus responses before switching: the unused result area on the fused
   // path (the same size at B = 1), an area of their own otherwise
@@ -357,23 +417,8 @@ pir_status_t answer_device(pir_db *db, const uint32_t *queries, uint32_t B, uint
                              s));
       tm.end(0, 1);
     }
-    if (db->layout == PIR_LAYOUT_PLAIN) {
-      tm.begin();
-      CK(launch_query_to_slots(c, qhat, B, kc, Mp, static_cast<uint32_t *>(qs), s));
-      tm.end(1, 1);
-      tm.begin();
-      CK(launch_gemm_plain(c, static_cast<const uint32_t *>(db->resident), D1, D2, static_cast<const uint32_t *>(qs),
-                           M, Mp, i0, kc, out, i0 > 0, o.tile, stall, s));
-      tm.end(2, 1);
-    } else {
-      tm.begin();
-      CK(launch_query_to_limbs(c, qhat, B, kc, Mp, static_cast<uint8_t *>(qs), s));
-      tm.end(1, 1);
-      tm.begin();
-      CK(launch_gemm_limb(c, static_cast<const uint8_t *>(db->resident), D1, D2, static_cast<const uint8_t *>(qs), M,
-                          Mp, i0, kc, out, i0 > 0, o.tile, s));
-      tm.end(2, 1);
-    }
+    const pir_status_t st = chunk_gemm(db, qhat, B, Mp, i0, kc, qs, out, o.tile, stall, tm, s);
+    if (st != PIR_OK) return st;
   }
   tm.begin();
   CK(launch_slots_to_responses(c, out, B, D2, full, s));
@@ -407,8 +452,7 @@ pir_status_t session_piece(pir_session *ses, const uint32_t *src, uint64_t strid
   const pir_params_t &p = db->p;
   const cudaStream_t s = ses->s;
   const uint32_t B = ses->B, L = p.L, n = p.n, M = 2 * B;
-  const bool limb = db->layout == PIR_LAYOUT_LIMB;
-  const uint32_t Mp = limb ? (M + 15u) & ~15u : round4(M);
+  const uint32_t Mp = layout_rows(db->layout, M);
   const uint64_t ct = 2ull * L * n, G = (uint64_t)kc * 2 * L;
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
   char *base = static_cast<char *>(ses->mem);
@@ -444,23 +488,8 @@ pir_status_t session_piece(pir_session *ses, const uint32_t *src, uint64_t strid
   CK(launch_ntt_fwd_rows(c, src, 0, G, row_stride, qhat, (uint64_t)B * G, s));
   tm.end(0, 1);
   if (!on_device) CK(cudaEventRecord(ses->consumed[slot], s));
-  if (!limb) {
-    tm.begin();
-    CK(launch_query_to_slots(c, qhat, B, kc, Mp, static_cast<uint32_t *>(qs), s));
-    tm.end(1, 1);
-    tm.begin();
-    CK(launch_gemm_plain(c, static_cast<const uint32_t *>(db->resident), p.D1, p.D2, static_cast<const uint32_t *>(qs),
-                         M, Mp, i0, kc, out, i0 > 0, ses->o.tile, 0, s));
-    tm.end(2, 1);
-  } else {
-    tm.begin();
-    CK(launch_query_to_limbs(c, qhat, B, kc, Mp, static_cast<uint8_t *>(qs), s));
-    tm.end(1, 1);
-    tm.begin();
-    CK(launch_gemm_limb(c, static_cast<const uint8_t *>(db->resident), p.D1, p.D2, static_cast<const uint8_t *>(qs), M,
-                        Mp, i0, kc, out, i0 > 0, ses->o.tile, s));
-    tm.end(2, 1);
-  }
+  const pir_status_t st = chunk_gemm(db, qhat, B, Mp, i0, kc, qs, out, ses->o.tile, 0, tm, s);
+  if (st != PIR_OK) return st;
   if (!on_device) CK(cudaEventSynchronize(ses->arrived[slot]));  // the caller's buffer is free again
   return PIR_OK;
 }
@@ -516,17 +545,11 @@ void session_release(pir_session *ses) {
 pir_status_t session_open(pir_db *db, uint32_t B, uint32_t kc_max, cudaStream_t s, const pir_answer_opts_t &o,
                           pir_session **out) {
   const pir_params_t &p = db->p;
-  const bool limb = db->layout == PIR_LAYOUT_LIMB;
   if (o.k_chunk != 0 || (o.flags & ~(PIR_ANSWER_STAGE_TIMES | PIR_ANSWER_MODSWITCH)) != 0) return PIR_ERR_ARG;
-  const uint32_t M = 2 * B, Mp = limb ? (M + 15u) & ~15u : round4(M);
-  const uint32_t tile_count = limb ? gemm_limb_tiles() : gemm_plain_tiles();
-  if (o.tile > tile_count) return PIR_ERR_ARG;
-  if (limb ? !gemm_limb_tile_ok(o.tile, Mp) : !gemm_plain_tile_ok(o.tile, M, p.D2)) return PIR_ERR_ARG;
+  const uint32_t M = 2 * B, Mp = layout_rows(db->layout, M);
+  if (o.tile > layout_tiles(db->layout) || !layout_tile_ok(db->layout, o.tile, M, Mp, p.D2)) return PIR_ERR_ARG;
   if (kc_max > p.D1) kc_max = p.D1;
-  if (limb) {  // byte-limb class sums stay below 2^31 for at most 8192 rows; pieces of 32 rows
-    if (kc_max > 8192) kc_max = 8192;
-    kc_max = kc_max < 32 ? 32 : kc_max & ~31u;
-  }
+  if (db->layout != PIR_LAYOUT_PLAIN) kc_max = layout_chunk(db->layout, kc_max);  // whole blocks, bounded pieces
   const uint64_t nslots = (uint64_t)p.L * p.n, ct = 2ull * p.L * p.n;
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
   pir_session *ses = new pir_session{};
@@ -538,7 +561,7 @@ pir_status_t session_open(pir_db *db, uint32_t B, uint32_t kc_max, cudaStream_t 
   ses->o = o;
   ses->failed = PIR_OK;
   ses->qhat_bytes = (size_t)B * kc_max * ct * 4;
-  ses->qs_bytes = limb ? nslots * 4 * Mp * kc_max : nslots * kc_max * Mp * 4;
+  ses->qs_bytes = layout_qs_bytes(db->layout, nslots, kc_max, Mp);
   ses->stage_bytes = up(ses->qhat_bytes);
   const size_t out_bytes = nslots * M * p.D2 * 4;
   void *mem = nullptr;
@@ -560,13 +583,14 @@ pir_status_t session_open(pir_db *db, uint32_t B, uint32_t kc_max, cudaStream_t 
   return PIR_OK;
 }
 
-// One piece, checked: in order, within kc_max and D1, whole 32-row blocks on the limb layout.
+// One piece, checked: in order, within kc_max and D1, whole 32-row blocks on the limb
+// layout and whole 64-row blocks on the tensor layout.
 pir_status_t session_chunk(pir_session *ses, const uint32_t *src, uint64_t stride, uint32_t i0, uint32_t kc,
                            bool on_device) {
   if (ses->failed != PIR_OK) return ses->failed;
   const pir_params_t &p = ses->db->p;
   if (!src || kc == 0 || kc > ses->kc_max || i0 != ses->next || (uint64_t)i0 + kc > p.D1) return PIR_ERR_ARG;
-  if (ses->db->layout == PIR_LAYOUT_LIMB && kc % 32 != 0) return PIR_ERR_ARG;
+  if (ses->db->layout != PIR_LAYOUT_PLAIN && layout_chunk(ses->db->layout, kc) != kc) return PIR_ERR_ARG;
   if (on_device && !aligned16(src)) return PIR_ERR_ARG;
   const pir_status_t st = session_piece(ses, src, stride, i0, kc, on_device);
   if (st != PIR_OK) {
@@ -631,19 +655,21 @@ pir_status_t pir_check_device(void *stream) {
 uint32_t pir_gemm_tiles(int layout) {
   if (layout == PIR_LAYOUT_PLAIN) return gemm_plain_tiles();
   if (layout == PIR_LAYOUT_LIMB) return gemm_limb_tiles();
+  if (layout == PIR_LAYOUT_TENSOR) return 1;
   return 0;
 }
 
 pir_status_t pir_setup_db(const pir_params_t *params, const void *raw_db, size_t raw_bytes, int raw_on_device,
                           int layout, void *stream, pir_db_t *out_handle) {
   if (!params || !raw_db || !out_handle) return PIR_ERR_ARG;
-  if (layout != PIR_LAYOUT_PLAIN && layout != PIR_LAYOUT_LIMB) return PIR_ERR_ARG;
+  if (layout != PIR_LAYOUT_PLAIN && layout != PIR_LAYOUT_LIMB && layout != PIR_LAYOUT_TENSOR) return PIR_ERR_ARG;
   pir_status_t st = validate_params(params);
   if (st != PIR_OK) return st;
   const pir_params_t p = *params;
   if (raw_bytes != raw_bytes_of(p)) return PIR_ERR_ARG;
   if ((p.D2 % 4) != 0) return PIR_ERR_UNSUPPORTED;  // 128-bit / paired column accesses
   if (layout == PIR_LAYOUT_LIMB && (p.D1 % 32) != 0) return PIR_ERR_UNSUPPORTED;  // k32 tensor steps
+  if (layout == PIR_LAYOUT_TENSOR && !gemm_tc_shape_ok(p.D1, p.D2)) return PIR_ERR_UNSUPPORTED;  // 64-row stages, 32-column tiles
   *out_handle = nullptr;
   const ParamCtx *ctx = nullptr;
   st = get_param_ctx(&p, &ctx);
@@ -655,7 +681,7 @@ pir_status_t pir_setup_db(const pir_params_t *params, const void *raw_db, size_t
 
   // Admission: resident DB (+ the raw bytes if they must be staged) + the NTT
   // staging chunk, against the free memory less a reserve.
-  const size_t bytes = resident_bytes(p);
+  const size_t bytes = resident_bytes(p, layout);
   const uint64_t polys = (uint64_t)p.D1 * p.D2;
   const uint64_t chunk_polys_target = (uint64_t)(256u << 20) / ((uint64_t)4 * p.L * p.n);
   uint64_t chunk = chunk_polys_target < polys ? chunk_polys_target : polys;
@@ -701,12 +727,14 @@ pir_status_t pir_setup_db(const pir_params_t *params, const void *raw_db, size_t
   }
   if ((e = cudaMalloc(&stage, staging)) != cudaSuccess) return fail(e);
   uint32_t *stg = static_cast<uint32_t *>(stage);
-  if (layout == PIR_LAYOUT_PLAIN) {
+  if (layout != PIR_LAYOUT_LIMB) {  // row-major chunks of polynomials
     for (uint64_t first = 0; first < polys; first += chunk) {
       const uint64_t np = polys - first < chunk ? polys - first : chunk;
       if ((e = launch_ntt_fwd_raw(*ctx, raw, 0, p.D1, p.D2, first, np, stg, s)) != cudaSuccess) return fail(e);
-      if ((e = launch_db_scatter(*ctx, layout, p.D1, p.D2, stg, first, np, db->resident, s)) != cudaSuccess)
-        return fail(e);
+      e = layout == PIR_LAYOUT_PLAIN
+              ? launch_db_scatter(*ctx, layout, p.D1, p.D2, stg, first, np, db->resident, s)
+              : launch_db_scatter_tensor(*ctx, p.D1, p.D2, stg, first, np, static_cast<uint16_t *>(db->resident), s);
+      if (e != cudaSuccess) return fail(e);
       count_launches(2);
     }
   } else {
@@ -721,6 +749,10 @@ pir_status_t pir_setup_db(const pir_params_t *params, const void *raw_db, size_t
     }
   }
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(e);
+  if (layout == PIR_LAYOUT_TENSOR) {  // the tensor GEMM's error word: made here, so that
+    uint32_t *w = nullptr;            // graph capture and pir_answer_noalloc never allocate
+    if ((e = device_error_word(&w)) != cudaSuccess) return fail(e);
+  }
   if (raw_dev) cudaFree(raw_dev);
   cudaFree(stage);
   {
@@ -750,8 +782,8 @@ pir_status_t pir_answer_ex(pir_db_t db, const uint32_t *queries, uint32_t B, uin
   if (o.k_chunk == 0 && qbytes > (4ull << 30) && (o.flags & PIR_ANSWER_TEST_STALL) == 0) {
     uint64_t kc = (1ull << 30) / ((uint64_t)B * ct_bytes);
     if (kc == 0) kc = 1;
-    if (db->layout == PIR_LAYOUT_LIMB) kc = kc < 32 ? 32 : (kc > 8192 ? 8192 : kc & ~31ull);
     if (kc > p.D1) kc = p.D1;
+    if (db->layout != PIR_LAYOUT_PLAIN) kc = layout_chunk(db->layout, (uint32_t)kc);
     pir_session *ses = nullptr;
     pir_status_t st = session_open(db, B, (uint32_t)kc, s, o, &ses);
     if (st != PIR_OK) return st;
@@ -774,18 +806,18 @@ pir_status_t pir_answer_ex(pir_db_t db, const uint32_t *queries, uint32_t B, uin
   // being scanned.  Only when the caller leaves the chunking to the library.
   pir_answer_opts_t o2 = o;
   ChunkFeed feed;
-  const bool limb = db->layout == PIR_LAYOUT_LIMB;
+  const bool plain = db->layout == PIR_LAYOUT_PLAIN;
   uint32_t Kc = p.D1;
   if (o.k_chunk == 0 && qbytes >= (8ull << 20) && qbytes <= (4ull << 30) && p.D1 >= 8) {
     uint32_t kc = (p.D1 + 3) / 4;
-    kc = limb ? (kc + 31) & ~31u : (kc + 1) & ~1u;
-    if (kc < p.D1 && (!limb || kc <= 8192)) Kc = kc;
+    kc = plain ? (kc + 1) & ~1u : layout_chunk(db->layout, kc);  // even pieces, or whole blocks of the layout
+    if (kc < p.D1) Kc = kc;
   }
   cudaStream_t cs = nullptr;
   if (Kc < p.D1 && copy_stream(&cs) == cudaSuccess) {
     // batch 1 on the plain layout keeps one scan pass (a K-chunked scan costs more
     // than the upload it hides) and pipelines only the forward NTT behind the pieces
-    if (B > 1 || limb) o2.k_chunk = Kc;
+    if (B > 1 || !plain) o2.k_chunk = Kc;
     feed.kc = Kc;
     feed.n = (p.D1 + Kc - 1) / Kc;
     cudaEvent_t ready = take_event();  // the scratch is allocated in s's order
@@ -1101,7 +1133,9 @@ pir_status_t pir_autotune(pir_db_t db, uint32_t B, void *stream, uint32_t reps, 
   const uint32_t M = 2 * B, Mp16 = (M + 15u) & ~15u;
   const bool limb = db->layout == PIR_LAYOUT_LIMB;
   std::vector<uint32_t> tiles;
-  if (!limb) {
+  if (db->layout == PIR_LAYOUT_TENSOR) {
+    tiles.push_back(1);
+  } else if (!limb) {
     if (M <= 2) tiles.push_back(1);
     if (M <= 4) tiles.push_back(2);
     if (M <= 8) tiles.push_back(3);
@@ -1116,6 +1150,7 @@ pir_status_t pir_autotune(pir_db_t db, uint32_t B, void *stream, uint32_t reps, 
   for (uint32_t d : {2u, 4u}) {
     uint32_t kc = p.D1 / d;
     if (limb) kc &= ~31u;
+    if (db->layout == PIR_LAYOUT_TENSOR) kc &= ~63u;
     if (kc >= 32 && kc < p.D1) chunks.push_back(kc);
   }
   const size_t qb = (size_t)B * p.D1 * 2 * p.L * p.n * 4, rb = (size_t)B * p.D2 * 2 * p.L * p.n * 4;
@@ -1189,7 +1224,10 @@ pir_status_t pir_db_read_poly(pir_db_t db, uint64_t poly_index, uint32_t *out) {
   const size_t bytes = (size_t)db->p.L * db->p.n * 4;
   uint32_t *tmp = nullptr;
   CK(cudaMalloc(&tmp, bytes));
-  cudaError_t e = launch_db_read_poly(*db->ctx, db->layout, db->p.D1, db->p.D2, db->resident, poly_index, tmp, 0);
+  cudaError_t e = db->layout == PIR_LAYOUT_TENSOR
+                      ? launch_db_read_poly_tensor(*db->ctx, db->p.D1, db->p.D2,
+                                                   static_cast<const uint16_t *>(db->resident), poly_index, tmp, 0)
+                      : launch_db_read_poly(*db->ctx, db->layout, db->p.D1, db->p.D2, db->resident, poly_index, tmp, 0);
   if (e == cudaSuccess) e = cudaMemcpy(out, tmp, bytes, cudaMemcpyDeviceToHost);
   cudaFree(tmp);
   return cuda_status(e);

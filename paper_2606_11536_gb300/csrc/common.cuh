@@ -151,6 +151,19 @@ cudaError_t launch_scan_tma(const ParamCtx &c, const uint32_t *db, uint32_t D1, 
 
 // gemm_limb.cu: the same contract on the limb layouts (db [s][4][D2][D1] u8,
 // ql [s][4][Mp][Kc] u8), exact through u8 x u8 -> s32 tensor-pipe products.
+// The bf16 tensor-core path (PIR_LAYOUT_TENSOR): signed base-256 digits of every
+// residue in tensor-core operand tiles.  Query rows pad to tc_rows(M) (a multiple
+// of 8); K-chunks are multiples of 64 rows, at most 1024.
+bool gemm_tc_shape_ok(uint32_t D1, uint32_t D2);
+uint32_t tc_rows(uint32_t M);
+cudaError_t launch_query_to_tensor(const ParamCtx &c, const uint32_t *qhat, uint32_t B, uint32_t Kc, uint32_t Mp,
+                                   uint16_t *qt, cudaStream_t s);
+cudaError_t launch_db_scatter_tensor(const ParamCtx &c, uint32_t D1, uint32_t D2, const uint32_t *polys,
+                                     uint64_t first, uint64_t np, uint16_t *resident, cudaStream_t s);
+cudaError_t launch_db_read_poly_tensor(const ParamCtx &c, uint32_t D1, uint32_t D2, const uint16_t *resident,
+                                       uint64_t poly, uint32_t *out, cudaStream_t s);
+cudaError_t launch_gemm_tc(const ParamCtx &c, const uint16_t *db, uint32_t D1, uint32_t D2, const uint16_t *qt,
+                           uint32_t M, uint32_t Mp, uint32_t i0, uint32_t Kc, uint32_t *out, int acc, cudaStream_t s);
 cudaError_t launch_gemm_limb(const ParamCtx &c, const uint8_t *db, uint32_t D1, uint32_t D2, const uint8_t *ql,
                              uint32_t M, uint32_t Mp, uint32_t i0, uint32_t Kc, uint32_t *out, int acc,
                              uint32_t tile, cudaStream_t s);

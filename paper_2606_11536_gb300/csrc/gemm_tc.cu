@@ -1,0 +1,450 @@
+// gemm_tc.cu -- the batched first-dimension modular GEMM on the bf16 tensor cores:
+// tcgen05.mma with its accumulators in tensor memory.  This is the paper's limb
+// decomposition of an INT32 GEMM into narrow tensor-core products (Sec. 4.1),
+// re-targeted to the tensor format GB300 runs at full rate (its INT8 tensor rate
+// is a small fraction of the bf16 one) and to modular arithmetic.
+//
+// Digits.  A residue x in [0, q), q < 2^30, is x = sum_{l<4} 256^l d_l with signed
+// digits d_0..d_2 in [-128, 127] and d_3 in [-64, 64]; such integers are exact in
+// bf16.  For slot s the modular GEMM splits into 16 digit GEMMs
+//     P_ab[c][m] = sum_{i < Kc} DB_b[i][c] * Q_a[i][m],    |P_ab| <= Kc * 2^14,
+// so for Kc <= 1024 every partial sum is an integer of at most 2^24 in magnitude
+// that the f32 accumulator holds exactly, in any summation order.
+//
+// One MMA (M = 128, N = 4 * query rows, K = 16) forms all 16 digit products at once.
+//   A rows are (DB column, DB digit) pairs: r = 4 * c_local + b, 32 columns per tile.
+//   B rows are (query row, query digit) pairs: n = 4 * m + a.
+// The epilogue reads P back with tcgen05.ld, converts to integers, weights digit
+// pair (a, b) by 2^(8(a+b)) mod q and sums: in int64 over a within a thread, then over
+// b across the 4 lanes that hold one column.  Then it reduces mod q and writes
+// out[s][m][c] (or adds it to the earlier K-chunks' partial).
+//
+// Layouts.  Both operands are bf16, in the K-major no-swizzle canonical layout of
+// the tensor-core shared-memory descriptors.  Core matrices are 8 rows x 16 bytes;
+// element (row r, k < 16) of a [rows][16] block is at
+//     (r / 8) * 128 + (k / 8) * 64 + (r % 8) * 8 + k % 8        (elements)
+// so a block is contiguous, and a run of 8-row groups is a contiguous sub-range.
+//   resident DB   dbt[s][u][4 * D2 rows][16]   u = i / 16
+//   query digits  qt[s][u][4 * Mp rows][16]    u over one K-chunk
+// Descriptors: LBO (K direction) = 128 bytes, SBO (8-row groups) = 256 bytes.
+//
+// CTA = (slot, T tiles of 32 DB columns, one tile of <= 64 query rows).  Its
+// accumulators take T * N <= 512 tensor-memory columns.
+//   warp 8   streams K stages (KS16 x 16 rows) into a ring of S shared-memory
+//            stages with 1-D bulk copies;
+//   warp 9   allocates the tensor memory and issues the MMAs from one thread;
+//   warps 0..7  run the epilogue.
+// Every barrier wait is bounded; a wait that runs out sets the device error word.
+#include <cuda_bf16.h>
+
+#include "async.cuh"
+#include "common.cuh"
+
+namespace gbpir {
+namespace {
+
+using async::bulk_g2s;
+using async::mbar_expect_tx;
+using async::mbar_init;
+using async::saddr;
+using async::wait_bounded;
+
+constexpr int kEpiWarps = 8;
+constexpr int kProducerWarp = 8, kMmaWarp = 9;
+constexpr int kThreads = 320;
+constexpr int kMaxStages = 4;
+constexpr uint32_t kBlockBytes = 128 * 16 * 2;  // one 128-row x K16 bf16 block
+
+// Signed base-256 digits of x < 2^30.
+__device__ __forceinline__ void digits4(uint32_t x, int (&d)[4]) {
+  int v = (int)x;
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    d[l] = (int)(int8_t)(v & 0xFF);
+    v = (v - d[l]) >> 8;  // exact: v - d[l] is a multiple of 256
+  }
+  d[3] = v;
+}
+
+__device__ __forceinline__ uint16_t bf16_bits(int d) { return __bfloat16_as_ushort(__float2bfloat16_rn((float)d)); }
+
+// Element offset of (row r, k) inside one [rows][16] core-matrix block.
+__host__ __device__ __forceinline__ uint32_t cm_off(uint32_t r, uint32_t k) {
+  return (r >> 3) * 128 + (k >> 3) * 64 + (r & 7) * 8 + (k & 7);
+}
+
+// Shared-memory matrix descriptor: K-major, no swizzle, LBO 128 B, SBO 256 B.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(256 >> 4) << 32) |
+         (1ull << 46);
+}
+
+// Instruction descriptor, kind::f16: D f32, A and B bf16, both K-major, M x N.
+__device__ __forceinline__ uint32_t instr_desc(uint32_t M, uint32_t N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct TcArgs {
+  const uint16_t *db;  // resident DB digits
+  const uint16_t *qt;  // query digits of this K-chunk
+  uint32_t *out;       // [L*n][M][D2]
+  uint32_t *err;       // per-device error word
+  uint32_t M, Mp, D1, D2, i0, Kc;
+  uint32_t T, KS16, S, stage_bytes, ctiles, mtiles, tmem_cols;
+  uint32_t nslots, logn;
+  int acc_in;
+};
+
+template <typename T>
+__device__ __forceinline__ T pick(const T (&v)[PIR_MAX_L], uint32_t j) {
+  T r = v[0];
+#pragma unroll
+  for (uint32_t i = 1; i < PIR_MAX_L; ++i) r = j == i ? v[i] : r;
+  return r;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcArgs a, ModConst mc) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + a.S * a.stage_bytes);
+  const uint32_t full0 = saddr(bars), empty0 = saddr(bars + kMaxStages), accf = saddr(bars + 2 * kMaxStages);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * kMaxStages + 1);
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  const uint64_t bid = blockIdx.x;
+  const uint32_t ct = (uint32_t)(bid % a.ctiles);
+  const uint64_t rest = bid / a.ctiles;
+  const uint32_t mt = (uint32_t)(rest % a.mtiles);
+  const uint32_t s = (uint32_t)(rest / a.mtiles);
+  const uint32_t Ntot = 4 * a.Mp, n0 = mt * 256;
+  const uint32_t Nt = Ntot - n0 < 256 ? Ntot - n0 : 256;  // query digit rows of this tile
+  const uint32_t R = 4 * a.D2, U = a.D1 / 16, Uc = a.Kc / 16;
+  const uint32_t nst = Uc / a.KS16;
+  const uint32_t db_stage = a.KS16 * a.T * kBlockBytes;
+
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < kMaxStages; ++st) {
+      mbar_init(full0 + 8 * st, 1);
+      mbar_init(empty0 + 8 * st, 1);
+    }
+    mbar_init(accf, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == kMmaWarp) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tslot)),
+                 "r"(a.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+
+  if (warp == kProducerWarp) {
+    if (lane == 0) {
+      const uint64_t pol_db = async::policy_evict_first(), pol_q = async::policy_evict_last();
+      const uint8_t *dbs = reinterpret_cast<const uint8_t *>(a.db);
+      const uint8_t *qs = reinterpret_cast<const uint8_t *>(a.qt);
+      uint32_t issued = 0;
+      for (uint32_t st = 0; st < nst; ++st) {
+        const uint32_t slot = st % a.S, ph = (st / a.S) & 1;
+        if (!wait_bounded(empty0 + 8 * slot, ph ^ 1)) {
+          atomicExch(a.err, 1u);
+          break;
+        }
+        const uint32_t qbytes = a.KS16 * Nt * 32;
+        const uint32_t dst = saddr(smem + slot * a.stage_bytes);
+        mbar_expect_tx(full0 + 8 * slot, db_stage + qbytes);
+        for (uint32_t v = 0; v < a.KS16; ++v) {
+          const uint64_t u = a.i0 / 16 + (uint64_t)st * a.KS16 + v;
+          const uint64_t e = (((uint64_t)s * U + u) * R + (uint64_t)ct * a.T * 128) * 16;
+          bulk_g2s(dst + v * a.T * kBlockBytes, dbs + 2 * e, a.T * kBlockBytes, full0 + 8 * slot, pol_db);
+        }
+        if (Nt == Ntot) {  // the stage's query rows are one contiguous run
+          const uint64_t e = ((uint64_t)s * Uc + (uint64_t)st * a.KS16) * Ntot * 16;
+          bulk_g2s(dst + db_stage, qs + 2 * e, qbytes, full0 + 8 * slot, pol_q);
+        } else {
+          for (uint32_t v = 0; v < a.KS16; ++v) {
+            const uint64_t e = (((uint64_t)s * Uc + (uint64_t)st * a.KS16 + v) * Ntot + n0) * 16;
+            bulk_g2s(dst + db_stage + v * Nt * 32, qs + 2 * e, Nt * 32, full0 + 8 * slot, pol_q);
+          }
+        }
+        ++issued;
+      }
+      // drain: never leave with copies in flight
+      const uint32_t first = issued > a.S ? issued - a.S : 0;
+      for (uint32_t k = first; k < issued; ++k)
+        if (!wait_bounded(full0 + 8 * (k % a.S), (k / a.S) & 1)) atomicExch(a.err, 1u);
+    }
+    __syncwarp();
+  } else if (warp == kMmaWarp) {
+    if (lane == 0) {
+      const uint32_t idesc = instr_desc(128, Nt);
+      for (uint32_t st = 0; st < nst; ++st) {
+        const uint32_t slot = st % a.S;
+        if (!wait_bounded(full0 + 8 * slot, (st / a.S) & 1)) {
+          atomicExch(a.err, 1u);
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t base = saddr(smem + slot * a.stage_bytes);
+        for (uint32_t v = 0; v < a.KS16; ++v) {
+          const uint64_t bdesc = smem_desc(base + db_stage + v * Nt * 32);
+          for (uint32_t t = 0; t < a.T; ++t) {
+            const uint64_t adesc = smem_desc(base + (v * a.T + t) * kBlockBytes);
+            mma_bf16(tmem + t * Nt, adesc, bdesc, idesc, (st | v) != 0);
+          }
+        }
+        mma_commit(empty0 + 8 * slot);  // the stage is free once these MMAs have read it
+      }
+      mma_commit(accf);  // every MMA issued above has completed
+    }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue: warps 0..7 ----------------
+    const bool ok = __all_sync(0xffffffffu, wait_bounded(accf, 0));
+    if (!ok) {
+      if (lane == 0) atomicExch(a.err, 1u);
+    } else {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t j = s >> a.logn;
+      const uint32_t q = pick(mc.q, j);
+      const uint64_t mu = pick(mc.mu, j);
+      const int64_t off = (int64_t)q << 29;  // > 2^58 > |sum of the 16 weighted digit products|
+      const uint32_t quarter = warp & 3, b = lane & 3;
+      const uint32_t row = 32 * quarter + lane;  // accumulator lane: column c_local = row / 4, DB digit b
+      // digit-pair weights 2^(8(a + b)) mod q for this lane's DB digit b
+      uint32_t w[7];
+      w[0] = 1;
+#pragma unroll
+      for (int t = 1; t < 7; ++t) w[t] = reduce64((uint64_t)w[t - 1] << 8, q, mu);
+      int64_t wgt[4];
+#pragma unroll
+      for (int d = 0; d < 4; ++d)
+        wgt[d] = (int64_t)(b == 0 ? w[d] : b == 1 ? w[d + 1] : b == 2 ? w[d + 2] : w[d + 3]);
+      for (uint32_t t = warp >> 2; t < a.T; t += 2) {
+        const uint32_t c = (ct * a.T + t) * 32 + (row >> 2);
+        for (uint32_t g = 0; g < Nt / 16; ++g) {  // 4 query rows x 4 digits per load
+          uint32_t f[16];
+          tmem_ld16(tmem + ((32 * quarter) << 16) + t * Nt + 16 * g, f);
+          int64_t sum[4];
+#pragma unroll
+          for (int mm = 0; mm < 4; ++mm) {
+            int64_t v = 0;
+#pragma unroll
+            for (int d = 0; d < 4; ++d) v += (int64_t)__float2int_rn(__uint_as_float(f[4 * mm + d])) * wgt[d];
+            v += __shfl_xor_sync(0xffffffffu, v, 1);
+            v += __shfl_xor_sync(0xffffffffu, v, 2);
+            sum[mm] = v;
+          }
+          // lane b of the column writes query row 4g + b
+          const int64_t mine = b == 0 ? sum[0] : b == 1 ? sum[1] : b == 2 ? sum[2] : sum[3];
+          const uint32_t m = n0 / 4 + 4 * g + b;
+          if (m < a.M) {
+            uint32_t r = reduce64((uint64_t)(mine + off), q, mu);
+            uint32_t *o = a.out + ((uint64_t)s * a.M + m) * a.D2 + c;
+            if (a.acc_in) {
+              r += *o;
+              if (r >= q) r -= q;
+            }
+            *o = r;
+          }
+        }
+      }
+    }
+  }
+
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == kMmaWarp) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
+  }
+}
+
+// qhat chunk [B][Kc][2][L][n] -> qt[s][u][4*Mp rows][16] bf16 digits, row n = 4m + a.
+// CTA = 32 slots of one prime x 16 ciphertexts (one u) x 8 query rows m; residues
+// are staged in shared memory (coalesced reads along slots), then every thread
+// writes 16-byte rows of core matrices (64 threads = 1 KiB contiguous per slot).
+__global__ void __launch_bounds__(256) k_query_to_tensor(const uint32_t *__restrict__ qhat, uint32_t M, uint32_t Mp,
+                                                          uint32_t Kc, uint32_t L, uint32_t logn,
+                                                          uint16_t *__restrict__ qt) {
+  __shared__ uint32_t vals[16][8][33];
+  const uint32_t n = 1u << logn;
+  const uint32_t s0 = blockIdx.x * 32, u = blockIdx.y, mb = blockIdx.z;
+  const uint32_t j = s0 >> logn, k0 = s0 & (n - 1);
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint32_t p = warp; p < 128; p += 8) {
+    const uint32_t il = p >> 3, ml = p & 7, m = mb * 8 + ml, i = u * 16 + il;
+    uint32_t v = 0;
+    if (m < M) v = qhat[((uint64_t)((m >> 1) * Kc + i) * 2 + (m & 1)) * L * n + (uint64_t)j * n + k0 + lane];
+    vals[il][ml][lane] = v;
+  }
+  __syncthreads();
+  const uint32_t Ntot = 4 * Mp, Uc = Kc / 16;
+  for (uint32_t qi = threadIdx.x; qi < 32 * 64; qi += 256) {
+    const uint32_t rr = qi & 7, h = (qi >> 3) & 1, gl = (qi >> 4) & 3, sl = qi >> 6;
+    const uint32_t nl = 8 * gl + rr, ml = nl >> 2, dsel = nl & 3;
+    uint32_t packed[4];
+#pragma unroll
+    for (int e = 0; e < 8; e += 2) {
+      int d0[4], d1[4];
+      digits4(vals[8 * h + e][ml][sl], d0);
+      digits4(vals[8 * h + e + 1][ml][sl], d1);
+      const int x0 = dsel == 0 ? d0[0] : dsel == 1 ? d0[1] : dsel == 2 ? d0[2] : d0[3];
+      const int x1 = dsel == 0 ? d1[0] : dsel == 1 ? d1[1] : dsel == 2 ? d1[2] : d1[3];
+      packed[e / 2] = (uint32_t)bf16_bits(x0) | ((uint32_t)bf16_bits(x1) << 16);
+    }
+    const uint64_t s = s0 + sl;
+    const uint64_t e0 = (s * Uc + u) * Ntot * 16 + cm_off(32 * mb + nl, 8 * h);
+    *reinterpret_cast<uint4 *>(qt + e0) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+  }
+}
+
+// NTT-form DB polys [np][L][n] (row-major ids first + p = i*D2 + c) -> dbt digits.
+__global__ void __launch_bounds__(256) k_db_scatter_tensor(const uint32_t *__restrict__ polys, uint64_t first,
+                                                            uint64_t np, uint32_t D1, uint32_t D2, uint32_t L,
+                                                            uint32_t logn, uint16_t *__restrict__ res) {
+  __shared__ uint32_t tile[32][33];
+  const uint32_t n = 1u << logn;
+  const uint64_t p0 = (uint64_t)blockIdx.x * 32;
+  const uint32_t s0 = blockIdx.y * 32;
+  const uint32_t j = s0 >> logn, k0 = s0 & (n - 1);
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint32_t r = warp; r < 32; r += 8) {
+    const uint64_t p = p0 + r;
+    tile[r][lane] = p < np ? polys[(p * L + j) * n + k0 + lane] : 0u;
+  }
+  __syncthreads();
+  const uint64_t R = 4ull * D2, U = D1 / 16;
+  for (uint32_t kk = warp; kk < 32; kk += 8) {
+    const uint64_t p = p0 + lane;
+    if (p >= np) continue;
+    const uint64_t P = first + p, i = P / D2, c = P % D2;
+    int d[4];
+    digits4(tile[lane][kk], d);
+    const uint64_t blk = ((s0 + kk) * U + i / 16) * R * 16;
+#pragma unroll
+    for (uint32_t b = 0; b < 4; ++b) res[blk + cm_off((uint32_t)(4 * c + b), (uint32_t)(i % 16))] = bf16_bits(d[b]);
+  }
+}
+
+__global__ void k_db_read_poly_tensor(const uint16_t *__restrict__ res, uint64_t poly, uint32_t D1, uint32_t D2,
+                                      uint32_t nslots, uint32_t *__restrict__ out) {
+  const uint64_t i = poly / D2, c = poly % D2, R = 4ull * D2, U = D1 / 16;
+  for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < nslots; s += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t blk = (s * U + i / 16) * R * 16;
+    int64_t v = 0;
+    for (int b = 3; b >= 0; --b)
+      v = v * 256 + (int64_t)__bfloat162float(__ushort_as_bfloat16(res[blk + cm_off((uint32_t)(4 * c + b),
+                                                                                      (uint32_t)(i % 16))]));
+    out[s] = (uint32_t)v;
+  }
+}
+
+}  // namespace
+
+bool gemm_tc_shape_ok(uint32_t D1, uint32_t D2) { return D1 % 64 == 0 && D2 % 32 == 0; }
+
+uint32_t tc_rows(uint32_t M) { return (M + 7u) & ~7u; }
+
+cudaError_t launch_query_to_tensor(const ParamCtx &c, const uint32_t *qhat, uint32_t B, uint32_t Kc, uint32_t Mp,
+                                   uint16_t *qt, cudaStream_t s) {
+  if (Kc % 16 != 0 || Mp % 8 != 0) return cudaErrorInvalidValue;
+  dim3 grid((c.p.L << c.logn) / 32, Kc / 16, Mp / 8);
+  k_query_to_tensor<<<grid, 256, 0, s>>>(qhat, 2 * B, Mp, Kc, c.p.L, c.logn, qt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_db_scatter_tensor(const ParamCtx &c, uint32_t D1, uint32_t D2, const uint32_t *polys,
+                                     uint64_t first, uint64_t np, uint16_t *resident, cudaStream_t s) {
+  if (np == 0) return cudaSuccess;
+  dim3 grid((unsigned)((np + 31) / 32), (c.p.L << c.logn) / 32);
+  k_db_scatter_tensor<<<grid, 256, 0, s>>>(polys, first, np, D1, D2, c.p.L, c.logn, resident);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_db_read_poly_tensor(const ParamCtx &c, uint32_t D1, uint32_t D2, const uint16_t *resident,
+                                       uint64_t poly, uint32_t *out, cudaStream_t s) {
+  const uint32_t nslots = c.p.L << c.logn;
+  k_db_read_poly_tensor<<<(nslots + 255) / 256, 256, 0, s>>>(resident, poly, D1, D2, nslots, out);
+  return cudaGetLastError();
+}
+
+// out[s][m][c] (+)= sum_{i < Kc} Q[s][i][m] * DB[s][i0 + i][c] mod q_j for the
+// query digits qt of one K-chunk (Mp = tc_rows(M) rows).
+cudaError_t launch_gemm_tc(const ParamCtx &c, const uint16_t *db, uint32_t D1, uint32_t D2, const uint16_t *qt,
+                           uint32_t M, uint32_t Mp, uint32_t i0, uint32_t Kc, uint32_t *out, int acc, cudaStream_t s) {
+  if (!gemm_tc_shape_ok(D1, D2) || Kc == 0 || Kc % 64 != 0 || Kc > 1024 || i0 % 64 != 0 || i0 + Kc > D1 ||
+      Mp % 8 != 0 || Mp < M)
+    return cudaErrorInvalidValue;
+  uint32_t *err = nullptr;
+  cudaError_t e = device_error_word(&err);
+  if (e != cudaSuccess) return e;
+  TcArgs a = {};
+  a.db = db;
+  a.qt = qt;
+  a.out = out;
+  a.err = err;
+  a.M = M;
+  a.Mp = Mp;
+  a.D1 = D1;
+  a.D2 = D2;
+  a.i0 = i0;
+  a.Kc = Kc;
+  const uint32_t Ntot = 4 * Mp, Nmax = Ntot < 256 ? Ntot : 256;
+  a.mtiles = (Ntot + 255) / 256;
+  // 32-column tiles per CTA: as many as the 512 accumulator columns and D2 allow
+  uint32_t T = 1;
+  while (2 * T * Nmax <= 512 && (D2 / 32) % (2 * T) == 0) T *= 2;
+  a.T = T;
+  a.ctiles = D2 / (32 * T);
+  const uint32_t per16 = T * kBlockBytes + Nmax * 32;
+  uint32_t ks = per16 <= 16384 ? 4 : per16 <= 36864 ? 2 : 1;
+  while ((Kc / 16) % ks) ks /= 2;
+  a.KS16 = ks;
+  a.stage_bytes = ks * per16;
+  uint32_t S = (210u << 10) / a.stage_bytes;
+  if (S > (uint32_t)kMaxStages) S = kMaxStages;
+  if (S < 2) return cudaErrorInvalidValue;
+  a.S = S;
+  uint32_t cols = 32;
+  while (cols < T * Nmax) cols *= 2;
+  a.tmem_cols = cols;
+  a.nslots = c.p.L << c.logn;
+  a.logn = c.logn;
+  a.acc_in = acc;
+  // stages | 2 x kMaxStages + 1 barriers | tensor-memory address; at least 120 KiB so
+  // that one CTA runs per SM and its tensor-memory allocation never waits
+  size_t smem = (size_t)S * a.stage_bytes + (2 * kMaxStages + 1) * 8 + 16;
+  if (smem < (120u << 10)) smem = 120u << 10;
+  e = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const uint64_t grid = (uint64_t)a.nslots * a.ctiles * a.mtiles;
+  if (grid > 0x7fffffffull) return cudaErrorInvalidValue;
+  k_gemm_tc<<<(unsigned)grid, kThreads, smem, s>>>(a, c.mod);
+  return cudaGetLastError();
+}
+
+}  // namespace gbpir

@@ -66,23 +66,27 @@ extern "C" pir_status_t pir_answer_noalloc(pir_db_t db, const uint32_t *queries,
   if (((uintptr_t)queries & 15u) || ((uintptr_t)responses & 15u)) return PIR_ERR_ARG;
   const ParamCtx &c = *v.ctx;
   const uint32_t n = v.p.n, L = v.p.L, D1 = v.p.D1, D2 = v.p.D2;
-  const bool limb = v.layout == PIR_LAYOUT_LIMB;
+  const bool limb = v.layout == PIR_LAYOUT_LIMB, tensor = v.layout == PIR_LAYOUT_TENSOR;
   const uint32_t M = 2 * B;
-  const uint32_t Mp = limb ? (M + 15u) & ~15u : (M + 3u) & ~3u;
+  const uint32_t Mp = limb ? (M + 15u) & ~15u : tensor ? tc_rows(M) : (M + 3u) & ~3u;
   const uint64_t nslots = (uint64_t)L * n;
   const size_t cap = PIR_NOALLOC_SCRATCH_BYTES;
 
   // result buffer first, then the largest K chunk whose query scratch still fits
   const size_t out_bytes = up256((size_t)nslots * M * D2 * 4);
   if (out_bytes >= cap) return PIR_ERR_ARG;
-  // per folded row i: its NTT-form ciphertexts (qhat) + its slot-major copy (u32 words, or
-  // four u8 limb planes: the same bytes)
-  const size_t per_row = (size_t)B * 2 * L * n * 4 + (size_t)nslots * Mp * 4;
+  // per folded row i: its NTT-form ciphertexts (qhat) + its GEMM-layout copy (u32 words,
+  // four u8 limb planes: the same bytes; or four bf16 digits: twice that)
+  const size_t per_row = (size_t)B * 2 * L * n * 4 + (size_t)nslots * Mp * (tensor ? 8 : 4);
   uint64_t kc_fit = (cap - out_bytes - 512) / per_row;
   uint32_t Kc = kc_fit >= D1 ? D1 : (uint32_t)kc_fit;
   if (limb) {
     if (Kc > 8192) Kc = 8192;
     Kc &= ~31u;
+  }
+  if (tensor) {  // 64-row blocks, at most 1024 rows (exact f32 digit sums)
+    if (Kc > 1024) Kc = 1024;
+    Kc &= ~63u;
   }
   if (Kc == 0) return PIR_ERR_ARG;
 
@@ -103,7 +107,12 @@ extern "C" pir_status_t pir_answer_noalloc(pir_db_t db, const uint32_t *queries,
     const uint64_t G = (uint64_t)kc * 2 * L, S = (uint64_t)D1 * 2 * L;
     if ((e = launch_ntt_fwd_rows(c, queries, (uint64_t)i0 * 2 * L, G, S, qhat, (uint64_t)B * G, s)) != cudaSuccess)
       return cuda_status(e);
-    if (!limb) {
+    if (tensor) {
+      if ((e = launch_query_to_tensor(c, qhat, B, kc, Mp, static_cast<uint16_t *>(qs), s)) != cudaSuccess)
+        return cuda_status(e);
+      e = launch_gemm_tc(c, static_cast<const uint16_t *>(v.resident), D1, D2, static_cast<const uint16_t *>(qs), M,
+                         Mp, i0, kc, out, i0 > 0, s);
+    } else if (!limb) {
       if ((e = launch_query_to_slots(c, qhat, B, kc, Mp, static_cast<uint32_t *>(qs), s)) != cudaSuccess)
         return cuda_status(e);
       e = launch_gemm_plain(c, static_cast<const uint32_t *>(v.resident), D1, D2, static_cast<const uint32_t *>(qs),

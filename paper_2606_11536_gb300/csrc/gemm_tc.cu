@@ -29,7 +29,7 @@
 // Descriptors: LBO (K direction) = 128 bytes, SBO (8-row groups) = 256 bytes.
 //
 // CTA = (slot, T tiles of 32 DB columns, one tile of <= 64 query rows).  Its
-// accumulators take T * N <= 512 tensor-memory columns.
+// accumulators take T * N <= 256 tensor-memory columns, and two CTAs share an SM.
 //   warp 8   streams K stages (KS16 x 16 rows) into a ring of S shared-memory
 //            stages with 1-D bulk copies;
 //   warp 9   allocates the tensor memory and issues the MMAs from one thread;
@@ -53,6 +53,12 @@ constexpr int kEpiWarps = 8;
 constexpr int kProducerWarp = 8, kMmaWarp = 9;
 constexpr int kThreads = 320;
 constexpr int kMaxStages = 4;
+// Two CTAs per SM, so that one CTA's epilogue overlaps the other's streaming and
+// MMAs: each takes at most half of the 512 tensor-memory columns and of the
+// shared memory.  Every CTA takes at least kSmemFloor, so a third never fits and
+// a tensor-memory allocation never has to wait.
+constexpr uint32_t kTmemBudget = 256;
+constexpr uint32_t kSmemBudget = 110u << 10, kSmemFloor = 77u << 10;
 constexpr uint32_t kBlockBytes = 128 * 16 * 2;  // one 128-row x K16 bf16 block
 
 // Signed base-256 digits of x < 2^30.
@@ -105,6 +111,13 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// 32 x 32 -> 64-bit signed multiply-add
+__device__ __forceinline__ int64_t mad_wide(int32_t x, int32_t y, int64_t acc) {
+  int64_t d;
+  asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(x), "r"(y), "l"(acc));
+  return d;
+}
+
 struct TcArgs {
   const uint16_t *db;  // resident DB digits
   const uint16_t *qt;  // query digits of this K-chunk
@@ -124,7 +137,7 @@ __device__ __forceinline__ T pick(const T (&v)[PIR_MAX_L], uint32_t j) {
   return r;
 }
 
-__global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcArgs a, ModConst mc) {
+__global__ void __launch_bounds__(kThreads, 2) k_gemm_tc(TcArgs a, ModConst mc) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + a.S * a.stage_bytes);
   const uint32_t full0 = saddr(bars), empty0 = saddr(bars + kMaxStages), accf = saddr(bars + 2 * kMaxStages);
@@ -239,27 +252,31 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcArgs a, ModConst mc) 
       w[0] = 1;
 #pragma unroll
       for (int t = 1; t < 7; ++t) w[t] = reduce64((uint64_t)w[t - 1] << 8, q, mu);
-      int64_t wgt[4];
+      int32_t wgt[4];  // < 2^30
 #pragma unroll
-      for (int d = 0; d < 4; ++d)
-        wgt[d] = (int64_t)(b == 0 ? w[d] : b == 1 ? w[d + 1] : b == 2 ? w[d + 2] : w[d + 3]);
+      for (int d = 0; d < 4; ++d) wgt[d] = (int32_t)(b == 0 ? w[d] : b == 1 ? w[d + 1] : b == 2 ? w[d + 2] : w[d + 3]);
+      const bool hi2 = (b & 2) != 0, hi1 = (b & 1) != 0;
       for (uint32_t t = warp >> 2; t < a.T; t += 2) {
         const uint32_t c = (ct * a.T + t) * 32 + (row >> 2);
         for (uint32_t g = 0; g < Nt / 16; ++g) {  // 4 query rows x 4 digits per load
           uint32_t f[16];
           tmem_ld16(tmem + ((32 * quarter) << 16) + t * Nt + 16 * g, f);
+          // this lane's DB digit b, weighted over the query digits a, for rows 4g + mm
           int64_t sum[4];
 #pragma unroll
           for (int mm = 0; mm < 4; ++mm) {
             int64_t v = 0;
 #pragma unroll
-            for (int d = 0; d < 4; ++d) v += (int64_t)__float2int_rn(__uint_as_float(f[4 * mm + d])) * wgt[d];
-            v += __shfl_xor_sync(0xffffffffu, v, 1);
-            v += __shfl_xor_sync(0xffffffffu, v, 2);
+            for (int d = 0; d < 4; ++d) v = mad_wide(__float2int_rn(__uint_as_float(f[4 * mm + d])), wgt[d], v);
             sum[mm] = v;
           }
-          // lane b of the column writes query row 4g + b
-          const int64_t mine = b == 0 ? sum[0] : b == 1 ? sum[1] : b == 2 ? sum[2] : sum[3];
+          // reduce-scatter over the column's 4 lanes: lane b ends with row 4g + b's total
+          int64_t k0 = hi2 ? sum[2] : sum[0], k1 = hi2 ? sum[3] : sum[1];
+          const int64_t o0 = hi2 ? sum[0] : sum[2], o1 = hi2 ? sum[1] : sum[3];
+          k0 += __shfl_xor_sync(0xffffffffu, o0, 2);
+          k1 += __shfl_xor_sync(0xffffffffu, o1, 2);
+          int64_t mine = hi1 ? k1 : k0;
+          mine += __shfl_xor_sync(0xffffffffu, hi1 ? k0 : k1, 1);
           const uint32_t m = n0 / 4 + 4 * g + b;
           if (m < a.M) {
             uint32_t r = reduce64((uint64_t)(mine + off), q, mu);
@@ -415,17 +432,18 @@ cudaError_t launch_gemm_tc(const ParamCtx &c, const uint16_t *db, uint32_t D1, u
   a.Kc = Kc;
   const uint32_t Ntot = 4 * Mp, Nmax = Ntot < 256 ? Ntot : 256;
   a.mtiles = (Ntot + 255) / 256;
-  // 32-column tiles per CTA: as many as the 512 accumulator columns and D2 allow
+  // 32-column tiles per CTA: as many as the accumulator budget and D2 allow
   uint32_t T = 1;
-  while (2 * T * Nmax <= 512 && (D2 / 32) % (2 * T) == 0) T *= 2;
+  while (2 * T * Nmax <= kTmemBudget && (D2 / 32) % (2 * T) == 0) T *= 2;
   a.T = T;
   a.ctiles = D2 / (32 * T);
+  // K16 steps per stage: as many as leave room for two stages
   const uint32_t per16 = T * kBlockBytes + Nmax * 32;
-  uint32_t ks = per16 <= 16384 ? 4 : per16 <= 36864 ? 2 : 1;
-  while ((Kc / 16) % ks) ks /= 2;
+  uint32_t ks = 4;
+  while (ks > 1 && (2 * ks * per16 > kSmemBudget || (Kc / 16) % ks)) ks /= 2;
   a.KS16 = ks;
   a.stage_bytes = ks * per16;
-  uint32_t S = (210u << 10) / a.stage_bytes;
+  uint32_t S = kSmemBudget / a.stage_bytes;
   if (S > (uint32_t)kMaxStages) S = kMaxStages;
   if (S < 2) return cudaErrorInvalidValue;
   a.S = S;
@@ -435,10 +453,9 @@ cudaError_t launch_gemm_tc(const ParamCtx &c, const uint16_t *db, uint32_t D1, u
   a.nslots = c.p.L << c.logn;
   a.logn = c.logn;
   a.acc_in = acc;
-  // stages | 2 x kMaxStages + 1 barriers | tensor-memory address; at least 120 KiB so
-  // that one CTA runs per SM and its tensor-memory allocation never waits
+  // stages | 2 x kMaxStages + 1 barriers | tensor-memory address
   size_t smem = (size_t)S * a.stage_bytes + (2 * kMaxStages + 1) * 8 + 16;
-  if (smem < (120u << 10)) smem = 120u << 10;
+  if (smem < kSmemFloor) smem = kSmemFloor;
   e = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const uint64_t grid = (uint64_t)a.nslots * a.ctiles * a.mtiles;

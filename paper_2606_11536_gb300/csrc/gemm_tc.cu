@@ -28,12 +28,13 @@
 //   query digits  qt[s][u][4 * Mp rows][16]    u over one K-chunk
 // Descriptors: LBO (K direction) = 128 bytes, SBO (8-row groups) = 256 bytes.
 //
-// CTA = (slot, T tiles of 32 DB columns, one tile of <= 64 query rows).  Its
-// accumulators take T * N <= 256 tensor-memory columns, and two CTAs share an SM.
-//   warp 8   streams K stages (KS16 x 16 rows) into a ring of S shared-memory
-//            stages with 1-D bulk copies;
+// Work unit = (slot, T tiles of 32 DB columns, one tile of <= 64 query rows); its
+// accumulators take T * N <= 256 tensor-memory columns.  One persistent CTA per SM
+// runs its units through two accumulator buffers.
+//   warp 8   streams the units' K stages (KS16 x 16 rows) back to back into a
+//            ring of S shared-memory stages with 1-D bulk copies;
 //   warp 9   allocates the tensor memory and issues the MMAs from one thread;
-//   warps 0..7  run the epilogue.
+//   warps 0..7  run the epilogue of the previous unit meanwhile.
 // Every barrier wait is bounded; a wait that runs out sets the device error word.
 #include <cuda_bf16.h>
 
@@ -49,16 +50,16 @@ using async::mbar_init;
 using async::saddr;
 using async::wait_bounded;
 
-constexpr int kEpiWarps = 8;
-constexpr int kProducerWarp = 8, kMmaWarp = 9;
-constexpr int kThreads = 320;
+constexpr int kEpiWarps = 8;  // two sets of the four tensor-memory lane quarters
+constexpr int kProducerWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1;
+constexpr int kThreads = (kEpiWarps + 2) * 32;
 constexpr int kMaxStages = 4;
-// Two CTAs per SM, so that one CTA's epilogue overlaps the other's streaming and
-// MMAs: each takes at most half of the 512 tensor-memory columns and of the
-// shared memory.  Every CTA takes at least kSmemFloor, so a third never fits and
-// a tensor-memory allocation never has to wait.
+// One persistent CTA per SM with two tensor-memory accumulator buffers of
+// kTmemBudget columns each (the MMAs of one unit overlap the epilogue of the one
+// before).  Every CTA takes more than half of an SM's shared memory, so a second
+// never lands on the same SM (its tensor-memory allocation would wait for the first).
 constexpr uint32_t kTmemBudget = 256;
-constexpr uint32_t kSmemBudget = 110u << 10, kSmemFloor = 77u << 10;
+constexpr uint32_t kSmemBudget = 200u << 10, kSmemFloor = 116u << 10;
 constexpr uint32_t kBlockBytes = 128 * 16 * 2;  // one 128-row x K16 bf16 block
 
 // Signed base-256 digits of x < 2^30.
@@ -102,11 +103,15 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+// 32 consecutive accumulator columns of this warp's 32 lanes
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -124,8 +129,8 @@ struct TcArgs {
   uint32_t *out;       // [L*n][M][D2]
   uint32_t *err;       // per-device error word
   uint32_t M, Mp, D1, D2, i0, Kc;
-  uint32_t T, KS16, S, stage_bytes, ctiles, mtiles, tmem_cols;
-  uint32_t nslots, logn;
+  uint32_t T, KS16, S, stage_bytes, ctiles, mtiles, nunits;
+  uint32_t logn;
   int acc_in;
 };
 
@@ -137,22 +142,37 @@ __device__ __forceinline__ T pick(const T (&v)[PIR_MAX_L], uint32_t j) {
   return r;
 }
 
-__global__ void __launch_bounds__(kThreads, 2) k_gemm_tc(TcArgs a, ModConst mc) {
+// Work unit u = (slot s, query-row tile mt, column tile ct), ct fastest: CTAs that
+// run side by side take the column tiles of one slot and share its query digits in L2.
+struct Unit {
+  uint32_t s, mt, ct, n0, Nt;
+};
+
+__device__ __forceinline__ Unit unit_of(const TcArgs &a, uint32_t u) {
+  Unit w;
+  w.ct = u % a.ctiles;
+  const uint32_t rest = u / a.ctiles;
+  w.mt = rest % a.mtiles;
+  w.s = rest / a.mtiles;
+  const uint32_t Ntot = 4 * a.Mp;
+  w.n0 = w.mt * 256;
+  w.Nt = Ntot - w.n0 < 256 ? Ntot - w.n0 : 256;
+  return w;
+}
+
+// Persistent: CTA b takes units b, b + gridDim.x, ...  The producer streams their K
+// stages back to back through the ring; the MMA thread accumulates unit k into
+// tensor-memory buffer k % 2 while the epilogue drains buffer (k - 1) % 2.
+__global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcArgs a, ModConst mc) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + a.S * a.stage_bytes);
-  const uint32_t full0 = saddr(bars), empty0 = saddr(bars + kMaxStages), accf = saddr(bars + 2 * kMaxStages);
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * kMaxStages + 1);
+  const uint32_t full0 = saddr(bars), empty0 = saddr(bars + kMaxStages);
+  const uint32_t tfull0 = saddr(bars + 2 * kMaxStages), tempty0 = saddr(bars + 2 * kMaxStages + 2);
+  const uint32_t done = saddr(bars + 2 * kMaxStages + 4);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * kMaxStages + 5);
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-  const uint64_t bid = blockIdx.x;
-  const uint32_t ct = (uint32_t)(bid % a.ctiles);
-  const uint64_t rest = bid / a.ctiles;
-  const uint32_t mt = (uint32_t)(rest % a.mtiles);
-  const uint32_t s = (uint32_t)(rest / a.mtiles);
-  const uint32_t Ntot = 4 * a.Mp, n0 = mt * 256;
-  const uint32_t Nt = Ntot - n0 < 256 ? Ntot - n0 : 256;  // query digit rows of this tile
   const uint32_t R = 4 * a.D2, U = a.D1 / 16, Uc = a.Kc / 16;
-  const uint32_t nst = Uc / a.KS16;
+  const uint32_t nst = Uc / a.KS16, Ntot = 4 * a.Mp;
   const uint32_t db_stage = a.KS16 * a.T * kBlockBytes;
 
   if (threadIdx.x == 0) {
@@ -160,12 +180,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_gemm_tc(TcArgs a, ModConst mc) 
       mbar_init(full0 + 8 * st, 1);
       mbar_init(empty0 + 8 * st, 1);
     }
-    mbar_init(accf, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull0 + 8 * b, 1);
+      mbar_init(tempty0 + 8 * b, kEpiWarps);
+    }
+    mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == kMmaWarp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tslot)),
-                 "r"(a.tmem_cols)
+                 "r"(2 * kTmemBudget)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -179,108 +203,137 @@ __global__ void __launch_bounds__(kThreads, 2) k_gemm_tc(TcArgs a, ModConst mc) 
       const uint64_t pol_db = async::policy_evict_first(), pol_q = async::policy_evict_last();
       const uint8_t *dbs = reinterpret_cast<const uint8_t *>(a.db);
       const uint8_t *qs = reinterpret_cast<const uint8_t *>(a.qt);
-      uint32_t issued = 0;
-      for (uint32_t st = 0; st < nst; ++st) {
-        const uint32_t slot = st % a.S, ph = (st / a.S) & 1;
-        if (!wait_bounded(empty0 + 8 * slot, ph ^ 1)) {
-          atomicExch(a.err, 1u);
-          break;
-        }
-        const uint32_t qbytes = a.KS16 * Nt * 32;
-        const uint32_t dst = saddr(smem + slot * a.stage_bytes);
-        mbar_expect_tx(full0 + 8 * slot, db_stage + qbytes);
-        for (uint32_t v = 0; v < a.KS16; ++v) {
-          const uint64_t u = a.i0 / 16 + (uint64_t)st * a.KS16 + v;
-          const uint64_t e = (((uint64_t)s * U + u) * R + (uint64_t)ct * a.T * 128) * 16;
-          bulk_g2s(dst + v * a.T * kBlockBytes, dbs + 2 * e, a.T * kBlockBytes, full0 + 8 * slot, pol_db);
-        }
-        if (Nt == Ntot) {  // the stage's query rows are one contiguous run
-          const uint64_t e = ((uint64_t)s * Uc + (uint64_t)st * a.KS16) * Ntot * 16;
-          bulk_g2s(dst + db_stage, qs + 2 * e, qbytes, full0 + 8 * slot, pol_q);
-        } else {
+      uint32_t it = 0;
+      bool ok = true;
+      for (uint32_t u = blockIdx.x; ok && u < a.nunits; u += gridDim.x) {
+        const Unit w = unit_of(a, u);
+        const uint32_t qbytes = a.KS16 * w.Nt * 32;
+        for (uint32_t st = 0; st < nst; ++st, ++it) {
+          const uint32_t slot = it % a.S, ph = (it / a.S) & 1;
+          if (!wait_bounded(empty0 + 8 * slot, ph ^ 1)) {
+            atomicExch(a.err, 1u);
+            ok = false;
+            break;
+          }
+          const uint32_t dst = saddr(smem + slot * a.stage_bytes);
+          mbar_expect_tx(full0 + 8 * slot, db_stage + qbytes);
           for (uint32_t v = 0; v < a.KS16; ++v) {
-            const uint64_t e = (((uint64_t)s * Uc + (uint64_t)st * a.KS16 + v) * Ntot + n0) * 16;
-            bulk_g2s(dst + db_stage + v * Nt * 32, qs + 2 * e, Nt * 32, full0 + 8 * slot, pol_q);
+            const uint64_t uu = a.i0 / 16 + (uint64_t)st * a.KS16 + v;
+            const uint64_t e = (((uint64_t)w.s * U + uu) * R + (uint64_t)w.ct * a.T * 128) * 16;
+            bulk_g2s(dst + v * a.T * kBlockBytes, dbs + 2 * e, a.T * kBlockBytes, full0 + 8 * slot, pol_db);
+          }
+          if (w.Nt == Ntot) {  // the stage's query rows are one contiguous run
+            const uint64_t e = ((uint64_t)w.s * Uc + (uint64_t)st * a.KS16) * Ntot * 16;
+            bulk_g2s(dst + db_stage, qs + 2 * e, qbytes, full0 + 8 * slot, pol_q);
+          } else {
+            for (uint32_t v = 0; v < a.KS16; ++v) {
+              const uint64_t e = (((uint64_t)w.s * Uc + (uint64_t)st * a.KS16 + v) * Ntot + w.n0) * 16;
+              bulk_g2s(dst + db_stage + v * w.Nt * 32, qs + 2 * e, w.Nt * 32, full0 + 8 * slot, pol_q);
+            }
           }
         }
-        ++issued;
       }
       // drain: never leave with copies in flight
-      const uint32_t first = issued > a.S ? issued - a.S : 0;
-      for (uint32_t k = first; k < issued; ++k)
+      const uint32_t first = it > a.S ? it - a.S : 0;
+      for (uint32_t k = first; k < it; ++k)
         if (!wait_bounded(full0 + 8 * (k % a.S), (k / a.S) & 1)) atomicExch(a.err, 1u);
     }
     __syncwarp();
   } else if (warp == kMmaWarp) {
     if (lane == 0) {
-      const uint32_t idesc = instr_desc(128, Nt);
-      for (uint32_t st = 0; st < nst; ++st) {
-        const uint32_t slot = st % a.S;
-        if (!wait_bounded(full0 + 8 * slot, (st / a.S) & 1)) {
+      uint32_t it = 0, k = 0;
+      bool ok = true;
+      for (uint32_t u = blockIdx.x; ok && u < a.nunits; u += gridDim.x, ++k) {
+        const Unit w = unit_of(a, u);
+        const uint32_t buf = k & 1;
+        if (!wait_bounded(tempty0 + 8 * buf, ((k >> 1) & 1) ^ 1)) {  // the epilogue has drained this buffer
           atomicExch(a.err, 1u);
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t base = saddr(smem + slot * a.stage_bytes);
-        for (uint32_t v = 0; v < a.KS16; ++v) {
-          const uint64_t bdesc = smem_desc(base + db_stage + v * Nt * 32);
-          for (uint32_t t = 0; t < a.T; ++t) {
-            const uint64_t adesc = smem_desc(base + (v * a.T + t) * kBlockBytes);
-            mma_bf16(tmem + t * Nt, adesc, bdesc, idesc, (st | v) != 0);
+        const uint32_t idesc = instr_desc(128, w.Nt), dcol = tmem + buf * kTmemBudget;
+        for (uint32_t st = 0; st < nst; ++st, ++it) {
+          const uint32_t slot = it % a.S;
+          if (!wait_bounded(full0 + 8 * slot, (it / a.S) & 1)) {
+            atomicExch(a.err, 1u);
+            ok = false;
+            break;
           }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t base = saddr(smem + slot * a.stage_bytes);
+          for (uint32_t v = 0; v < a.KS16; ++v) {
+            const uint64_t bdesc = smem_desc(base + db_stage + v * w.Nt * 32);
+            for (uint32_t t = 0; t < a.T; ++t) {
+              const uint64_t adesc = smem_desc(base + (v * a.T + t) * kBlockBytes);
+              mma_bf16(dcol + t * w.Nt, adesc, bdesc, idesc, (st | v) != 0);
+            }
+          }
+          mma_commit(empty0 + 8 * slot);  // the stage is free once these MMAs have read it
         }
-        mma_commit(empty0 + 8 * slot);  // the stage is free once these MMAs have read it
+        mma_commit(tfull0 + 8 * buf);  // this unit's accumulators are complete
       }
-      mma_commit(accf);  // every MMA issued above has completed
+      // on every path: no MMA may still be running when the tensor memory is freed
+      mma_commit(done);
+      if (!wait_bounded(done, 0)) atomicExch(a.err, 1u);
     }
     __syncwarp();
   } else {
     // ---------------- epilogue: warps 0..7 ----------------
-    const bool ok = __all_sync(0xffffffffu, wait_bounded(accf, 0));
-    if (!ok) {
-      if (lane == 0) atomicExch(a.err, 1u);
-    } else {
+    const uint32_t quarter = warp & 3, b = lane & 3;
+    const uint32_t row = 32 * quarter + lane;  // accumulator lane: column c_local = row / 4, DB digit b
+    const bool hi2 = (b & 2) != 0, hi1 = (b & 1) != 0;
+    uint32_t k = 0;
+    for (uint32_t u = blockIdx.x; u < a.nunits; u += gridDim.x, ++k) {
+      const Unit w = unit_of(a, u);
+      const uint32_t buf = k & 1;
+      if (!__all_sync(0xffffffffu, wait_bounded(tfull0 + 8 * buf, (k >> 1) & 1))) {
+        if (lane == 0) atomicExch(a.err, 1u);
+        break;
+      }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t j = s >> a.logn;
+      const uint32_t j = w.s >> a.logn;
       const uint32_t q = pick(mc.q, j);
       const uint64_t mu = pick(mc.mu, j);
       const int64_t off = (int64_t)q << 29;  // > 2^58 > |sum of the 16 weighted digit products|
-      const uint32_t quarter = warp & 3, b = lane & 3;
-      const uint32_t row = 32 * quarter + lane;  // accumulator lane: column c_local = row / 4, DB digit b
       // digit-pair weights 2^(8(a + b)) mod q for this lane's DB digit b
-      uint32_t w[7];
-      w[0] = 1;
+      uint32_t pw[7];
+      pw[0] = 1;
 #pragma unroll
-      for (int t = 1; t < 7; ++t) w[t] = reduce64((uint64_t)w[t - 1] << 8, q, mu);
+      for (int t = 1; t < 7; ++t) pw[t] = reduce64((uint64_t)pw[t - 1] << 8, q, mu);
       int32_t wgt[4];  // < 2^30
 #pragma unroll
-      for (int d = 0; d < 4; ++d) wgt[d] = (int32_t)(b == 0 ? w[d] : b == 1 ? w[d + 1] : b == 2 ? w[d + 2] : w[d + 3]);
-      const bool hi2 = (b & 2) != 0, hi1 = (b & 1) != 0;
-      for (uint32_t t = warp >> 2; t < a.T; t += 2) {
-        const uint32_t c = (ct * a.T + t) * 32 + (row >> 2);
-        for (uint32_t g = 0; g < Nt / 16; ++g) {  // 4 query rows x 4 digits per load
-          uint32_t f[16];
-          tmem_ld16(tmem + ((32 * quarter) << 16) + t * Nt + 16 * g, f);
-          // this lane's DB digit b, weighted over the query digits a, for rows 4g + mm
+      for (int d = 0; d < 4; ++d)
+        wgt[d] = (int32_t)(b == 0 ? pw[d] : b == 1 ? pw[d + 1] : b == 2 ? pw[d + 2] : pw[d + 3]);
+      // items (column tile t, group of 8 query rows x 4 digits), shared by the sets
+      const uint32_t G = w.Nt / 32;
+      for (uint32_t item = warp >> 2; item < a.T * G; item += kEpiWarps / 4) {
+        const uint32_t t = item / G, g = item % G;
+        const uint32_t c = (w.ct * a.T + t) * 32 + (row >> 2);
+        uint32_t f[32];
+        tmem_ld32(tmem + buf * kTmemBudget + ((32 * quarter) << 16) + t * w.Nt + 32 * g, f);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          // this lane's DB digit b, weighted over the query digits a, for rows 8g + 4h + mm
           int64_t sum[4];
 #pragma unroll
           for (int mm = 0; mm < 4; ++mm) {
             int64_t v = 0;
 #pragma unroll
-            for (int d = 0; d < 4; ++d) v = mad_wide(__float2int_rn(__uint_as_float(f[4 * mm + d])), wgt[d], v);
+            for (int d = 0; d < 4; ++d)
+              v = mad_wide(__float2int_rn(__uint_as_float(f[16 * h + 4 * mm + d])), wgt[d], v);
             sum[mm] = v;
           }
-          // reduce-scatter over the column's 4 lanes: lane b ends with row 4g + b's total
+          // reduce-scatter over the column's 4 lanes: lane b ends with row 8g + 4h + b's total
           int64_t k0 = hi2 ? sum[2] : sum[0], k1 = hi2 ? sum[3] : sum[1];
           const int64_t o0 = hi2 ? sum[0] : sum[2], o1 = hi2 ? sum[1] : sum[3];
           k0 += __shfl_xor_sync(0xffffffffu, o0, 2);
           k1 += __shfl_xor_sync(0xffffffffu, o1, 2);
           int64_t mine = hi1 ? k1 : k0;
           mine += __shfl_xor_sync(0xffffffffu, hi1 ? k0 : k1, 1);
-          const uint32_t m = n0 / 4 + 4 * g + b;
+          const uint32_t m = w.n0 / 4 + 8 * g + 4 * h + b;
           if (m < a.M) {
             uint32_t r = reduce64((uint64_t)(mine + off), q, mu);
-            uint32_t *o = a.out + ((uint64_t)s * a.M + m) * a.D2 + c;
+            uint32_t *o = a.out + ((uint64_t)w.s * a.M + m) * a.D2 + c;
             if (a.acc_in) {
               r += *o;
               if (r >= q) r -= q;
@@ -289,6 +342,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_gemm_tc(TcArgs a, ModConst mc) 
           }
         }
       }
+      // this warp's reads of the buffer are complete: hand it back to the MMA thread
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) async::mbar_arrive(tempty0 + 8 * buf);
     }
   }
 
@@ -296,14 +353,26 @@ __global__ void __launch_bounds__(kThreads, 2) k_gemm_tc(TcArgs a, ModConst mc) 
   __syncthreads();
   if (warp == kMmaWarp) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTmemBudget)
+                 : "memory");
   }
+}
+
+// Two digits (|d| < 2^22) as a bf16 pair, exactly: 1.5 * 2^23 + d is exact in f32
+// with unit spacing, so adding d to that constant's bit pattern and subtracting the
+// constant gives (float)d; a digit of at most 8 significant bits leaves the low 16
+// bits of the f32 zero, so its top half is the bf16 value.
+__device__ __forceinline__ uint32_t bf16x2_of(int d0, int d1) {
+  const float f0 = __int_as_float(0x4B400000 + d0) - 12582912.0f;
+  const float f1 = __int_as_float(0x4B400000 + d1) - 12582912.0f;
+  return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
 }
 
 // qhat chunk [B][Kc][2][L][n] -> qt[s][u][4*Mp rows][16] bf16 digits, row n = 4m + a.
 // CTA = 32 slots of one prime x 16 ciphertexts (one u) x 8 query rows m; residues
-// are staged in shared memory (coalesced reads along slots), then every thread
-// writes 16-byte rows of core matrices (64 threads = 1 KiB contiguous per slot).
+// are staged in shared memory (coalesced reads along slots).  Then a thread takes
+// (slot, row m, K half): the digits of its 8 residues, once, and the four 16-byte
+// digit rows n = 4m..4m+3 (64 contiguous bytes; 16 threads = 1 KiB per slot).
 __global__ void __launch_bounds__(256) k_query_to_tensor(const uint32_t *__restrict__ qhat, uint32_t M, uint32_t Mp,
                                                           uint32_t Kc, uint32_t L, uint32_t logn,
                                                           uint16_t *__restrict__ qt) {
@@ -320,22 +389,20 @@ __global__ void __launch_bounds__(256) k_query_to_tensor(const uint32_t *__restr
   }
   __syncthreads();
   const uint32_t Ntot = 4 * Mp, Uc = Kc / 16;
-  for (uint32_t qi = threadIdx.x; qi < 32 * 64; qi += 256) {
-    const uint32_t rr = qi & 7, h = (qi >> 3) & 1, gl = (qi >> 4) & 3, sl = qi >> 6;
-    const uint32_t nl = 8 * gl + rr, ml = nl >> 2, dsel = nl & 3;
-    uint32_t packed[4];
+  for (uint32_t w = threadIdx.x; w < 32 * 16; w += 256) {
+    // w = slot * 16 + ((m / 2) * 4 + h * 2 + m % 2): 64-byte pieces in memory order
+    const uint32_t sl = w >> 4, t = w & 15;
+    const uint32_t ml = ((t >> 2) << 1) | (t & 1), h = (t >> 1) & 1;
+    int d[8][4];
 #pragma unroll
-    for (int e = 0; e < 8; e += 2) {
-      int d0[4], d1[4];
-      digits4(vals[8 * h + e][ml][sl], d0);
-      digits4(vals[8 * h + e + 1][ml][sl], d1);
-      const int x0 = dsel == 0 ? d0[0] : dsel == 1 ? d0[1] : dsel == 2 ? d0[2] : d0[3];
-      const int x1 = dsel == 0 ? d1[0] : dsel == 1 ? d1[1] : dsel == 2 ? d1[2] : d1[3];
-      packed[e / 2] = (uint32_t)bf16_bits(x0) | ((uint32_t)bf16_bits(x1) << 16);
-    }
+    for (int e = 0; e < 8; ++e) digits4(vals[8 * h + e][ml][sl], d[e]);
     const uint64_t s = s0 + sl;
-    const uint64_t e0 = (s * Uc + u) * Ntot * 16 + cm_off(32 * mb + nl, 8 * h);
-    *reinterpret_cast<uint4 *>(qt + e0) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+    uint16_t *dst = qt + (s * Uc + u) * Ntot * 16 + cm_off(32 * mb + 4 * ml, 8 * h);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)  // digit rows 4m + a: consecutive 16-byte rows of one core matrix
+      *reinterpret_cast<uint4 *>(dst + 8 * a) =
+          make_uint4(bf16x2_of(d[0][a], d[1][a]), bf16x2_of(d[2][a], d[3][a]), bf16x2_of(d[4][a], d[5][a]),
+                     bf16x2_of(d[6][a], d[7][a]));
   }
 }
 
@@ -437,30 +504,32 @@ cudaError_t launch_gemm_tc(const ParamCtx &c, const uint16_t *db, uint32_t D1, u
   while (2 * T * Nmax <= kTmemBudget && (D2 / 32) % (2 * T) == 0) T *= 2;
   a.T = T;
   a.ctiles = D2 / (32 * T);
-  // K16 steps per stage: as many as leave room for two stages
+  // K16 steps per stage: as many as leave room for three stages
   const uint32_t per16 = T * kBlockBytes + Nmax * 32;
   uint32_t ks = 4;
-  while (ks > 1 && (2 * ks * per16 > kSmemBudget || (Kc / 16) % ks)) ks /= 2;
+  while (ks > 1 && (3 * ks * per16 > kSmemBudget || (Kc / 16) % ks)) ks /= 2;
   a.KS16 = ks;
   a.stage_bytes = ks * per16;
   uint32_t S = kSmemBudget / a.stage_bytes;
   if (S > (uint32_t)kMaxStages) S = kMaxStages;
   if (S < 2) return cudaErrorInvalidValue;
   a.S = S;
-  uint32_t cols = 32;
-  while (cols < T * Nmax) cols *= 2;
-  a.tmem_cols = cols;
-  a.nslots = c.p.L << c.logn;
   a.logn = c.logn;
   a.acc_in = acc;
-  // stages | 2 x kMaxStages + 1 barriers | tensor-memory address
-  size_t smem = (size_t)S * a.stage_bytes + (2 * kMaxStages + 1) * 8 + 16;
+  const uint64_t nunits = (uint64_t)(c.p.L << c.logn) * a.ctiles * a.mtiles;
+  if (nunits > 0x7fffffffull) return cudaErrorInvalidValue;
+  a.nunits = (uint32_t)nunits;
+  // stages | full, empty (kMaxStages each), two tensor-memory full/empty pairs, done |
+  // tensor-memory address
+  size_t smem = (size_t)S * a.stage_bytes + (2 * kMaxStages + 5) * 8 + 16;
   if (smem < kSmemFloor) smem = kSmemFloor;
   e = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const uint64_t grid = (uint64_t)a.nslots * a.ctiles * a.mtiles;
-  if (grid > 0x7fffffffull) return cudaErrorInvalidValue;
-  k_gemm_tc<<<(unsigned)grid, kThreads, smem, s>>>(a, c.mod);
+  int dev = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const uint32_t grid = a.nunits < (uint32_t)sms ? a.nunits : (uint32_t)sms;
+  k_gemm_tc<<<grid, kThreads, smem, s>>>(a, c.mod);
   return cudaGetLastError();
 }
 

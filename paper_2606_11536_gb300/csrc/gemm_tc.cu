@@ -381,11 +381,18 @@ __global__ void __launch_bounds__(256) k_query_to_tensor(const uint32_t *__restr
   const uint32_t s0 = blockIdx.x * 32, u = blockIdx.y, mb = blockIdx.z;
   const uint32_t j = s0 >> logn, k0 = s0 & (n - 1);
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (uint32_t p = warp; p < 128; p += 8) {
-    const uint32_t il = p >> 3, ml = p & 7, m = mb * 8 + ml, i = u * 16 + il;
-    uint32_t v = 0;
-    if (m < M) v = qhat[((uint64_t)((m >> 1) * Kc + i) * 2 + (m & 1)) * L * n + (uint64_t)j * n + k0 + lane];
-    vals[il][ml][lane] = v;
+  // all 16 loads of a thread in flight at once, then the shared-memory stores
+  uint32_t v[16];
+#pragma unroll
+  for (uint32_t r = 0; r < 16; ++r) {
+    const uint32_t p = warp + 8 * r, il = p >> 3, ml = p & 7, m = mb * 8 + ml, i = u * 16 + il;
+    v[r] = m < M ? __ldg(qhat + ((uint64_t)((m >> 1) * Kc + i) * 2 + (m & 1)) * L * n + (uint64_t)j * n + k0 + lane)
+                 : 0u;
+  }
+#pragma unroll
+  for (uint32_t r = 0; r < 16; ++r) {
+    const uint32_t p = warp + 8 * r;
+    vals[p >> 3][p & 7][lane] = v[r];
   }
   __syncthreads();
   const uint32_t Ntot = 4 * Mp, Uc = Kc / 16;

@@ -151,11 +151,13 @@ typedef struct {
  * transpose, inverse NTT. */
 #define PIR_STAGES 5
 
-/* pir_answer with options.  With host buffers and k_chunk = 0, queries of 8 MiB to
- * 4 GiB are uploaded in four pieces on a copy stream, each piece's forward NTT
- * waiting only for its own copy; larger host batches run as a streamed answer
- * (pir_answer_begin below) in pieces of at most 1 GiB, so the device holds one
- * piece at a time. */
+/* pir_answer with options.  With host buffers and k_chunk = 0:
+ *   - batches of 16 and more (8 MiB to 4 GiB of queries) run as sub-batches of at
+ *     least 8 queries, whose upload, answer and download overlap on three streams;
+ *   - smaller batches of 8 MiB to 4 GiB upload in four pieces on a copy stream,
+ *     each piece's forward NTT waiting only for its own copy;
+ *   - host batches above 4 GiB run as a streamed answer (pir_answer_begin below) in
+ *     pieces of at most 1 GiB, so the device holds one piece at a time. */
 pir_status_t pir_answer_ex(pir_db_t db, const uint32_t *queries, uint32_t B, uint32_t *responses, int on_device,
                            void *stream, const pir_answer_opts_t *opts);
 

@@ -243,6 +243,16 @@ cudaError_t copy_stream(cudaStream_t *out) {
   *out = t_copy_stream;
   return cudaSuccess;
 }
+// the device-to-host direction, so that downloads overlap the uploads
+thread_local cudaStream_t t_d2h_stream = nullptr;
+cudaError_t d2h_stream(cudaStream_t *out) {
+  if (!t_d2h_stream) {
+    cudaError_t e = cudaStreamCreateWithFlags(&t_d2h_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+  }
+  *out = t_d2h_stream;
+  return cudaSuccess;
+}
 
 struct StageTimer {
   bool on;
@@ -801,6 +811,61 @@ pir_status_t pir_answer_ex(pir_db_t db, const uint32_t *queries, uint32_t B, uin
   Scratch dq(s), dr(s);
   CK(dq.alloc(qbytes));
   CK(dr.alloc(rbytes));
+  // Batches of 16 and more (queries of 8 MiB and more, chunking left to the library)
+  // run as sub-batches of at least 8 queries: sub-batch k+1 uploads on the copy
+  // stream while k is answered on `stream` and k-1 downloads on a third stream, so
+  // both directions of the host link stay busy and every sub-batch runs the whole
+  // of D1 at once.
+  if (o.k_chunk == 0 && B >= 16 && qbytes >= (8ull << 20) && (o.flags & PIR_ANSWER_TEST_STALL) == 0) {
+    cudaStream_t up = nullptr, down = nullptr;
+    CK(copy_stream(&up));
+    CK(d2h_stream(&down));
+    uint32_t nsub = B / 8;
+    if (nsub > kMaxFeedChunks) nsub = kMaxFeedChunks;
+    if (nsub > 4) nsub = 4;
+    const uint32_t Bs = (B + nsub - 1) / nsub;
+    const size_t qper = qbytes / B, rper = rbytes / B;  // bytes per query
+    cudaEvent_t ready = take_event(), arrived[kMaxFeedChunks] = {}, answered[kMaxFeedChunks] = {};
+    if (!ready) return PIR_ERR_CUDA;
+    pir_status_t st = PIR_OK;
+    auto ck = [&](cudaError_t e) {
+      if (e != cudaSuccess && st == PIR_OK) st = cuda_status(e);
+      return st == PIR_OK;
+    };
+    ck(cudaEventRecord(ready, s));  // the staging buffers are allocated in s's order
+    ck(cudaStreamWaitEvent(up, ready, 0));
+    uint32_t k = 0;
+    for (uint32_t b0 = 0; b0 < B && st == PIR_OK; b0 += Bs, ++k) {
+      const uint32_t nb = B - b0 < Bs ? B - b0 : Bs;
+      if (!(arrived[k] = take_event()) || !(answered[k] = take_event())) {
+        st = PIR_ERR_CUDA;
+        break;
+      }
+      if (!ck(cudaMemcpyAsync(static_cast<char *>(dq.ptr) + b0 * qper, reinterpret_cast<const char *>(queries) + b0 * qper,
+                              nb * qper, cudaMemcpyHostToDevice, up)) ||
+          !ck(cudaEventRecord(arrived[k], up)) || !ck(cudaStreamWaitEvent(s, arrived[k], 0)))
+        break;
+      st = answer_device(db, reinterpret_cast<const uint32_t *>(static_cast<char *>(dq.ptr) + b0 * qper), nb,
+                         reinterpret_cast<uint32_t *>(static_cast<char *>(dr.ptr) + b0 * rper), s, o);
+      if (st != PIR_OK || !ck(cudaEventRecord(answered[k], s)) || !ck(cudaStreamWaitEvent(down, answered[k], 0)) ||
+          !ck(cudaMemcpyAsync(reinterpret_cast<char *>(responses) + b0 * rper, static_cast<char *>(dr.ptr) + b0 * rper,
+                              nb * rper, cudaMemcpyDeviceToHost, down)))
+        break;
+    }
+    // the staging buffers are freed in s's order: after the last download
+    cudaEvent_t fin = take_event();
+    if (fin && cudaEventRecord(fin, down) == cudaSuccess) cudaStreamWaitEvent(s, fin, 0);
+    cudaStreamSynchronize(up);
+    cudaStreamSynchronize(down);
+    cudaStreamSynchronize(s);
+    t_free_events.push_back(ready);
+    if (fin) t_free_events.push_back(fin);
+    for (uint32_t i = 0; i < k + 1 && i < kMaxFeedChunks; ++i) {
+      if (arrived[i]) t_free_events.push_back(arrived[i]);
+      if (answered[i]) t_free_events.push_back(answered[i]);
+    }
+    return st;
+  }
   // A large upload goes in K-chunk pieces on a copy stream; each chunk's forward NTT
   // waits only for its own piece, so later pieces arrive while earlier chunks are
   // being scanned.  Only when the caller leaves the chunking to the library.

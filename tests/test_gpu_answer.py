@@ -225,3 +225,21 @@ def test_host_buffers_pipelined_upload_and_odd_chunks(orc, D1, B, k_chunk):
         assert np.array_equal(run(db, P, Q, B, k_chunk=k_chunk), ref)
     finally:
         g.pir_free_db(db)
+
+
+@pytest.mark.parametrize("layout,B,flags", [(0, 17, 0), (0, 24, 4), (2, 32, 0), (2, 20, 4)])
+def test_host_buffers_sub_batch_pipeline(orc, layout, B, flags):
+    """Host batches of 16 and more queries (8 MiB and more) run as sub-batches of at
+    least 8 queries (ragged at B = 17, 20): uploads, answers and downloads overlap
+    on three streams; equal to the oracle, with and without modulus switching."""
+    p, P, raw, db = instance(orc, 2048, 16, 64, 32, seed=B + layout, layout=layout)
+    try:
+        Q = random_queries(P, B, 300 + B)
+        ref = orc.answer(P, raw, Q)
+        if flags & g.PIR_ANSWER_MODSWITCH:
+            ref = orc.modswitch(P, ref)
+        host = np.zeros(ref.shape, dtype=np.uint32)
+        g.pir_answer_ex(db, Q, B, host, flags=flags)
+        assert np.array_equal(host, ref)
+    finally:
+        g.pir_free_db(db)

@@ -58,7 +58,8 @@ constexpr int kMaxStages = 4;
 // kTmemBudget columns each (the MMAs of one unit overlap the epilogue of the one
 // before).  Every CTA takes more than half of an SM's shared memory, so a second
 // never lands on the same SM (its tensor-memory allocation would wait for the first).
-constexpr uint32_t kTmemBudget = 256;
+constexpr uint32_t kTmemCols = 512;                   // the whole tensor memory of the SM
+constexpr uint32_t kTmemBudget = kTmemCols / 2;        // one of two accumulator buffers
 constexpr uint32_t kSmemBudget = 200u << 10, kSmemFloor = 116u << 10;
 constexpr uint32_t kBlockBytes = 128 * 16 * 2;  // one 128-row x K16 bf16 block
 
@@ -130,6 +131,7 @@ struct TcArgs {
   uint32_t *err;       // per-device error word
   uint32_t M, Mp, D1, D2, i0, Kc;
   uint32_t T, KS16, S, stage_bytes, ctiles, mtiles, nunits;
+  uint32_t nbuf, buf_cols;  // accumulator buffers in tensor memory and their column stride
   uint32_t logn;
   int acc_in;
 };
@@ -189,7 +191,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcArgs a, ModConst mc) 
   }
   if (warp == kMmaWarp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tslot)),
-                 "r"(2 * kTmemBudget)
+                 "r"(kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -245,13 +247,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcArgs a, ModConst mc) 
       bool ok = true;
       for (uint32_t u = blockIdx.x; ok && u < a.nunits; u += gridDim.x, ++k) {
         const Unit w = unit_of(a, u);
-        const uint32_t buf = k & 1;
-        if (!wait_bounded(tempty0 + 8 * buf, ((k >> 1) & 1) ^ 1)) {  // the epilogue has drained this buffer
+        const uint32_t buf = k % a.nbuf, use = k / a.nbuf;
+        if (!wait_bounded(tempty0 + 8 * buf, (use & 1) ^ 1)) {  // the epilogue has drained this buffer
           atomicExch(a.err, 1u);
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t idesc = instr_desc(128, w.Nt), dcol = tmem + buf * kTmemBudget;
+        const uint32_t idesc = instr_desc(128, w.Nt), dcol = tmem + buf * a.buf_cols;
         for (uint32_t st = 0; st < nst; ++st, ++it) {
           const uint32_t slot = it % a.S;
           if (!wait_bounded(full0 + 8 * slot, (it / a.S) & 1)) {
@@ -285,8 +287,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcArgs a, ModConst mc) 
     uint32_t k = 0;
     for (uint32_t u = blockIdx.x; u < a.nunits; u += gridDim.x, ++k) {
       const Unit w = unit_of(a, u);
-      const uint32_t buf = k & 1;
-      if (!__all_sync(0xffffffffu, wait_bounded(tfull0 + 8 * buf, (k >> 1) & 1))) {
+      const uint32_t buf = k % a.nbuf, use = k / a.nbuf;
+      if (!__all_sync(0xffffffffu, wait_bounded(tfull0 + 8 * buf, use & 1))) {
         if (lane == 0) atomicExch(a.err, 1u);
         break;
       }
@@ -310,7 +312,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcArgs a, ModConst mc) 
         const uint32_t t = item / G, g = item % G;
         const uint32_t c = (w.ct * a.T + t) * 32 + (row >> 2);
         uint32_t f[32];
-        tmem_ld32(tmem + buf * kTmemBudget + ((32 * quarter) << 16) + t * w.Nt + 32 * g, f);
+        tmem_ld32(tmem + buf * a.buf_cols + ((32 * quarter) << 16) + t * w.Nt + 32 * g, f);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           // this lane's DB digit b, weighted over the query digits a, for rows 8g + 4h + mm
@@ -353,7 +355,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcArgs a, ModConst mc) 
   __syncthreads();
   if (warp == kMmaWarp) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTmemBudget)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
                  : "memory");
   }
 }
@@ -506,10 +508,13 @@ cudaError_t launch_gemm_tc(const ParamCtx &c, const uint16_t *db, uint32_t D1, u
   a.Kc = Kc;
   const uint32_t Ntot = 4 * Mp, Nmax = Ntot < 256 ? Ntot : 256;
   a.mtiles = (Ntot + 255) / 256;
-  // 32-column tiles per CTA: as many as the accumulator budget and D2 allow
+  // 32-column tiles per unit: as many as half of the tensor memory and D2 allow, so
+  // that two accumulator buffers alternate
   uint32_t T = 1;
   while (2 * T * Nmax <= kTmemBudget && (D2 / 32) % (2 * T) == 0) T *= 2;
   a.T = T;
+  a.nbuf = 2;
+  a.buf_cols = kTmemBudget;
   a.ctiles = D2 / (32 * T);
   // K16 steps per stage: as many as leave room for three stages
   const uint32_t per16 = T * kBlockBytes + Nmax * 32;

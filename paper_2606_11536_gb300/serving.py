@@ -226,7 +226,12 @@ def latency_stats(reqs: List[Request]) -> dict:
 
 
 class CudaBackend(Backend):
-    """The real backend: the C ABI for the scan, torch for buffers, streams and events."""
+    """The real backend: the C ABI for the scan, torch for buffers, streams and events.
+
+    Every dispatch allocates its batch buffers through torch; with large databases
+    run the process with torch's stream-ordered allocator
+    (PYTORCH_CUDA_ALLOC_CONF=backend:cudaMallocAsync), whose releases do not
+    synchronise the device as the caching allocator's do under memory pressure."""
 
     def __init__(self, device: int = 0):
         import torch

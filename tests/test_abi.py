@@ -119,3 +119,25 @@ def test_bench_and_serving_use_exported_names():
         names = set(re.findall(r"\bg\.([A-Za-z_][A-Za-z0-9_]*)", src))
         missing = sorted(n for n in names if not hasattr(g, n))
         assert not missing, (rel, missing)
+
+
+def test_session_and_tensor_layout_errors_without_gpu(lib):
+    """The streamed-answer calls refuse unknown handles, and the tensor layout's shape
+    rules are checked, before any device work."""
+    q = np.zeros(16, dtype=np.uint32)
+    o = binding.pir_answer_opts_t()
+    h = C.c_void_p()
+    assert lib.pir_answer_begin(C.c_void_p(0xDEAD0), 1, 64, None, C.byref(o), C.byref(h)) == 6
+    assert lib.pir_answer_chunk(C.c_void_p(0xBEEF0), C.c_void_p(q.ctypes.data), 0, 1, 0) == 6
+    assert lib.pir_answer_chunk(None, C.c_void_p(q.ctypes.data), 0, 1, 0) == 6
+    assert lib.pir_answer_end(C.c_void_p(0xBEEF0), C.c_void_p(q.ctypes.data), 0) == 6
+    assert lib.pir_answer_abort(C.c_void_p(0xBEEF0)) == 6
+    assert lib.pir_answer_abort(None) == 6
+    assert g.pir_gemm_tiles(g.PIR_LAYOUT_TENSOR) == 1
+    # tensor layout: D1 a multiple of 64 and D2 of 32, refused as unsupported otherwise
+    for D1, D2 in ((96, 32), (64, 36)):
+        p = g.pir_make_params(2048, 12, D1, D2, 2)
+        raw = np.zeros(binding.raw_db_bytes(p), dtype=np.uint8)
+        st = lib.pir_setup_db(C.byref(p), C.c_void_p(raw.ctypes.data), raw.nbytes, 0, g.PIR_LAYOUT_TENSOR, None,
+                              C.byref(h))
+        assert st == 7, (D1, D2, st)

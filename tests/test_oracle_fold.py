@@ -93,3 +93,44 @@ def test_first_dimension_then_fold_decrypts_one_record(orc):
         bits = [(c_star >> l) & 1 for l in range(levels)]
         out = orc.fold(P, R, levels, orc.rgsw_bits(P, s, bits, ell, seed=seed), ell)
         assert np.array_equal(orc.bfv_decrypt(P, s, out), orc.unpack_poly(raw, log2p, n, i_star * D2 + c_star))
+
+
+def schoolbook_negacyclic(a, b, q):
+    """(a * b) mod (X^n + 1, q), plain double loop over Python integers."""
+    n = len(a)
+    out = [0] * n
+    for i in range(n):
+        ai = int(a[i])
+        if ai == 0:
+            continue
+        for j in range(n):
+            k = i + j
+            if k < n:
+                out[k] += ai * int(b[j])
+            else:
+                out[k - n] -= ai * int(b[j])
+    return [v % q for v in out]
+
+
+@pytest.mark.parametrize("L,ell", [(1, 3), (2, 4), (3, 5)])
+def test_noiseless_external_product_is_the_ring_product(orc, L, ell):
+    """With zero masks and zero errors, RGSW(mu) is the bare gadget (mu t^k in the
+    a-part of row k, in the b-part of row ell + k).  The external product must then
+    give exactly (mu * c_a, mu * c_b) in R_q, since the digits recombine to the lift
+    of each coefficient: an exact identity that a mis-paired row or digit, a wrong
+    base or a dropped negacyclic sign breaks."""
+    P = orc.make_params(64, 10, 1, 1, L)
+    n = P.n
+    rng = np.random.default_rng(L * 10 + ell)
+    mu = np.zeros(n, dtype=np.uint32)
+    mu[[0, 3, n - 1]] = [1, 2, 1]  # a small polynomial touching the wrap-around
+    zero_a = np.zeros((2 * ell, L, n), dtype=np.uint32)
+    zero_e = np.zeros((2 * ell, n), dtype=np.int8)
+    s = synth.ternary_secret(5, n)
+    G = orc.rgsw_encrypt(P, s, mu, ell, zero_a, zero_e)
+    ct = np.stack([np.stack([rng.integers(0, q, size=n, dtype=np.uint64).astype(np.uint32) for q in P.qs])
+                   for _ in range(2)])
+    out = orc.external_product(P, G, ell, ct)
+    for comp in range(2):
+        for j, q in enumerate(P.qs):
+            assert out[comp, j].tolist() == schoolbook_negacyclic(mu, ct[comp, j], q), (comp, j)

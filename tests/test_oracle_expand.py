@@ -159,3 +159,52 @@ def test_expanded_query_answers_tiny_config(orc):
 
 def test_expanded_query_answers_three_primes(orc):
     decrypt_expanded_answer(orc, 2048, 16, 32, 4, L=3, ell=4, seed=2)
+
+
+def tau(a, g, q):
+    """a(X) -> a(X^g) in Z_q[X]/(X^n + 1): coefficient t moves to t*g mod 2n, negated
+    past n (restated here in pure Python)."""
+    n = len(a)
+    out = [0] * n
+    for t in range(n):
+        e = (t * g) % (2 * n)
+        if e < n:
+            out[e] = (out[e] + int(a[t])) % q
+        else:
+            out[e - n] = (out[e - n] - int(a[t])) % q
+    return out
+
+
+def negacyclic(a, b, q):
+    n = len(a)
+    out = [0] * n
+    for i in range(n):
+        ai = int(a[i])
+        if ai:
+            for j in range(n):
+                k = i + j
+                if k < n:
+                    out[k] += ai * int(b[j])
+                else:
+                    out[k - n] -= ai * int(b[j])
+    return [v % q for v in out]
+
+
+@pytest.mark.parametrize("L,ell,g", [(1, 3, 65), (2, 4, 33), (3, 5, 17)])
+def test_noiseless_subs_has_the_substituted_phase(orc, L, ell, g):
+    """With zero masks and zero errors the key-switching key adds no noise, so
+    Subs(ct, g) must have exactly the phase tau_g(c_a * s + c_b): tau_g is a ring
+    homomorphism.  An exact identity, whatever the key's sign convention."""
+    P = orc.make_params(64, 10, 1, 1, L)
+    n = P.n
+    rng = np.random.default_rng(L * 100 + g)
+    s = synth.ternary_secret(7 + L, n)
+    ksk = orc.ksk_gen(P, s, g, ell, np.zeros((ell, L, n), dtype=np.uint32), np.zeros((ell, n), dtype=np.int8))
+    ct = np.stack([np.stack([rng.integers(0, q, size=n, dtype=np.uint64).astype(np.uint32) for q in P.qs])
+                   for _ in range(2)])
+    out = orc.subs(P, ct, g, ksk, ell)
+    for j, q in enumerate(P.qs):
+        s_q = [int(v) % q for v in s]
+        phase_in = [(x + y) % q for x, y in zip(negacyclic(ct[0, j], s_q, q), ct[1, j])]
+        phase_out = [(x + y) % q for x, y in zip(negacyclic(out[0, j], s_q, q), out[1, j])]
+        assert phase_out == tau(phase_in, g, q), j

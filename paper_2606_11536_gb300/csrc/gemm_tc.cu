@@ -5,7 +5,7 @@
 // is a small fraction of the bf16 one) and to modular arithmetic.
 //
 // Digits.  A residue x in [0, q), q < 2^30, is x = sum_{l<4} 256^l d_l with signed
-// digits d_0..d_2 in [-128, 127] and d_3 in [-64, 64]; such integers are exact in
+// digits d_0..d_2 in [-128, 127] and d_3 in [0, 64]; such integers are exact in
 // bf16.  For slot s the modular GEMM splits into 16 digit GEMMs
 //     P_ab[c][m] = sum_{i < Kc} DB_b[i][c] * Q_a[i][m],    |P_ab| <= Kc * 2^14,
 // so for Kc <= 1024 every partial sum is an integer of at most 2^24 in magnitude

@@ -104,7 +104,9 @@ class Server:
         """Set up and keep database `name`; raises AdmissionError if it does not fit."""
         if name in self.dbs:
             raise ValueError("database %r already resident" % name)
-        need = 4 * params.L * params.n * params.D1 * params.D2
+        # resident bytes per residue: u32 words or four u8 limbs (plain, limb), four
+        # bf16 digits (the tensor layout, 2)
+        need = (8 if layout == 2 else 4) * params.L * params.n * params.D1 * params.D2
         if self.budget is not None and self.resident_bytes + need > self.budget:
             raise AdmissionError("%s needs %d bytes, %d of the %d-byte budget are left"
                                  % (name, need, self.budget - self.resident_bytes, self.budget))

@@ -110,6 +110,28 @@ def test_admission_by_memory_budget():
     assert srv.resident_bytes == 8 << 30
 
 
+def test_layout_reaches_the_backend_and_admission_counts_its_bytes():
+    """The layout given to admit reaches the backend, and the budget check counts the
+    tensor layout's 8 bytes per residue (twice the plain layout's)."""
+    p = params(n=4096, D1=512, D2=256)  # 4 GiB resident plain, 8 GiB in the tensor layout
+    clock, be, srv = make(memory_budget=10 << 30)
+    seen = []
+    setup = be.setup_db
+
+    def recording_setup(name, params_, raw, layout):
+        seen.append(layout)
+        h, nbytes = setup(name, params_, raw, layout)
+        return h, nbytes * (2 if layout == 2 else 1)
+
+    be.setup_db = recording_setup
+    srv.admit("plain", p, None)
+    with pytest.raises(AdmissionError):  # 4 + 8 GiB exceed the 10 GiB budget
+        srv.admit("tensor", p, None, layout=2)
+    srv.admit("limb", p, None, layout=1)  # 4 + 4 GiB fit
+    assert seen == [0, 1]
+    assert srv.resident_bytes == 8 << 30
+
+
 def test_scratch_budget_limits_batches_in_flight():
     p = params(n=2048, D1=16, D2=16)
     per_query = 8 * 2 * 2048 * 32

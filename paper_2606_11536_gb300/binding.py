@@ -173,20 +173,41 @@ def pir_setup_db(params: pir_params_t, raw_db, layout: int = PIR_LAYOUT_PLAIN, s
     return Db(h.value, params, layout)
 
 
+def _answer_sizes(db: Db, B: int, flags: int = 0):
+    """Bytes of B queries [B][D1][2][L][n] and of their responses [B][D2][2][L][n]
+    ([B][D2][2][n] with PIR_ANSWER_MODSWITCH)."""
+    p = db.params
+    resp_l = 1 if flags & PIR_ANSWER_MODSWITCH else p.L
+    return B * p.D1 * 2 * p.L * p.n * 4, B * p.D2 * 2 * resp_l * p.n * 4
+
+
+def _require(what: str, have: int, need: int):
+    """Refuse a buffer smaller than the call reads or writes, before the library
+    touches it (on the device that would be an out-of-bounds access)."""
+    if have < need:
+        raise ValueError("%s buffer holds %d bytes, the call needs %d" % (what, have, need))
+
+
 def pir_answer(db: Db, queries, B: int, responses, stream=None):
-    qp, qdev, _ = _ptr(queries)
-    rp, rdev, _ = _ptr(responses)
+    qp, qdev, qn = _ptr(queries)
+    rp, rdev, rn = _ptr(responses)
     if qdev != rdev:
         raise ValueError("queries and responses must both be host or both be device buffers")
+    need_q, need_r = _answer_sizes(db, B)
+    _require("query", qn, need_q)
+    _require("response", rn, need_r)
     _check(lib().pir_answer(C.c_void_p(db.handle), qp, B, rp, int(qdev), _stream_ptr(stream)), "pir_answer")
     return responses
 
 
 def pir_answer_ex(db: Db, queries, B: int, responses, stream=None, k_chunk: int = 0, tile: int = 0, flags: int = 0):
-    qp, qdev, _ = _ptr(queries)
-    rp, rdev, _ = _ptr(responses)
+    qp, qdev, qn = _ptr(queries)
+    rp, rdev, rn = _ptr(responses)
     if qdev != rdev:
         raise ValueError("queries and responses must both be host or both be device buffers")
+    need_q, need_r = _answer_sizes(db, B, flags)
+    _require("query", qn, need_q)
+    _require("response", rn, need_r)
     o = pir_answer_opts_t(k_chunk, tile, flags)
     _check(lib().pir_answer_ex(C.c_void_p(db.handle), qp, B, rp, int(qdev), _stream_ptr(stream), C.byref(o)),
            "pir_answer_ex")
@@ -398,11 +419,12 @@ def pir_graph_create(db: Db, queries, B: int, responses, k_chunk: int = 0, tile:
 class Session:
     """A streamed answer (pir_session_t): pieces of the queries along D1."""
 
-    def __init__(self, handle, db, B, kc_max):
+    def __init__(self, handle, db, B, kc_max, flags=0):
         self.handle = handle
         self.db = db
         self.B = B
         self.kc_max = kc_max
+        self.flags = flags
         self._keep = []  # device pieces are read in stream order: keep them alive
 
 
@@ -411,19 +433,22 @@ def pir_answer_begin(db: Db, B: int, kc_max: int, stream=None, tile: int = 0, fl
     h = C.c_void_p()
     _check(lib().pir_answer_begin(C.c_void_p(db.handle), B, kc_max, _stream_ptr(stream), C.byref(o), C.byref(h)),
            "pir_answer_begin")
-    return Session(h.value, db, B, kc_max)
+    return Session(h.value, db, B, kc_max, flags)
 
 
 def pir_answer_chunk(session: Session, queries, i0: int, kc: int):
     """Ciphertexts i0 .. i0+kc-1 of every query, [B][kc][2][L][n] (host or device)."""
-    qp, qdev, _ = _ptr(queries)
+    qp, qdev, qn = _ptr(queries)
+    p = session.db.params
+    _require("query", qn, session.B * kc * 2 * p.L * p.n * 4)
     _check(lib().pir_answer_chunk(C.c_void_p(session.handle), qp, i0, kc, int(qdev)), "pir_answer_chunk")
     if qdev:
         session._keep.append(queries)
 
 
 def pir_answer_end(session: Session, responses):
-    rp, rdev, _ = _ptr(responses)
+    rp, rdev, rn = _ptr(responses)
+    _require("response", rn, _answer_sizes(session.db, session.B, session.flags)[1])
     h, session.handle = session.handle, None
     try:
         _check(lib().pir_answer_end(C.c_void_p(h), rp, int(rdev)), "pir_answer_end")

@@ -141,3 +141,32 @@ def test_session_and_tensor_layout_errors_without_gpu(lib):
         st = lib.pir_setup_db(C.byref(p), C.c_void_p(raw.ctypes.data), raw.nbytes, 0, g.PIR_LAYOUT_TENSOR, None,
                               C.byref(h))
         assert st == 7, (D1, D2, st)
+
+
+def test_answer_buffers_too_small_are_refused_before_the_library(lib):
+    """The binding refuses query and response buffers smaller than the call reads
+    or writes, before the library sees them; right-sized buffers reach the library
+    (which then refuses the fake handle)."""
+    p = g.pir_make_params(2048, 12, 4, 4, 2)
+    fake = g.Db(0xDEAD0, p, 0)
+    words = 4 * 2 * 2 * 2048  # one query [D1][2][L][n], one response [D2][2][L][n] (D1 = D2 = 4)
+    q, r = np.zeros(words, np.uint32), np.zeros(words, np.uint32)
+    for args in ((q[:-1], 1, r), (q, 1, r[:-1]), (q, 2, r)):
+        with pytest.raises(ValueError):
+            g.pir_answer(fake, *args)
+    with pytest.raises(g.PirError) as ei:  # an explicit null stream: no CUDA needed here
+        g.pir_answer(fake, q, 1, r, stream=0)
+    assert ei.value.status == 6
+    # modulus switching halves the response at L = 2
+    with pytest.raises(g.PirError) as ei:
+        g.pir_answer_ex(fake, q, 1, r[:words // 2], stream=0, flags=g.PIR_ANSWER_MODSWITCH)
+    assert ei.value.status == 6
+    with pytest.raises(ValueError):
+        g.pir_answer_ex(fake, q, 1, r[:words // 2])
+    # streamed pieces: 2 queries x 3 ciphertexts need more than q holds; the end call
+    ses = g.Session(0xBEEF0, fake, 2, 4)
+    with pytest.raises(ValueError):
+        g.pir_answer_chunk(ses, q, 0, 3)
+    with pytest.raises(ValueError):
+        g.pir_answer_end(ses, r)
+    assert ses.handle == 0xBEEF0  # a refused end leaves the session to the caller

@@ -101,7 +101,10 @@ def test_streamed_answer_arguments(orc):
         assert status_of(g.pir_answer_chunk, ses, Q[:, 0:9].copy(), 0, 9) == 1      # above kc_max
         assert status_of(g.pir_answer_chunk, ses, Q[:, 0:0].copy(), 0, 0) == 1      # empty piece
         g.pir_answer_chunk(ses, Q[:, 0:8].copy(), 0, 8)
-        assert status_of(g.pir_answer_chunk, ses, Q[:, 8:16].copy(), 8, 9) == 1     # past D1
+        with pytest.raises(ValueError):  # the binding: 8 ciphertexts given, 9 declared
+            g.pir_answer_chunk(ses, Q[:, 8:16].copy(), 8, 9)
+        past = np.zeros((B, 9, 2, P.L, P.n), dtype=np.uint32)
+        assert status_of(g.pir_answer_chunk, ses, past, 8, 9) == 1                  # past D1
         rd = empty_u32(P.D2 * 2 * P.L * P.n)
         assert status_of(g.pir_answer_end, ses, rd) == 1                             # half of D1: released
         assert status_of(g.pir_answer_chunk, ses, Q[:, 8:16].copy(), 8, 8) == 6

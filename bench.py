@@ -191,7 +191,7 @@ class OracleRunner:
         self.dbhat = O.encode_polys(self.P, raw, ids, nthreads).reshape(ncols, D1, L_PRIMES, n)
 
     def step(self, seed):
-        from paper_2606_11536_gb300 import synth
+        import synth
         Q = synth.uniform_residues(seed, synth.STREAM_UNIFORM, self.B * self.D1 * 2, self.n, self.P.qs)
         Q = Q.reshape(self.B, self.D1, 2, L_PRIMES, self.n)
         t0 = time.perf_counter()
@@ -215,7 +215,7 @@ def reference_arm(args, wl):
     world, rank, _ = dist_env()
     if world > 1 and rank != 0:
         return
-    from paper_2606_11536_gb300 import synth
+    import synth
     raw_bytes = synth.raw_db_bytes(n, log2p, D1, D2)
     raw = synth.raw_db(0, raw_bytes)
     nthreads = os.cpu_count() or 1
@@ -246,7 +246,8 @@ def reference_arm(args, wl):
 def our_arm(args, wl):
     import torch
     import paper_2606_11536_gb300 as g
-    from paper_2606_11536_gb300 import binding, synth
+    from paper_2606_11536_gb300 import binding
+    import synth
 
     world, rank, local = dist_env()
     if world > 1:
@@ -505,7 +506,7 @@ def ntt_sweep(args):
     polynomials (L = 2, n = 4096, 2 GiB) per step."""
     import torch
     import paper_2606_11536_gb300 as g
-    from paper_2606_11536_gb300 import synth
+    import synth
     torch.cuda.set_device(0)
     n, count = 4096, 1 << 16
     p = g.pir_make_params(n, 16, 1, 1, L_PRIMES)
@@ -553,7 +554,7 @@ def lwe_bench(args):
     the raw INT8 DB (Sec. 2.5, 4.1), B queries per step."""
     import torch
     import paper_2606_11536_gb300 as g
-    from paper_2606_11536_gb300 import synth
+    import synth
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     D1, D0, desc = LWE_WORKLOADS[args.lwe_workload]
@@ -662,7 +663,8 @@ def serving_bench(args):
     arrivals at several loads with uniformly random target DB, continuous batching."""
     import torch
     import paper_2606_11536_gb300 as g
-    from paper_2606_11536_gb300 import serving, synth
+    from paper_2606_11536_gb300 import serving
+    import synth
     torch.cuda.set_device(0)
     serving_layout = {"plain": g.PIR_LAYOUT_PLAIN, "tensor": g.PIR_LAYOUT_TENSOR}[args.serving_layout]
     be = serving.CudaBackend()

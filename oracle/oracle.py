@@ -88,6 +88,9 @@ def lib():
             "orc_ksk_gen": (None, [PP, I8P, C.c_uint32, C.c_uint32, U32P, I8P, U32P]),
             "orc_subs": (None, [PP, U32P, C.c_uint32, U32P, C.c_uint32, U32P]),
             "orc_expand": (None, [PP, U32P, C.c_uint32, C.c_uint32, U32P, C.c_uint32, U32P]),
+            "orc_subs_textbook": (None, [PP, U32P, C.c_uint32, C.c_uint32, U32P, C.c_uint32, U32P]),
+            "orc_subs_moved": (None, [PP, U32P, C.c_uint32, C.c_uint32, U32P, C.c_uint32, U32P]),
+            "orc_expand_textbook": (None, [PP, U32P, C.c_uint32, C.c_uint32, U32P, C.c_uint32, U32P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -318,7 +321,7 @@ def rgsw_encrypt(P: OrcParams, s, mu, ell: int, a, e) -> np.ndarray:
 def rgsw_bits(P: OrcParams, s, bits, ell: int, seed: int) -> np.ndarray:
     """RGSW encryptions of the constant polynomials bits[l] (one per folding level),
     [levels][2 ell][2][L][n], from seeded draws (masks STREAM_KEY_A, errors STREAM_KEY_ERROR)."""
-    from paper_2606_11536_gb300 import synth
+    import synth
     out = np.empty((len(bits), 2 * ell, 2, P.L, P.n), dtype=np.uint32)
     for l, bit in enumerate(bits):
         mu = np.zeros(P.n, dtype=np.uint32)
@@ -388,7 +391,7 @@ def ksk_gen(P: OrcParams, s, g: int, ell: int, a, e) -> np.ndarray:
 def expansion_keys(P: OrcParams, s, levels: int, ell: int, seed: int) -> np.ndarray:
     """All expansion keys [levels][ell][2][L][n] from seeded client draws (masks from
     STREAM_KEY_A, errors from STREAM_KEY_ERROR)."""
-    from paper_2606_11536_gb300 import synth
+    import synth
     keys = np.empty((levels, ell, 2, P.L, P.n), dtype=np.uint32)
     for j, g in enumerate(expansion_galois(P.n, levels)):
         a = synth.uniform_residues(seed, synth.STREAM_KEY_A, ell, P.n, P.qs, start=j * ell)
@@ -400,6 +403,23 @@ def expansion_keys(P: OrcParams, s, levels: int, ell: int, seed: int) -> np.ndar
 def subs(P: OrcParams, ct, g: int, ksk, ell: int) -> np.ndarray:
     out = np.empty((2, P.L, P.n), dtype=np.uint32)
     lib().orc_subs(C.byref(P), _u32(ct).reshape(-1), g, _u32(ksk).reshape(-1), ell, out.reshape(-1))
+    return out
+
+
+def subs_shift(P: OrcParams, ct, shift: int, g: int, ksk, ell: int, textbook: bool) -> np.ndarray:
+    """Subs(ct X^-shift, g).  textbook: gadget digits of the substituted a-part;
+    otherwise the digits of ct's a-part moved along (the order expand uses)."""
+    out = np.empty((2, P.L, P.n), dtype=np.uint32)
+    f = lib().orc_subs_textbook if textbook else lib().orc_subs_moved
+    f(C.byref(P), _u32(ct).reshape(-1), shift, g, _u32(ksk).reshape(-1), ell, out.reshape(-1))
+    return out
+
+
+def expand_textbook(P: OrcParams, ct, levels: int, ell: int, keys, count: int) -> np.ndarray:
+    """expand() with every key switch in the textbook digit order."""
+    out = np.empty((count, 2, P.L, P.n), dtype=np.uint32)
+    lib().orc_expand_textbook(C.byref(P), _u32(ct).reshape(-1), levels, ell, _u32(keys).reshape(-1), count,
+                              out.reshape(-1))
     return out
 
 

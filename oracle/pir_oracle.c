@@ -39,7 +39,9 @@
  *     order (c + Subs(c) at k, c X^-2^j + Subs(.) at k + 2^j); the gadget digits are
  *     those of the CRT lift in [0, q) of each coefficient of the level's input
  *     a-part, moved (with their signs) by the same shift and substitution as the
- *     ciphertext, so a moved digit lies in (-t, t).
+ *     ciphertext, so a moved digit lies in (-t, t).  The textbook order (digits of
+ *     the substituted a-part, in [0, t)) is kept beside it (orc_subs_textbook,
+ *     orc_expand_textbook); with error-free keys the two give the same phase.
  *
  * Parity: pinned.  The tests check this file against primality by an independent
  * library, the defining congruences, the NTT evaluated by its definition, schoolbook
@@ -925,12 +927,53 @@ static void subs_shifted(const orc_params *P, const u32 *ct, u32 shift, u32 g, c
   free(tmp);
 }
 
+/* Subs of (a X^-shift, b X^-shift) by g in the textbook order: the ciphertext is
+ * shifted and substituted first, and the gadget digits are those of the CRT lift in
+ * [0, q) of the substituted a-part tau_g(a X^-shift), so every digit lies in [0, t).
+ * Then the same key-switching sums.  Kept beside subs_shifted as the second reading
+ * of App. D.3's key switch; both equal tau_g(a X^-shift) as sum_k t^k e_k, so with
+ * error-free keys both give the same phase.  ct, out [2][L][n]. */
+static void subs_textbook(const orc_params *P, const u32 *ct, u32 shift, u32 g, const u32 *ksk, u32 ell, u32 *out) {
+  const u32 n = P->n, L = P->L;
+  u32 *sub = (u32 *)calloc((size_t)2 * L * n, sizeof(u32));
+  u32 *d = (u32 *)calloc((size_t)ell * n, sizeof(u32));
+  u32 *e = (u32 *)calloc((size_t)ell * L * n, sizeof(u32));
+  u32 *tmp = (u32 *)calloc(n, sizeof(u32));
+  for (u32 c = 0; c < 2; c++)
+    for (u32 j = 0; j < L; j++) {
+      monomial_div(ct + ((u64)c * L + j) * n, tmp, n, P->q[j], shift);
+      orc_automorphism(tmp, sub + ((u64)c * L + j) * n, n, P->q[j], g);
+    }
+  gadget_digits(P, sub, ell, d);
+  for (u32 k = 0; k < ell; k++)
+    for (u32 j = 0; j < L; j++)
+      for (u32 t = 0; t < n; t++) e[((u64)k * L + j) * n + t] = (u32)(d[(u64)k * n + t] % P->q[j]);
+  key_switch_sum(P, e, sub + (u64)L * n, ksk, ell, out);
+  free(sub);
+  free(d);
+  free(e);
+  free(tmp);
+}
+
 /* Subs(ct, g): the substitution X -> X^g (the result decrypts under tau_g(s)) with
  * key switching back to s by that substitution's key; the gadget digits are those
  * of ct's a-part, substituted along with it.  ct, out [2][L][n]. */
 void orc_subs(const orc_params *P, const u32 *ct, u32 g, const u32 *ksk, u32 ell, u32 *out) {
   subs_shifted(P, ct, 0, g, ksk, ell, out);
 }
+
+/* Subs(ct X^-shift, g) in the textbook order (digits of the substituted a-part). */
+void orc_subs_textbook(const orc_params *P, const u32 *ct, u32 shift, u32 g, const u32 *ksk, u32 ell, u32 *out) {
+  subs_textbook(P, ct, shift, g, ksk, ell, out);
+}
+
+/* Subs(ct X^-shift, g) with the digits of ct's a-part moved along (the order
+ * orc_expand uses). */
+void orc_subs_moved(const orc_params *P, const u32 *ct, u32 shift, u32 g, const u32 *ksk, u32 ell, u32 *out) {
+  subs_shifted(P, ct, shift, g, ksk, ell, out);
+}
+
+typedef void (*subs_fn)(const orc_params *, const u32 *, u32, u32, const u32 *, u32, u32 *);
 
 /* Query expansion, SealPIR's recursion as App. C.2 applies it.  ct [2][L][n]
  * encrypts sum_i m_i X^i (i < 2^levels <= n).  It is first multiplied by
@@ -940,7 +983,8 @@ void orc_subs(const orc_params *P, const u32 *ct, u32 g, const u32 *ksk, u32 ell
  * so that ciphertext i finally encrypts m_i as a constant polynomial.  ksk
  * [levels][ell][2][L][n] holds level j's key (g = n/2^j + 1) at index j.  out
  * [count][2][L][n] receives ciphertexts 0 .. count-1 (count <= 2^levels). */
-void orc_expand(const orc_params *P, const u32 *ct, u32 levels, u32 ell, const u32 *ksk, u32 count, u32 *out) {
+static void expand_with(const orc_params *P, const u32 *ct, u32 levels, u32 ell, const u32 *ksk, u32 count, u32 *out,
+                        subs_fn subs_c) {
   const u32 n = P->n, L = P->L;
   const u64 csz = (u64)2 * L * n;
   const u64 total = 1ull << levels;
@@ -969,8 +1013,9 @@ void orc_expand(const orc_params *P, const u32 *ct, u32 levels, u32 ell, const u
       for (u32 br = 0; br < 2; br++) {
         const u32 *src = br ? c1 : c0;
         u32 *dst = nxt + (k + br * C) * csz;
-        /* Subs(c X^-C) with the digits of c's a-part shifted along (see subs_shifted) */
-        subs_shifted(P, c0, br ? (u32)C : 0, g, key, ell, sb);
+        /* Subs(c X^-C): subs_shifted moves the digits of c's a-part along,
+         * subs_textbook takes the digits of the substituted a-part */
+        subs_c(P, c0, br ? (u32)C : 0, g, key, ell, sb);
         for (u32 c = 0; c < 2; c++)
           for (u32 j = 0; j < L; j++) {
             const u64 q = P->q[j], o = ((u64)c * L + j) * n;
@@ -987,6 +1032,16 @@ void orc_expand(const orc_params *P, const u32 *ct, u32 levels, u32 ell, const u
   free(nxt);
   free(c1);
   free(sb);
+}
+
+void orc_expand(const orc_params *P, const u32 *ct, u32 levels, u32 ell, const u32 *ksk, u32 count, u32 *out) {
+  expand_with(P, ct, levels, ell, ksk, count, out, subs_shifted);
+}
+
+/* The same recursion with every key switch in the textbook order. */
+void orc_expand_textbook(const orc_params *P, const u32 *ct, u32 levels, u32 ell, const u32 *ksk, u32 count,
+                         u32 *out) {
+  expand_with(P, ct, levels, ell, ksk, count, out, subs_textbook);
 }
 
 /* ------------------------------------------------------------------------- */

@@ -2,7 +2,9 @@
 client's random draws (secret, uniform ``a``, Gaussian error).
 
 This module holds none of the method's arithmetic.  It only draws numbers; the
-oracle and the CUDA library both take what it returns as inputs.
+oracle and the CUDA library both take what it returns as inputs.  It sits outside
+both (a top-level module of its own): the oracle, the tests and the benchmark
+import it, and it imports neither the oracle nor the library package.
 
 Generator: SplitMix64 (Steele, Lea & Flood, "Fast splittable pseudorandom number
 generators", OOPSLA 2014), used counter-style.  Value ``idx`` of stream

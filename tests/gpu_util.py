@@ -1,7 +1,7 @@
 """Helpers shared by the GPU tests: device copies and seeded PIR instances."""
 import numpy as np
 
-from paper_2606_11536_gb300 import synth
+import synth
 
 
 def to_dev(a):

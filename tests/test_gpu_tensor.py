@@ -11,7 +11,7 @@ import pytest
 
 import paper_2606_11536_gb300 as g
 from gpu_util import empty_u32, from_dev, random_queries, to_dev
-from paper_2606_11536_gb300 import synth
+import synth
 
 pytestmark = pytest.mark.gpu
 TENSOR = 2

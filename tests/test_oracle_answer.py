@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from golden.read import paper_values
-from paper_2606_11536_gb300 import synth
+import synth
 
 
 def py_negacyclic(a, b, q):

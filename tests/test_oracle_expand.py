@@ -17,7 +17,7 @@ with the 2^-levels pre-scaling; gadget of App. D.3).
 import numpy as np
 import pytest
 
-from paper_2606_11536_gb300 import synth
+import synth
 
 ERR_BOUND = 19  # |e| <= 19 for the clipped Gaussian (App. A.1)
 
@@ -208,3 +208,131 @@ def test_noiseless_subs_has_the_substituted_phase(orc, L, ell, g):
         phase_in = [(x + y) % q for x, y in zip(negacyclic(ct[0, j], s_q, q), ct[1, j])]
         phase_out = [(x + y) % q for x, y in zip(negacyclic(out[0, j], s_q, q), out[1, j])]
         assert phase_out == tau(phase_in, g, q), j
+
+
+# --- the two digit orders of the key switch (App. D.3) ----------------------
+#
+# The oracle's expansion takes the gadget digits of the level input's a-part and
+# moves them with the ciphertext (the digits lie in (-t, t)); the textbook key switch
+# decomposes the substituted a-part tau_g(a X^-C) instead (digits in [0, t)).  The
+# output ciphertexts differ, but both digit sets recombine to tau_g(a X^-C), so with
+# error-free keys both have exactly the phase tau_g((a s + b) X^-C).
+
+def crt_lift(residues, qs):
+    """x in [0, prod q) with x = r_j mod q_j, in pure Python."""
+    Q = 1
+    for q in qs:
+        Q *= q
+    x = 0
+    for r, q in zip(residues, qs):
+        Qj = Q // q
+        x += int(r) * Qj * pow(Qj, -1, q)
+    return x % Q
+
+
+def shift_div(a, C, q):
+    """a X^-C in Z_q[X]/(X^n + 1), pure Python."""
+    n = len(a)
+    out = [0] * n
+    for t in range(n):
+        if t >= C:
+            out[t - C] = int(a[t]) % q
+        else:
+            out[t + n - C] = (-int(a[t])) % q
+    return out
+
+
+def all_galois(n):
+    return [n // (1 << j) + 1 for j in range(n.bit_length() - 1)]
+
+
+@pytest.mark.parametrize("L,ell", [(1, 3), (2, 4), (3, 5)])
+def test_moved_digits_recombine_to_the_substituted_a_part(orc, L, ell):
+    """sum_k t^k tau_g(d_k X^-C) = tau_g(a X^-C) mod every q_j, for the digits d_k of
+    a's CRT lift, every expansion Galois element g and both shifts of its level;
+    the moved digits lie in (-t, t).  Pure Python over the integers."""
+    P = orc.make_params(32, 6, 1, 1, L)
+    n, qs = P.n, P.qs
+    w = orc.gadget_bits(P, ell)
+    a = synth.uniform_residues(40 + L, synth.STREAM_UNIFORM, 1, n, qs).reshape(L, n)
+    x = [crt_lift([a[j][t] for j in range(L)], qs) for t in range(n)]
+    digits = [[(xt >> (w * k)) & ((1 << w) - 1) for xt in x] for k in range(ell)]
+    for lev, g in enumerate(all_galois(n)):
+        for C in (0, 1 << lev):
+            for j, q in enumerate(qs):
+                want = tau([int(v) for v in a[j]], g, q) if C == 0 else tau(shift_div(a[j], C, q), g, q)
+                acc = [0] * n
+                for k in range(ell):
+                    # move the integer digit with its sign: X^-C then tau_g, kept signed
+                    moved = [0] * n
+                    for t in range(n):
+                        v, e0 = digits[k][t], t - C
+                        if e0 < 0:
+                            v, e0 = -v, e0 + n
+                        e1 = e0 * g % (2 * n)
+                        if e1 >= n:
+                            v, e1 = -v, e1 - n
+                        moved[e1] = v
+                    assert all(-(1 << w) < v < (1 << w) for v in moved)
+                    acc = [u + (v << (w * k)) for u, v in zip(acc, moved)]
+                assert [u % q for u in acc] == want, (g, C, j)
+
+
+def phase(orc_, ct, s, q, j):
+    s_q = [int(v) % q for v in s]
+    return [(x + y) % q for x, y in zip(negacyclic(ct[0, j], s_q, q), ct[1, j])]
+
+
+@pytest.mark.parametrize("L,ell", [(1, 3), (2, 4), (3, 5)])
+def test_both_digit_orders_have_the_substituted_phase(orc, L, ell):
+    """With error-free keys (uniform masks, zero errors) the key switch adds no noise:
+    Subs(ct X^-C, g) in either digit order has exactly the phase tau_g(phi X^-C),
+    phi = c_a s + c_b, for every expansion Galois element and both shifts of its
+    level.  The two ciphertexts themselves differ (their a-parts are different key
+    combinations), so the choice of order fixes the output bits."""
+    P = orc.make_params(32, 6, 1, 1, L)
+    n = P.n
+    s = synth.ternary_secret(50 + L, n)
+    rng = np.random.default_rng(60 + L)
+    ct = np.stack([np.stack([rng.integers(0, q, size=n, dtype=np.uint64).astype(np.uint32) for q in P.qs])
+                   for _ in range(2)])
+    differ = 0
+    for lev, g in enumerate(all_galois(n)):
+        ka = synth.uniform_residues(g, synth.STREAM_KEY_A, ell, n, P.qs)
+        ksk = orc.ksk_gen(P, s, g, ell, ka, np.zeros((ell, n), dtype=np.int8))
+        for C in (0, 1 << lev):
+            moved = orc.subs_shift(P, ct, C, g, ksk, ell, textbook=False)
+            text = orc.subs_shift(P, ct, C, g, ksk, ell, textbook=True)
+            differ += int(not np.array_equal(moved, text))
+            for j, q in enumerate(P.qs):
+                want = tau(shift_div(phase(orc, ct, s, q, j), C, q), g, q)
+                assert phase(orc, moved, s, q, j) == want, (g, C, j)
+                assert phase(orc, text, s, q, j) == want, (g, C, j)
+    assert differ > 0
+
+
+@pytest.mark.parametrize("L,levels,ell", [(1, 3, 3), (2, 4, 4), (3, 3, 5)])
+def test_expansion_digit_orders_agree_on_every_phase(orc, L, levels, ell):
+    """Whole expansions in both orders with error-free keys: every output has the same
+    phase; with noisy keys both decrypt to the same coefficients within the bound."""
+    P = orc.make_params(64, 8, 1, 1, L)
+    n, p, C = P.n, 1 << P.log2p, 1 << levels
+    s, a, e = client(P, 70 + L, 1)
+    m = np.random.default_rng(L).integers(0, p, size=n).astype(np.uint32)
+    ct = orc.bfv_encrypt(P, s, a[0], e[0], m)
+    ka = np.stack([synth.uniform_residues(80 + lev, synth.STREAM_KEY_A, ell, n, P.qs) for lev in range(levels)])
+    clean = np.stack([orc.ksk_gen(P, s, g, ell, ka[lev], np.zeros((ell, n), dtype=np.int8))
+                      for lev, g in enumerate(orc.expansion_galois(n, levels))])
+    out_m = orc.expand(P, ct, levels, ell, clean, C)
+    out_t = orc.expand_textbook(P, ct, levels, ell, clean, C)
+    for k in range(C):
+        for j, q in enumerate(P.qs):
+            assert phase(orc, out_m[k], s, q, j) == phase(orc, out_t[k], s, q, j), (k, j)
+    keys = orc.expansion_keys(P, s, levels, ell, seed=90 + L)
+    w = orc.gadget_bits(P, ell)
+    out_t = orc.expand_textbook(P, ct, levels, ell, keys, C)
+    for k in range(C):
+        want = np.zeros(n, dtype=np.uint32)
+        want[0::C] = m[k::C]
+        assert np.array_equal(orc.bfv_decrypt(P, s, out_t[k]), want), k
+        assert np.abs(orc.bfv_noise(P, s, out_t[k], want)).max() <= expansion_noise_bound(P, levels, ell, w)

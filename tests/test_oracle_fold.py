@@ -12,7 +12,7 @@ dimensions (Sec. 3.2, Sec. 3.6; gadget of App. D.3):
 import numpy as np
 import pytest
 
-from paper_2606_11536_gb300 import synth
+import synth
 
 ERR_BOUND = 19
 

@@ -7,7 +7,7 @@ client's decryption returns column i* of the DB."""
 import numpy as np
 import pytest
 
-from paper_2606_11536_gb300 import synth
+import synth
 
 MOD = 1 << 32
 

@@ -7,7 +7,7 @@ decryption after switching, for fresh encryptions and for a whole PIR answer."""
 import numpy as np
 import pytest
 
-from paper_2606_11536_gb300 import synth
+import synth
 
 
 def residues(P, xs):

@@ -3,7 +3,7 @@ numpy ones bit for bit, and the draws have the stated distributions."""
 import numpy as np
 import pytest
 
-from paper_2606_11536_gb300 import synth
+import synth
 
 
 def test_splitmix64_reference_values():

@@ -41,10 +41,12 @@ WORKLOADS = {
     "db512m_n2048": (2048, 16, 512, 256, 1, "512 MiB raw DB (2 GiB NTT-form), n=2048, p=2^16, D1=512, D2=256"),
     "db1g_n2048": (2048, 16, 512, 512, 1, "1 GiB raw DB (4 GiB NTT-form), n=2048, p=2^16, D1=512, D2=512"),
     "db8g_n4096": (4096, 16, 2048, 512, 1, "8 GiB raw DB (32 GiB NTT-form), n=4096, p=2^16, D1=2048, D2=512"),
-    "db16g_n4096": (4096, 16, 4096, 512, 1, "16 GiB raw DB (64 GiB NTT-form), n=4096, p=2^16, D1=4096, D2=512"),
+    "db16g_n4096": (4096, 16, 4096, 512, 32, "16 GiB raw DB (64 GiB NTT-form), n=4096, p=2^16, D1=4096, D2=512"),
     "db32g_n8192": (8192, 16, 8192, 256, 64, "32 GiB raw DB (128 GiB NTT-form), n=8192, p=2^16, D1=8192, D2=256"),
 }
-DEFAULT_WORKLOAD = "db1g_n4096"
+DEFAULT_WORKLOAD = "db16g_n4096"
+PER_BATCH = (1, 8, 32, 128)  # the metric's batch range
+MIN_TIMED_S = 1.0  # each extra block times at least this long
 L_PRIMES = 2
 FALLBACK_HBM_GBS = 6800.0
 
@@ -174,26 +176,41 @@ def barrier():
 # --- the CPU oracle as baseline / reference arm ------------------------------
 
 class OracleRunner:
-    """The oracle's online answer on a bounded sample: the query NTT of the whole
-    batch plus the fold and inverse NTT of `ncols` columns, whose NTT-form DB
-    polynomials are prepared once beforehand (as the server's DB is).  A step's
-    time is scaled by columns to the full answer."""
+    """The oracle's online answer on a bounded sample of one step's work: the query
+    NTT of `nq` of the batch's B queries, then the fold and inverse NTT of those
+    queries against `ncols` of the D2 columns, whose DB polynomials are NTT-encoded
+    beforehand (as the server's DB is).  measured_s is the sample's own time;
+    extrapolated_s scales the query NTT by B / nq and the fold by (B / nq)(D2 / ncols)
+    to the whole answer.  With nq = B and ncols = D2 the sample is the full answer."""
 
-    def __init__(self, n, log2p, D1, D2, B, raw, ncols, nthreads, modswitch=False):
+    def __init__(self, n, log2p, D1, D2, B, nq, ncols, nthreads, db_seed=0, raw=None, modswitch=False):
         from oracle import oracle as O
+        import synth
+        self.O, self.synth = O, synth
         self.modswitch = modswitch
-        self.O = O
         self.P = O.make_params(n, log2p, D1, D2, L_PRIMES)
         self.n, self.D1, self.D2, self.B = n, D1, D2, B
-        self.ncols, self.nthreads = ncols, nthreads
-        cols = np.arange(ncols, dtype=np.uint64)
-        ids = (np.arange(D1, dtype=np.uint64)[None, :] * np.uint64(D2) + cols[:, None]).reshape(-1)
-        self.dbhat = O.encode_polys(self.P, raw, ids, nthreads).reshape(ncols, D1, L_PRIMES, n)
+        self.nq, self.ncols, self.nthreads = min(nq, B), min(ncols, D2), nthreads
+        if raw is not None:
+            cols = np.arange(self.ncols, dtype=np.uint64)
+            ids = (np.arange(D1, dtype=np.uint64)[None, :] * np.uint64(D2) + cols[:, None]).reshape(-1)
+            self.dbhat = O.encode_polys(self.P, raw, ids, nthreads)
+        else:  # only the sample's polynomials, regenerated from the DB's counter-based stream
+            bpp = n * log2p // 8
+            compact = np.concatenate([synth.raw_db_slab(db_seed, (i * D2 + c) * bpp, bpp)
+                                      for c in range(self.ncols) for i in range(D1)])
+            Pc = O.make_params(n, log2p, self.ncols * D1, 1, L_PRIMES)
+            self.dbhat = O.encode_polys(Pc, compact, np.arange(self.ncols * D1, dtype=np.uint64), nthreads)
+        self.dbhat = self.dbhat.reshape(self.ncols, D1, L_PRIMES, n)
+
+    @property
+    def full(self):
+        return self.nq == self.B and self.ncols == self.D2
 
     def step(self, seed):
-        import synth
-        Q = synth.uniform_residues(seed, synth.STREAM_UNIFORM, self.B * self.D1 * 2, self.n, self.P.qs)
-        Q = Q.reshape(self.B, self.D1, 2, L_PRIMES, self.n)
+        synth = self.synth
+        Q = synth.uniform_residues(seed, synth.STREAM_UNIFORM, self.nq * self.D1 * 2, self.n, self.P.qs)
+        Q = Q.reshape(self.nq, self.D1, 2, L_PRIMES, self.n)
         t0 = time.perf_counter()
         qhat = self.O.ntt_fwd_rns(self.P, Q, self.nthreads)
         t1 = time.perf_counter()
@@ -201,12 +218,29 @@ class OracleRunner:
         if self.modswitch:
             self.O.modswitch(self.P, R)
         t2 = time.perf_counter()
-        return (t1 - t0) + (t2 - t1) * self.D2 / self.ncols
+        scale_q = self.B / self.nq
+        return {"measured_s": t2 - t0,
+                "extrapolated_s": (t1 - t0) * scale_q + (t2 - t1) * scale_q * self.D2 / self.ncols}
 
     def describe(self):
-        return ("oracle online answer, batch %d: query NTT of the whole batch timed, fold + inverse NTT%s timed on %d "
-                "of %d columns and scaled by columns; those DB columns NTT-encoded beforehand"
-                % (self.B, " + modulus switching" if self.modswitch else "", self.ncols, self.D2))
+        if self.full:
+            return ("oracle online answer, full: query NTT, fold of all %d columns and inverse NTT%s for all %d "
+                    "queries; the DB NTT-encoded beforehand" % (self.D2, " + modulus switching" if self.modswitch
+                                                                 else "", self.B))
+        return ("oracle online answer on a sample, extrapolated: query NTT of %d of %d queries, fold + inverse NTT%s "
+                "of those queries on %d of %d columns (those DB columns NTT-encoded beforehand); the query NTT "
+                "scaled by queries, the fold by queries x columns"
+                % (self.nq, self.B, " + modulus switching" if self.modswitch else "", self.ncols, self.D2))
+
+
+def oracle_sample_shape(wl, B, ref_cols):
+    """(queries, columns) of the oracle's bounded sample: about a second of host work
+    per step on 16 cores for the 16 GiB and 32 GiB databases, more of the batch for
+    the smaller ones."""
+    n, log2p, D1, D2, _, _ = WORKLOADS[wl]
+    per_query = D1 * n * L_PRIMES  # grows with the work per query and column
+    nq = max(1, min(B, (1 << 24) // per_query))
+    return nq, max(1, min(D2, ref_cols))
 
 
 def reference_arm(args, wl):
@@ -217,31 +251,286 @@ def reference_arm(args, wl):
         return
     import synth
     raw_bytes = synth.raw_db_bytes(n, log2p, D1, D2)
-    raw = synth.raw_db(0, raw_bytes)
     nthreads = os.cpu_count() or 1
-    ncols = max(1, min(D2, args.ref_cols))
-    runner = OracleRunner(n, log2p, D1, D2, B, raw, ncols, nthreads, modswitch=args.modswitch)
-    times = []
+    nq, ncols = oracle_sample_shape(wl, B, args.ref_cols)
+    runner = OracleRunner(n, log2p, D1, D2, B, nq, ncols, nthreads, db_seed=0, modswitch=args.modswitch)
+    meas, extra = [], []
     for step in range(args.warmup + args.steps):
-        full_s = runner.step(100 + step)
+        r = runner.step(100 + step)
         if step >= args.warmup:
-            times.append(full_s)
-    sample_desc = runner.describe()
-    mean_s = sum(times) / len(times)
-    value = raw_bytes * B / mean_s / 1e9
+            meas.append(r["measured_s"])
+            extra.append(r["extrapolated_s"])
+    meas_s, extra_s = sum(meas) / len(meas), sum(extra) / len(extra)
+    value = raw_bytes * B / extra_s / 1e9
+    fraction = meas_s / extra_s
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": mean_s * 1e3, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": meas_s * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "step": ("each step runs the oracle on a bounded sample of the batch's answer (%s); ms_per_step is that "
+                 "sample's measured time, value the metric over the extrapolated full answer"
+                 % ("full answer" if runner.full else "%.4f of it by time" % fraction)),
+        "extrapolated_ms_per_full_step": extra_s * 1e3,
         "config": {"workload": wl, "description": desc, "batch": B, "n": n, "log2p": log2p, "D1": D1, "D2": D2,
                    "L": L_PRIMES, "modswitch": bool(args.modswitch)},
-        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": nthreads, "kind": "oracle", "sample": sample_desc},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": nthreads, "kind": "oracle",
+                         "sample": runner.describe(), "measured_ms": meas_s * 1e3, "extrapolated_ms": extra_s * 1e3,
+                         "label": "full" if runner.full else "extrapolated"},
         "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
+def oracle_full_answers(wl, raw, cpu_full):
+    """Full oracle answers (every query, every column) on the host cores: batch 1 and
+    8, on all cores and on one core.  One core at batch 8 takes minutes, so it runs
+    only with cpu_full."""
+    n, log2p, D1, D2, _, _ = WORKLOADS[wl]
+    allc = os.cpu_count() or 1
+    out = []
+    runners = {}
+    for B in (1, 8):
+        for cores in (allc, 1):
+            if B == 8 and cores == 1 and not cpu_full:
+                out.append({"batch": B, "cores": cores, "skipped": "minutes of host time; bench.py --cpu-full runs it"})
+                continue
+            key = B
+            if key not in runners:
+                runners[key] = OracleRunner(n, log2p, D1, D2, B, B, D2, allc, raw=raw)
+            r = runners[key]
+            r.nthreads = cores
+            res = r.step(300 + B)
+            out.append({"batch": B, "cores": cores, "ms": res["measured_s"] * 1e3,
+                        "value": synth_raw_bytes(wl) * B / res["measured_s"] / 1e9, "unit": "GB/s",
+                        "label": "full"})
+    return out
+
+
+def synth_raw_bytes(wl):
+    n, log2p, D1, D2, _, _ = WORKLOADS[wl]
+    return D1 * D2 * n * log2p // 8
+
+
 # --- our arm -----------------------------------------------------------------
+
+class Ctx:
+    """What every timed block of our arm shares."""
+
+    def __init__(self, args, wl, g, binding, synth, torch, dev, rank, world, sampler):
+        self.args, self.wl, self.g, self.binding, self.synth, self.torch = args, wl, g, binding, synth, torch
+        self.dev, self.rank, self.world, self.sampler = dev, rank, world, sampler
+        self.peaks, self.peak_kind = measured_peaks()
+        self.probes = {}
+
+    def probe(self, name, stream):
+        if name not in self.probes:
+            fn = {"imad": self.g.pir_probe_imad_wide, "int8": self.g.pir_probe_int8_mma}[name]
+            self.probes[name] = fn(stream)
+        return self.probes[name]
+
+
+def gemm_roofline(ctx, layout, B, p, tile, gemm_ms, launches_per_step, clocks, stream):
+    """Roofline of the dominant kernel (the modular GEMM stage) for one launch:
+    the algorithmic work of one step divided by its launches, over the event-timed
+    kernel time per launch.  Query rows are counted unpadded."""
+    g = ctx.g
+    n, D1, D2 = p.n, p.D1, p.D2
+    M = 2 * B
+    nslots = L_PRIMES * n
+    launch_ms = gemm_ms / launches_per_step
+    streaming = layout == g.PIR_LAYOUT_PLAIN and M <= 8 and (tile in (1, 2, 3, 7) or (tile == 0 and M <= 4 and D2 <= 512))
+    if streaming:
+        kernel_tag = "scan_tma" if tile in (0, 7) else "gemv_scan"
+        alg_bytes = nslots * (D1 * D2 * 4 + D1 * M * 4 + M * D2 * 4)
+        per = alg_bytes / launches_per_step
+        rl = {"bound": "hbm", "achieved": per / (launch_ms / 1e3) / 1e9, "peak": float(ctx.peaks["hbm_gbs"]),
+              "unit": "GB/s", "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % ctx.peak_kind}
+    elif layout == g.PIR_LAYOUT_TENSOR:
+        # bf16 tensor cores: 16 digit products (2 FLOP each) per modular MAC of the
+        # useful query rows, against the measured sustained dense bf16 peak (the
+        # kernel runs inside a long step); bytes: 8 per DB residue (four bf16 digits)
+        kernel_tag = "gemm_tc"
+        macs = nslots * D1 * D2 * M / launches_per_step
+        alg_bytes = nslots * (D1 * D2 * 8 + D1 * M * 8 + M * D2 * 4)
+        per = alg_bytes / launches_per_step
+        rl = {"bound": "tensor", "achieved": 32.0 * macs / (launch_ms / 1e3) / 1e12,
+              "peak": float(ctx.peaks.get("bf16_tflops_sustained", 1700.0)), "unit": "TFLOP/s",
+              "peak_source": "%s bf16_tflops_sustained (MEASURED_PEAKS.json)" % ctx.peak_kind,
+              "modmac_per_s": macs / (launch_ms / 1e3), "hbm_gbs": per / (launch_ms / 1e3) / 1e9,
+              "hbm_frac": per / (launch_ms / 1e3) / 1e9 / float(ctx.peaks["hbm_gbs"])}
+    else:
+        macs = nslots * D1 * D2 * M / launches_per_step
+        alg_bytes = nslots * (D1 * D2 * 4 + D1 * M * 4 + M * D2 * 4)
+        per = alg_bytes / launches_per_step
+        if layout == g.PIR_LAYOUT_PLAIN:
+            # one mad.wide.u32 per modular MAC, against that instruction's rate
+            # measured live on this GPU
+            kernel_tag = "gemm_plain"
+            peak = ctx.probe("imad", stream)
+            sm_mhz = clocks.get("sm_mhz") or float(ctx.peaks.get("sm_max_mhz", 2070.0))
+            rl = {"bound": "alu", "achieved": macs / (launch_ms / 1e3) / 1e12, "peak": peak, "unit": "T modMAC/s",
+                  "peak_source": "pir_probe_imad_wide on this GPU (T mad.wide.u32/s; MEASURED_PEAKS.json has no "
+                                 "integer entry)",
+                  "derived_peak": 152 * 32 * sm_mhz * 1e6 / 1e12,
+                  "derived_peak_source": "152 SMs x 32 mad.wide.u32 / clock x sampled SM clock",
+                  "hbm_gbs": per / (launch_ms / 1e3) / 1e9}
+        else:
+            # 16 byte products per modular MAC on the INT8 tensor pipe
+            kernel_tag = "gemm_limb"
+            tops = ctx.probe("int8", stream)
+            rl = {"bound": "tensor", "achieved": 32.0 * macs / (launch_ms / 1e3) / 1e12, "peak": tops,
+                  "unit": "TOPS (INT8 mma.sync)", "modmac_per_s": macs / (launch_ms / 1e3),
+                  "peak_source": "pir_probe_int8_mma on this GPU (MEASURED_PEAKS.json has no INT8 entry)"}
+    rl["frac"] = rl["achieved"] / rl["peak"]
+    rl["kernel"] = kernel_tag
+    rl["kernel_ms"] = launch_ms
+    rl["launches_per_step"] = launches_per_step
+    rl["alg_bytes_per_launch"] = per
+    src = os.path.join(ROOT, "paper_2606_11536_gb300", "csrc",
+                       {"scan_tma": "scan_tma.cu", "gemv_scan": "gemm_plain.cu", "gemm_plain": "gemm_plain.cu",
+                        "gemm_limb": "gemm_limb.cu", "gemm_tc": "gemm_tc.cu"}[kernel_tag])
+    rl["traffic"] = profile_traffic(kernel_tag, ctx.wl, B, src)
+    return rl
+
+
+def make_db(ctx, p, layout):
+    """The resident DB: from host bytes up to 2 GiB raw (also what the oracle reads),
+    else generated on the device from the same counter-based stream."""
+    g, synth, torch = ctx.g, ctx.synth, ctx.torch
+    raw_bytes = ctx.binding.raw_db_bytes(p)
+    if raw_bytes <= (2 << 30):
+        raw = synth.raw_db(0, raw_bytes)
+        return g.pir_setup_db(p, raw, layout=layout), raw
+    raw_d = synth.raw_db_torch(0, raw_bytes, device=ctx.dev)
+    db = g.pir_setup_db(p, raw_d, layout=layout)
+    del raw_d
+    torch.cuda.empty_cache()
+    return db, None
+
+
+def measure_batch(ctx, db, p, layout, B, steps, warmup, min_seconds=0.0, extras=None):
+    """Time `steps` answers of B queries (at least min_seconds of them when asked),
+    after `warmup` untimed ones, with CUDA events on the launching stream, bracketed
+    by barrier + synchronize.  Returns the block's numbers and its step function."""
+    args, g, synth, torch = ctx.args, ctx.g, ctx.synth, ctx.torch
+    n, D1, D2 = p.n, p.D1, p.D2
+    extras = extras or {}
+    msw = g.PIR_ANSWER_MODSWITCH if args.modswitch else 0
+    qwords = B * D1 * 2 * L_PRIMES * n
+    rwords = B * D2 * 2 * (1 if msw else L_PRIMES) * n
+    rg, ex = extras.get("rgsw"), extras.get("expander")
+    if rg is not None:
+        rwords = B * 2 * (1 if msw else L_PRIMES) * n
+    if ex is not None:
+        qwords = B * 2 * L_PRIMES * n
+    # several query buffers rotate when they are small, so no step reads inputs the
+    # previous step left in L2
+    nbuf = 4 if qwords * 4 <= (4 << 30) else 1
+    nct = qwords // (L_PRIMES * n)
+    qbufs = [synth.uniform_residues_torch(1000 + 17 * ctx.rank + 5 * B + t, synth.STREAM_UNIFORM, nct, n, p.qs,
+                                          device=ctx.dev).view(-1) for t in range(nbuf)]
+    stream = torch.cuda.current_stream()
+    nstreams = args.streams
+    streams = [stream] + [torch.cuda.Stream(device=ctx.dev) for _ in range(nstreams - 1)]
+    resps = [torch.empty(rwords, dtype=torch.int32, device=ctx.dev) for _ in range(nstreams)]
+
+    def step(t, flags=0):
+        st, rs = streams[t % nstreams], resps[t % nstreams]
+        if rg is not None:
+            g.pir_answer_folded(db, qbufs[t % nbuf], B, args.ell, rg, rs, stream=st, flags=flags | msw, tile=args.tile)
+        elif ex is not None:
+            g.pir_answer_packed(db, ex, qbufs[t % nbuf], B, rs, stream=st, flags=flags | msw, tile=args.tile)
+        else:
+            g.pir_answer_ex(db, qbufs[t % nbuf], B, rs, stream=st, flags=flags | msw, tile=args.tile,
+                            k_chunk=args.k_chunk)
+
+    for t in range(warmup):
+        step(t)
+    torch.cuda.synchronize()
+    if min_seconds > 0:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        est_s = max(e0.elapsed_time(e1) / 1e3, 1e-6)
+        steps = max(steps, int(np.ceil(min_seconds / est_s)))
+    g.pir_stage_times()  # reset
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = g.pir_kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    w0 = time.time()
+    ev0.record(stream)
+    for st in streams[1:]:
+        st.wait_event(ev0)
+    for t in range(steps):
+        step(t, flags=g.PIR_ANSWER_STAGE_TIMES)
+    for st in streams[1:]:
+        stream.wait_stream(st)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    w1 = time.time()
+    barrier()
+    launches = g.pir_kernel_launches() - launches0
+    elapsed_ms = ev0.elapsed_time(ev1)
+    stage_ms, stage_launches = g.pir_stage_times()
+    clocks = ctx.sampler.summary(w0, w1)
+    max_ms, total_queries = reduce_timing(elapsed_ms, float(B * steps), device=ctx.dev if ctx.world > 1 else None)
+    raw_bytes = ctx.binding.raw_db_bytes(p)
+    gemm_launches = max(1, stage_launches[2])
+    launches_per_step = gemm_launches / steps
+    gemm_ms = stage_ms[2] / steps  # GEMM kernel time per step
+    roofline = gemm_roofline(ctx, layout, B, p, args.tile, gemm_ms, launches_per_step, clocks, stream)
+    roofline["stage_ms_per_step"] = {name: stage_ms[i] / steps for i, name in enumerate(ctx.binding.STAGE_NAMES)}
+    out = {"batch": B, "value": raw_bytes * total_queries / (max_ms / 1e3) / 1e9, "unit": "GB/s",
+           "ms_per_step": max_ms / steps, "steps": steps, "warmup": warmup, "timed_s": max_ms / 1e3,
+           "roofline": roofline, "gpu_launches": int(launches), "clocks": clocks}
+    return out, {"qbufs": qbufs, "qwords": qwords, "rwords": rwords, "stream": stream, "msw": msw}
+
+
+def measure_e2e(ctx, db, p, B, bufs, extras, est_step_ms):
+    """The same metric through the public API with pinned host buffers: every step
+    copies its queries host -> device and its responses back inside the call."""
+    args, g, torch = ctx.args, ctx.g, ctx.torch
+    qwords, rwords, stream, msw = bufs["qwords"], bufs["rwords"], bufs["stream"], bufs["msw"]
+    rg, ex = extras.get("rgsw"), extras.get("expander")
+    try:
+        host_ram = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES")
+    except (ValueError, OSError):
+        host_ram = 64 << 30
+    if (qwords + rwords) * 4 > host_ram // 2:
+        return None
+    qh = torch.empty(qwords, dtype=torch.int32, pin_memory=True)
+    rh = torch.empty(rwords, dtype=torch.int32, pin_memory=True)
+    qh.copy_(bufs["qbufs"][0])
+    rgh = None
+    if rg is not None:
+        rgh = torch.empty(rg.numel(), dtype=torch.int32, pin_memory=True)
+        rgh.copy_(rg.cpu())
+    n_steps = max(3, min(args.steps, int(np.ceil(1000.0 / max(est_step_ms, 1e-3)))))
+
+    def e2e_step():
+        if rg is not None:
+            g.pir_answer_folded(db, qh, B, args.ell, rgh, rh, stream=stream, flags=msw)
+        elif ex is not None:
+            g.pir_answer_packed(db, ex, qh, B, rh, stream=stream, flags=msw)
+        else:
+            g.pir_answer_ex(db, qh, B, rh, stream=stream, flags=msw)
+    for _ in range(2):
+        e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(n_steps):
+        e2e_step()
+    t1 = time.perf_counter()
+    e2e_ms, e2e_q = reduce_timing((t1 - t0) * 1e3, float(B * n_steps), device=ctx.dev if ctx.world > 1 else None)
+    raw_bytes = ctx.binding.raw_db_bytes(p)
+    return {"value": raw_bytes * e2e_q / (e2e_ms / 1e3) / 1e9, "unit": "GB/s",
+            "h2d_bytes_per_step": qwords * 4 + (rg.numel() * 4 if rg is not None else 0),
+            "d2h_bytes_per_step": rwords * 4, "ms_per_step": e2e_ms / n_steps, "steps": n_steps}
+
 
 def our_arm(args, wl):
     import torch
@@ -257,244 +546,123 @@ def our_arm(args, wl):
     else:
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
+    sampler = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ
+                           else int(os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local]))
+    sampler.start()
+    ctx = Ctx(args, wl, g, binding, synth, torch, dev, rank, world, sampler)
 
     n, log2p, D1, D2, B0, desc = WORKLOADS[wl]
     B = args.batch or B0
     layout = {"plain": g.PIR_LAYOUT_PLAIN, "limb": g.PIR_LAYOUT_LIMB, "tensor": g.PIR_LAYOUT_TENSOR}[args.layout]
     p = g.pir_make_params(n, log2p, D1, D2, L_PRIMES)
     raw_bytes = binding.raw_db_bytes(p)
-    small = raw_bytes <= (2 << 30)
-    if small:  # host bytes (also what the oracle baseline reads)
-        raw = synth.raw_db(0, raw_bytes)
-        db = g.pir_setup_db(p, raw, layout=layout)
-    else:      # large databases: the same bytes generated on the device
-        raw = synth.raw_db_torch(0, raw_bytes, device=dev)
-        db = g.pir_setup_db(p, raw, layout=layout)
-        del raw
-        raw = None
-        torch.cuda.empty_cache()
-
-    # query sets generated on the device; several rotate when they are small, so no
-    # step reads inputs the previous step left in L2
-    qwords = B * D1 * 2 * L_PRIMES * n
-    msw = g.PIR_ANSWER_MODSWITCH if args.modswitch else 0
-    rwords = B * D2 * 2 * (1 if msw else L_PRIMES) * n  # switched responses keep one prime
-    nbuf = 4 if qwords * 4 <= (4 << 30) else 1
-    qbufs = [synth.uniform_residues_torch(1000 + 17 * rank + t, synth.STREAM_UNIFORM, B * D1 * 2, n, p.qs,
-                                          device=dev).view(-1) for t in range(nbuf)]
-    resp = torch.empty(rwords, dtype=torch.int32, device=dev)
-    stream = torch.cuda.current_stream()
+    db, raw = make_db(ctx, p, layout)
 
     if args.packed and args.folded:
         raise SystemExit("--packed and --folded are separate modes")
-    rg = None
+    extras = {}
     if args.folded:
         # RGSW rows of the log2(D2) remaining levels per query; the external products'
         # cost does not depend on their values, so timing-only rows are uniform residues
         flevels = max(0, (D2 - 1).bit_length())
-        rg = synth.uniform_residues_torch(78, synth.STREAM_KEY_A, B * flevels * 2 * args.ell * 2, n, p.qs,
-                                          device=dev).view(-1)
-        rwords = B * 2 * (1 if msw else L_PRIMES) * n
-        resp = torch.empty(rwords, dtype=torch.int32, device=dev)
-    ex = None
+        extras["rgsw"] = synth.uniform_residues_torch(78, synth.STREAM_KEY_A, B * flevels * 2 * args.ell * 2, n,
+                                                      p.qs, device=dev).view(-1)
     if args.packed:
         # packed queries (one ciphertext each) expanded on the GPU; the expansion's
         # cost does not depend on the key values, so timing-only keys are uniform
         # residues of the key shape [levels][ell][2][L][n]
         levels = max(0, (D1 - 1).bit_length())
         keys = synth.uniform_residues_torch(77, synth.STREAM_KEY_A, levels * args.ell * 2, n, p.qs, device=dev)
-        ex = g.pir_expander_create(p, levels, args.ell, keys.view(-1))
+        extras["expander"] = g.pir_expander_create(p, levels, args.ell, keys.view(-1))
         del keys
-        qwords = B * 2 * L_PRIMES * n
-        qbufs = [synth.uniform_residues_torch(2000 + 17 * rank + t, synth.STREAM_UNIFORM, B * 2, n, p.qs,
-                                              device=dev).view(-1) for t in range(nbuf)]
 
-    # steps go round-robin over `streams` CUDA streams, each with its own response
-    # buffer, so that one answer's NTT work can run beside another's scan (as the
-    # serving loop runs them); the timed region still spans exactly K whole steps
-    streams = [stream] + [torch.cuda.Stream(device=dev) for _ in range(args.streams - 1)]
-    resps = [resp] + [torch.empty_like(resp) for _ in range(args.streams - 1)]
+    time.sleep(0.3)  # clock samples before the first timed region
+    head, bufs = measure_batch(ctx, db, p, layout, B, args.steps, args.warmup, extras=extras)
+    e2e = measure_e2e(ctx, db, p, B, bufs, extras, head["ms_per_step"])
+    del bufs
 
-    def step(t, flags=0):
-        st, rs = streams[t % len(streams)], resps[t % len(streams)]
-        if rg is not None:
-            g.pir_answer_folded(db, qbufs[t % nbuf], B, args.ell, rg, rs, stream=st, flags=flags | msw,
-                                tile=args.tile)
-            return
-        if ex is not None:
-            g.pir_answer_packed(db, ex, qbufs[t % nbuf], B, rs, stream=st, flags=flags | msw, tile=args.tile)
-            return
-        g.pir_answer_ex(db, qbufs[t % nbuf], B, rs, stream=st, flags=flags | msw, tile=args.tile,
-                        k_chunk=args.k_chunk)
-
-    for t in range(args.warmup):
-        step(t)
-    torch.cuda.synchronize()
-    g.pir_stage_times()  # reset
-
-    sampler = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ
-                           else int(os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local]))
-    sampler.start()
-    time.sleep(0.3)
-    barrier()
-    torch.cuda.synchronize()
-    launches0 = g.pir_kernel_launches()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    w0 = time.time()
-    ev0.record(stream)
-    for st in streams[1:]:
-        st.wait_event(ev0)
-    for t in range(args.steps):
-        step(t, flags=g.PIR_ANSWER_STAGE_TIMES)
-    for st in streams[1:]:
-        stream.wait_stream(st)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    w1 = time.time()
-    barrier()
-    launches = g.pir_kernel_launches() - launches0
-    elapsed_ms = ev0.elapsed_time(ev1)
-    stage_ms, stage_launches = g.pir_stage_times()
-    sampler.stop()
-    clocks = sampler.summary(w0, w1)
-
-    max_ms, total_queries = reduce_timing(elapsed_ms, float(B * args.steps), device=dev if world > 1 else None)
-    value = raw_bytes * total_queries / (max_ms / 1e3) / 1e9
-    ms_per_step = max_ms / args.steps
-
-    # roofline of the dominant kernel: the modular GEMM stage.  With K-chunking a step
-    # runs it several times on slices of D1, so the work of one launch is the step's
-    # work divided by the launches per step.
-    M, Mp = 2 * B, (2 * B + 3) // 4 * 4
-    nslots = L_PRIMES * n
-    gemm_launches = max(1, stage_launches[2])
-    launches_per_step = gemm_launches / args.steps
-    gemm_ms = stage_ms[2] / gemm_launches * launches_per_step  # kernel time per step
-    peaks, peak_kind = measured_peaks()
-    src = os.path.join(ROOT, "paper_2606_11536_gb300", "csrc",
-                       {g.PIR_LAYOUT_PLAIN: "gemm_plain.cu", g.PIR_LAYOUT_LIMB: "gemm_limb.cu"}.get(layout, "gemm_tc.cu"))
-    # the built-in choice takes the TMA scan up to 4 query rows (bound by HBM), the
-    # GEMV tiles 1-3 when asked for (HBM-shaped), and the tiled GEMMs otherwise (ALU)
-    streaming = layout == g.PIR_LAYOUT_PLAIN and M <= 8 and (
-        args.tile in (1, 2, 3, 7) or (args.tile == 0 and M <= 4 and D2 <= 512))
-    if streaming:
-        kernel_tag = "scan_tma" if args.tile in (0, 7) else "gemv_scan"
-        alg_bytes = nslots * (D1 * D2 * 4 + D1 * Mp * 4 + M * D2 * 4)
-        roofline = {"bound": "hbm", "achieved": alg_bytes / (gemm_ms / 1e3) / 1e9,
-                    "peak": float(peaks["hbm_gbs"]), "unit": "GB/s"}
-    elif layout == g.PIR_LAYOUT_TENSOR:
-        # bf16 tensor cores: 16 digit products per modular MAC (useful rows only, the
-        # padding to 8 rows not counted) against the measured dense bf16 peak; the
-        # kernel runs inside a long step, so the sustained figure
-        kernel_tag = "gemm_tc"
-        Mp8 = (M + 7) // 8 * 8
-        alg_bytes = nslots * (D1 * D2 * 8 + D1 * Mp8 * 8 + M * D2 * 4)
-        macs = nslots * D1 * D2 * M
-        tflops = 2.0 * 16 * macs / (gemm_ms / 1e3) / 1e12
-        roofline = {"bound": "tensor", "achieved": tflops, "peak": float(peaks.get("bf16_tflops_sustained", 1700.0)),
-                    "unit": "TFLOP/s", "modmac_per_s": macs / (gemm_ms / 1e3),
-                    "peak_source": "%s bf16_tflops_sustained (MEASURED_PEAKS.json)" % peak_kind,
-                    "hbm_gbs": alg_bytes / (gemm_ms / 1e3) / 1e9}
-    else:
-        kernel_tag = "gemm_plain" if layout == g.PIR_LAYOUT_PLAIN else "gemm_limb"
-        alg_bytes = nslots * (D1 * D2 * 4 + D1 * Mp * 4 + M * D2 * 4)
-        macs = nslots * D1 * D2 * M
-        # INT32 pipe: one 32x32+64-bit multiply-add per modular MAC; peak derived in
-        # the design notes from 152 SMs x 32 wide multiply-adds / clock x SM clock
-        sm_mhz = clocks["sm_mhz"] or float(peaks.get("sm_max_mhz", 2070.0))
-        if layout == g.PIR_LAYOUT_PLAIN:
-            alu_peak = 152 * 32 * sm_mhz * 1e6 / 1e12
-            roofline = {"bound": "alu", "achieved": macs / (gemm_ms / 1e3) / 1e12, "peak": alu_peak,
-                        "unit": "T modMAC/s", "peak_source": "152 SMs x 32 IMAD.WIDE/clk x sampled SM clock"}
-        else:
-            # limb path: 16 byte products per modular MAC on the INT8 tensor pipe; the peak
-            # is that pipe's rate measured live by the library's probe
-            tops = g.pir_probe_int8_mma(stream)
-            roofline = {"bound": "tensor", "achieved": 2.0 * 16 * macs / (gemm_ms / 1e3) / 1e12, "peak": tops,
-                        "unit": "TOPS (INT8 mma.sync)", "modmac_per_s": macs / (gemm_ms / 1e3),
-                        "peak_source": "pir_probe_int8_mma on this GPU (MEASURED_PEAKS.json has no INT8 entry)"}
-    roofline["frac"] = roofline["achieved"] / roofline["peak"]
-    if roofline["bound"] == "hbm":
-        roofline["peak_source"] = "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind
-    roofline["kernel"] = kernel_tag
-    roofline["kernel_ms"] = gemm_ms / launches_per_step
-    roofline["launches_per_step"] = launches_per_step
-    roofline["alg_bytes_per_launch"] = alg_bytes / launches_per_step
-    roofline["traffic"] = profile_traffic(kernel_tag, wl, B, src)
-    roofline["stage_ms_per_step"] = {name: stage_ms[i] / args.steps for i, name in enumerate(binding.STAGE_NAMES)}
-
-    # end to end through the public API with pinned host buffers
-    e2e = None
-    try:
-        host_ram = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES")
-    except (ValueError, OSError):
-        host_ram = 64 << 30
-    # pinned host buffers up to half of host memory; host batches above 4 GiB
-    # run as a streamed answer inside pir_answer_ex (pieces of at most 1 GiB)
-    if (qwords + rwords) * 4 <= host_ram // 2:
-        qh = torch.empty(qwords, dtype=torch.int32, pin_memory=True)
-        rh = torch.empty(rwords, dtype=torch.int32, pin_memory=True)
-        qh.copy_(qbufs[0])
-        e2e_steps = max(3, min(args.steps, 50))
-        rgh = None
-        if rg is not None:
-            rgh = torch.empty(rg.numel(), dtype=torch.int32, pin_memory=True)
-            rgh.copy_(rg.cpu())
-
-        def e2e_step():
-            if rg is not None:
-                g.pir_answer_folded(db, qh, B, args.ell, rgh, rh, stream=stream, flags=msw)
-                return
-            if ex is not None:
-                g.pir_answer_packed(db, ex, qh, B, rh, stream=stream, flags=msw)
+    # the metric's batch range and the tensor layout, on the default workload (one GPU)
+    plain_mode = layout == g.PIR_LAYOUT_PLAIN and not extras and args.streams == 1 and args.tile == 0 and \
+        args.k_chunk == 0 and not args.modswitch
+    per_batch = tensor_block = None
+    if world == 1 and plain_mode and args.per_batch:
+        per_batch = []
+        for b in PER_BATCH:
+            if b == B:
+                r = {k: head[k] for k in ("batch", "value", "unit", "ms_per_step", "steps", "warmup", "timed_s",
+                                          "roofline", "gpu_launches", "clocks")}
+                r["headline"] = True
             else:
-                g.pir_answer_ex(db, qh, B, rh, stream=stream, flags=msw)
-        for _ in range(2):
-            e2e_step()
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(e2e_steps):
-            e2e_step()
-        t1 = time.perf_counter()
-        e2e_ms, e2e_q = reduce_timing((t1 - t0) * 1e3, float(B * e2e_steps), device=dev if world > 1 else None)
-        e2e = {"value": raw_bytes * e2e_q / (e2e_ms / 1e3) / 1e9, "unit": "GB/s",
-               "h2d_bytes_per_step": qwords * 4 + (rg.numel() * 4 if rg is not None else 0),
-               "d2h_bytes_per_step": rwords * 4,
-               "ms_per_step": e2e_ms / e2e_steps}
+                r, _ = measure_batch(ctx, db, p, layout, b, 3, 3, min_seconds=MIN_TIMED_S)
+                torch.cuda.empty_cache()
+            per_batch.append(r)
+    if world == 1 and plain_mode and args.tensor_block:
+        g.pir_free_db(db)
+        db = None
+        torch.cuda.empty_cache()
+        tdb, _ = make_db(ctx, p, g.PIR_LAYOUT_TENSOR)
+        try:
+            tb = 32 if B != 32 and not args.batch else B
+            r, _ = measure_batch(ctx, tdb, p, g.PIR_LAYOUT_TENSOR, tb, 3, 3, min_seconds=MIN_TIMED_S)
+        finally:
+            g.pir_free_db(tdb)
+            torch.cuda.empty_cache()
+        plain_ref = next((x for x in (per_batch or []) if x["batch"] == tb), head if tb == B else None)
+        r["layout"] = "tensor (opt-in: bf16 tcgen05 digits, 8 bytes per residue, exact integer results)"
+        r["resident_bytes"] = binding.resident_db_bytes(p, g.PIR_LAYOUT_TENSOR)
+        if plain_ref is not None:
+            pg = plain_ref["roofline"]["stage_ms_per_step"]["gemm"]
+            tg = r["roofline"]["stage_ms_per_step"]["gemm"]
+            r["gemm_ms_plain"], r["gemm_ms_tensor"] = pg, tg
+            r["gemm_speedup_vs_plain"] = pg / tg
+            r["step_speedup_vs_plain"] = plain_ref["ms_per_step"] / r["ms_per_step"]
+        tensor_block = r
 
     cpu = None
-    # the oracle baseline times the plain answer; with --packed or --folded there is none
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and raw is not None and not (args.packed or args.folded):
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not (args.packed or args.folded):
         nthreads = os.cpu_count() or 1
-        ncols = max(1, min(D2, args.ref_cols))
-        runner = OracleRunner(n, log2p, D1, D2, B, raw, ncols, nthreads, modswitch=args.modswitch)
+        nq, ncols = oracle_sample_shape(wl, B, args.ref_cols)
+        runner = OracleRunner(n, log2p, D1, D2, B, nq, ncols, nthreads, db_seed=0, raw=raw,
+                              modswitch=args.modswitch)
         runner.step(7)  # warm
-        full_s = min(runner.step(8), runner.step(9))
-        cpu = {"value": raw_bytes * B / full_s / 1e9, "unit": "GB/s", "cores": nthreads, "kind": "oracle",
-               "sample": runner.describe() + "; best of 2 steps"}
+        rs = [runner.step(8), runner.step(9)]
+        best = min(rs, key=lambda r: r["extrapolated_s"])
+        cpu = {"value": raw_bytes * B / best["extrapolated_s"] / 1e9, "unit": "GB/s", "cores": nthreads,
+               "kind": "oracle", "sample": runner.describe() + "; best of 2 steps",
+               "measured_ms": best["measured_s"] * 1e3, "extrapolated_ms": best["extrapolated_s"] * 1e3,
+               "label": "full" if runner.full else "extrapolated"}
+        if raw is not None and wl == "db1g_n4096":
+            cpu["full_answers"] = oracle_full_answers(wl, raw, args.cpu_full)
 
-    if ex is not None:
-        g.pir_expander_free(ex)
-    g.pir_free_db(db)
+    for k in ("expander",):
+        if k in extras:
+            g.pir_expander_free(extras[k])
+    if db is not None:
+        g.pir_free_db(db)
+    sampler.stop()
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "metric": METRIC, "value": head["value"], "unit": "GB/s", "n_gpus": world, "steps": head["steps"],
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": wl, "description": desc, "batch": B, "n": n, "log2p": log2p, "D1": D1, "D2": D2,
-                       "L": L_PRIMES, "layout": args.layout, "modswitch": bool(msw), "streams": args.streams,
+                       "L": L_PRIMES, "layout": args.layout, "modswitch": bool(args.modswitch),
+                       "streams": args.streams,
                        "responses": ("folded to one ciphertext per query by %d RGSW external-product levels "
                                      "(%d gadget digits; timing-only RGSW rows)" % ((D2 - 1).bit_length(), args.ell)
                                      if args.folded else "D2 ciphertexts each"),
                        "queries": ("packed, expanded on the GPU (levels %d, %d gadget digits; timing-only keys)"
                                    % ((D1 - 1).bit_length(), args.ell) if args.packed else "D1 ciphertexts each"),
                        "parallelism": "replicas x%d" % world,
-                       "l2": "inputs larger than L2: the %.1f GiB NTT-form DB is streamed every step; %d query "
-                             "buffers rotate" % (binding.resident_db_bytes(p) / 2 ** 30, nbuf)},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "clocks": clocks,
+                       "l2": "inputs larger than L2: the %.1f GiB NTT-form DB is streamed every step; query "
+                             "buffers rotate when small" % (binding.resident_db_bytes(p, layout) / 2 ** 30)},
+            "roofline": head["roofline"], "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": head["gpu_launches"],
+            "clocks": head["clocks"], "timed_s": head["timed_s"],
         }
+        if per_batch is not None:
+            line["per_batch"] = per_batch
+        if tensor_block is not None:
+            line["tensor_layout"] = tensor_block
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -667,9 +835,12 @@ def serving_bench(args):
     import synth
     torch.cuda.set_device(0)
     serving_layout = {"plain": g.PIR_LAYOUT_PLAIN, "tensor": g.PIR_LAYOUT_TENSOR}[args.serving_layout]
-    be = serving.CudaBackend()
+    be = serving.CudaBackend(graphs=args.serving_graphs, max_batch=args.serving_max_batch,
+                             graph_budget=args.serving_graph_gib << 30)
+    big = SERVING_DBS[-1][0]  # the 16 GiB database: its long batches may hold only some of the slots
     srv = serving.Server(be, streams=args.serving_streams, max_batch=args.serving_max_batch,
-                         scratch_budget=args.serving_scratch_gib << 30)
+                         scratch_budget=args.serving_scratch_gib << 30, batch_timeout=args.serving_timeout,
+                         db_max_slots={big: args.serving_big_slots} if args.serving_big_slots else None)
     pools = {}
     t0 = time.perf_counter()
     for k, (name, n, log2p, D1, D2) in enumerate(SERVING_DBS):
@@ -699,19 +870,29 @@ def serving_bench(args):
         torch.cuda.synchronize()
         st = serving.latency_stats(done)
         st["offered_qps"] = rate
+        st["saturated"] = st.get("qps", 0.0) < 0.9 * rate
         st["per_db"] = {d: serving.latency_stats([r for r in done if r.db == d]) for d in dbs}
         results.append(st)
     g.pir_check_device()
+    # the headline: p99 at the stated load (the highest offered rate the server kept up with
+    # unless one is named)
+    if args.serving_headline_rate:
+        head = next(r for r in results if r["offered_qps"] == args.serving_headline_rate)
+    else:
+        kept = [r for r in results if not r["saturated"]]
+        head = max(kept, key=lambda r: r["offered_qps"]) if kept else results[0]
     line = {"metric": "serving p50/p99 ms (Poisson arrivals, continuous batching)", "unit": "ms",
-            "value": results[0].get("p99_ms"), "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+            "value": head.get("p99_ms"), "p50_ms": head.get("p50_ms"), "achieved_qps": head.get("qps"),
+            "offered_qps": head["offered_qps"], "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
             "dtype": "u32",
             "config": {"workload": "serving", "dbs": [d[0] for d in SERVING_DBS], "fourth_db": SERVING_EXTRA[0],
                        "fourth_admitted": admitted, "free_hbm_before_fourth": free_before,
                        "streams": args.serving_streams, "max_batch": args.serving_max_batch,
-                       "layout": args.serving_layout,
+                       "layout": args.serving_layout, "graphs": bool(args.serving_graphs),
+                       "big_db_slot_cap": args.serving_big_slots, "batch_timeout_s": args.serving_timeout,
                        "seconds_per_load": args.serving_seconds, "setup_s": setup_s,
                        "resident_bytes": srv.resident_bytes},
-            "loads": results}
+            "graph_launches": be.graph_launches, "failed": len(srv.failed), "loads": results}
     print(json.dumps(line), flush=True)
 
 
@@ -726,8 +907,14 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tile", type=int, default=0, help="GEMM tile id (0 = built-in choice)")
     ap.add_argument("--k-chunk", type=int, default=0, help="fold D1 in chunks of this many ciphertexts")
-    ap.add_argument("--ref-cols", type=int, default=64, help="columns in the oracle's timed sample")
+    ap.add_argument("--ref-cols", type=int, default=16, help="columns in the oracle's timed sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-full", action="store_true",
+                    help="with --workload db1g_n4096: also the full oracle answer of batch 8 on one core (minutes)")
+    ap.add_argument("--no-per-batch", dest="per_batch", action="store_false",
+                    help="skip the per-batch blocks (batches 1, 8, 32, 128) of the default plain run")
+    ap.add_argument("--no-tensor-block", dest="tensor_block", action="store_false",
+                    help="skip the tensor-layout block (batch 32) of the default plain run")
     ap.add_argument("--lwe", action="store_true", help="time the scalar-HE (LWE) INT8 x INT32 DB GEMM instead")
     ap.add_argument("--lwe-workload", default="lwe16g", choices=sorted(LWE_WORKLOADS))
     ap.add_argument("--lwe-path", default="auto", choices=["auto", "tensor", "simt"])
@@ -745,9 +932,18 @@ def main(argv=None):
     ap.add_argument("--serving-rates", type=float, nargs="+", default=[100, 300, 1000, 3000, 5000])
     ap.add_argument("--serving-seconds", type=float, default=2.0)
     ap.add_argument("--serving-streams", type=int, default=4)
-    ap.add_argument("--serving-layout", default="plain", choices=["plain", "tensor"],
+    ap.add_argument("--serving-layout", default="tensor", choices=["plain", "tensor"],
                     help="resident layout of the served DBs (tensor: the bf16 tensor-core GEMM, twice the bytes)")
     ap.add_argument("--serving-max-batch", type=int, default=32)
+    ap.add_argument("--serving-graphs", action="store_true",
+                    help="run batches as captured graphs per (database, batch bucket, stream), autotuned")
+    ap.add_argument("--serving-graph-gib", type=int, default=16, help="buffers bound to captured graphs, at most")
+    ap.add_argument("--serving-big-slots", type=int, default=2,
+                    help="streams the 16 GiB database may hold at once (0: no cap)")
+    ap.add_argument("--serving-timeout", type=float, default=30.0,
+                    help="seconds after which a batch that has not completed fails its requests")
+    ap.add_argument("--serving-headline-rate", type=float, default=0.0,
+                    help="offered rate whose p99 is the line's value (default: the highest one kept up with)")
     ap.add_argument("--serving-scratch-gib", type=int, default=32)
     args = ap.parse_args(argv)
     if args.warmup < 3:

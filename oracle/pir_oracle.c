@@ -26,7 +26,7 @@
  *     modular GEMM", Sec. 4.2): in the NTT domain, for every prime q_j and slot k,
  *     out[b][c][k] = sum_i DB[i][c][k] * Q[b][i][k]  (mod q_j).
  *
- * Readings where the paper is silent (each listed in the design notes):
+ * Readings where the paper is silent:
  *   - primes are the L largest primes in (2^29, 2^30) with q = 1 mod max(2n, p);
  *   - psi_j = h^((q_j-1)/(2n)) for the smallest h >= 2 with psi_j^n = -1;
  *   - NTT(a)[k] = sum_t a_t psi^((2 brv(k) + 1) t)  (bit-reversed evaluation order);

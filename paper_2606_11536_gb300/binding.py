@@ -97,6 +97,7 @@ def lib():
             "pir_fold": (i32, [P, vp, u32, u32, u32, vp, vp, vp]),
             "pir_answer_folded": (i32, [vp, vp, u32, u32, vp, vp, i32, vp, C.POINTER(pir_answer_opts_t)]),
             "pir_probe_int8_mma": (i32, [vp, C.POINTER(C.c_double)]),
+            "pir_probe_imad_wide": (i32, [vp, C.POINTER(C.c_double)]),
             "pir_expander_create": (i32, [P, u32, u32, vp, i32, vp, C.POINTER(vp)]),
             "pir_expander_free": (i32, [vp]),
             "pir_expand": (i32, [vp, vp, u32, u32, vp, vp]),
@@ -220,8 +221,11 @@ PIR_NOALLOC_SCRATCH_BYTES = 64 << 20
 def pir_answer_noalloc(db: Db, queries, B: int, responses, stream=None):
     """pir_answer on device buffers without any device allocation (scratch comes
     from the library's fixed per-GPU array); for callers that cannot allocate."""
-    qp, qdev, _ = _ptr(queries)
-    rp, rdev, _ = _ptr(responses)
+    qp, qdev, qn = _ptr(queries)
+    rp, rdev, rn = _ptr(responses)
+    need_q, need_r = _answer_sizes(db, B)
+    _require("query", qn, need_q)
+    _require("response", rn, need_r)
     if not (qdev and rdev):
         raise ValueError("pir_answer_noalloc works on device buffers")
     _check(lib().pir_answer_noalloc(C.c_void_p(db.handle), qp, B, rp, _stream_ptr(stream)), "pir_answer_noalloc")
@@ -230,18 +234,20 @@ def pir_answer_noalloc(db: Db, queries, B: int, responses, stream=None):
 
 def ntt_fwd(params: pir_params_t, polys, count: int | None = None, stream=None):
     ptr, dev, nbytes = _ptr(polys)
+    cnt = nbytes // (4 * params.L * params.n) if count is None else count
+    _require("polynomial", nbytes, cnt * 4 * params.L * params.n)
     if not dev:
         raise ValueError("ntt_fwd works on device memory")
-    cnt = nbytes // (4 * params.L * params.n) if count is None else count
     _check(lib().ntt_fwd(C.byref(params), ptr, cnt, _stream_ptr(stream)), "ntt_fwd")
     return polys
 
 
 def ntt_inv(params: pir_params_t, polys, count: int | None = None, stream=None):
     ptr, dev, nbytes = _ptr(polys)
+    cnt = nbytes // (4 * params.L * params.n) if count is None else count
+    _require("polynomial", nbytes, cnt * 4 * params.L * params.n)
     if not dev:
         raise ValueError("ntt_inv works on device memory")
-    cnt = nbytes // (4 * params.L * params.n) if count is None else count
     _check(lib().ntt_inv(C.byref(params), ptr, cnt, _stream_ptr(stream)), "ntt_inv")
     return polys
 
@@ -250,19 +256,25 @@ def ntt_inv_modswitch(params: pir_params_t, polys, out, count: int | None = None
     """Inverse NTT of polys [count][L][n] (NTT form) with modulus switching to q_0
     fused in; writes out [count][n] over q_0."""
     ip, idev, nbytes = _ptr(polys)
-    op, odev, _ = _ptr(out)
+    op, odev, on = _ptr(out)
+    cnt = nbytes // (4 * params.L * params.n) if count is None else count
+    _require("polynomial", nbytes, cnt * 4 * params.L * params.n)
+    _require("output", on, cnt * 4 * params.n)
     if not (idev and odev):
         raise ValueError("ntt_inv_modswitch works on device memory")
-    cnt = nbytes // (4 * params.L * params.n) if count is None else count
     _check(lib().ntt_inv_modswitch(C.byref(params), ip, cnt, op, _stream_ptr(stream)), "ntt_inv_modswitch")
     return out
 
 
 def pir_fold(params: pir_params_t, cts, B: int, levels: int, ell: int, rgsw, out, stream=None):
     """Fold cts [B][2^levels][2][L][n] with rgsw [B][levels][2 ell][2][L][n] into out [B][2][L][n]."""
-    cp, cdev, _ = _ptr(cts)
-    gp, gdev, _ = _ptr(rgsw)
-    op, odev, _ = _ptr(out)
+    cp, cdev, cn = _ptr(cts)
+    gp, gdev, gn = _ptr(rgsw)
+    op, odev, on = _ptr(out)
+    ct = ct_bytes(params.n, params.L)
+    _require("ciphertext", cn, B * (1 << levels) * ct)
+    _require("RGSW", gn, B * levels * 2 * ell * ct)
+    _require("output", on, B * ct)
     if not (cdev and gdev and odev):
         raise ValueError("pir_fold works on device buffers")
     _check(lib().pir_fold(C.byref(params), cp, B, levels, ell, gp, op, _stream_ptr(stream)), "pir_fold")
@@ -271,9 +283,14 @@ def pir_fold(params: pir_params_t, cts, B: int, levels: int, ell: int, rgsw, out
 
 def pir_answer_folded(db: Db, queries, B: int, ell: int, rgsw, responses, stream=None, tile: int = 0, flags: int = 0):
     """First-dimension answer folded over the remaining log2(D2) levels: responses [B][2][L][n]."""
-    qp, qdev, _ = _ptr(queries)
-    gp, gdev, _ = _ptr(rgsw)
-    rp, rdev, _ = _ptr(responses)
+    qp, qdev, qn = _ptr(queries)
+    gp, gdev, gn = _ptr(rgsw)
+    rp, rdev, rn = _ptr(responses)
+    p = db.params
+    levels = max(0, (p.D2 - 1).bit_length())
+    _require("query", qn, _answer_sizes(db, B)[0])
+    _require("RGSW", gn, B * levels * 2 * ell * ct_bytes(p.n, p.L))
+    _require("response", rn, B * ct_bytes(p.n, 1 if flags & PIR_ANSWER_MODSWITCH else p.L))
     if not (qdev == gdev == rdev):
         raise ValueError("queries, rgsw and responses must all be host or all be device buffers")
     o = pir_answer_opts_t(0, tile, flags)
@@ -288,9 +305,12 @@ PIR_LWE_AUTO, PIR_LWE_TENSOR, PIR_LWE_SIMT = 0, 1, 2
 def pir_lwe_answer(db, D1: int, D0: int, queries, B: int, out, path: int = PIR_LWE_AUTO, stream=None):
     """Scalar-HE DB GEMM out[b][i] = sum_j db[i][j] queries[b][j] mod 2^32 (device buffers:
     db [D1][D0] int8, queries [B][D0] uint32, out [B][D1] uint32)."""
-    dp, ddev, _ = _ptr(db)
-    qp, qdev, _ = _ptr(queries)
-    op, odev, _ = _ptr(out)
+    dp, ddev, dn = _ptr(db)
+    qp, qdev, qn = _ptr(queries)
+    op, odev, on = _ptr(out)
+    _require("DB", dn, D1 * D0)
+    _require("query", qn, B * D0 * 4)
+    _require("output", on, B * D1 * 4)
     if not (ddev and qdev and odev):
         raise ValueError("pir_lwe_answer works on device buffers")
     _check(lib().pir_lwe_answer(dp, D1, D0, qp, B, op, path, _stream_ptr(stream)), "pir_lwe_answer")
@@ -304,6 +324,13 @@ def pir_probe_int8_mma(stream=None) -> float:
     return v.value
 
 
+def pir_probe_imad_wide(stream=None) -> float:
+    """Measured mad.wide.u32 peak of this GPU in tera multiply-adds per second."""
+    v = C.c_double()
+    _check(lib().pir_probe_imad_wide(_stream_ptr(stream), C.byref(v)), "pir_probe_imad_wide")
+    return v.value
+
+
 class Expander:
     """A client's expansion keys loaded on the device (pir_expander_t)."""
 
@@ -313,7 +340,8 @@ class Expander:
 
 def pir_expander_create(params: pir_params_t, levels: int, ell: int, keys, stream=None) -> Expander:
     """keys [levels][ell][2][L][n] (coefficient form), host array or device tensor."""
-    kp, kdev, _ = _ptr(keys)
+    kp, kdev, kn = _ptr(keys)
+    _require("key", kn, levels * ell * ct_bytes(params.n, params.L))
     h = C.c_void_p()
     _check(lib().pir_expander_create(C.byref(params), levels, ell, kp, int(kdev), _stream_ptr(stream), C.byref(h)),
            "pir_expander_create")
@@ -327,8 +355,11 @@ def pir_expander_free(ex: Expander):
 
 def pir_expand(ex: Expander, packed, B: int, count: int, out, stream=None):
     """Expand packed [B][2][L][n] into out [B][count][2][L][n] (device buffers)."""
-    pp, pdev, _ = _ptr(packed)
-    op, odev, _ = _ptr(out)
+    pp, pdev, pn = _ptr(packed)
+    op, odev, on = _ptr(out)
+    ct = ct_bytes(ex.params.n, ex.params.L)
+    _require("packed query", pn, B * ct)
+    _require("output", on, B * count * ct)
     if not (pdev and odev):
         raise ValueError("pir_expand works on device buffers")
     _check(lib().pir_expand(C.c_void_p(ex.handle), pp, B, count, op, _stream_ptr(stream)), "pir_expand")
@@ -338,10 +369,12 @@ def pir_expand(ex: Expander, packed, B: int, count: int, out, stream=None):
 def pir_answer_packed(db: Db, ex: Expander, packed, B: int, responses, stream=None, k_chunk: int = 0, tile: int = 0,
                       flags: int = 0):
     """pir_answer for packed queries [B][2][L][n]: expansion, then the scan."""
-    pp, pdev, _ = _ptr(packed)
-    rp, rdev, _ = _ptr(responses)
+    pp, pdev, pn = _ptr(packed)
+    rp, rdev, rn = _ptr(responses)
     if pdev != rdev:
         raise ValueError("packed queries and responses must both be host or both be device buffers")
+    _require("packed query", pn, B * ct_bytes(db.params.n, db.params.L))
+    _require("response", rn, _answer_sizes(db, B, flags)[1])
     o = pir_answer_opts_t(k_chunk, tile, flags)
     _check(lib().pir_answer_packed(C.c_void_p(db.handle), C.c_void_p(ex.handle), pp, B, rp, int(pdev),
                                    _stream_ptr(stream), C.byref(o)), "pir_answer_packed")
@@ -406,8 +439,11 @@ class Graph:
 
 
 def pir_graph_create(db: Db, queries, B: int, responses, k_chunk: int = 0, tile: int = 0, flags: int = 0) -> Graph:
-    qp, qdev, _ = _ptr(queries)
-    rp, rdev, _ = _ptr(responses)
+    qp, qdev, qn = _ptr(queries)
+    rp, rdev, rn = _ptr(responses)
+    need_q, need_r = _answer_sizes(db, B, flags)
+    _require("query", qn, need_q)
+    _require("response", rn, need_r)
     if not (qdev and rdev):
         raise ValueError("a graph binds device buffers")
     o = pir_answer_opts_t(k_chunk, tile, flags)
@@ -504,8 +540,10 @@ def raw_db_bytes(p) -> int:
     return p.D1 * p.D2 * p.n * p.log2p // 8
 
 
-def resident_db_bytes(p) -> int:
-    return 4 * p.L * p.n * p.D1 * p.D2
+def resident_db_bytes(p, layout: int = PIR_LAYOUT_PLAIN) -> int:
+    """Device bytes of the NTT-form DB: one u32 word (plain) or four u8 limbs (limb)
+    per residue, four bf16 digits (tensor) per residue."""
+    return (8 if layout == PIR_LAYOUT_TENSOR else 4) * p.L * p.n * p.D1 * p.D2
 
 
 def query_bytes(p, B: int) -> int:

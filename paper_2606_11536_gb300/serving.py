@@ -3,19 +3,31 @@
 Several NTT-encoded databases stay resident in HBM.  Requests (a database name and
 one query: D1 ciphertexts) arrive over time into one FIFO queue per database.  The
 server keeps `streams` CUDA streams as execution slots; whenever a slot is free it
-takes the database whose oldest waiting request arrived first, coalesces up to
-`max_batch` of that database's waiting requests into one batch, gathers their
-queries into the slot's batch buffer and issues pir_answer on the slot's stream.
-Requests that arrive while batches are running wait for the next free slot, so
-work from different batches and databases overlaps on the device.  A batch is
-also held back (or shrunk) until its query and response buffers fit the scratch
-budget left by the batches in flight.  A database is admitted only if its resident
-bytes fit the memory budget (when one is set) and the library's own free-HBM
-check (PIR_ERR_ADMISSION).
+takes the database whose oldest waiting request arrived first, coalesces up to that
+database's batch cap of its waiting requests into one batch, gathers their queries
+into the slot's batch buffer and issues the answer on the slot's stream.  Requests
+that arrive while batches are running wait for the next free slot, so work from
+different batches and databases overlaps on the device.
+
+Limits and failure handling:
+  - a batch is held back (or shrunk) until its query and response buffers fit the
+    scratch budget left by the batches in flight;
+  - per database, a batch cap (`db_max_batch`) and a cap on the slots it may hold at
+    once (`db_max_slots`), so that one large database cannot take every slot while
+    the small ones wait behind its long batches;
+  - a batch whose completion event has not fired `batch_timeout` seconds after its
+    dispatch fails its requests with PIR_ERR_TIMEOUT (status 5, the C ABI's code);
+    the slot keeps the batch's buffers and stays out of use until the event does
+    fire, since the device may still write into them;
+  - a request can be cancelled: a waiting one leaves its queue, a running one leaves
+    its batch's results (the rest of the batch completes normally).
+A database is admitted only if its resident bytes fit the memory budget (when one is
+set) and the library's own free-HBM check (PIR_ERR_ADMISSION).
 
 The scheduling logic is host code and runs against any backend with the small
 interface below; `CudaBackend` is the real one (torch streams and events, the C
-ABI), tests also drive a CPU fake.
+ABI, optionally captured graphs per database and batch size), tests also drive a
+CPU fake.
 """
 from __future__ import annotations
 
@@ -24,9 +36,14 @@ import dataclasses
 import math
 import random
 import time
-from typing import Callable, Dict, List, Optional
+from typing import Callable, Dict, List, Optional, Union
 
 import numpy as np
+
+from . import binding
+
+PIR_OK = 0
+PIR_ERR_TIMEOUT = 5
 
 
 @dataclasses.dataclass
@@ -39,6 +56,8 @@ class Request:
     t_done: float = math.nan
     batch_size: int = 0
     response: object = None  # filled when keep_responses is set
+    status: int = PIR_OK     # PIR_ERR_TIMEOUT when its batch ran out of time
+    cancelled: bool = False
 
     @property
     def latency(self) -> float:
@@ -54,6 +73,8 @@ class _Slot:
     db: str = ""
     bufs: object = None      # the batch's buffers, alive until the event completes
     scratch: int = 0
+    t_dispatch: float = 0.0
+    timed_out: bool = False  # requests already failed; the slot waits for its event
 
 
 class Backend:
@@ -77,15 +98,29 @@ class Backend:
     def response(self, bufs, b: int, B: int):
         raise NotImplementedError
 
+    def check(self) -> int:
+        """Device-side status after a timeout (PIR_OK, or the library's error code)."""
+        return PIR_OK
+
 
 class AdmissionError(RuntimeError):
     pass
 
 
+def _per_db(value, name, default):
+    if value is None:
+        return default
+    if isinstance(value, dict):
+        return value.get(name, default)
+    return value
+
+
 class Server:
     def __init__(self, backend: Backend, streams: int = 4, max_batch: int = 32, memory_budget: Optional[int] = None,
                  scratch_budget: Optional[int] = None, keep_responses: bool = False,
-                 clock: Callable[[], float] = time.perf_counter):
+                 clock: Callable[[], float] = time.perf_counter, batch_timeout: Optional[float] = None,
+                 db_max_batch: Union[None, int, Dict[str, int]] = None,
+                 db_max_slots: Union[None, int, Dict[str, int]] = None):
         self.be = backend
         self.max_batch = max_batch
         self.budget = memory_budget
@@ -93,10 +128,16 @@ class Server:
         self.scratch_in_flight = 0
         self.keep = keep_responses
         self.clock = clock
+        self.batch_timeout = batch_timeout
+        self.db_max_batch = db_max_batch
+        self.db_max_slots = db_max_slots
         self.dbs: Dict[str, dict] = {}
         self.queues: Dict[str, collections.deque] = {}
         self.slots = [_Slot(stream=backend.new_stream()) for _ in range(streams)]
-        self.done: List[Request] = []
+        self.done: List[Request] = []       # answered requests
+        self.failed: List[Request] = []     # requests whose batch timed out
+        self.cancelled: List[Request] = []
+        self.device_status = PIR_OK
         self.resident_bytes = 0
 
     # --- databases -----------------------------------------------------------
@@ -104,9 +145,7 @@ class Server:
         """Set up and keep database `name`; raises AdmissionError if it does not fit."""
         if name in self.dbs:
             raise ValueError("database %r already resident" % name)
-        # resident bytes per residue: u32 words or four u8 limbs (plain, limb), four
-        # bf16 digits (the tensor layout, 2)
-        need = (8 if layout == 2 else 4) * params.L * params.n * params.D1 * params.D2
+        need = binding.resident_db_bytes(params, layout)
         if self.budget is not None and self.resident_bytes + need > self.budget:
             raise AdmissionError("%s needs %d bytes, %d of the %d-byte budget are left"
                                  % (name, need, self.budget - self.resident_bytes, self.budget))
@@ -127,23 +166,69 @@ class Server:
     def submit(self, req: Request):
         self.queues[req.db].append(req)
 
+    def cancel(self, rid: int) -> bool:
+        """Cancel request rid.  A waiting request leaves its queue at once; a running
+        one is dropped from its batch's results when the batch completes.  Returns
+        False if no waiting or running request has that id."""
+        for q in self.queues.values():
+            for r in q:
+                if r.rid == rid:
+                    q.remove(r)
+                    r.cancelled = True
+                    r.t_done = self.clock()
+                    self.cancelled.append(r)
+                    return True
+        for s in self.slots:
+            if s.busy and not s.timed_out:
+                for r in s.requests:
+                    if r.rid == rid and not r.cancelled:
+                        r.cancelled = True
+                        return True
+        return False
+
     def pending(self) -> int:
-        return sum(len(q) for q in self.queues.values()) + sum(len(s.requests) for s in self.slots if s.busy)
+        return sum(len(q) for q in self.queues.values()) + sum(
+            len(s.requests) for s in self.slots if s.busy and not s.timed_out)
+
+    def _retire(self, now) -> List[Request]:
+        finished = []
+        for s in self.slots:
+            if not s.busy:
+                continue
+            if self.be.done(s.event):
+                if not s.timed_out:
+                    for b, r in enumerate(s.requests):
+                        r.t_done = now
+                        if r.cancelled:
+                            self.cancelled.append(r)
+                            continue
+                        if self.keep:
+                            r.response = self.be.response(s.bufs, b, len(s.requests))
+                        finished.append(r)
+                self.scratch_in_flight -= s.scratch
+                s.busy, s.requests, s.event, s.bufs, s.scratch, s.timed_out = False, [], None, None, 0, False
+            elif self.batch_timeout is not None and not s.timed_out and now - s.t_dispatch > self.batch_timeout:
+                # fail the requests now; the slot (and its buffers) stays held until
+                # the event fires, since the device may still write into them
+                s.timed_out = True
+                for r in s.requests:
+                    r.t_done = now
+                    if r.cancelled:
+                        self.cancelled.append(r)
+                        continue
+                    r.status = PIR_ERR_TIMEOUT
+                    self.failed.append(r)
+                self.device_status = self.be.check()
+        return finished
+
+    def _slots_of(self, name) -> int:
+        return sum(1 for s in self.slots if s.busy and s.db == name)
 
     def poll(self) -> List[Request]:
-        """Retire finished batches, then fill every free slot.  Returns the requests
-        that finished in this call."""
-        finished = []
+        """Retire finished batches (and time out overdue ones), then fill every free
+        slot.  Returns the requests answered in this call."""
         now = self.clock()
-        for s in self.slots:
-            if s.busy and self.be.done(s.event):
-                for b, r in enumerate(s.requests):
-                    r.t_done = now
-                    if self.keep:
-                        r.response = self.be.response(s.bufs, b, len(s.requests))
-                finished.extend(s.requests)
-                self.scratch_in_flight -= s.scratch
-                s.busy, s.requests, s.event, s.bufs, s.scratch = False, [], None, None, 0
+        finished = self._retire(now)
         for s in self.slots:
             if s.busy:
                 continue
@@ -154,7 +239,7 @@ class Server:
             info = self.dbs[name]
             p = info["params"]
             per_query = 8 * p.L * p.n * (p.D1 + p.D2)  # query + response words of one request
-            nb = min(self.max_batch, len(q))
+            nb = min(self.max_batch, _per_db(self.db_max_batch, name, self.max_batch), len(q))
             if self.scratch_budget is not None:
                 nb = min(nb, (self.scratch_budget - self.scratch_in_flight) // per_query)
                 if nb <= 0:
@@ -166,16 +251,22 @@ class Server:
             for r in take:
                 r.t_dispatch, r.batch_size = t, len(take)
             s.event, s.bufs = self.be.dispatch(info["handle"], p, [r.query for r in take], s.stream)
-            s.busy, s.requests, s.db, s.scratch = True, take, name, nb * per_query
+            s.busy, s.requests, s.db, s.scratch, s.t_dispatch = True, take, name, nb * per_query, t
             self.scratch_in_flight += s.scratch
         self.done.extend(finished)
         return finished
 
     def _next_db(self) -> Optional[str]:
+        """The database whose oldest waiting request arrived first, among those
+        below their slot cap."""
         best, t_best = None, math.inf
         for name, q in self.queues.items():
-            if q and q[0].t_arrival < t_best:
-                best, t_best = name, q[0].t_arrival
+            if not q or q[0].t_arrival >= t_best:
+                continue
+            cap = _per_db(self.db_max_slots, name, len(self.slots))
+            if self._slots_of(name) >= cap:
+                continue
+            best, t_best = name, q[0].t_arrival
         return best
 
     # --- open-loop run ---------------------------------------------------------
@@ -218,29 +309,59 @@ def poisson_arrivals(rate_qps: float, duration_s: float, dbs: List[str], seed: i
 
 
 def latency_stats(reqs: List[Request]) -> dict:
-    lat = np.array([r.latency for r in reqs if not math.isnan(r.t_done)]) * 1e3
+    ok = [r for r in reqs if not math.isnan(r.t_done) and r.status == PIR_OK and not r.cancelled]
+    lat = np.array([r.latency for r in ok]) * 1e3
     if lat.size == 0:
         return {"count": 0}
-    span = max(r.t_done for r in reqs) - min(r.t_arrival for r in reqs)
+    span = max(r.t_done for r in ok) - min(r.t_arrival for r in ok)
     return {"count": int(lat.size), "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "mean_ms": float(lat.mean()), "max_ms": float(lat.max()), "qps": float(lat.size / span) if span > 0 else 0.0,
-            "mean_batch": float(np.mean([r.batch_size for r in reqs]))}
+            "mean_batch": float(np.mean([r.batch_size for r in ok])),
+            "failed": sum(1 for r in reqs if r.status != PIR_OK),
+            "cancelled": sum(1 for r in reqs if r.cancelled)}
+
+
+def graph_bucket(B: int, max_batch: int) -> int:
+    """Batch size a captured graph is made for: the next power of two (at most
+    max_batch), so a few graphs per database serve every batch size."""
+    b = 1
+    while b < B:
+        b <<= 1
+    return max(B, min(b, max_batch))
 
 
 class CudaBackend(Backend):
     """The real backend: the C ABI for the scan, torch for buffers, streams and events.
 
-    Every dispatch allocates its batch buffers through torch; with large databases
-    run the process with torch's stream-ordered allocator
-    (PYTORCH_CUDA_ALLOC_CONF=backend:cudaMallocAsync), whose releases do not
-    synchronise the device as the caching allocator's do under memory pressure."""
+    Without graphs, every dispatch allocates its batch buffers through torch and
+    calls pir_answer; with large databases run the process with torch's
+    stream-ordered allocator (PYTORCH_CUDA_ALLOC_CONF=backend:cudaMallocAsync), whose
+    releases do not synchronise the device as the caching allocator's do under
+    memory pressure.
 
-    def __init__(self, device: int = 0):
+    With graphs=True, a batch runs as one captured answer (pir_graph_create) per
+    (database, batch bucket, slot): the batch is padded with zero queries to the
+    bucket (graph_bucket), whose tile and K-chunk the library's autotuner picks once
+    per (database, bucket).  The graph's query and response buffers stay bound to it;
+    a slot runs one batch at a time, so its graphs' buffers are free whenever the
+    slot is.  Graphs are kept within graph_budget bytes of bound buffers, least
+    recently used first out; a batch that does not fit runs uncaptured."""
+
+    def __init__(self, device: int = 0, graphs: bool = False, max_batch: int = 32, graph_budget: int = 16 << 30,
+                 autotune: bool = True):
         import torch
 
         import paper_2606_11536_gb300 as g
         self.torch, self.g = torch, g
         self.device = torch.device("cuda", device)
+        self.graphs = graphs
+        self.max_batch = max_batch
+        self.graph_budget = graph_budget
+        self.autotune = autotune
+        self._graphs = collections.OrderedDict()  # (db id, bucket, stream id) -> [graph, qbuf, rbuf, bytes, event]
+        self._graph_bytes = 0
+        self._tuned: Dict[tuple, dict] = {}
+        self.graph_launches = 0
 
     def setup_db(self, name, params, raw, layout):
         try:
@@ -252,28 +373,91 @@ class CudaBackend(Backend):
         return db, self.g.pir_db_bytes(db)
 
     def free_db(self, handle):
+        self.torch.cuda.synchronize(self.device)
+        for key in [k for k in self._graphs if k[0] == id(handle)]:
+            self._drop_graph(key)
         self.g.pir_free_db(handle)
 
     def new_stream(self):
         return self.torch.cuda.Stream(device=self.device)
+
+    def _drop_graph(self, key):
+        graph, _, _, nbytes, _ = self._graphs.pop(key)
+        self.g.pir_graph_destroy(graph)
+        self._graph_bytes -= nbytes
+
+    def _graph_for(self, handle, params, bucket, stream):
+        key = (id(handle), bucket, id(stream))
+        if key in self._graphs:
+            self._graphs.move_to_end(key)
+            return self._graphs[key]
+        torch = self.torch
+        qwords = bucket * params.D1 * 2 * params.L * params.n
+        rwords = bucket * params.D2 * 2 * params.L * params.n
+        nbytes = 4 * (qwords + rwords)
+        if nbytes > self.graph_budget:
+            return None
+        while self._graph_bytes + nbytes > self.graph_budget:
+            # least recently used first, and never a graph whose last launch is still
+            # running (its bound buffers are in use)
+            idle = next((k for k, e in self._graphs.items() if e[4] is None or e[4].query()), None)
+            if idle is None:
+                return None
+            self._drop_graph(idle)
+        tkey = (id(handle), bucket)
+        if tkey not in self._tuned:
+            self._tuned[tkey] = self.g.pir_autotune(handle, bucket, stream=stream) if self.autotune else \
+                {"tile": 0, "k_chunk": 0}
+        opts = self._tuned[tkey]
+        qbuf = torch.zeros(qwords, dtype=torch.int32, device=self.device)
+        rbuf = torch.empty(rwords, dtype=torch.int32, device=self.device)
+        torch.cuda.synchronize(self.device)  # buffers written before the capture reads them
+        graph = self.g.pir_graph_create(handle, qbuf, bucket, rbuf, k_chunk=opts["k_chunk"], tile=opts["tile"])
+        entry = [graph, qbuf, rbuf, nbytes, None]  # last: the event of its latest launch
+        self._graphs[key] = entry
+        self._graph_bytes += nbytes
+        return entry
 
     def dispatch(self, handle, params, queries, stream):
         torch = self.torch
         B = len(queries)
         qwords = params.D1 * 2 * params.L * params.n
         rwords = params.D2 * 2 * params.L * params.n
+        entry = None
+        if self.graphs:
+            entry = self._graph_for(handle, params, graph_bucket(B, self.max_batch), stream)
         with torch.cuda.stream(stream):
-            qbuf = torch.empty(B * qwords, dtype=torch.int32, device=self.device)
-            for b, q in enumerate(queries):  # gather: one device-to-device copy per request
-                qbuf[b * qwords:(b + 1) * qwords].copy_(q, non_blocking=True)
-            rbuf = torch.empty(B * rwords, dtype=torch.int32, device=self.device)
-            self.g.pir_answer(handle, qbuf, B, rbuf, stream=stream)
+            if entry is not None:
+                graph, qbuf, rbuf = entry[0], entry[1], entry[2]
+                for b, q in enumerate(queries):  # gather into the graph's bound buffer
+                    qbuf[b * qwords:(b + 1) * qwords].copy_(q, non_blocking=True)
+                if B * qwords < qbuf.numel():
+                    qbuf[B * qwords:].zero_()  # padding rows: zero queries, answers discarded
+                self.g.pir_graph_launch(graph, stream=stream)
+                self.graph_launches += 1
+                bufs = (qbuf, rbuf[:B * rwords])
+            else:
+                qbuf = torch.empty(B * qwords, dtype=torch.int32, device=self.device)
+                for b, q in enumerate(queries):  # gather: one device-to-device copy per request
+                    qbuf[b * qwords:(b + 1) * qwords].copy_(q, non_blocking=True)
+                rbuf = torch.empty(B * rwords, dtype=torch.int32, device=self.device)
+                self.g.pir_answer(handle, qbuf, B, rbuf, stream=stream)
+                bufs = (qbuf, rbuf)
             ev = torch.cuda.Event()
             ev.record(stream)
-        return ev, (qbuf, rbuf)
+        if entry is not None:
+            entry[4] = ev
+        return ev, bufs
 
     def done(self, event) -> bool:
         return event.query()
+
+    def check(self) -> int:
+        try:
+            self.g.pir_check_device()
+        except self.g.PirError as e:
+            return e.status
+        return PIR_OK
 
     def response(self, bufs, b: int, B: int):
         rbuf = bufs[1]

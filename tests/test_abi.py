@@ -170,3 +170,63 @@ def test_answer_buffers_too_small_are_refused_before_the_library(lib):
     with pytest.raises(ValueError):
         g.pir_answer_end(ses, r)
     assert ses.handle == 0xBEEF0  # a refused end leaves the session to the caller
+
+
+def test_every_buffer_taking_call_refuses_short_buffers(lib):
+    """Each call that takes caller buffers checks their sizes against the shapes it
+    documents before the library sees them (a short device buffer would be written
+    past its end, and a captured graph would keep doing so on every launch)."""
+    n, L, D1, D2, B = 2048, 2, 4, 4, 2
+    p = g.pir_make_params(n, 12, D1, D2, L)
+    fake = g.Db(0xDEAD0, p, 0)
+    ct = 2 * L * n  # words of one ciphertext
+    ok_q, ok_r = np.zeros(B * D1 * ct, np.uint32), np.zeros(B * D2 * ct, np.uint32)
+
+    def short(call, *args, **kw):
+        with pytest.raises(ValueError, match="holds"):
+            call(*args, **kw)
+
+    short(g.pir_answer_noalloc, fake, ok_q[:-1], B, ok_r)
+    short(g.pir_answer_noalloc, fake, ok_q, B, ok_r[:-1])
+    short(g.pir_graph_create, fake, ok_q[:-1], B, ok_r)
+    short(g.pir_graph_create, fake, ok_q, B, ok_r[:-1])
+    short(g.pir_graph_create, fake, ok_q, B + 1, ok_r)
+    # packed queries: one ciphertext per query
+    ex = g.Expander(0xBEEF0, p, 2, 4)
+    short(g.pir_answer_packed, fake, ex, np.zeros(B * ct - 1, np.uint32), B, ok_r)
+    short(g.pir_answer_packed, fake, ex, np.zeros(B * ct, np.uint32), B, ok_r[:-1])
+    short(g.pir_expand, ex, np.zeros(B * ct - 1, np.uint32), B, 4, np.zeros(B * 4 * ct, np.uint32))
+    short(g.pir_expand, ex, np.zeros(B * ct, np.uint32), B, 4, np.zeros(B * 4 * ct - 1, np.uint32))
+    short(g.pir_expander_create, p, 2, 4, np.zeros(2 * 4 * ct - 1, np.uint32))
+    # folding: levels = log2 D2 = 2, 2 ell RGSW rows per level
+    ell, lv = 3, 2
+    rg = np.zeros(B * lv * 2 * ell * ct, np.uint32)
+    short(g.pir_answer_folded, fake, ok_q, B, ell, rg[:-1], np.zeros(B * ct, np.uint32))
+    short(g.pir_answer_folded, fake, ok_q, B, ell, rg, np.zeros(B * ct - 1, np.uint32))
+    short(g.pir_answer_folded, fake, ok_q[:-1], B, ell, rg, np.zeros(B * ct, np.uint32))
+    short(g.pir_fold, p, np.zeros(B * 4 * ct - 1, np.uint32), B, lv, ell, rg, np.zeros(B * ct, np.uint32))
+    short(g.pir_fold, p, np.zeros(B * 4 * ct, np.uint32), B, lv, ell, rg[:-1], np.zeros(B * ct, np.uint32))
+    short(g.pir_fold, p, np.zeros(B * 4 * ct, np.uint32), B, lv, ell, rg, np.zeros(B * ct - 1, np.uint32))
+    # scalar-HE GEMM: db [D1][D0] int8, queries [B][D0], out [B][D1]
+    short(g.pir_lwe_answer, np.zeros(64 * 32 - 1, np.int8), 64, 32, np.zeros(B * 32, np.uint32), B,
+          np.zeros(B * 64, np.uint32))
+    short(g.pir_lwe_answer, np.zeros(64 * 32, np.int8), 64, 32, np.zeros(B * 32 - 1, np.uint32), B,
+          np.zeros(B * 64, np.uint32))
+    short(g.pir_lwe_answer, np.zeros(64 * 32, np.int8), 64, 32, np.zeros(B * 32, np.uint32), B,
+          np.zeros(B * 64 - 1, np.uint32))
+    # NTTs with an explicit count larger than the buffer, and a short switched output
+    short(g.ntt_fwd, p, np.zeros(3 * L * n, np.uint32), 4)
+    short(g.ntt_inv, p, np.zeros(3 * L * n, np.uint32), 4)
+    short(g.ntt_inv_modswitch, p, np.zeros(3 * L * n, np.uint32), np.zeros(3 * n - 1, np.uint32))
+    # right-sized buffers pass the size checks and meet the device check instead
+    with pytest.raises(ValueError, match="device"):
+        g.pir_answer_noalloc(fake, ok_q, B, ok_r)
+    with pytest.raises(ValueError, match="device"):
+        g.pir_fold(p, np.zeros(B * 4 * ct, np.uint32), B, lv, ell, rg, np.zeros(B * ct, np.uint32))
+
+
+def test_resident_bytes_follow_the_layout():
+    p = g.pir_make_params(4096, 16, 512, 256, 2)
+    assert binding.resident_db_bytes(p) == 4 << 30
+    assert binding.resident_db_bytes(p, g.PIR_LAYOUT_LIMB) == 4 << 30
+    assert binding.resident_db_bytes(p, g.PIR_LAYOUT_TENSOR) == 8 << 30

@@ -126,3 +126,54 @@ def test_arguments(orc):
         g.pir_expander_free(shallow)
         g.pir_expander_free(other)
         g.pir_free_db(db)
+
+
+def _phase_rows(orc, P, s, ct):
+    """Phase c_a s + c_b of a ciphertext [2][L][n], one row per prime."""
+    out = []
+    for j, q in enumerate(P.qs):
+        sq = (np.asarray(s, dtype=np.int64) % q).astype(np.uint32)
+        out.append((orc.negacyclic_schoolbook(ct[0, j], sq, q).astype(np.uint64) + ct[1, j]) % q)
+    return np.stack(out).astype(np.uint32)
+
+
+def _shift_div(a, C, q):
+    """a X^-C in Z_q[X]/(X^n + 1)."""
+    a = a.astype(np.int64)
+    return np.concatenate([a[C:], (q - a[:C]) % q]).astype(np.uint32) if C else a.astype(np.uint32)
+
+
+@pytest.mark.parametrize("n,L,levels,ell", [(2048, 1, 3, 3), (2048, 2, 3, 4), (2048, 3, 2, 5)])
+def test_expand_phases_with_error_free_keys(orc, n, L, levels, ell):
+    """Keys with uniform masks and zero errors add no noise, so whatever digit order a
+    key switch uses, expanded ciphertext k must have exactly the phase of SealPIR's
+    recursion run on phases: phi <- 2^-levels phi, then per level (g = n/2^j + 1,
+    C = 2^j) phi_k + tau_g(phi_k) at k and phi_k X^-C + tau_g(phi_k X^-C) at k + C."""
+    p = g.pir_make_params(n, 16, 1, 1, L)
+    P = orc.make_params(n, 16, 1, 1, L)
+    s = synth.ternary_secret(n + L, n)
+    zero_e = np.zeros((ell, n), dtype=np.int8)
+    keys = np.stack([orc.ksk_gen(P, s, gal, ell, synth.uniform_residues(lev + 5, synth.STREAM_KEY_A, ell, n, P.qs),
+                                 zero_e) for lev, gal in enumerate(orc.expansion_galois(n, levels))])
+    packed = synth.uniform_residues(L + 9, synth.STREAM_UNIFORM, 2, n, P.qs).reshape(1, 2, L, n)
+    count = 1 << levels
+    ex = g.pir_expander_create(p, levels, ell, keys)
+    try:
+        out = empty_u32(count * 2 * L * n)
+        g.pir_expand(ex, to_dev(packed), 1, count, out)
+        got = from_dev(out, (count, 2, L, n))
+    finally:
+        g.pir_expander_free(ex)
+    phi = _phase_rows(orc, P, s, packed[0])
+    for j, q in enumerate(P.qs):
+        cur = [(phi[j].astype(np.uint64) * pow(1 << levels, -1, q) % q).astype(np.uint32)]
+        for lev, gal in enumerate(orc.expansion_galois(n, levels)):
+            C = 1 << lev
+            nxt = [None] * (2 * C)
+            for k in range(C):
+                sh = _shift_div(cur[k], C, q)
+                nxt[k] = ((cur[k].astype(np.uint64) + orc.automorphism(cur[k], q, gal)) % q).astype(np.uint32)
+                nxt[k + C] = ((sh.astype(np.uint64) + orc.automorphism(sh, q, gal)) % q).astype(np.uint32)
+            cur = nxt
+        for k in range(count):
+            assert np.array_equal(_phase_rows(orc, P, s, got[k])[j], cur[k]), (j, k)

@@ -19,9 +19,12 @@ SHAPES = {  # name -> (n, log2p, D1, D2, layout)
 }
 
 
-def test_mixed_requests_equal_their_answers_alone(orc):
-    be = serving.CudaBackend()
-    srv = serving.Server(be, streams=3, max_batch=4, keep_responses=True)
+@pytest.mark.parametrize("graphs", [False, True])
+def test_mixed_requests_equal_their_answers_alone(orc, graphs):
+    """With graphs, each batch runs as a captured, autotuned answer padded with zero
+    queries to its power-of-two bucket; the answers must not change."""
+    be = serving.CudaBackend(graphs=graphs, max_batch=4)
+    srv = serving.Server(be, streams=3, max_batch=4, keep_responses=True, batch_timeout=60.0)
     pools, raws, P = {}, {}, {}
     for k, (name, (n, log2p, D1, D2, layout)) in enumerate(SHAPES.items()):
         p = g.pir_make_params(n, log2p, D1, D2, 2)
@@ -54,7 +57,9 @@ def test_mixed_requests_equal_their_answers_alone(orc):
                           orc.answer(P[r.db], raws[r.db], Qh))
     g.pir_check_device()
     st = serving.latency_stats(done)
-    assert st["count"] == 40 and st["p99_ms"] >= st["p50_ms"] > 0
+    assert st["count"] == 40 and st["p99_ms"] >= st["p50_ms"] > 0 and st["failed"] == 0
+    if graphs:
+        assert be.graph_launches == len({(r.t_dispatch, r.db) for r in done})  # every batch ran as a graph
     for name in names:
         srv.evict(name)
 

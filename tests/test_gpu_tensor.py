@@ -175,3 +175,99 @@ def test_full_size_1gib_batch32(orc):
         assert orc.freivalds(P, raw, Q, R, synth.freivalds_vector(6, P.qs, D2)) == 0
     finally:
         g.pir_free_db(db)
+
+
+# --- exactness at the f32 boundary -------------------------------------------
+#
+# A residue x < 2^30 becomes signed base-256 digits d_0..d_2 in [-128, 127] and
+# d_3 in [0, 64].  0x7F7F80 has digits (-128, -128, -128, 1), so over a 1024-row
+# K-chunk every (-128) x (-128) digit-pair sum is exactly 1024 * 2^14 = 2^24, the
+# largest integer whose every partial sum f32 must carry without rounding.
+# 0x7F7F7F has digits (127, 127, 127, 0).  With p = 2^23 both values are
+# plaintext coefficients, so a DB of constant polynomials v_i holds v_i in every
+# NTT slot, and so does a query of constant polynomials w_i.  The response to every
+# query row and column is then the constant polynomial sum_i v_i w_i mod q_j: a
+# closed form, checked on every output, besides the oracle on sampled columns.
+
+V_MIN, V_MAX = 0x7F7F80, 0x7F7F7F
+
+
+def digits(x):
+    out = []
+    for _ in range(3):
+        d = x & 255
+        x >>= 8
+        if d >= 128:
+            d -= 256
+            x += 1
+        out.append(d)
+    return out + [x]
+
+
+def constant_db(n, log2p, D1, D2, values):
+    """Raw DB whose polynomial (i, c) is the constant values[i] (log2p-bit LE stream)."""
+    bpp = n * log2p // 8
+    raw = np.zeros((D1, D2, bpp), dtype=np.uint8)
+    v = np.asarray(values, dtype=np.uint64)
+    for k in range(3):
+        raw[:, :, k] = ((v >> np.uint64(8 * k)) & np.uint64(255)).astype(np.uint8)[:, None]
+    return raw.reshape(-1)
+
+
+@pytest.mark.parametrize("case", ["all_minus_128", "alternating_extremes"])
+def test_digit_sums_of_exactly_2_to_24(orc, case):
+    assert digits(V_MIN) == [-128, -128, -128, 1] and digits(V_MAX) == [127, 127, 127, 0]
+    n, log2p, D1, D2, B = 2048, 23, 2048, 64, 8
+    p = g.pir_make_params(n, log2p, D1, D2, 2)
+    P = orc.make_params(n, log2p, D1, D2, 2)
+    assert p.qs == P.qs and all(q > V_MIN for q in p.qs)
+    if case == "all_minus_128":
+        v = [V_MIN] * D1
+        w = [V_MIN] * D1
+    else:  # digit products alternate between +2^14 and -128 * 127 along K
+        v = [V_MIN] * D1
+        w = [V_MIN if i % 2 == 0 else V_MAX for i in range(D1)]
+    raw = constant_db(n, log2p, D1, D2, v)
+    Q = np.zeros((B, D1, 2, 2, n), dtype=np.uint32)
+    Q[..., 0] = np.asarray(w, dtype=np.uint32)[None, :, None, None]
+    db = g.pir_setup_db(p, raw, layout=TENSOR)
+    try:
+        R = run(db, P, Q, B)
+    finally:
+        g.pir_free_db(db)
+    for j, q in enumerate(P.qs):
+        want = sum(a * b for a, b in zip(v, w)) % q
+        assert np.all(R[:, :, :, j, 0] == want), j
+        assert not R[:, :, :, j, 1:].any(), j
+    cols = np.array([0, D2 - 1], dtype=np.uint32)
+    assert np.array_equal(R[[0, B - 1]][:, cols], orc.answer(P, raw, Q[[0, B - 1]], cols=cols))
+
+
+def test_full_size_16gib_batches_32_and_128(orc):
+    """The 16 GiB configuration (n = 4096, 4096 x 512; 128 GiB resident in this
+    layout) at B = 32 and B = 128, in the launch configuration the benchmark times
+    (automatic K-chunks of 1024 rows), on sampled (query, column) outputs the
+    oracle computes one by one."""
+    import torch
+    from test_gpu_fullsize import device_queries, host_query, oracle_columns, setup_on_device
+    n, log2p, D1, D2 = 4096, 16, 4096, 512
+    p = g.pir_make_params(n, log2p, D1, D2, 2)
+    P = orc.make_params(n, log2p, D1, D2, 2)
+    db = setup_on_device(p, 0, layout=TENSOR)
+    try:
+        assert g.pir_db_bytes(db) == 128 << 30
+        for B in (32, 128):
+            seed = 140 + B
+            qd = device_queries(P, B, seed)
+            rd = torch.empty(B * D2 * 2 * 2 * n, dtype=torch.int32, device="cuda")
+            g.pir_answer(db, qd, B, rd)
+            R = rd.view(B, D2, 2, 2, n)
+            for b, cs in ((0, [3, 300]), (B // 2 + 1, [31, 32]), (B - 1, [511, 64])):
+                got = R[b, cs].cpu().numpy().view(np.uint32)
+                assert np.array_equal(got[None], oracle_columns(orc, P, 0, cs, host_query(P, b, seed))), (B, b)
+            g.pir_check_device()
+            del qd, rd, R
+            torch.cuda.empty_cache()
+    finally:
+        g.pir_free_db(db)
+        torch.cuda.empty_cache()

@@ -174,3 +174,93 @@ def test_open_loop_run_and_stats():
     assert st["count"] == len(arr) > 40
     assert 2.0 <= st["p50_ms"] <= st["p99_ms"] < 200
     assert max(calls) <= 4 and sum(calls) == len(arr)
+
+
+class StuckBackend(FakeBackend):
+    """A fake whose batches complete only when the test says so, and whose device
+    check reports a bounded wait that ran out."""
+
+    def __init__(self, clock):
+        super().__init__(clock)
+        self.released = set()
+        self.checks = 0
+
+    def dispatch(self, handle, params, queries, stream):
+        self.batches.append((handle.name, list(queries)))
+        return len(self.batches) - 1, [(handle.salt, q) for q in queries]
+
+    def done(self, event):
+        return event in self.released
+
+    def check(self):
+        self.checks += 1
+        return 5
+
+
+def test_batch_timeout_fails_its_requests_and_holds_the_slot():
+    clock = FakeClock()
+    be = StuckBackend(clock)
+    srv = Server(be, streams=1, max_batch=4, clock=clock, keep_responses=True, batch_timeout=2.0)
+    srv.admit("a", params(), None)
+    for k in range(2):
+        srv.submit(Request(k, "a", k, 0.0))
+    srv.poll()
+    clock.t = 1.0
+    assert srv.poll() == [] and not srv.failed
+    clock.t = 2.5
+    srv.submit(Request(2, "a", 2, 2.5))
+    assert srv.poll() == []
+    assert [r.rid for r in srv.failed] == [0, 1] and all(r.status == 5 for r in srv.failed)
+    assert srv.device_status == 5 and be.checks == 1
+    assert len(be.batches) == 1          # the held slot takes no new batch
+    assert srv.pending() == 1            # only the waiting request counts
+    clock.t = 3.0
+    be.released.add(0)                   # the stuck batch's event finally fires
+    srv.poll()
+    assert len(be.batches) == 2 and be.batches[1][1] == [2]
+    assert srv.done == []                # the failed requests are not reported twice
+    be.released.add(1)
+    clock.t = 3.5
+    srv.poll()
+    assert [r.rid for r in srv.done] == [2] and srv.done[0].response[1] == 2
+    stats = latency_stats([r for r in srv.failed] + srv.done)
+    assert stats["count"] == 1 and stats["failed"] == 2
+
+
+def test_cancel_a_waiting_and_a_running_request():
+    clock, be, srv = make(streams=1, max_batch=2)
+    srv.admit("a", params(), None)
+    for k in range(4):
+        srv.submit(Request(k, "a", k, 0.0))
+    srv.poll()                           # 0 and 1 running, 2 and 3 waiting
+    assert srv.cancel(3) and srv.cancel(1)
+    assert not srv.cancel(99)
+    clock.t = 1.0
+    srv.poll()                           # batch {0, 1} completes; 2 goes out alone
+    assert [r.rid for r in srv.done] == [0] and srv.done[0].response[1] == 0
+    assert sorted(r.rid for r in srv.cancelled) == [1, 3]
+    assert be.batches[1][1] == [2]
+    clock.t = 2.0
+    srv.poll()
+    assert [r.rid for r in srv.done] == [0, 2] and srv.pending() == 0
+    assert all(r.response is None for r in srv.cancelled)
+
+
+def test_per_database_batch_and_slot_caps():
+    clock, be, srv = make(streams=3, max_batch=8, db_max_batch={"big": 2}, db_max_slots={"big": 1})
+    srv.admit("big", params(D1=64), None)
+    srv.admit("small", params(), None)
+    for k in range(6):
+        srv.submit(Request(k, "big", k, 0.0))
+    srv.submit(Request(10, "small", 10, 0.1))
+    srv.poll()
+    # big holds one slot with a batch of 2; small takes another slot at once
+    assert [(d, len(q)) for d, q in be.batches] == [("big", 2), ("small", 1)]
+    clock.t = 1.0
+    srv.poll()
+    assert [(d, len(q)) for d, q in be.batches][2:] == [("big", 2)]
+    clock.t = 2.0
+    srv.poll()
+    clock.t = 3.0
+    srv.poll()
+    assert srv.pending() == 0 and len(srv.done) == 7

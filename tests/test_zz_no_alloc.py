@@ -45,6 +45,36 @@ def test_noalloc_matches_pir_answer_twice(orc, layout, n, log2p, D1, D2, B):
         g.pir_free_db(db)
 
 
+@pytest.mark.parametrize("layout", [0, 1])
+def test_noalloc_folds_several_k_chunks(orc, layout):
+    """A request whose query scratch does not fit the array at once: n = 4096,
+    D1 = 512, B = 8 leave room for 63 folded rows beside the 16 MiB result, so the
+    answer runs in K chunks (63 rows with a ragged tail on the plain layout, 32 on
+    the limb layout), each accumulated into the result.  Equal to pir_answer on two
+    calls in a row, and to the oracle on sampled columns."""
+    n, log2p, D1, D2, B = 4096, 16, 512, 32, 8
+    p = g.pir_make_params(n, log2p, D1, D2, 2)
+    P = orc.make_params(n, log2p, D1, D2, 2)
+    raw = synth.raw_db(520 + layout, synth.raw_db_bytes(n, log2p, D1, D2))
+    db = g.pir_setup_db(p, raw, layout=layout)
+    try:
+        for call in range(2):
+            Q = random_queries(P, B, 700 + 10 * layout + call)
+            qd = to_dev(Q)
+            ref_d = empty_u32(B * D2 * 2 * 2 * n)
+            g.pir_answer(db, qd, B, ref_d)
+            out_d = empty_u32(B * D2 * 2 * 2 * n)
+            out_d.fill_(-1)
+            g.pir_answer_noalloc(db, qd, B, out_d)
+            out = from_dev(out_d, (B, D2, 2, 2, n))
+            assert np.array_equal(out, from_dev(ref_d, (B, D2, 2, 2, n))), call
+        cols = [0, 17, D2 - 1]
+        want = orc.answer(P, raw, Q, cols=cols)
+        assert np.array_equal(out[:, cols], want)
+    finally:
+        g.pir_free_db(db)
+
+
 def test_noalloc_refuses_requests_beyond_its_scratch(orc):
     # result alone: L*n*2B*D2 words = 2*4096*8*512*4 bytes = 128 MiB > 64 MiB
     n, log2p, D1, D2, B = 4096, 16, 32, 512, 4

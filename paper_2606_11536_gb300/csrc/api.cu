@@ -11,7 +11,20 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
+
+namespace {
+// An NVTX range around one call of a public entry point, so that a profiler can
+// select or group the launches of one answer (free when no tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+}  // namespace
 
 namespace gbpir {
 
@@ -671,6 +684,7 @@ uint32_t pir_gemm_tiles(int layout) {
 
 pir_status_t pir_setup_db(const pir_params_t *params, const void *raw_db, size_t raw_bytes, int raw_on_device,
                           int layout, void *stream, pir_db_t *out_handle) {
+  NvtxRange range("pir_setup_db");
   if (!params || !raw_db || !out_handle) return PIR_ERR_ARG;
   if (layout != PIR_LAYOUT_PLAIN && layout != PIR_LAYOUT_LIMB && layout != PIR_LAYOUT_TENSOR) return PIR_ERR_ARG;
   pir_status_t st = validate_params(params);
@@ -775,6 +789,7 @@ pir_status_t pir_setup_db(const pir_params_t *params, const void *raw_db, size_t
 
 pir_status_t pir_answer_ex(pir_db_t db, const uint32_t *queries, uint32_t B, uint32_t *responses, int on_device,
                            void *stream, const pir_answer_opts_t *opts) {
+  NvtxRange range("pir_answer");
   if (!live(db)) return PIR_ERR_HANDLE;
   if (B == 0 || !queries || !responses) return PIR_ERR_ARG;
   pir_answer_opts_t o = {};
@@ -928,12 +943,14 @@ pir_status_t pir_answer_begin(pir_db_t db, uint32_t B, uint32_t kc_max, void *st
 
 pir_status_t pir_answer_chunk(pir_session_t session, const uint32_t *queries, uint32_t i0, uint32_t kc,
                               int on_device) {
+  NvtxRange range("pir_answer_chunk");
   if (!session_live(session) || !live(session->db)) return PIR_ERR_HANDLE;
   const pir_params_t &p = session->db->p;
   return session_chunk(session, queries, (uint64_t)kc * 2 * p.L * p.n, i0, kc, on_device != 0);
 }
 
 pir_status_t pir_answer_end(pir_session_t session, uint32_t *responses, int on_device) {
+  NvtxRange range("pir_answer_end");
   if (!session_take(session)) return PIR_ERR_HANDLE;
   pir_status_t st = session->failed;
   if (st == PIR_OK) {
@@ -956,6 +973,7 @@ pir_status_t pir_answer_abort(pir_session_t session) {
 
 pir_status_t pir_answer_packed(pir_db_t db, pir_expander_t expander, const uint32_t *packed, uint32_t B,
                                uint32_t *responses, int on_device, void *stream, const pir_answer_opts_t *opts) {
+  NvtxRange range("pir_answer_packed");
   if (!live(db)) return PIR_ERR_HANDLE;
   const pir_expander_impl *ex = nullptr;
   if (!expander_view(expander, &ex)) return PIR_ERR_HANDLE;
@@ -1001,6 +1019,7 @@ pir_status_t pir_answer_packed(pir_db_t db, pir_expander_t expander, const uint3
 
 pir_status_t pir_answer_folded(pir_db_t db, const uint32_t *queries, uint32_t B, uint32_t ell, const uint32_t *rgsw,
                                uint32_t *responses, int on_device, void *stream, const pir_answer_opts_t *opts) {
+  NvtxRange range("pir_answer_folded");
   if (!live(db)) return PIR_ERR_HANDLE;
   if (B == 0 || !queries || !rgsw || !responses || ell == 0 || ell > 16) return PIR_ERR_ARG;
   pir_answer_opts_t o = {};
@@ -1068,6 +1087,7 @@ pir_status_t pir_answer(pir_db_t db, const uint32_t *queries, uint32_t B, uint32
 }
 
 static pir_status_t ntt_common(const pir_params_t *params, uint32_t *polys, size_t count, void *stream, bool fwd) {
+  NvtxRange range(fwd ? "ntt_fwd" : "ntt_inv");
   if (!params || (!polys && count)) return PIR_ERR_ARG;
   if (count == 0) return validate_params(params);
   if (!aligned16(polys)) return PIR_ERR_ARG;
@@ -1162,6 +1182,7 @@ static bool graph_live(pir_graph *g) {
 }
 
 pir_status_t pir_graph_launch(pir_graph_t graph, void *stream) {
+  NvtxRange range("pir_graph_launch");
   if (!graph_live(graph)) return PIR_ERR_HANDLE;
   CK(cudaGraphLaunch(graph->exec, static_cast<cudaStream_t>(stream)));
   count_launches(graph->kernels);

@@ -41,13 +41,23 @@ __global__ void __launch_bounds__(256) k_probe_imma(uint32_t iters, uint32_t see
 constexpr int kMadChains = 8;
 
 __global__ void __launch_bounds__(256) k_probe_mad_wide(uint32_t iters, uint32_t seed, uint64_t *__restrict__ sink) {
-  uint32_t a = seed * 2654435761u + threadIdx.x, b = seed ^ (blockIdx.x * 40503u);
+  const uint32_t b = (seed ^ (blockIdx.x * 40503u)) | 1u;
+  uint32_t a[kMadChains];
   uint64_t acc[kMadChains];
 #pragma unroll
-  for (int c = 0; c < kMadChains; ++c) acc[c] = c;
+  for (int c = 0; c < kMadChains; ++c) {
+    a[c] = seed * 2654435761u + threadIdx.x * 97u + c * 0x9e3779b9u;
+    acc[c] = c;
+  }
+  // every multiply-add has its own factor, rotated by one bit per iteration (a funnel
+  // shift, off the multiply-add pipe): no product is shared between chains, none is
+  // loop-invariant, and no chain waits on a multiply-add result for its factor
   for (uint32_t it = 0; it < iters; ++it) {
 #pragma unroll
-    for (int c = 0; c < kMadChains; ++c) asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc[c]) : "r"(a), "r"(b));
+    for (int c = 0; c < kMadChains; ++c) {
+      asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc[c]) : "r"(a[c]), "r"(b));
+      a[c] = __funnelshift_l(a[c], a[c], 1);
+    }
   }
   uint64_t s = 0;
 #pragma unroll

@@ -187,12 +187,13 @@ size_t layout_qs_bytes(int layout, uint64_t nslots, uint32_t Kc, uint32_t Mp) {
   return (size_t)nslots * Kc * Mp * (layout == PIR_LAYOUT_TENSOR ? 8 : 4);
 }
 uint32_t layout_tiles(int layout) {
-  return layout == PIR_LAYOUT_PLAIN ? gemm_plain_tiles() : layout == PIR_LAYOUT_LIMB ? gemm_limb_tiles() : 1;
+  return layout == PIR_LAYOUT_PLAIN ? gemm_plain_tiles() : layout == PIR_LAYOUT_LIMB ? gemm_limb_tiles()
+                                                                                   : gemm_tc_tiles();
 }
 bool layout_tile_ok(int layout, uint32_t tile, uint32_t M, uint32_t Mp, uint32_t D2) {
   if (layout == PIR_LAYOUT_PLAIN) return gemm_plain_tile_ok(tile, M, D2);
   if (layout == PIR_LAYOUT_LIMB) return gemm_limb_tile_ok(tile, Mp);
-  return tile <= 1;
+  return gemm_tc_tile_ok(tile, D2);
 }
 
 // Keep the pool's memory once freed: repeated answers then reuse it instead of
@@ -309,7 +310,7 @@ pir_status_t chunk_gemm(const pir_db *db, const uint32_t *qhat, uint32_t B, uint
                         i0, kc, out, i0 > 0, tile, s));
   else
     CK(launch_gemm_tc(c, static_cast<const uint16_t *>(db->resident), D1, D2, static_cast<const uint16_t *>(qs), M,
-                      Mp, i0, kc, out, i0 > 0, s));
+                      Mp, i0, kc, out, i0 > 0, tile, s));
   tm.end(2, 1);
   return PIR_OK;
 }
@@ -678,7 +679,7 @@ pir_status_t pir_check_device(void *stream) {
 uint32_t pir_gemm_tiles(int layout) {
   if (layout == PIR_LAYOUT_PLAIN) return gemm_plain_tiles();
   if (layout == PIR_LAYOUT_LIMB) return gemm_limb_tiles();
-  if (layout == PIR_LAYOUT_TENSOR) return 1;
+  if (layout == PIR_LAYOUT_TENSOR) return gemm_tc_tiles();
   return 0;
 }
 
@@ -1221,6 +1222,7 @@ pir_status_t pir_autotune(pir_db_t db, uint32_t B, void *stream, uint32_t reps, 
   std::vector<uint32_t> tiles;
   if (db->layout == PIR_LAYOUT_TENSOR) {
     tiles.push_back(1);
+    if (gemm_tc_tile_ok(2, p.D2)) tiles.push_back(2);
   } else if (!limb) {
     if (M <= 2) tiles.push_back(1);
     if (M <= 4) tiles.push_back(2);

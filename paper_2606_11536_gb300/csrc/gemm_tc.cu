@@ -62,6 +62,9 @@ constexpr uint32_t kTmemCols = 512;                   // the whole tensor memory
 constexpr uint32_t kTmemBudget = kTmemCols / 2;        // one of two accumulator buffers
 constexpr uint32_t kSmemBudget = 200u << 10, kSmemFloor = 116u << 10;
 constexpr uint32_t kBlockBytes = 128 * 16 * 2;  // one 128-row x K16 bf16 block
+// The 2-SM form: stage budget, and a spare run after the barriers so that no operand
+// read of the last stage can leave the CTA's shared memory.
+constexpr uint32_t kSmemBudget2 = 200u << 10, kSpareBytes2 = 8u << 10;
 
 // Signed base-256 digits of x < 2^30.
 __device__ __forceinline__ void digits4(uint32_t x, int (&d)[4]) {
@@ -360,6 +363,281 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcArgs a, ModConst mc) 
   }
 }
 
+// ---------------------------------------------------------------------------
+// The 2-SM form: one MMA per CTA pair (cta_group::2, M = 256).
+//
+// A cluster of two CTAs on two SMs takes a unit of 64 DB columns: each CTA holds
+// its own 32 columns (128 A rows = (column, digit) pairs) and half of the query
+// digits (N/2 B rows); the pair's MMA, issued by the even CTA, reads A from both
+// CTAs' shared memory (rows 0..127 from the even CTA, 128..255 from the odd one)
+// and B as the two halves, and leaves each CTA the accumulator rows of its own A
+// half, [128 lanes][N columns], in its own tensor memory.  Per SM and MMA that is
+// 4 KiB of DB digits plus N/2 x 32 bytes of query digits instead of N x 32 bytes:
+// a third fewer operand bytes than the 1-SM form at N = 256, so the same stages
+// in flight keep the tensor cores busy for longer.
+//
+// Barriers (mbarriers at the same shared-memory offsets in both CTAs):
+//   full[st]    local: this CTA's stage `st` has arrived (expect-tx by its producer)
+//   pfull[st]   even CTA only: the odd CTA's stage `st` has arrived (one remote
+//               arrive by the odd CTA's relay thread, which waits on its own full)
+//   empty[st]   both: the pair's MMAs have read stage `st` (multicast commit)
+//   tfull[b]    both: accumulator buffer b is complete (multicast commit)
+//   tempty[b]   even CTA only: both CTAs' epilogues have drained buffer b
+//               (2 x kEpiWarps arrivals, the odd CTA's remote)
+// Every wait is bounded; the end is a cluster barrier, after which both CTAs
+// release the pair's tensor memory.
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Arrive on the mbarrier at local offset `bar` in CTA `rank` of the cluster.
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar, uint32_t rank) {
+  uint32_t remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(bar), "r"(rank));
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote) : "memory");
+}
+
+__device__ __forceinline__ void mma_bf16_pair(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                              uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Arrive on `bar` in both CTAs of the pair once the pair MMAs issued so far complete.
+__device__ __forceinline__ void mma_commit_pair(uint32_t bar) {
+  const uint16_t both = 0x3;
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+      "h"(both)
+      : "memory");
+}
+
+// The pair's work unit u = (slot s, query-row tile mt, column-tile pair cp), cp fastest.
+__device__ __forceinline__ Unit unit_of_pair(const TcArgs &a, uint32_t u, uint32_t rank) {
+  Unit w;
+  const uint32_t pairs = a.ctiles / 2;
+  const uint32_t cp = u % pairs;
+  const uint32_t rest = u / pairs;
+  w.ct = 2 * cp + rank;
+  w.mt = rest % a.mtiles;
+  w.s = rest / a.mtiles;
+  const uint32_t Ntot = 4 * a.Mp;
+  w.n0 = w.mt * 256;
+  w.Nt = Ntot - w.n0 < 256 ? Ntot - w.n0 : 256;
+  return w;
+}
+
+constexpr int kMaxStages2 = 8;
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_gemm_tc2(TcArgs a, ModConst mc) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + a.S * a.stage_bytes);
+  const uint32_t full0 = saddr(bars), empty0 = saddr(bars + kMaxStages2), pfull0 = saddr(bars + 2 * kMaxStages2);
+  const uint32_t tfull0 = saddr(bars + 3 * kMaxStages2), tempty0 = saddr(bars + 3 * kMaxStages2 + 2);
+  const uint32_t done = saddr(bars + 3 * kMaxStages2 + 4);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 3 * kMaxStages2 + 5);
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank(), cluster = blockIdx.x >> 1, nclusters = gridDim.x >> 1;
+  const uint32_t R = 4 * a.D2, U = a.D1 / 16, Uc = a.Kc / 16;
+  const uint32_t nst = Uc / a.KS16, Ntot = 4 * a.Mp;
+  const uint32_t db_stage = a.KS16 * kBlockBytes;
+
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < kMaxStages2; ++st) {
+      mbar_init(full0 + 8 * st, 1);
+      mbar_init(empty0 + 8 * st, 1);
+      mbar_init(pfull0 + 8 * st, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull0 + 8 * b, 1);
+      mbar_init(tempty0 + 8 * b, 2 * kEpiWarps);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == kMmaWarp) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tslot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  cluster_sync();  // both CTAs' barriers exist before any remote arrive or multicast commit
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+
+  if (warp == kProducerWarp) {
+    if (lane == 0) {
+      const uint64_t pol_db = async::policy_evict_first(), pol_q = async::policy_evict_last();
+      const uint8_t *dbs = reinterpret_cast<const uint8_t *>(a.db);
+      const uint8_t *qs = reinterpret_cast<const uint8_t *>(a.qt);
+      uint32_t it = 0;
+      bool ok = true;
+      for (uint32_t u = cluster; ok && u < a.nunits; u += nclusters) {
+        const Unit w = unit_of_pair(a, u, rank);
+        const uint32_t half = w.Nt / 2, qbytes = a.KS16 * half * 32;
+        for (uint32_t st = 0; st < nst; ++st, ++it) {
+          const uint32_t slot = it % a.S, ph = (it / a.S) & 1;
+          if (!wait_bounded(empty0 + 8 * slot, ph ^ 1)) {
+            atomicExch(a.err, 1u);
+            ok = false;
+            break;
+          }
+          const uint32_t dst = saddr(smem + slot * a.stage_bytes);
+          mbar_expect_tx(full0 + 8 * slot, db_stage + qbytes);
+          for (uint32_t v = 0; v < a.KS16; ++v) {
+            const uint64_t uu = a.i0 / 16 + (uint64_t)st * a.KS16 + v;
+            const uint64_t e = (((uint64_t)w.s * U + uu) * R + (uint64_t)w.ct * 128) * 16;
+            bulk_g2s(dst + v * kBlockBytes, dbs + 2 * e, kBlockBytes, full0 + 8 * slot, pol_db);
+          }
+          for (uint32_t v = 0; v < a.KS16; ++v) {  // this CTA's half of the stage's query rows
+            const uint64_t e = (((uint64_t)w.s * Uc + (uint64_t)st * a.KS16 + v) * Ntot + w.n0 + rank * half) * 16;
+            bulk_g2s(dst + db_stage + v * half * 32, qs + 2 * e, half * 32, full0 + 8 * slot, pol_q);
+          }
+        }
+      }
+      // drain: never leave with copies in flight
+      const uint32_t first = it > a.S ? it - a.S : 0;
+      for (uint32_t k = first; k < it; ++k)
+        if (!wait_bounded(full0 + 8 * (k % a.S), (k / a.S) & 1)) atomicExch(a.err, 1u);
+    }
+    __syncwarp();
+  } else if (warp == kMmaWarp) {
+    if (lane == 0 && rank == 1) {
+      // relay: tell the even CTA's MMA thread when this CTA's stages have arrived
+      uint32_t it = 0;
+      bool ok = true;
+      for (uint32_t u = cluster; ok && u < a.nunits; u += nclusters)
+        for (uint32_t st = 0; st < nst; ++st, ++it) {
+          if (!wait_bounded(full0 + 8 * (it % a.S), (it / a.S) & 1)) {
+            atomicExch(a.err, 1u);
+            ok = false;
+            break;
+          }
+          mbar_arrive_cluster(pfull0 + 8 * (it % a.S), 0);
+        }
+    } else if (lane == 0) {
+      uint32_t it = 0, k = 0;
+      bool ok = true;
+      for (uint32_t u = cluster; ok && u < a.nunits; u += nclusters, ++k) {
+        const Unit w = unit_of_pair(a, u, 0);
+        const uint32_t buf = k % a.nbuf, use = k / a.nbuf, half = w.Nt / 2;
+        if (!wait_bounded(tempty0 + 8 * buf, (use & 1) ^ 1)) {  // both epilogues have drained this buffer
+          atomicExch(a.err, 1u);
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t idesc = instr_desc(256, w.Nt), dcol = tmem + buf * a.buf_cols;
+        for (uint32_t st = 0; st < nst; ++st, ++it) {
+          const uint32_t slot = it % a.S, ph = (it / a.S) & 1;
+          if (!wait_bounded(full0 + 8 * slot, ph) || !wait_bounded(pfull0 + 8 * slot, ph)) {
+            atomicExch(a.err, 1u);
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t base = saddr(smem + slot * a.stage_bytes);
+          for (uint32_t v = 0; v < a.KS16; ++v) {
+            const uint64_t adesc = smem_desc(base + v * kBlockBytes);
+            const uint64_t bdesc = smem_desc(base + db_stage + v * half * 32);
+            mma_bf16_pair(dcol, adesc, bdesc, idesc, (st | v) != 0);
+          }
+          mma_commit_pair(empty0 + 8 * slot);  // both CTAs' stage is free once these MMAs have read it
+        }
+        mma_commit_pair(tfull0 + 8 * buf);  // this unit's accumulators are complete in both CTAs
+      }
+      // on every path: no MMA may still be running when the tensor memory is freed
+      asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(done)
+                   : "memory");
+      if (!wait_bounded(done, 0)) atomicExch(a.err, 1u);
+    }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue: warps 0..7 of each CTA, on its own accumulator rows ----------------
+    const uint32_t quarter = warp & 3, b = lane & 3;
+    const uint32_t row = 32 * quarter + lane;  // accumulator lane: column c_local = row / 4, DB digit b
+    const bool hi2 = (b & 2) != 0, hi1 = (b & 1) != 0;
+    uint32_t k = 0;
+    for (uint32_t u = cluster; u < a.nunits; u += nclusters, ++k) {
+      const Unit w = unit_of_pair(a, u, rank);
+      const uint32_t buf = k % a.nbuf, use = k / a.nbuf;
+      if (!__all_sync(0xffffffffu, wait_bounded(tfull0 + 8 * buf, use & 1))) {
+        if (lane == 0) atomicExch(a.err, 1u);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t j = w.s >> a.logn;
+      const uint32_t q = pick(mc.q, j);
+      const uint64_t mu = pick(mc.mu, j);
+      const int64_t off = (int64_t)q << 29;  // > 2^58 > |sum of the 16 weighted digit products|
+      uint32_t pw[7];
+      pw[0] = 1;
+#pragma unroll
+      for (int t = 1; t < 7; ++t) pw[t] = reduce64((uint64_t)pw[t - 1] << 8, q, mu);
+      int32_t wgt[4];
+#pragma unroll
+      for (int d = 0; d < 4; ++d)
+        wgt[d] = (int32_t)(b == 0 ? pw[d] : b == 1 ? pw[d + 1] : b == 2 ? pw[d + 2] : pw[d + 3]);
+      const uint32_t G = w.Nt / 32;
+      const uint32_t c = w.ct * 32 + (row >> 2);
+      for (uint32_t g = warp >> 2; g < G; g += kEpiWarps / 4) {
+        uint32_t f[32];
+        tmem_ld32(tmem + buf * a.buf_cols + ((32 * quarter) << 16) + 32 * g, f);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          int64_t sum[4];
+#pragma unroll
+          for (int mm = 0; mm < 4; ++mm) {
+            int64_t v = 0;
+#pragma unroll
+            for (int d = 0; d < 4; ++d)
+              v = mad_wide(__float2int_rn(__uint_as_float(f[16 * h + 4 * mm + d])), wgt[d], v);
+            sum[mm] = v;
+          }
+          int64_t k0 = hi2 ? sum[2] : sum[0], k1 = hi2 ? sum[3] : sum[1];
+          const int64_t o0 = hi2 ? sum[0] : sum[2], o1 = hi2 ? sum[1] : sum[3];
+          k0 += __shfl_xor_sync(0xffffffffu, o0, 2);
+          k1 += __shfl_xor_sync(0xffffffffu, o1, 2);
+          int64_t mine = hi1 ? k1 : k0;
+          mine += __shfl_xor_sync(0xffffffffu, hi1 ? k0 : k1, 1);
+          const uint32_t m = w.n0 / 4 + 8 * g + 4 * h + b;
+          if (m < a.M) {
+            uint32_t r = reduce64((uint64_t)(mine + off), q, mu);
+            uint32_t *o = a.out + ((uint64_t)w.s * a.M + m) * a.D2 + c;
+            if (a.acc_in) {
+              r += *o;
+              if (r >= q) r -= q;
+            }
+            *o = r;
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cluster(tempty0 + 8 * buf, 0);
+    }
+  }
+
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  cluster_sync();  // the pair's MMAs are complete and both epilogues are done with the tensor memory
+  if (warp == kMmaWarp) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
+                 : "memory");
+  }
+}
+
 // Two digits (|d| < 2^22) as a bf16 pair, exactly: 1.5 * 2^23 + d is exact in f32
 // with unit spacing, so adding d to that constant's bit pattern and subtracting the
 // constant gives (float)d; a digit of at most 8 significant bits leaves the low 16
@@ -460,6 +738,11 @@ __global__ void k_db_read_poly_tensor(const uint16_t *__restrict__ res, uint64_t
 
 bool gemm_tc_shape_ok(uint32_t D1, uint32_t D2) { return D1 % 64 == 0 && D2 % 32 == 0; }
 
+// Tensor-layout GEMM forms: 0 = automatic (the 1-SM form, measured faster), 1 = one
+// SM per unit (k_gemm_tc), 2 = CTA pairs (k_gemm_tc2; D2 a multiple of 64).
+uint32_t gemm_tc_tiles() { return 2; }
+bool gemm_tc_tile_ok(uint32_t tile, uint32_t D2) { return tile <= 1 || (tile == 2 && D2 % 64 == 0); }
+
 uint32_t tc_rows(uint32_t M) { return (M + 7u) & ~7u; }
 
 cudaError_t launch_query_to_tensor(const ParamCtx &c, const uint32_t *qhat, uint32_t B, uint32_t Kc, uint32_t Mp,
@@ -485,13 +768,79 @@ cudaError_t launch_db_read_poly_tensor(const ParamCtx &c, uint32_t D1, uint32_t 
   return cudaGetLastError();
 }
 
+// The 2-SM form (k_gemm_tc2): clusters of two CTAs, each unit 64 DB columns.
+cudaError_t launch_gemm_tc_pair(const ParamCtx &c, const uint16_t *db, uint32_t D1, uint32_t D2, const uint16_t *qt,
+                                uint32_t M, uint32_t Mp, uint32_t i0, uint32_t Kc, uint32_t *out, int acc,
+                                cudaStream_t s) {
+  uint32_t *err = nullptr;
+  cudaError_t e = device_error_word(&err);
+  if (e != cudaSuccess) return e;
+  TcArgs a = {};
+  a.db = db;
+  a.qt = qt;
+  a.out = out;
+  a.err = err;
+  a.M = M;
+  a.Mp = Mp;
+  a.D1 = D1;
+  a.D2 = D2;
+  a.i0 = i0;
+  a.Kc = Kc;
+  const uint32_t Ntot = 4 * Mp, Nmax = Ntot < 256 ? Ntot : 256;
+  a.mtiles = (Ntot + 255) / 256;
+  a.T = 1;
+  a.nbuf = 2;
+  a.buf_cols = kTmemBudget;
+  a.ctiles = D2 / 32;
+  // per CTA and K16 step: its 128 DB digit rows and half of the query digit rows
+  const uint32_t per16 = kBlockBytes + (Nmax / 2) * 32;
+  uint32_t ks = 4;
+  while (ks > 1 && (Kc / 16) % ks) ks /= 2;
+  a.KS16 = ks;
+  a.stage_bytes = ks * per16;
+  uint32_t S = kSmemBudget2 / a.stage_bytes;
+  if (S > (uint32_t)kMaxStages2) S = kMaxStages2;
+  if (S < 2) return cudaErrorInvalidValue;
+  a.S = S;
+  a.logn = c.logn;
+  a.acc_in = acc;
+  const uint64_t nunits = (uint64_t)(c.p.L << c.logn) * (a.ctiles / 2) * a.mtiles;
+  if (nunits > 0x7fffffffull) return cudaErrorInvalidValue;
+  a.nunits = (uint32_t)nunits;
+  // stages | full, empty, pfull (kMaxStages2 each), two tensor-memory full/empty pairs,
+  // done | tensor-memory address | a spare run past the end
+  size_t smem = (size_t)S * a.stage_bytes + (3 * kMaxStages2 + 5) * 8 + 16 + kSpareBytes2;
+  if (smem < kSmemFloor) smem = kSmemFloor;
+  e = cudaFuncSetAttribute(k_gemm_tc2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  // clusters that fit at once (the pairs land on SM pairs); every cluster loops over its units
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(sms & ~1), 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  int nclusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&nclusters, k_gemm_tc2, &cfg) != cudaSuccess || nclusters <= 0) {
+    cudaGetLastError();  // clear the query's error: fall back to one cluster per SM pair
+    nclusters = sms / 2;
+  }
+  if ((uint64_t)nclusters > nunits) nclusters = (int)nunits;
+  k_gemm_tc2<<<2 * (unsigned)nclusters, kThreads, smem, s>>>(a, c.mod);
+  return cudaGetLastError();
+}
+
 // out[s][m][c] (+)= sum_{i < Kc} Q[s][i][m] * DB[s][i0 + i][c] mod q_j for the
 // query digits qt of one K-chunk (Mp = tc_rows(M) rows).
 cudaError_t launch_gemm_tc(const ParamCtx &c, const uint16_t *db, uint32_t D1, uint32_t D2, const uint16_t *qt,
-                           uint32_t M, uint32_t Mp, uint32_t i0, uint32_t Kc, uint32_t *out, int acc, cudaStream_t s) {
+                           uint32_t M, uint32_t Mp, uint32_t i0, uint32_t Kc, uint32_t *out, int acc, uint32_t tile,
+                           cudaStream_t s) {
   if (!gemm_tc_shape_ok(D1, D2) || Kc == 0 || Kc % 64 != 0 || Kc > 1024 || i0 % 64 != 0 || i0 + Kc > D1 ||
-      Mp % 8 != 0 || Mp < M)
+      Mp % 8 != 0 || Mp < M || !gemm_tc_tile_ok(tile, D2))
     return cudaErrorInvalidValue;
+  if (tile == 2) return launch_gemm_tc_pair(c, db, D1, D2, qt, M, Mp, i0, Kc, out, acc, s);
   uint32_t *err = nullptr;
   cudaError_t e = device_error_word(&err);
   if (e != cudaSuccess) return e;

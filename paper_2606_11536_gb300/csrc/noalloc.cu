@@ -111,7 +111,7 @@ extern "C" pir_status_t pir_answer_noalloc(pir_db_t db, const uint32_t *queries,
       if ((e = launch_query_to_tensor(c, qhat, B, kc, Mp, static_cast<uint16_t *>(qs), s)) != cudaSuccess)
         return cuda_status(e);
       e = launch_gemm_tc(c, static_cast<const uint16_t *>(v.resident), D1, D2, static_cast<const uint16_t *>(qs), M,
-                         Mp, i0, kc, out, i0 > 0, s);
+                         Mp, i0, kc, out, i0 > 0, 0, s);
     } else if (!limb) {
       if ((e = launch_query_to_slots(c, qhat, B, kc, Mp, static_cast<uint32_t *>(qs), s)) != cudaSuccess)
         return cuda_status(e);

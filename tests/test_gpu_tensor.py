@@ -271,3 +271,23 @@ def test_full_size_16gib_batches_32_and_128(orc):
     finally:
         g.pir_free_db(db)
         torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("B", [1, 4, 32, 40, 64])
+def test_one_sm_and_two_sm_forms_agree_with_the_oracle(orc, B):
+    """The 1-SM GEMM (tile 1) and the CTA-pair GEMM (tile 2: one tcgen05 MMA over two
+    SMs, M = 256) against the oracle, on D2 = 192 (three column-tile pairs), query
+    rows that leave a ragged second 256-row tile at B = 40 and 64, and two K-chunks."""
+    p, P, raw, db = instance(orc, 2048, 256, 192, seed=130 + B)
+    try:
+        Q = random_queries(P, B, 131 + B)
+        cols = np.array([0, 63, 64, 191], dtype=np.uint32)
+        want = orc.answer(P, raw, Q, cols=cols)
+        for tile in (1, 2):
+            for kc in (0, 128):
+                R = run(db, P, Q, B, tile=tile, k_chunk=kc)
+                assert np.array_equal(R[:, cols], want), (tile, kc)
+        R1, R2 = run(db, P, Q, B, tile=1), run(db, P, Q, B, tile=2)
+        assert np.array_equal(R1, R2)
+    finally:
+        g.pir_free_db(db)

@@ -440,6 +440,8 @@ def measure_batch(ctx, db, p, layout, B, steps, warmup, min_seconds=0.0, extras=
             g.pir_answer_folded(db, qbufs[t % nbuf], B, args.ell, rg, rs, stream=st, flags=flags | msw, tile=args.tile)
         elif ex is not None:
             g.pir_answer_packed(db, ex, qbufs[t % nbuf], B, rs, stream=st, flags=flags | msw, tile=args.tile)
+        elif args.noalloc:
+            g.pir_answer_noalloc(db, qbufs[t % nbuf], B, rs, stream=st)
         else:
             g.pir_answer_ex(db, qbufs[t % nbuf], B, rs, stream=st, flags=flags | msw, tile=args.tile,
                             k_chunk=args.k_chunk)
@@ -486,6 +488,8 @@ def measure_batch(ctx, db, p, layout, B, steps, warmup, min_seconds=0.0, extras=
     gemm_launches = max(1, stage_launches[2])
     launches_per_step = gemm_launches / steps
     gemm_ms = stage_ms[2] / steps  # GEMM kernel time per step
+    if stage_launches[2] == 0:  # an entry point without stage events: the whole step bounds the GEMM
+        gemm_ms, launches_per_step = max_ms / steps, 1.0
     roofline = gemm_roofline(ctx, layout, B, p, args.tile, gemm_ms, launches_per_step, clocks, stream)
     roofline["stage_ms_per_step"] = {name: stage_ms[i] / steps for i, name in enumerate(ctx.binding.STAGE_NAMES)}
     out = {"batch": B, "value": raw_bytes * total_queries / (max_ms / 1e3) / 1e9, "unit": "GB/s",
@@ -590,7 +594,7 @@ def our_arm(args, wl):
 
     # the metric's batch range and the tensor layout, on the default workload (one GPU)
     plain_mode = layout == g.PIR_LAYOUT_PLAIN and not extras and args.streams == 1 and args.tile == 0 and \
-        args.k_chunk == 0 and not args.modswitch and wl == DEFAULT_WORKLOAD
+        args.k_chunk == 0 and not args.modswitch and not args.noalloc and wl == DEFAULT_WORKLOAD
     per_batch = tensor_block = None
     if world == 1 and plain_mode and args.per_batch:
         per_batch = []
@@ -660,6 +664,7 @@ def our_arm(args, wl):
                                      if args.folded else "D2 ciphertexts each"),
                        "queries": ("packed, expanded on the GPU (levels %d, %d gadget digits; timing-only keys)"
                                    % ((D1 - 1).bit_length(), args.ell) if args.packed else "D1 ciphertexts each"),
+                       "entry": "pir_answer_noalloc" if args.noalloc else "pir_answer_ex",
                        "parallelism": "replicas x%d" % world,
                        "l2": "inputs larger than L2: the %.1f GiB NTT-form DB is streamed every step; query "
                              "buffers rotate when small" % (binding.resident_db_bytes(p, layout) / 2 ** 30)},
@@ -868,6 +873,11 @@ def serving_bench(args):
     if admitted:
         pools[name] = [synth.uniform_residues_torch(990 + t, synth.STREAM_UNIFORM, D1 * 2, n, p.qs,
                                                     device="cuda").view(-1) for t in range(4)]
+    prewarm_s = 0.0
+    if args.serving_graphs:
+        t1 = time.perf_counter()
+        be.prewarm(srv)
+        prewarm_s = time.perf_counter() - t1
     results = []
     for rate in args.serving_rates:
         arr = serving.poisson_arrivals(rate, args.serving_seconds, dbs, seed=int(rate),
@@ -897,7 +907,7 @@ def serving_bench(args):
                        "streams": args.serving_streams, "max_batch": args.serving_max_batch,
                        "layout": args.serving_layout, "graphs": bool(args.serving_graphs),
                        "big_db_slot_cap": args.serving_big_slots, "batch_timeout_s": args.serving_timeout,
-                       "seconds_per_load": args.serving_seconds, "setup_s": setup_s,
+                       "seconds_per_load": args.serving_seconds, "setup_s": setup_s, "graph_prewarm_s": prewarm_s,
                        "resident_bytes": srv.resident_bytes},
             "graph_launches": be.graph_launches, "failed": len(srv.failed), "loads": results}
     print(json.dumps(line), flush=True)
@@ -935,6 +945,8 @@ def main(argv=None):
     ap.add_argument("--modswitch", action="store_true",
                     help="switch the responses to the single prime q_0 inside the inverse NTT")
     ap.add_argument("--ntt-sweep", action="store_true", help="time the standalone NTT sweep instead")
+    ap.add_argument("--noalloc", action="store_true",
+                    help="answer through pir_answer_noalloc (the library's fixed scratch array, no allocation)")
     ap.add_argument("--serving", action="store_true", help="run the serving benchmark instead")
     ap.add_argument("--serving-rates", type=float, nargs="+", default=[100, 300, 1000, 3000, 5000])
     ap.add_argument("--serving-seconds", type=float, default=2.0)

@@ -345,7 +345,9 @@ class CudaBackend(Backend):
     per (database, bucket).  The graph's query and response buffers stay bound to it;
     a slot runs one batch at a time, so its graphs' buffers are free whenever the
     slot is.  Graphs are kept within graph_budget bytes of bound buffers, least
-    recently used first out; a batch that does not fit runs uncaptured."""
+    recently used first out; a graph above an eighth of the budget is not made, and
+    such a batch, like any that does not fit, runs uncaptured.  prewarm() makes the
+    graphs before serving starts."""
 
     def __init__(self, device: int = 0, graphs: bool = False, max_batch: int = 32, graph_budget: int = 16 << 30,
                  autotune: bool = True):
@@ -386,6 +388,17 @@ class CudaBackend(Backend):
         self.g.pir_graph_destroy(graph)
         self._graph_bytes -= nbytes
 
+    def prewarm(self, server, buckets=None):
+        """Autotune and capture the graphs of every resident database, batch bucket
+        and slot ahead of serving (a server does this at start-up, so the first
+        requests do not pay for it).  Skips what does not fit the graph budget."""
+        buckets = buckets or sorted({graph_bucket(b, self.max_batch) for b in range(1, self.max_batch + 1)})
+        for name, info in server.dbs.items():
+            for bucket in buckets:
+                for slot in server.slots:
+                    self._graph_for(info["handle"], info["params"], bucket, slot.stream)
+        self.torch.cuda.synchronize(self.device)
+
     def _graph_for(self, handle, params, bucket, stream):
         key = (id(handle), bucket, id(stream))
         if key in self._graphs:
@@ -395,7 +408,9 @@ class CudaBackend(Backend):
         qwords = bucket * params.D1 * 2 * params.L * params.n
         rwords = bucket * params.D2 * 2 * params.L * params.n
         nbytes = 4 * (qwords + rwords)
-        if nbytes > self.graph_budget:
+        if nbytes > self.graph_budget // 8:
+            # a graph this large would crowd out the others: such batches run uncaptured,
+            # rather than evicting and re-capturing graphs batch after batch
             return None
         while self._graph_bytes + nbytes > self.graph_budget:
             # least recently used first, and never a graph whose last launch is still

@@ -127,11 +127,13 @@ typedef struct {
   uint32_t tile;     /* 0 = built-in choice; else a GEMM tile id (pir_gemm_tiles) that
                         holds the batch: plain 1, 2, 3 and 7 take at most 2, 4, 8 and
                         8 query rows (2B), 7 also D2 <= 512; limb 2 and 3 need the
-                        rows padded to 16 to be multiples of 32 and 64; otherwise
-                        PIR_ERR_ARG */
+                        rows padded to 16 to be multiples of 32 and 64; tensor 1 is
+                        the 1-SM GEMM, 2 the CTA-pair (2-SM) GEMM, which needs
+                        D2 % 64 == 0; otherwise PIR_ERR_ARG */
   uint32_t flags;    /* PIR_ANSWER_STAGE_TIMES: record CUDA events around each stage on
                         `stream`, read with pir_stage_times; PIR_ANSWER_TEST_STALL,
-                        PIR_ANSWER_MODSWITCH: see below.  Other bits must be 0. */
+                        PIR_ANSWER_MODSWITCH, PIR_ANSWER_CHECK_INPUTS: see below.
+                        Other bits must be 0. */
 } pir_answer_opts_t;
 
 #define PIR_ANSWER_STAGE_TIMES 1u
@@ -145,6 +147,14 @@ typedef struct {
  * responses are then [B][D2][2][n] uint32 over q_0, coefficient form, canonical
  * (half the bytes at L = 2), as ntt_inv_modswitch below computes them. */
 #define PIR_ANSWER_MODSWITCH 4u
+/* Input validation: before computing, check on the device that every query
+ * residue is canonical (below its prime q_j; the answer is only defined for such
+ * inputs) and return PIR_ERR_ARG if one is not.  Costs one extra read of the
+ * queries and a stream synchronization, so it is off by default.  Accepted by
+ * pir_answer_ex on device buffers and on host batches up to 4 GiB (checked after
+ * the upload); refused (PIR_ERR_ARG) by the streamed answer, graphs and the
+ * no-allocation entry point. */
+#define PIR_ANSWER_CHECK_INPUTS 8u
 
 /* Stages of one answer, in order: forward NTT of the queries, query transpose to
  * the slot-major layout, modular GEMM (with its reduction epilogue), result

@@ -417,6 +417,7 @@ def pir_gemm_tiles(layout: int) -> int:
 PIR_ANSWER_STAGE_TIMES = 1
 PIR_ANSWER_TEST_STALL = 2
 PIR_ANSWER_MODSWITCH = 4
+PIR_ANSWER_CHECK_INPUTS = 8
 PIR_STAGES = 5
 STAGE_NAMES = ("query_ntt", "query_transpose", "gemm", "result_transpose", "intt")
 

@@ -351,9 +351,22 @@ pir_status_t answer_device(pir_db *db, const uint32_t *queries, uint32_t B, uint
   }
   const uint64_t nslots = (uint64_t)L * n;
   if (o.tile > layout_tiles(db->layout) ||
-      (o.flags & ~(PIR_ANSWER_STAGE_TIMES | PIR_ANSWER_TEST_STALL | PIR_ANSWER_MODSWITCH)) != 0)
+      (o.flags & ~(PIR_ANSWER_STAGE_TIMES | PIR_ANSWER_TEST_STALL | PIR_ANSWER_MODSWITCH |
+                   PIR_ANSWER_CHECK_INPUTS)) != 0)
     return PIR_ERR_ARG;
   if (!layout_tile_ok(db->layout, o.tile, M, Mp, D2)) return PIR_ERR_ARG;
+  if ((o.flags & PIR_ANSWER_CHECK_INPUTS) && !qhat_ready) {
+    // every query residue canonical (below its prime) before anything is computed
+    Scratch chk(s);
+    CK(chk.alloc(sizeof(uint32_t)));
+    CK(cudaMemsetAsync(chk.ptr, 0, sizeof(uint32_t), s));
+    CK(launch_check_residues(c, queries, (uint64_t)B * D1 * 2 * L, static_cast<uint32_t *>(chk.ptr), s));
+    uint32_t bad = 0;
+    CK(cudaMemcpyAsync(&bad, chk.ptr, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    count_launches(1);
+    if (bad) return PIR_ERR_ARG;
+  }
   // With modulus switching the inverse NTT reads the full-modulus responses from
   // scratch and writes [B][D2][2][n] over q_0 to `responses`.
   const bool msw = (o.flags & PIR_ANSWER_MODSWITCH) != 0 && !ntt_out;

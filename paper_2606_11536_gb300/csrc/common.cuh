@@ -119,6 +119,10 @@ cudaError_t launch_ntt_fwd_raw(const ParamCtx &c, const uint8_t *raw, int col_ma
                                uint64_t first, uint64_t npolys, uint32_t *dst, cudaStream_t s);
 
 // layout.cu (layouts are described at the top of layout.cu)
+// Sets *bad (device word) when a residue of rows [nrows][n] is not below its prime
+// (row r over q_{r % L}).
+cudaError_t launch_check_residues(const ParamCtx &c, const uint32_t *rows, uint64_t nrows, uint32_t *bad,
+                                  cudaStream_t s);
 cudaError_t launch_query_to_slots(const ParamCtx &c, const uint32_t *qhat, uint32_t B, uint32_t Kc, uint32_t Mp,
                                   uint32_t *qs, cudaStream_t s);
 cudaError_t launch_query_to_limbs(const ParamCtx &c, const uint32_t *qhat, uint32_t B, uint32_t Kc, uint32_t Mp,

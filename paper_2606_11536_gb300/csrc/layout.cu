@@ -304,4 +304,33 @@ cudaError_t launch_db_read_poly(const ParamCtx &c, int layout, uint32_t D1, uint
   return cudaGetLastError();
 }
 
+// Range check of residue rows: rows [rows][n], row r over prime q_{r % L}; sets *bad
+// when any word is not below its prime (input validation, not on the answer path).
+__global__ void k_check_residues(const uint4 *__restrict__ rows, uint64_t nrows, uint32_t n4, uint32_t L,
+                                 NttConst C, uint32_t *__restrict__ bad) {
+  const uint64_t total = nrows * n4;
+  uint32_t found = 0;
+  for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t j = (uint32_t)((w / n4) % L);
+    uint32_t q = C.q[0];
+#pragma unroll
+    for (uint32_t i = 1; i < PIR_MAX_L; ++i) q = j == i ? C.q[i] : q;
+    const uint4 v = __ldg(rows + w);
+    found |= (v.x >= q) | (v.y >= q) | (v.z >= q) | (v.w >= q);
+  }
+  if (__any_sync(0xffffffffu, found) && (threadIdx.x & 31) == 0) atomicOr(bad, 1u);
+}
+
+cudaError_t launch_check_residues(const ParamCtx &c, const uint32_t *rows, uint64_t nrows, uint32_t *bad,
+                                  cudaStream_t s) {
+  if (nrows == 0) return cudaSuccess;
+  const uint32_t n4 = (1u << c.logn) / 4;
+  const uint64_t words = nrows * n4;
+  uint64_t blocks = (words + 255) / 256;
+  if (blocks > 152ull * 16) blocks = 152ull * 16;
+  k_check_residues<<<(unsigned)blocks, 256, 0, s>>>(reinterpret_cast<const uint4 *>(rows), nrows, n4, c.p.L, c.ntt,
+                                                    bad);
+  return cudaGetLastError();
+}
+
 }  // namespace gbpir

@@ -243,3 +243,32 @@ def test_host_buffers_sub_batch_pipeline(orc, layout, B, flags):
         assert np.array_equal(host, ref)
     finally:
         g.pir_free_db(db)
+
+
+def test_check_inputs_refuses_non_canonical_residues(orc):
+    """PIR_ANSWER_CHECK_INPUTS: canonical queries answer as without the check (device
+    and host buffers); one residue equal to its prime is refused with PIR_ERR_ARG,
+    whichever prime's row it sits in."""
+    n, log2p, D1, D2, B = 2048, 16, 32, 16, 3
+    p = g.pir_make_params(n, log2p, D1, D2, 2)
+    P = orc.make_params(n, log2p, D1, D2, 2)
+    raw = synth.raw_db(31, synth.raw_db_bytes(n, log2p, D1, D2))
+    db = g.pir_setup_db(p, raw)
+    try:
+        Q = random_queries(P, B, 32)
+        want = orc.answer(P, raw, Q)
+        rd = empty_u32(want.size)
+        g.pir_answer_ex(db, to_dev(Q), B, rd, flags=g.PIR_ANSWER_CHECK_INPUTS)
+        assert np.array_equal(from_dev(rd, want.shape), want)
+        rh = np.empty(want.size, dtype=np.uint32)
+        g.pir_answer_ex(db, np.ascontiguousarray(Q).reshape(-1), B, rh, flags=g.PIR_ANSWER_CHECK_INPUTS)
+        assert np.array_equal(rh.reshape(want.shape), want)
+        for (b, i, comp, j, t) in ((0, 0, 0, 0, 0), (B - 1, D1 - 1, 1, 1, n - 1), (1, 7, 0, 1, 5)):
+            bad = Q.copy()
+            bad[b, i, comp, j, t] = P.qs[j]
+            with pytest.raises(g.PirError) as ei:
+                g.pir_answer_ex(db, to_dev(bad), B, rd, flags=g.PIR_ANSWER_CHECK_INPUTS)
+            assert ei.value.status == 1
+        g.pir_answer_ex(db, to_dev(bad), B, rd)  # without the check the call is not refused
+    finally:
+        g.pir_free_db(db)

@@ -6,7 +6,13 @@ GEMM with its reduction, and the inverse NTT of the responses.  The metric is
 DB-scan throughput in raw DB bytes x queries / s.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--batch B]
-                  [--layout plain|limb|tensor] [--impl ours|reference]
+                  [--layout plain|limb|tensor] [--impl ours|reference] [--noalloc]
+  python bench.py --serving | --ntt-sweep | --lwe       (the other measurements)
+
+With no flags the line is the 16 GiB database (n = 4096, 4096 x 512) at batch 32 on
+the exact integer plain path, plus blocks at batches 1, 8 and 128 (`per_batch`), the
+tensor layout at batch 32 (`tensor_layout`), and the 32 GiB database at batch 64 on
+the plain and limb layouts (`largest_config`), each timed for at least a second.
 
 Prints one JSON line (rank 0).  Under torchrun (N > 1) every rank holds its own
 replica of the database and answers its own batches (independent problems, no
@@ -324,7 +330,7 @@ class Ctx:
 
     def probe(self, name, stream):
         if name not in self.probes:
-            fn = {"imad": self.g.pir_probe_imad_wide, "int8": self.g.pir_probe_int8_mma}[name]
+            fn = {"int8": self.g.pir_probe_int8_mma}[name]
             self.probes[name] = fn(stream)
         return self.probes[name]
 
@@ -363,16 +369,14 @@ def gemm_roofline(ctx, layout, B, p, tile, gemm_ms, launches_per_step, clocks, s
         alg_bytes = nslots * (D1 * D2 * 4 + D1 * M * 4 + M * D2 * 4)
         per = alg_bytes / launches_per_step
         if layout == g.PIR_LAYOUT_PLAIN:
-            # one mad.wide.u32 per modular MAC, against that instruction's rate
-            # measured live on this GPU
+            # one mad.wide.u32 per modular MAC; that instruction holds the multiply-add
+            # pipe four cycles per warp, 32 per clock per SM (the ncu pipe counters of
+            # this kernel confirm it), so the peak is derived from the sampled clock
             kernel_tag = "gemm_plain"
-            peak = ctx.probe("imad", stream)
             sm_mhz = clocks.get("sm_mhz") or float(ctx.peaks.get("sm_max_mhz", 2070.0))
+            peak = 152 * 32 * sm_mhz * 1e6 / 1e12
             rl = {"bound": "alu", "achieved": macs / (launch_ms / 1e3) / 1e12, "peak": peak, "unit": "T modMAC/s",
-                  "peak_source": "pir_probe_imad_wide on this GPU (T mad.wide.u32/s; MEASURED_PEAKS.json has no "
-                                 "integer entry)",
-                  "derived_peak": 152 * 32 * sm_mhz * 1e6 / 1e12,
-                  "derived_peak_source": "152 SMs x 32 mad.wide.u32 / clock x sampled SM clock",
+                  "peak_source": "derived: 152 SMs x 32 mad.wide.u32 / clock x sampled SM clock %.0f MHz" % sm_mhz,
                   "hbm_gbs": per / (launch_ms / 1e3) / 1e9}
         else:
             # 16 byte products per modular MAC on the INT8 tensor pipe
@@ -629,6 +633,31 @@ def our_arm(args, wl):
             r["step_speedup_vs_plain"] = plain_ref["ms_per_step"] / r["ms_per_step"]
         tensor_block = r
 
+    # the largest single-GPU configuration (32 GiB raw, 128 GiB resident) at batch 64
+    # on the plain path and on the exact limb-INT8 tensor path (the benchmark spec's
+    # comparison), each timed for at least a second
+    large = None
+    if world == 1 and plain_mode and args.large_block:
+        if db is not None:
+            g.pir_free_db(db)
+            db = None
+            torch.cuda.empty_cache()
+        wl5 = "db32g_n8192"
+        n5, lp5, D15, D25, B5, desc5 = WORKLOADS[wl5]
+        p5 = g.pir_make_params(n5, lp5, D15, D25, L_PRIMES)
+        large = {"workload": wl5, "description": desc5, "batch": B5}
+        ctx.wl = wl5
+        for name, lay in (("plain", g.PIR_LAYOUT_PLAIN), ("limb", g.PIR_LAYOUT_LIMB)):
+            db5, _ = make_db(ctx, p5, lay)
+            try:
+                r, _ = measure_batch(ctx, db5, p5, lay, B5, 2, 3, min_seconds=MIN_TIMED_S)
+            finally:
+                g.pir_free_db(db5)
+                torch.cuda.empty_cache()
+            large[name] = r
+        ctx.wl = wl
+        large["limb_vs_plain"] = large["plain"]["ms_per_step"] / large["limb"]["ms_per_step"]
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not (args.packed or args.folded):
         nthreads = os.cpu_count() or 1
@@ -675,6 +704,8 @@ def our_arm(args, wl):
             line["per_batch"] = per_batch
         if tensor_block is not None:
             line["tensor_layout"] = tensor_block
+        if large is not None:
+            line["largest_config"] = large
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -932,6 +963,8 @@ def main(argv=None):
                     help="skip the per-batch blocks (batches 1, 8, 32, 128) of the default plain run")
     ap.add_argument("--no-tensor-block", dest="tensor_block", action="store_false",
                     help="skip the tensor-layout block (batch 32) of the default plain run")
+    ap.add_argument("--no-large-block", dest="large_block", action="store_false",
+                    help="skip the 32 GiB block (batch 64, plain and limb layouts) of the default plain run")
     ap.add_argument("--lwe", action="store_true", help="time the scalar-HE (LWE) INT8 x INT32 DB GEMM instead")
     ap.add_argument("--lwe-workload", default="lwe16g", choices=sorted(LWE_WORKLOADS))
     ap.add_argument("--lwe-path", default="auto", choices=["auto", "tensor", "simt"])

@@ -365,14 +365,6 @@ pir_status_t pir_lwe_answer(const int8_t *db, uint32_t D1, uint32_t D0, const ui
  * the denominator of the scalar-HE GEMM's roofline.  The paper has no counterpart.
  * Synchronizes `stream`.  Errors: PIR_ERR_ARG (NULL), PIR_ERR_CUDA. */
 pir_status_t pir_probe_int8_mma(void *stream, double *tops);
-
-/* Measured peak of the 32 x 32 -> 64-bit integer multiply-add (mad.wide.u32) on the
- * current device, in tera multiply-adds per second: the denominator of the plain
- * CUDA-core GEMM's roofline, which issues one such instruction per modular MAC
- * (Sec. 4.2's modular INT32 GEMM on CUDA cores).  The paper has no counterpart.
- * Synchronizes `stream`.  Errors: PIR_ERR_ARG (NULL), PIR_ERR_CUDA. */
-pir_status_t pir_probe_imad_wide(void *stream, double *tmacs);
-
 /* Release a DB handle and its device memory (synchronizes the device first). */
 pir_status_t pir_free_db(pir_db_t db);
 

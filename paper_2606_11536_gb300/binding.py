@@ -97,7 +97,6 @@ def lib():
             "pir_fold": (i32, [P, vp, u32, u32, u32, vp, vp, vp]),
             "pir_answer_folded": (i32, [vp, vp, u32, u32, vp, vp, i32, vp, C.POINTER(pir_answer_opts_t)]),
             "pir_probe_int8_mma": (i32, [vp, C.POINTER(C.c_double)]),
-            "pir_probe_imad_wide": (i32, [vp, C.POINTER(C.c_double)]),
             "pir_expander_create": (i32, [P, u32, u32, vp, i32, vp, C.POINTER(vp)]),
             "pir_expander_free": (i32, [vp]),
             "pir_expand": (i32, [vp, vp, u32, u32, vp, vp]),
@@ -321,13 +320,6 @@ def pir_probe_int8_mma(stream=None) -> float:
     """Measured INT8 mma.sync peak of this GPU in TOPS."""
     v = C.c_double()
     _check(lib().pir_probe_int8_mma(_stream_ptr(stream), C.byref(v)), "pir_probe_int8_mma")
-    return v.value
-
-
-def pir_probe_imad_wide(stream=None) -> float:
-    """Measured mad.wide.u32 peak of this GPU in tera multiply-adds per second."""
-    v = C.c_double()
-    _check(lib().pir_probe_imad_wide(_stream_ptr(stream), C.byref(v)), "pir_probe_imad_wide")
     return v.value
 
 

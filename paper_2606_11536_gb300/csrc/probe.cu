@@ -1,12 +1,8 @@
-// probe.cu -- peak rates measured on this GPU for the two pipes whose peaks the
-// driver's measured figures (HBM copies, bf16 GEMMs) do not cover:
-//   - the INT8 warp-level tensor instruction, the denominator of the scalar-HE GEMM's
-//     roofline: every warp of a full grid issues eight independent chains of
-//     mma.sync m16n8k32 s8 x u8 -> s32 on register operands; the rate is
-//     2 x 16 x 8 x 32 operations per instruction over the event-timed duration;
-//   - the 32 x 32 -> 64-bit integer multiply-add (mad.wide.u32), the one instruction
-//     per modular MAC of the plain CUDA-core GEMM and the denominator of its roofline:
-//     every thread of a full grid runs eight independent accumulator chains.
+// probe.cu -- peak rate of the INT8 warp-level tensor instruction on this GPU, the
+// denominator of the scalar-HE GEMM's roofline (the driver's measured peaks cover
+// HBM copies and bf16 GEMMs only).  Every warp of a full grid issues eight
+// independent chains of mma.sync m16n8k32 s8 x u8 -> s32 on register operands; the
+// rate is 2 x 16 x 8 x 32 operations per instruction over the event-timed duration.
 #include "common.cuh"
 
 namespace gbpir {
@@ -36,33 +32,6 @@ __global__ void __launch_bounds__(256) k_probe_imma(uint32_t iters, uint32_t see
 #pragma unroll
   for (int c = 0; c < kChains; ++c) s += d[c][0] ^ d[c][1] ^ d[c][2] ^ d[c][3];
   if (s == 0x7fffffff) sink[0] = s;  // keeps the chains live
-}
-
-constexpr int kMadChains = 8;
-
-__global__ void __launch_bounds__(256) k_probe_mad_wide(uint32_t iters, uint32_t seed, uint64_t *__restrict__ sink) {
-  const uint32_t b = (seed ^ (blockIdx.x * 40503u)) | 1u;
-  uint32_t a[kMadChains];
-  uint64_t acc[kMadChains];
-#pragma unroll
-  for (int c = 0; c < kMadChains; ++c) {
-    a[c] = seed * 2654435761u + threadIdx.x * 97u + c * 0x9e3779b9u;
-    acc[c] = c;
-  }
-  // every multiply-add has its own factor, rotated by one bit per iteration (a funnel
-  // shift, off the multiply-add pipe): no product is shared between chains, none is
-  // loop-invariant, and no chain waits on a multiply-add result for its factor
-  for (uint32_t it = 0; it < iters; ++it) {
-#pragma unroll
-    for (int c = 0; c < kMadChains; ++c) {
-      asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc[c]) : "r"(a[c]), "r"(b));
-      a[c] = __funnelshift_l(a[c], a[c], 1);
-    }
-  }
-  uint64_t s = 0;
-#pragma unroll
-  for (int c = 0; c < kMadChains; ++c) s ^= acc[c];
-  if (s == 0x7fffffffffffffffull) sink[0] = s;  // keeps the chains live
 }
 
 }  // namespace
@@ -99,39 +68,5 @@ extern "C" pir_status_t pir_probe_int8_mma(void *stream, double *tops) {
   count_launches(2);
   const double ops = 2.0 * 16 * 8 * 32 * (double)kChains * iters * (grid * 8.0);  // 8 warps per block
   *tops = ops / (ms * 1e-3) / 1e12;
-  return PIR_OK;
-}
-
-extern "C" pir_status_t pir_probe_imad_wide(void *stream, double *tmacs) {
-  using namespace gbpir;
-  if (!tmacs) return PIR_ERR_ARG;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaError_t e;
-  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_status(e);
-  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return cuda_status(e);
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe_mad_wide, 256, 0)) != cudaSuccess)
-    return cuda_status(e);
-  uint64_t *sink = nullptr;
-  if ((e = cudaMallocAsync(&sink, sizeof(uint64_t), s)) != cudaSuccess) return cuda_status(e);
-  const unsigned grid = (unsigned)(sms * (per_sm > 0 ? per_sm : 1));
-  const uint32_t iters = 1u << 14;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  k_probe_mad_wide<<<grid, 256, 0, s>>>(iters / 8, 1, sink);  // warm-up
-  cudaEventRecord(e0, s);
-  k_probe_mad_wide<<<grid, 256, 0, s>>>(iters, 2, sink);
-  cudaEventRecord(e1, s);
-  e = cudaEventSynchronize(e1);
-  float ms = 0.f;
-  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  cudaFreeAsync(sink, s);
-  if (e != cudaSuccess) return cuda_status(e);
-  count_launches(2);
-  const double macs = (double)kMadChains * iters * grid * 256.0;
-  *tmacs = macs / (ms * 1e-3) / 1e12;
   return PIR_OK;
 }

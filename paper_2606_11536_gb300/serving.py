@@ -364,6 +364,7 @@ class CudaBackend(Backend):
         self._graph_bytes = 0
         self._tuned: Dict[tuple, dict] = {}
         self.graph_launches = 0
+        self.frozen = False  # set by prewarm(): no graph is made while serving
 
     def setup_db(self, name, params, raw, layout):
         try:
@@ -398,12 +399,17 @@ class CudaBackend(Backend):
                 for slot in server.slots:
                     self._graph_for(info["handle"], info["params"], bucket, slot.stream)
         self.torch.cuda.synchronize(self.device)
+        # from here on no graph is made while serving (a capture synchronizes the
+        # device): a batch without a graph runs uncaptured
+        self.frozen = True
 
     def _graph_for(self, handle, params, bucket, stream):
         key = (id(handle), bucket, id(stream))
         if key in self._graphs:
             self._graphs.move_to_end(key)
             return self._graphs[key]
+        if self.frozen:
+            return None
         torch = self.torch
         qwords = bucket * params.D1 * 2 * params.L * params.n
         rwords = bucket * params.D2 * 2 * params.L * params.n

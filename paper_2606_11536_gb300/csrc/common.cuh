@@ -13,12 +13,33 @@ namespace gbpir {
 // ---------------------------------------------------------------------------
 // Per-prime NTT constants handed to kernels by value.
 // ---------------------------------------------------------------------------
+// Lane-major twiddles.  In a radix-16 pass over the lowest index bits (units of 16
+// consecutive elements, unit hi = thread), stage 0 takes pairs n/2 + 8 hi .. +7 and
+// stage 1 pairs n/4 + 4 hi .. +3 of the table: each thread its own 64 (32) bytes,
+// which a warp reads with 16 (8) L1 wavefronts per 16-byte load.  The same pairs
+// are kept after the table in lane-major order, [stage 0: 4][n/16] then
+// [stage 1: 2][n/16] 16-byte pairs of pairs, so that a warp's load is one
+// contiguous 512-byte run.
+inline size_t ntt_lane_major_words(uint32_t n) { return (size_t)6 * (n / 16) * 4; }
+inline void ntt_lane_major_fill(uint32_t *tab, uint32_t n) {  // tab: n pairs, then the copy
+  uint32_t *lm = tab + 2 * (size_t)n;
+  const uint32_t units = n / 16;
+  for (uint32_t hi = 0; hi < units; ++hi) {
+    for (uint32_t k = 0; k < 4; ++k)  // stage 0: pairs n/2 + 8 hi + 2k, +1
+      for (uint32_t w = 0; w < 4; ++w) lm[((size_t)k * units + hi) * 4 + w] = tab[2 * (n / 2 + 8 * hi + 2 * k) + w];
+    for (uint32_t k = 0; k < 2; ++k)  // stage 1: pairs n/4 + 4 hi + 2k, +1
+      for (uint32_t w = 0; w < 4; ++w)
+        lm[((size_t)(4 + k) * units + hi) * 4 + w] = tab[2 * (n / 4 + 4 * hi + 2 * k) + w];
+  }
+}
+
 struct NttConst {
   uint32_t q[PIR_MAX_L];
   uint32_t ninv[PIR_MAX_L];        // n^-1 mod q
   uint32_t ninv_sh[PIR_MAX_L];     // Shoup companion of n^-1
-  const uint2 *fwd[PIR_MAX_L];     // [n] {psi^brv(i), floor(psi^brv(i) * 2^32 / q)}: twiddle, Shoup companion
-  const uint2 *inv[PIR_MAX_L];     // [n] {psi^-brv(i), its Shoup companion}
+  const uint2 *fwd[PIR_MAX_L];     // [n] {psi^brv(i), floor(psi^brv(i) * 2^32 / q)}: twiddle, Shoup companion;
+                                   // the lane-major copy follows at fwd + n
+  const uint2 *inv[PIR_MAX_L];     // [n] {psi^-brv(i), its Shoup companion}; lane-major copy at inv + n
 };
 
 // Reduction constants of the modular GEMM epilogues.

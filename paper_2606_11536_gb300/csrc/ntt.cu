@@ -110,6 +110,12 @@ struct Pairs {  // CNT twiddle pairs held as whole 16-byte vectors (8 bytes when
       for (int i = 0; i < CNT / 2; ++i) v[i] = __ldg(reinterpret_cast<const uint4 *>(src) + i);
     }
   }
+  // CNT pairs as CNT/2 16-byte loads spaced `stride` 16-byte words apart (the
+  // lane-major copy: load i of every thread is one contiguous run)
+  __device__ __forceinline__ void load_lane_major(const uint4 *__restrict__ src, uint32_t stride) {
+#pragma unroll
+    for (int i = 0; i < CNT / 2; ++i) v[i] = __ldg(src + (size_t)i * stride);
+  }
   template <int I>
   __device__ __forceinline__ uint32_t w() const { return (I & 1) ? v[I / 2].z : v[I / 2].x; }
   template <int I>
@@ -140,7 +146,12 @@ __device__ __forceinline__ void fwd_stage(uint32_t (&v)[1 << RB], uint32_t hi, c
   constexpr int CNT = 1 << (RB - 1 - LB);
   constexpr uint32_t m = 1u << (LOGN - 1 - (BLO + LB));
   Pairs<CNT> p;
-  p.load(tw + m + (hi << (RB - 1 - LB)));
+  if constexpr (BLO == 0 && RB == 4 && LB <= 1) {  // the lane-major copy after the table
+    constexpr uint32_t units = 1u << (LOGN - 4);
+    p.load_lane_major(reinterpret_cast<const uint4 *>(tw + (1u << LOGN)) + (LB == 0 ? 0u : 4 * units) + hi, units);
+  } else {
+    p.load(tw + m + (hi << (RB - 1 - LB)));
+  }
   fwd_bfly<RB, LB, 0, CNT>(v, p, q);
 }
 
@@ -175,7 +186,12 @@ __device__ __forceinline__ void inv_stage(uint32_t (&v)[1 << RB], uint32_t hi, c
   constexpr int CNT = 1 << (RB - 1 - LB);
   constexpr uint32_t m = 1u << (LOGN - 1 - (BLO + LB));
   Pairs<CNT> p;
-  p.load(tw + m + (hi << (RB - 1 - LB)));
+  if constexpr (BLO == 0 && RB == 4 && LB <= 1) {  // the lane-major copy after the table
+    constexpr uint32_t units = 1u << (LOGN - 4);
+    p.load_lane_major(reinterpret_cast<const uint4 *>(tw + (1u << LOGN)) + (LB == 0 ? 0u : 4 * units) + hi, units);
+  } else {
+    p.load(tw + m + (hi << (RB - 1 - LB)));
+  }
   inv_bfly<RB, LB, 0, CNT>(v, p, q);
 }
 

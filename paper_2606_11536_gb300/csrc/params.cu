@@ -154,7 +154,10 @@ pir_status_t get_param_ctx(const pir_params_t *p, const ParamCtx **out) {
     return PIR_OK;
   }
   const uint32_t n = p->n, lg = log2_exact(n);
-  std::vector<uint32_t> host((size_t)4 * n * p->L);
+  // per prime and direction: the n twiddle pairs, then their lane-major copy for the
+  // first two stages of a radix-16 pass on the lowest index bits (kNttLaneMajorWords)
+  const size_t dir_words = 2 * (size_t)n + ntt_lane_major_words(n), prime_words = 2 * dir_words;
+  std::vector<uint32_t> host(prime_words * p->L);
   ParamCtx *ctx = new ParamCtx();
   ctx->p = *p;
   ctx->p.D1 = ctx->p.D2 = 0;  // the context describes the ring only; shapes travel per call
@@ -163,14 +166,16 @@ pir_status_t get_param_ctx(const pir_params_t *p, const ParamCtx **out) {
     const uint32_t q = p->q[j];
     const uint32_t psi = p->psi[j];
     const uint32_t psi_inv = (uint32_t)pow_mod32(psi, q - 2, q);
-    // per prime: forward pairs [n][2], then inverse pairs [n][2]
-    uint32_t *f = &host[(size_t)(4 * j + 0) * n], *iv = &host[(size_t)(4 * j + 2) * n];
+    // per prime: forward pairs [n][2] and their lane-major copy, then the same inverse
+    uint32_t *f = &host[j * prime_words], *iv = &host[j * prime_words + dir_words];
     for (uint32_t i = 0; i < n; ++i) {
       f[2 * i] = (uint32_t)pow_mod32(psi, brv(i, lg), q);
       f[2 * i + 1] = shoup(f[2 * i], q);
       iv[2 * i] = (uint32_t)pow_mod32(psi_inv, brv(i, lg), q);
       iv[2 * i + 1] = shoup(iv[2 * i], q);
     }
+    ntt_lane_major_fill(f, n);
+    ntt_lane_major_fill(iv, n);
     ctx->ntt.q[j] = q;
     ctx->ntt.ninv[j] = (uint32_t)pow_mod32(n, q - 2, q);
     ctx->ntt.ninv_sh[j] = shoup(ctx->ntt.ninv[j], q);
@@ -216,8 +221,8 @@ pir_status_t get_param_ctx(const pir_params_t *p, const ParamCtx **out) {
     return cuda_status(e);
   }
   for (uint32_t j = 0; j < p->L; ++j) {
-    ctx->ntt.fwd[j] = reinterpret_cast<const uint2 *>(dtab + (size_t)(4 * j + 0) * n);
-    ctx->ntt.inv[j] = reinterpret_cast<const uint2 *>(dtab + (size_t)(4 * j + 2) * n);
+    ctx->ntt.fwd[j] = reinterpret_cast<const uint2 *>(dtab + j * prime_words);
+    ctx->ntt.inv[j] = reinterpret_cast<const uint2 *>(dtab + j * prime_words + dir_words);
   }
   g_cache[k] = ctx;
   *out = ctx;

@@ -332,7 +332,7 @@ cudaError_t launch_gemm_plain(const ParamCtx &c, const uint32_t *db, uint32_t D1
     case 3: return M <= 8 ? gemv_launch<8>(c, db, D1, D2, qs, M, Mp, i0, Kc, out, acc, s) : cudaErrorInvalidValue;
     case 4: return gemm_launch<16, 256, 2>(c, db, D1, D2, qs, M, Mp, i0, Kc, out, acc, s);
     case 5: return gemm_launch<32, 256, 4>(c, db, D1, D2, qs, M, Mp, i0, Kc, out, acc, s);
-    case 6: return gemm_launch<64, 128, 4>(c, db, D1, D2, qs, M, Mp, i0, Kc, out, acc, s);
+    case 6: return gemm_launch<64, 128, 4, 32>(c, db, D1, D2, qs, M, Mp, i0, Kc, out, acc, s);  // 32-row stages: 1% faster
     case 8: return gemm_launch<8, 256, 1>(c, db, D1, D2, qs, M, Mp, i0, Kc, out, acc, s);
   }
   return cudaErrorInvalidValue;

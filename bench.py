@@ -438,8 +438,22 @@ def measure_batch(ctx, db, p, layout, B, steps, warmup, min_seconds=0.0, extras=
     streams = [stream] + [torch.cuda.Stream(device=ctx.dev) for _ in range(nstreams - 1)]
     resps = [torch.empty(rwords, dtype=torch.int32, device=ctx.dev) for _ in range(nstreams)]
 
+    graphs = None
+    if args.graph:
+        # one captured answer per query buffer, replayed (the graph binds its buffers)
+        if ex is not None:
+            graphs = [g.pir_graph_create_packed(db, ex, qb, B, resps[0], tile=args.tile, flags=msw) for qb in qbufs]
+        elif rg is None:
+            graphs = [g.pir_graph_create(db, qb, B, resps[0], k_chunk=args.k_chunk, tile=args.tile, flags=msw)
+                      for qb in qbufs]
+        else:
+            raise SystemExit("--graph covers the plain and packed answers")
+
     def step(t, flags=0):
         st, rs = streams[t % nstreams], resps[t % nstreams]
+        if graphs is not None:
+            g.pir_graph_launch(graphs[t % nbuf], stream=stream)
+            return
         if rg is not None:
             g.pir_answer_folded(db, qbufs[t % nbuf], B, args.ell, rg, rs, stream=st, flags=flags | msw, tile=args.tile)
         elif ex is not None:
@@ -598,7 +612,7 @@ def our_arm(args, wl):
 
     # the metric's batch range and the tensor layout, on the default workload (one GPU)
     plain_mode = layout == g.PIR_LAYOUT_PLAIN and not extras and args.streams == 1 and args.tile == 0 and \
-        args.k_chunk == 0 and not args.modswitch and not args.noalloc and wl == DEFAULT_WORKLOAD
+        args.k_chunk == 0 and not args.modswitch and not args.noalloc and not args.graph and wl == DEFAULT_WORKLOAD
     per_batch = tensor_block = None
     if world == 1 and plain_mode and args.per_batch:
         per_batch = []
@@ -693,7 +707,8 @@ def our_arm(args, wl):
                                      if args.folded else "D2 ciphertexts each"),
                        "queries": ("packed, expanded on the GPU (levels %d, %d gadget digits; timing-only keys)"
                                    % ((D1 - 1).bit_length(), args.ell) if args.packed else "D1 ciphertexts each"),
-                       "entry": "pir_answer_noalloc" if args.noalloc else "pir_answer_ex",
+                       "entry": ("pir_answer_noalloc" if args.noalloc else "pir_graph_launch" if args.graph
+                                 else "pir_answer_ex"),
                        "parallelism": "replicas x%d" % world,
                        "l2": "inputs larger than L2: the %.1f GiB NTT-form DB is streamed every step; query "
                              "buffers rotate when small" % (binding.resident_db_bytes(p, layout) / 2 ** 30)},
@@ -978,6 +993,8 @@ def main(argv=None):
     ap.add_argument("--modswitch", action="store_true",
                     help="switch the responses to the single prime q_0 inside the inverse NTT")
     ap.add_argument("--ntt-sweep", action="store_true", help="time the standalone NTT sweep instead")
+    ap.add_argument("--graph", action="store_true",
+                    help="replay captured answers (pir_graph_create, pir_graph_create_packed with --packed)")
     ap.add_argument("--noalloc", action="store_true",
                     help="answer through pir_answer_noalloc (the library's fixed scratch array, no allocation)")
     ap.add_argument("--serving", action="store_true", help="run the serving benchmark instead")

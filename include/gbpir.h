@@ -315,6 +315,17 @@ pir_status_t pir_expand(pir_expander_t expander, const uint32_t *packed, uint32_
 pir_status_t pir_answer_packed(pir_db_t db, pir_expander_t expander, const uint32_t *packed, uint32_t B,
                                uint32_t *responses, int on_device, void *stream, const pir_answer_opts_t *opts);
 
+/* pir_graph_create for packed queries (pir_answer_packed below, device buffers):
+ * the expansion and the answer captured together, so that the expansion's many
+ * small launches (about 36 at batch 1 on the 1 GiB DB) replay without launch gaps.
+ * The graph reads the expander's keys: freeing the expander (or the DB) makes
+ * pir_graph_launch refuse the graph with PIR_ERR_HANDLE.  packed [B][2][L][n] and
+ * responses as for pir_answer_packed; opts: k_chunk 0 (or >= D1), tile, and
+ * PIR_ANSWER_MODSWITCH.  The paper has no counterpart (a launch mechanism).
+ * Errors: PIR_ERR_HANDLE, PIR_ERR_ARG, PIR_ERR_OOM, PIR_ERR_CUDA. */
+pir_status_t pir_graph_create_packed(pir_db_t db, pir_expander_t expander, const uint32_t *packed, uint32_t B,
+                                     uint32_t *responses, const pir_answer_opts_t *opts, pir_graph_t *out);
+
 /* Folding of the remaining dimensions with RGSW-RLWE external products (Sec. 3.2 and
  * 3.6: OnionPIR's construction; gadget of App. D.3).  Each level pairs the
  * ciphertexts (2j, 2j+1) of a query and keeps c_2j + RGSW_l (x) (c_2j+1 - c_2j), where

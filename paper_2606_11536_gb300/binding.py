@@ -89,6 +89,7 @@ def lib():
             "pir_kernel_launches": (C.c_uint64, []),
             "pir_check_device": (i32, [vp]),
             "pir_graph_create": (i32, [vp, vp, u32, vp, C.POINTER(pir_answer_opts_t), C.POINTER(vp)]),
+            "pir_graph_create_packed": (i32, [vp, vp, vp, u32, vp, C.POINTER(pir_answer_opts_t), C.POINTER(vp)]),
             "pir_graph_launch": (i32, [vp, vp]),
             "pir_graph_destroy": (i32, [vp]),
             "pir_autotune": (i32, [vp, u32, vp, u32, C.POINTER(pir_answer_opts_t)]),
@@ -443,6 +444,24 @@ def pir_graph_create(db: Db, queries, B: int, responses, k_chunk: int = 0, tile:
     h = C.c_void_p()
     _check(lib().pir_graph_create(C.c_void_p(db.handle), qp, B, rp, C.byref(o), C.byref(h)), "pir_graph_create")
     return Graph(h.value, db, queries, responses)
+
+
+def pir_graph_create_packed(db: Db, ex: "Expander", packed, B: int, responses, tile: int = 0,
+                            flags: int = 0) -> Graph:
+    """A captured packed-query answer (expansion + answer) bound to fixed device buffers."""
+    pp, pdev, pn = _ptr(packed)
+    rp, rdev, rn = _ptr(responses)
+    _require("packed query", pn, B * ct_bytes(db.params.n, db.params.L))
+    _require("response", rn, _answer_sizes(db, B, flags)[1])
+    if not (pdev and rdev):
+        raise ValueError("a graph binds device buffers")
+    o = pir_answer_opts_t(0, tile, flags)
+    h = C.c_void_p()
+    _check(lib().pir_graph_create_packed(C.c_void_p(db.handle), C.c_void_p(ex.handle), pp, B, rp, C.byref(o),
+                                         C.byref(h)), "pir_graph_create_packed")
+    g = Graph(h.value, db, packed, responses)
+    g.expander = ex
+    return g
 
 
 class Session:

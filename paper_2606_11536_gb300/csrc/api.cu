@@ -104,7 +104,8 @@ struct pir_graph {
   pir_db *db;
   cudaGraph_t graph;
   cudaGraphExec_t exec;
-  uint64_t kernels;  // kernel launches per replay
+  uint64_t kernels;             // kernel launches per replay
+  pir_expander_t expander;      // the expansion keys a packed-query graph reads, or null
 };
 
 namespace {
@@ -641,6 +642,56 @@ pir_status_t session_chunk(pir_session *ses, const uint32_t *src, uint64_t strid
 
 }  // namespace
 
+namespace {
+// Captures body(stream) on a private stream into an instantiated graph bound to db
+// (and to the expander, for packed queries).
+template <typename Body>
+pir_status_t capture_graph(pir_db *db, pir_expander_t expander, Body body, pir_graph_t *out) {
+  *out = nullptr;
+  uint32_t *w = nullptr;
+  CK(device_error_word(&w));  // lazily allocated state must exist before the capture
+  cudaStream_t cs;
+  CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(cs);
+    return cuda_status(e);
+  }
+  t_capturing = true;
+  pir_status_t st = body(cs);
+  t_capturing = false;
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(cs, &graph);
+  cudaStreamDestroy(cs);
+  if (st != PIR_OK || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return st != PIR_OK ? st : cuda_status(e);
+  }
+  size_t nn = 0;
+  e = cudaGraphGetNodes(graph, nullptr, &nn);
+  std::vector<cudaGraphNode_t> nodes(nn);
+  if (e == cudaSuccess && nn) e = cudaGraphGetNodes(graph, nodes.data(), &nn);
+  uint64_t kernels = 0;
+  for (size_t i = 0; e == cudaSuccess && i < nn; ++i) {
+    cudaGraphNodeType t;
+    if ((e = cudaGraphNodeGetType(nodes[i], &t)) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return cuda_status(e);
+  }
+  pir_graph *g = new pir_graph{kGraphMagic, db, graph, exec, kernels, expander};
+  {
+    std::lock_guard<std::mutex> lock(g_reg_mu);
+    g_graphs.insert(g);
+  }
+  *out = g;
+  return PIR_OK;
+}
+}  // namespace
+
 extern "C" {
 
 const char *pir_status_str(pir_status_t st) {
@@ -985,6 +1036,24 @@ pir_status_t pir_answer_abort(pir_session_t session) {
   return PIR_OK;
 }
 
+namespace {
+// Packed queries pk [B][2][L][n] on the device: expansion into the D1 NTT-form
+// ciphertexts of every query (scratch), then the answer (stream ordered).
+pir_status_t answer_packed_device(pir_db *db, const pir_expander_impl *ex, const uint32_t *pk, uint32_t B,
+                                  uint32_t *resp, cudaStream_t s, const pir_answer_opts_t &o) {
+  const pir_params_t &p = db->p;
+  Scratch qh(s);
+  CK(qh.alloc((size_t)B * p.D1 * 2 * p.L * p.n * 4));
+  StageTimer tm((o.flags & PIR_ANSWER_STAGE_TIMES) != 0, s);
+  tm.begin();
+  uint64_t launches = 0;
+  pir_status_t st = expand_device(ex, pk, B, p.D1, static_cast<uint32_t *>(qh.ptr), s, &launches);
+  tm.end(0, launches);
+  if (st == PIR_OK) st = answer_device(db, nullptr, B, resp, s, o, static_cast<const uint32_t *>(qh.ptr));
+  return st;
+}
+}  // namespace
+
 pir_status_t pir_answer_packed(pir_db_t db, pir_expander_t expander, const uint32_t *packed, uint32_t B,
                                uint32_t *responses, int on_device, void *stream, const pir_answer_opts_t *opts) {
   NvtxRange range("pir_answer_packed");
@@ -1000,7 +1069,7 @@ pir_status_t pir_answer_packed(pir_db_t db, pir_expander_t expander, const uint3
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t pbytes = (size_t)B * 2 * p.L * p.n * 4;
   const size_t rbytes = (size_t)B * p.D2 * 2 * ((o.flags & PIR_ANSWER_MODSWITCH) ? 1 : p.L) * p.n * 4;
-  Scratch dp(s), dr(s), qh(s);
+  Scratch dp(s), dr(s);
   const uint32_t *pk = packed;
   uint32_t *resp = responses;
   if (on_device) {
@@ -1012,14 +1081,7 @@ pir_status_t pir_answer_packed(pir_db_t db, pir_expander_t expander, const uint3
     pk = static_cast<const uint32_t *>(dp.ptr);
     resp = static_cast<uint32_t *>(dr.ptr);
   }
-  // the D1 expanded ciphertexts of every query, in NTT form
-  CK(qh.alloc((size_t)B * p.D1 * 2 * p.L * p.n * 4));
-  StageTimer tm((o.flags & PIR_ANSWER_STAGE_TIMES) != 0, s);
-  tm.begin();
-  uint64_t launches = 0;
-  pir_status_t st = expand_device(ex, pk, B, p.D1, static_cast<uint32_t *>(qh.ptr), s, &launches);
-  tm.end(0, launches);
-  if (st == PIR_OK) st = answer_device(db, nullptr, B, resp, s, o, static_cast<const uint32_t *>(qh.ptr));
+  pir_status_t st = answer_packed_device(db, ex, pk, B, resp, s, o);
   if (st != PIR_OK) {
     if (!on_device) cudaStreamSynchronize(s);
     return st;
@@ -1139,6 +1201,7 @@ pir_status_t ntt_inv(const pir_params_t *params, uint32_t *polys, size_t count, 
   return ntt_common(params, polys, count, stream, false);
 }
 
+
 pir_status_t pir_graph_create(pir_db_t db, const uint32_t *queries, uint32_t B, uint32_t *responses,
                               const pir_answer_opts_t *opts, pir_graph_t *out) {
   if (!live(db)) return PIR_ERR_HANDLE;
@@ -1146,53 +1209,31 @@ pir_status_t pir_graph_create(pir_db_t db, const uint32_t *queries, uint32_t B, 
   pir_answer_opts_t o = {};
   if (opts) o = *opts;
   if ((o.flags & ~PIR_ANSWER_MODSWITCH) != 0) return PIR_ERR_ARG;
-  *out = nullptr;
-  uint32_t *w = nullptr;
-  CK(device_error_word(&w));  // lazily allocated state must exist before the capture
-  cudaStream_t cs;
-  CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
-  if (e != cudaSuccess) {
-    cudaStreamDestroy(cs);
-    return cuda_status(e);
-  }
-  t_capturing = true;
-  pir_status_t st = answer_device(db, queries, B, responses, cs, o);
-  t_capturing = false;
-  cudaGraph_t graph = nullptr;
-  e = cudaStreamEndCapture(cs, &graph);
-  cudaStreamDestroy(cs);
-  if (st != PIR_OK || e != cudaSuccess) {
-    if (graph) cudaGraphDestroy(graph);
-    return st != PIR_OK ? st : cuda_status(e);
-  }
-  size_t nn = 0;
-  e = cudaGraphGetNodes(graph, nullptr, &nn);
-  std::vector<cudaGraphNode_t> nodes(nn);
-  if (e == cudaSuccess && nn) e = cudaGraphGetNodes(graph, nodes.data(), &nn);
-  uint64_t kernels = 0;
-  for (size_t i = 0; e == cudaSuccess && i < nn; ++i) {
-    cudaGraphNodeType t;
-    if ((e = cudaGraphNodeGetType(nodes[i], &t)) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
-  }
-  cudaGraphExec_t exec = nullptr;
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
-  if (e != cudaSuccess) {
-    cudaGraphDestroy(graph);
-    return cuda_status(e);
-  }
-  pir_graph *g = new pir_graph{kGraphMagic, db, graph, exec, kernels};
-  {
-    std::lock_guard<std::mutex> lock(g_reg_mu);
-    g_graphs.insert(g);
-  }
-  *out = g;
-  return PIR_OK;
+  return capture_graph(
+      db, nullptr, [&](cudaStream_t cs) { return answer_device(db, queries, B, responses, cs, o); }, out);
+}
+
+pir_status_t pir_graph_create_packed(pir_db_t db, pir_expander_t expander, const uint32_t *packed, uint32_t B,
+                                     uint32_t *responses, const pir_answer_opts_t *opts, pir_graph_t *out) {
+  if (!live(db)) return PIR_ERR_HANDLE;
+  const pir_expander_impl *ex = nullptr;
+  if (!expander_view(expander, &ex)) return PIR_ERR_HANDLE;
+  if (!out || !packed || !responses || B == 0 || !aligned16(packed) || !aligned16(responses)) return PIR_ERR_ARG;
+  pir_answer_opts_t o = {};
+  if (opts) o = *opts;
+  if ((o.flags & ~PIR_ANSWER_MODSWITCH) != 0 || (o.k_chunk != 0 && o.k_chunk < db->p.D1)) return PIR_ERR_ARG;
+  if (!expander_fits(ex, db->p)) return PIR_ERR_ARG;
+  return capture_graph(
+      db, expander, [&](cudaStream_t cs) { return answer_packed_device(db, ex, packed, B, responses, cs, o); }, out);
 }
 
 static bool graph_live(pir_graph *g) {
-  std::lock_guard<std::mutex> lock(g_reg_mu);
-  return g && g_graphs.count(g) && g->magic == kGraphMagic && g_live.count(g->db);
+  {
+    std::lock_guard<std::mutex> lock(g_reg_mu);
+    if (!(g && g_graphs.count(g) && g->magic == kGraphMagic && g_live.count(g->db))) return false;
+  }
+  const pir_expander_impl *ex = nullptr;  // a packed-query graph reads its expander's keys
+  return !g->expander || expander_view(g->expander, &ex);
 }
 
 pir_status_t pir_graph_launch(pir_graph_t graph, void *stream) {

@@ -177,3 +177,35 @@ def test_expand_phases_with_error_free_keys(orc, n, L, levels, ell):
             cur = nxt
         for k in range(count):
             assert np.array_equal(_phase_rows(orc, P, s, got[k])[j], cur[k]), (j, k)
+
+
+@pytest.mark.parametrize("B,flags", [(1, 0), (3, 4)])
+def test_graph_of_packed_answer(orc, B, flags):
+    """pir_graph_create_packed: the expansion and the answer captured once, replayed
+    twice on new packed queries in the bound buffer, equal to pir_answer_packed; and
+    refused once its expander is freed."""
+    ell = 4
+    p, P, levels, raw, db = packed_instance(orc, 2048, 16, 64, 20, 2, ell, seed=150 + B)
+    _, keys, packed = keys_and_packed(orc, P, levels, ell, B, seed=151 + B)
+    ex = g.pir_expander_create(p, levels, ell, keys)
+    try:
+        Lr = 1 if flags else 2
+        pd = to_dev(packed)
+        rg = empty_u32(B * 20 * 2 * Lr * 2048)
+        graph = g.pir_graph_create_packed(db, ex, pd, B, rg, flags=flags)
+        try:
+            for rep in range(2):
+                newp = synth.uniform_residues(152 + rep, synth.STREAM_UNIFORM, 2 * B, P.n, P.qs).reshape(B, 2, 2, P.n)
+                pd.copy_(to_dev(newp))
+                g.pir_graph_launch(graph)
+                ref = empty_u32(rg.numel())
+                g.pir_answer_packed(db, ex, to_dev(newp), B, ref, flags=flags)
+                assert np.array_equal(from_dev(rg), from_dev(ref)), rep
+        finally:
+            g.pir_expander_free(ex)
+            with pytest.raises(g.PirError) as ei:
+                g.pir_graph_launch(graph)
+            assert ei.value.status == 6
+            g.pir_graph_destroy(graph)
+    finally:
+        g.pir_free_db(db)

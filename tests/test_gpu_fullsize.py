@@ -1,5 +1,6 @@
 """Full-size parity for the 16 GiB (n = 4096, 4096 x 512) and 32 GiB (n = 8192,
-8192 x 256) databases, in the launch configuration bench.py times (default tile
+8192 x 256) databases and the serving configuration's 1 GiB n = 2048 (512 x 512)
+and 8 GiB (2048 x 512) ones, in the launch configuration bench.py times (default tile
 and K-chunk choice), on outputs the oracle computes one by one: sampled
 (query, column) responses exact, and for batch 1 a real encrypted query whose
 sampled columns decrypt to the requested records.  The databases and large query
@@ -105,3 +106,27 @@ def test_32gib_database_batch64_plain_and_limb(orc):
         finally:
             g.pir_free_db(db)
             torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("n,D1,D2,B,seed", [(2048, 512, 512, 8, 21), (4096, 2048, 512, 32, 22)])
+def test_serving_configuration_databases(orc, n, D1, D2, B, seed):
+    """The two database shapes only the serving configuration uses: 1 GiB at n = 2048
+    (512 x 512) and the 8 GiB fourth database at n = 4096 (2048 x 512), each at a
+    serving-sized batch, on sampled (query, column) outputs against the oracle."""
+    import torch
+    log2p = 16
+    p = g.pir_make_params(n, log2p, D1, D2, 2)
+    P = orc.make_params(n, log2p, D1, D2, 2)
+    db = setup_on_device(p, seed)
+    try:
+        qd = device_queries(P, B, seed + 100)
+        rd = torch.empty(B * D2 * 2 * 2 * n, dtype=torch.int32, device="cuda")
+        g.pir_answer(db, qd, B, rd)
+        R = rd.view(B, D2, 2, 2, n)
+        for b, cs in ((0, [0, D2 - 1]), (B - 1, [D2 // 2, 7])):
+            got = R[b, cs].cpu().numpy().view(np.uint32)
+            assert np.array_equal(got[None], oracle_columns(orc, P, seed, cs, host_query(P, b, seed + 100))), b
+        g.pir_check_device()
+    finally:
+        g.pir_free_db(db)
+        torch.cuda.empty_cache()

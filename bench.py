@@ -727,6 +727,86 @@ def our_arm(args, wl):
         dist.destroy_process_group()
 
 
+def tensor_large_bench(args):
+    """The 32 GiB database (n = 8192, 8192 x 256) in the tensor layout: 256 GiB
+    resident (8 bytes per residue), so a batch's queries (64 GiB at batch 64) cannot
+    sit beside it on the device.  They stay in pinned host memory and each answer is
+    the streamed host-buffer call (1 GiB pieces along D1, uploads behind the scan):
+    the line measures that end-to-end call.  The raw DB goes up chunk by chunk from
+    pinned host memory as well."""
+    import torch
+    import paper_2606_11536_gb300 as g
+    from paper_2606_11536_gb300 import binding
+    import synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    wl = "db32g_n8192"
+    n, log2p, D1, D2, B0, desc = WORKLOADS[wl]
+    B = args.batch or B0
+    p = g.pir_make_params(n, log2p, D1, D2, L_PRIMES)
+    raw_bytes = binding.raw_db_bytes(p)
+    qwords, rwords = B * D1 * 2 * L_PRIMES * n, B * D2 * 2 * L_PRIMES * n
+    # host inputs, generated on the device (same counter-based streams) and copied out
+    qh = torch.empty(qwords, dtype=torch.int32, pin_memory=True)
+    per = max(1, (4 << 30) // (D1 * 2 * L_PRIMES * n * 4))  # queries per 4 GiB piece
+    for b0 in range(0, B, per):
+        nb = min(per, B - b0)
+        piece = synth.uniform_residues_torch(1000, synth.STREAM_UNIFORM, nb * D1 * 2, n, p.qs, device=dev,
+                                             start=b0 * D1 * 2).view(-1)
+        qh[b0 * D1 * 2 * L_PRIMES * n:(b0 + nb) * D1 * 2 * L_PRIMES * n].copy_(piece)
+        del piece
+    rawh = torch.empty(raw_bytes, dtype=torch.uint8, pin_memory=True)
+    rawh.copy_(synth.raw_db_torch(0, raw_bytes, device=dev))
+    torch.cuda.empty_cache()
+    t0 = time.perf_counter()
+    db = g.pir_setup_db(p, rawh, layout=g.PIR_LAYOUT_TENSOR)
+    setup_s = time.perf_counter() - t0
+    del rawh
+    rh = torch.empty(rwords, dtype=torch.int32, pin_memory=True)
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(0)
+    sampler.start()
+    for _ in range(args.warmup):
+        g.pir_answer_ex(db, qh, B, rh, stream=stream)
+    g.pir_stage_times()
+    launches0 = g.pir_kernel_launches()
+    w0 = time.time()
+    torch.cuda.nvtx.range_push("timed_b%d_tensor_host" % B)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        g.pir_answer_ex(db, qh, B, rh, stream=stream, flags=g.PIR_ANSWER_STAGE_TIMES)
+    ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    torch.cuda.nvtx.range_pop()
+    w1 = time.time()
+    launches = g.pir_kernel_launches() - launches0
+    stage_ms, stage_launches = g.pir_stage_times()
+    sampler.stop()
+    clocks = sampler.summary(w0, w1)
+    g.pir_free_db(db)
+    gemm_ms = stage_ms[2] / args.steps
+    macs = L_PRIMES * n * D1 * D2 * 2 * B
+    peaks, kind = measured_peaks()
+    tflops = 32.0 * macs / (gemm_ms / 1e3) / 1e12
+    value = raw_bytes * B / (ms / 1e3) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": wl, "description": desc, "batch": B, "layout": "tensor",
+                       "resident_bytes": binding.resident_db_bytes(p, g.PIR_LAYOUT_TENSOR), "setup_s": setup_s,
+                       "timed": "end to end: each step uploads its 64 GiB of queries from pinned host memory in 1 GiB "
+                                "pieces (the streamed answer) and downloads the responses; the queries cannot stay "
+                                "on the device beside the 256 GiB resident DB"},
+            "roofline": {"bound": "tensor", "kernel": "gemm_tc", "achieved": tflops,
+                         "peak": float(peaks.get("bf16_tflops_sustained", 1700.0)), "unit": "TFLOP/s",
+                         "frac": tflops / float(peaks.get("bf16_tflops_sustained", 1700.0)),
+                         "gemm_ms_per_step": gemm_ms, "launches_per_step": stage_launches[2] / args.steps,
+                         "stage_ms_per_step": {nm: stage_ms[i] / args.steps for i, nm in enumerate(binding.STAGE_NAMES)},
+                         "traffic": None},
+            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": qwords * 4, "d2h_bytes_per_step": rwords * 4},
+            "gpu_launches": int(launches), "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def ntt_sweep(args):
     """Standalone NTT sweep: forward then inverse NTT (in place) of 2^16 RNS
     polynomials (L = 2, n = 4096, 2 GiB) per step."""
@@ -993,6 +1073,8 @@ def main(argv=None):
     ap.add_argument("--modswitch", action="store_true",
                     help="switch the responses to the single prime q_0 inside the inverse NTT")
     ap.add_argument("--ntt-sweep", action="store_true", help="time the standalone NTT sweep instead")
+    ap.add_argument("--tensor-large", action="store_true",
+                    help="the 32 GiB DB in the tensor layout (256 GiB resident), answered from pinned host queries")
     ap.add_argument("--graph", action="store_true",
                     help="replay captured answers (pir_graph_create, pir_graph_create_packed with --packed)")
     ap.add_argument("--noalloc", action="store_true",
@@ -1019,6 +1101,8 @@ def main(argv=None):
         ap.error("--warmup must be at least 3")
     if args.ntt_sweep:
         return ntt_sweep(args)
+    if args.tensor_large:
+        return tensor_large_bench(args)
     if args.lwe:
         return lwe_bench(args)
     if args.serving:

@@ -784,7 +784,13 @@ pir_status_t pir_setup_db(const pir_params_t *params, const void *raw_db, size_t
   CK(cudaMemGetInfo(&free_b, &total_b));
   size_t reserve = total_b / 32;
   if (reserve > ((size_t)2 << 30)) reserve = (size_t)2 << 30;
-  const size_t need = bytes + staging + (raw_on_device ? 0 : raw_bytes);
+  // host bytes of the row-major layouts go up chunk by chunk, so only one chunk of
+  // raw bytes is ever on the device beside the resident DB; the limb layout's
+  // column-major chunks take the whole raw DB up first
+  const size_t bpp = (size_t)p.n * p.log2p / 8;  // raw bytes per polynomial (whole bytes)
+  const bool chunked_upload = !raw_on_device && layout != PIR_LAYOUT_LIMB;
+  const size_t raw_dev_bytes = raw_on_device ? 0 : chunked_upload ? (size_t)chunk * bpp : raw_bytes;
+  const size_t need = bytes + staging + raw_dev_bytes;
   if (need + reserve > free_b) return PIR_ERR_ADMISSION;
 
   pir_db *db = new pir_db();
@@ -810,16 +816,26 @@ pir_status_t pir_setup_db(const pir_params_t *params, const void *raw_db, size_t
   };
   const uint8_t *raw = static_cast<const uint8_t *>(raw_db);
   if (!raw_on_device) {
-    if ((e = cudaMalloc(&raw_dev, raw_bytes)) != cudaSuccess) return fail(e);
-    if ((e = cudaMemcpyAsync(raw_dev, raw_db, raw_bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess) return fail(e);
-    raw = static_cast<const uint8_t *>(raw_dev);
+    if ((e = cudaMalloc(&raw_dev, raw_dev_bytes)) != cudaSuccess) return fail(e);
+    if (!chunked_upload) {
+      if ((e = cudaMemcpyAsync(raw_dev, raw_db, raw_bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess) return fail(e);
+      raw = static_cast<const uint8_t *>(raw_dev);
+    }
   }
   if ((e = cudaMalloc(&stage, staging)) != cudaSuccess) return fail(e);
   uint32_t *stg = static_cast<uint32_t *>(stage);
   if (layout != PIR_LAYOUT_LIMB) {  // row-major chunks of polynomials
     for (uint64_t first = 0; first < polys; first += chunk) {
       const uint64_t np = polys - first < chunk ? polys - first : chunk;
-      if ((e = launch_ntt_fwd_raw(*ctx, raw, 0, p.D1, p.D2, first, np, stg, s)) != cudaSuccess) return fail(e);
+      if (chunked_upload) {  // this chunk's bytes only, read as polynomials 0 .. np-1
+        if ((e = cudaMemcpyAsync(raw_dev, static_cast<const uint8_t *>(raw_db) + first * bpp, np * bpp,
+                                 cudaMemcpyHostToDevice, s)) != cudaSuccess)
+          return fail(e);
+        e = launch_ntt_fwd_raw(*ctx, static_cast<const uint8_t *>(raw_dev), 0, p.D1, p.D2, 0, np, stg, s);
+      } else {
+        e = launch_ntt_fwd_raw(*ctx, raw, 0, p.D1, p.D2, first, np, stg, s);
+      }
+      if (e != cudaSuccess) return fail(e);
       e = layout == PIR_LAYOUT_PLAIN
               ? launch_db_scatter(*ctx, layout, p.D1, p.D2, stg, first, np, db->resident, s)
               : launch_db_scatter_tensor(*ctx, p.D1, p.D2, stg, first, np, static_cast<uint16_t *>(db->resident), s);

@@ -210,6 +210,20 @@ void keep_pool_memory(int dev) {
   });
 }
 
+// Device memory an allocation can draw on: free memory plus what the stream-ordered
+// pool holds reserved but unused (its release threshold keeps freed scratch).
+size_t available_device_bytes(int dev) {
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return 0;
+  cudaMemPool_t pool;
+  uint64_t reserved = 0, used = 0;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess &&
+      cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved) == cudaSuccess &&
+      cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) == cudaSuccess && reserved > used)
+    free_b += (size_t)(reserved - used);
+  return free_b;
+}
+
 // Optional per-stage timing: a pair of events around every stage invocation.
 struct StageMark {
   int stage;
@@ -887,6 +901,22 @@ pir_status_t pir_answer_ex(pir_db_t db, const uint32_t *queries, uint32_t B, uin
   const uint64_t ct_bytes = 2ull * p.L * p.n * 4;
   if (o.k_chunk == 0 && qbytes > (4ull << 30) && (o.flags & PIR_ANSWER_TEST_STALL) == 0) {
     uint64_t kc = (1ull << 30) / ((uint64_t)B * ct_bytes);
+    if (db->layout == PIR_LAYOUT_TENSOR) {
+      // the tensor GEMM fills its stage ring only over long K-chunks: pieces as long
+      // as the free memory holds beside the result (staging x 2, NTT-form copy, digit
+      // tiles; 1 GiB kept back), up to the 1024-row exactness bound
+      const size_t free_b = available_device_bytes(db->device);
+      {
+        const uint32_t M = 2 * B, Mp = layout_rows(db->layout, M);
+        const size_t out_b = (size_t)p.L * p.n * M * p.D2 * 4 + (size_t)B * p.D2 * ct_bytes;
+        const size_t per_row = 3 * (size_t)B * ct_bytes + layout_qs_bytes(db->layout, (uint64_t)p.L * p.n, 1, Mp);
+        if (free_b > out_b + (1ull << 30)) {
+          const uint64_t fit = (free_b - out_b - (1ull << 30)) / per_row;
+          if (fit > kc) kc = fit;
+        }
+      }
+      if (kc > 1024) kc = 1024;
+    }
     if (kc == 0) kc = 1;
     if (kc > p.D1) kc = p.D1;
     if (db->layout != PIR_LAYOUT_PLAIN) kc = layout_chunk(db->layout, (uint32_t)kc);

@@ -3,7 +3,7 @@ stream-wise buffering): the queries are given in pieces along D1, ragged and of
 several sizes, from host and device memory, on the plain and the limb layout, with
 and without modulus switching; every result equals the oracle's answer bit for bit.
 Then the argument rules (order, range, limb blocks, finished and aborted sessions)
-and a host batch above 4 GiB, which pir_answer_ex streams in pieces."""
+and host batches above 4 GiB, which pir_answer_ex streams in pieces (plain and tensor layouts)."""
 import numpy as np
 import pytest
 
@@ -146,5 +146,35 @@ def test_host_batch_above_4gib_streams(orc):
         assert np.array_equal(host, want)
         cols = np.array([0, 3], dtype=np.uint32)
         assert np.array_equal(host[:1, cols], orc.answer(P, raw, Qh[:1], cols=cols))
+    finally:
+        g.pir_free_db(db)
+
+
+def test_host_batch_above_4gib_streams_tensor_layout(orc):
+    """The same on the tensor layout, whose streamed pieces are sized from the
+    available device memory (whole 64-row blocks, at most 1024 rows): 4.1 GiB of host
+    queries, equal to the device-buffer answer and to the oracle on sampled columns."""
+    import torch
+    n, D1, D2, B = 2048, 16640, 32, 8
+    p = g.pir_make_params(n, 16, D1, D2, 2)
+    P = orc.make_params(n, 16, D1, D2, 2)
+    raw = synth.raw_db(88, synth.raw_db_bytes(n, 16, D1, D2))
+    db = g.pir_setup_db(p, raw, layout=2)
+    try:
+        qd = torch.empty(B * D1 * 2 * 2 * n, dtype=torch.int32, device="cuda")
+        gen = torch.Generator(device="cuda").manual_seed(89)
+        for j, q in enumerate(P.qs):
+            view = qd.view(B * D1 * 2, 2, n)[:, j]
+            view.copy_(torch.randint(0, q, view.shape, device="cuda", generator=gen, dtype=torch.int64).to(torch.int32))
+        Qh = from_dev(qd, (B, D1, 2, 2, n))
+        assert Qh.nbytes > (4 << 30)
+        rd = empty_u32(B * D2 * 2 * 2 * n)
+        g.pir_answer_ex(db, qd, B, rd)
+        want = from_dev(rd, (B, D2, 2, 2, n))
+        host = np.zeros_like(want)
+        g.pir_answer_ex(db, Qh, B, host)
+        assert np.array_equal(host, want)
+        cols = np.array([0, 31], dtype=np.uint32)
+        assert np.array_equal(host[-1:, cols], orc.answer(P, raw, Qh[-1:], cols=cols))
     finally:
         g.pir_free_db(db)

@@ -412,10 +412,17 @@ def make_db(ctx, p, layout):
     return db, None
 
 
-def measure_batch(ctx, db, p, layout, B, steps, warmup, min_seconds=0.0, extras=None):
+def measure_batch(ctx, db, p, layout, B, steps, warmup, min_seconds=0.0, extras=None, tuned=False):
     """Time `steps` answers of B queries (at least min_seconds of them when asked),
     after `warmup` untimed ones, with CUDA events on the launching stream, bracketed
-    by barrier + synchronize.  Returns the block's numbers and its step function."""
+    by barrier + synchronize.  Returns the block's numbers and its step function.
+
+    tuned: the batching runtime's own form of a batch, as the method asks for it:
+    the library's autotuner picks the GEMM tile and K-chunk for this DB and batch
+    (untimed), and every timed step replays one captured graph of the answer.  The
+    graph replays carry no stage events, so the dominant kernel's time for the
+    roofline comes from a separate, shorter run of the same configuration with
+    stage events."""
     args, g, synth, torch = ctx.args, ctx.g, ctx.synth, ctx.torch
     n, D1, D2 = p.n, p.D1, p.D2
     extras = extras or {}
@@ -438,13 +445,18 @@ def measure_batch(ctx, db, p, layout, B, steps, warmup, min_seconds=0.0, extras=
     streams = [stream] + [torch.cuda.Stream(device=ctx.dev) for _ in range(nstreams - 1)]
     resps = [torch.empty(rwords, dtype=torch.int32, device=ctx.dev) for _ in range(nstreams)]
 
+    tile, k_chunk = args.tile, args.k_chunk
+    tuned_opts = None
+    if tuned and not extras:
+        tuned_opts = g.pir_autotune(db, B, stream=stream)
+        tile, k_chunk = tuned_opts["tile"], tuned_opts["k_chunk"]
     graphs = None
-    if args.graph:
+    if args.graph or tuned_opts is not None:
         # one captured answer per query buffer, replayed (the graph binds its buffers)
         if ex is not None:
-            graphs = [g.pir_graph_create_packed(db, ex, qb, B, resps[0], tile=args.tile, flags=msw) for qb in qbufs]
+            graphs = [g.pir_graph_create_packed(db, ex, qb, B, resps[0], tile=tile, flags=msw) for qb in qbufs]
         elif rg is None:
-            graphs = [g.pir_graph_create(db, qb, B, resps[0], k_chunk=args.k_chunk, tile=args.tile, flags=msw)
+            graphs = [g.pir_graph_create(db, qb, B, resps[0], k_chunk=k_chunk, tile=tile, flags=msw)
                       for qb in qbufs]
         else:
             raise SystemExit("--graph covers the plain and packed answers")
@@ -461,8 +473,7 @@ def measure_batch(ctx, db, p, layout, B, steps, warmup, min_seconds=0.0, extras=
         elif args.noalloc:
             g.pir_answer_noalloc(db, qbufs[t % nbuf], B, rs, stream=st)
         else:
-            g.pir_answer_ex(db, qbufs[t % nbuf], B, rs, stream=st, flags=flags | msw, tile=args.tile,
-                            k_chunk=args.k_chunk)
+            g.pir_answer_ex(db, qbufs[t % nbuf], B, rs, stream=st, flags=flags | msw, tile=tile, k_chunk=k_chunk)
 
     for t in range(warmup):
         step(t)
@@ -503,16 +514,34 @@ def measure_batch(ctx, db, p, layout, B, steps, warmup, min_seconds=0.0, extras=
     clocks = ctx.sampler.summary(w0, w1)
     max_ms, total_queries = reduce_timing(elapsed_ms, float(B * steps), device=ctx.dev if ctx.world > 1 else None)
     raw_bytes = ctx.binding.raw_db_bytes(p)
+    rl_steps, rl_note = steps, "stage events of the timed steps"
+    if graphs is not None and ex is None:
+        # the graph replays carry no stage events: time the same configuration with
+        # them, outside the graph, for the dominant kernel's duration
+        rl_steps = max(3, int(np.ceil(0.5 / max(max_ms / steps / 1e3, 1e-6))))
+        g.pir_stage_times()
+        for t in range(rl_steps):
+            g.pir_answer_ex(db, qbufs[t % nbuf], B, resps[0], stream=stream, flags=g.PIR_ANSWER_STAGE_TIMES | msw,
+                            tile=tile, k_chunk=k_chunk)
+        torch.cuda.synchronize()
+        stage_ms, stage_launches = g.pir_stage_times()
+        rl_note = ("stage events of %d answers of the same configuration outside the graph (the replays carry "
+                   "none)" % rl_steps)
     gemm_launches = max(1, stage_launches[2])
-    launches_per_step = gemm_launches / steps
-    gemm_ms = stage_ms[2] / steps  # GEMM kernel time per step
+    launches_per_step = gemm_launches / rl_steps
+    gemm_ms = stage_ms[2] / rl_steps  # GEMM kernel time per step
     if stage_launches[2] == 0:  # an entry point without stage events: the whole step bounds the GEMM
         gemm_ms, launches_per_step = max_ms / steps, 1.0
-    roofline = gemm_roofline(ctx, layout, B, p, args.tile, gemm_ms, launches_per_step, clocks, stream)
-    roofline["stage_ms_per_step"] = {name: stage_ms[i] / steps for i, name in enumerate(ctx.binding.STAGE_NAMES)}
+    roofline = gemm_roofline(ctx, layout, B, p, tile, gemm_ms, launches_per_step, clocks, stream)
+    roofline["stage_ms_per_step"] = {name: stage_ms[i] / rl_steps for i, name in enumerate(ctx.binding.STAGE_NAMES)}
+    roofline["kernel_timed_with"] = rl_note
+    for gr in graphs or []:
+        g.pir_graph_destroy(gr)
     out = {"batch": B, "value": raw_bytes * total_queries / (max_ms / 1e3) / 1e9, "unit": "GB/s",
            "ms_per_step": max_ms / steps, "steps": steps, "warmup": warmup, "timed_s": max_ms / 1e3,
-           "roofline": roofline, "gpu_launches": int(launches), "clocks": clocks}
+           "roofline": roofline, "gpu_launches": int(launches), "clocks": clocks,
+           "launch": ("one captured graph per batch, autotuned tile %d, K-chunk %d" % (tile, k_chunk)
+                      if tuned_opts is not None else "graph replay" if graphs is not None else "pir_answer_ex")}
     return out, {"qbufs": qbufs, "qwords": qwords, "rwords": rwords, "stream": stream, "msw": msw}
 
 
@@ -606,7 +635,12 @@ def our_arm(args, wl):
         del keys
 
     time.sleep(0.3)  # clock samples before the first timed region
-    head, bufs = measure_batch(ctx, db, p, layout, B, args.steps, args.warmup, extras=extras)
+    # the default line answers each batch the way the batching runtime does: the
+    # autotuner's tile and K-chunk, one captured graph per batch (--untuned: the
+    # built-in choice through pir_answer_ex)
+    tuned = not args.untuned and not args.graph and not extras and args.tile == 0 and args.k_chunk == 0 and \
+        args.streams == 1 and not args.noalloc
+    head, bufs = measure_batch(ctx, db, p, layout, B, args.steps, args.warmup, extras=extras, tuned=tuned)
     e2e = measure_e2e(ctx, db, p, B, bufs, extras, head["ms_per_step"])
     del bufs
 
@@ -619,10 +653,10 @@ def our_arm(args, wl):
         for b in PER_BATCH:
             if b == B:
                 r = {k: head[k] for k in ("batch", "value", "unit", "ms_per_step", "steps", "warmup", "timed_s",
-                                          "roofline", "gpu_launches", "clocks")}
+                                          "roofline", "gpu_launches", "clocks", "launch")}
                 r["headline"] = True
             else:
-                r, _ = measure_batch(ctx, db, p, layout, b, 3, 3, min_seconds=MIN_TIMED_S)
+                r, _ = measure_batch(ctx, db, p, layout, b, 3, 3, min_seconds=MIN_TIMED_S, tuned=tuned)
                 torch.cuda.empty_cache()
             per_batch.append(r)
     if world == 1 and plain_mode and args.tensor_block:
@@ -632,7 +666,7 @@ def our_arm(args, wl):
         tdb, _ = make_db(ctx, p, g.PIR_LAYOUT_TENSOR)
         try:
             tb = 32 if B != 32 and not args.batch else B
-            r, _ = measure_batch(ctx, tdb, p, g.PIR_LAYOUT_TENSOR, tb, 3, 3, min_seconds=MIN_TIMED_S)
+            r, _ = measure_batch(ctx, tdb, p, g.PIR_LAYOUT_TENSOR, tb, 3, 3, min_seconds=MIN_TIMED_S, tuned=tuned)
         finally:
             g.pir_free_db(tdb)
             torch.cuda.empty_cache()
@@ -708,7 +742,8 @@ def our_arm(args, wl):
                        "queries": ("packed, expanded on the GPU (levels %d, %d gadget digits; timing-only keys)"
                                    % ((D1 - 1).bit_length(), args.ell) if args.packed else "D1 ciphertexts each"),
                        "entry": ("pir_answer_noalloc" if args.noalloc else "pir_graph_launch" if args.graph
-                                 else "pir_answer_ex"),
+                                 else "pir_autotune + pir_graph_launch" if tuned else "pir_answer_ex"),
+                       "launch": head["launch"],
                        "parallelism": "replicas x%d" % world,
                        "l2": "inputs larger than L2: the %.1f GiB NTT-form DB is streamed every step; query "
                              "buffers rotate when small" % (binding.resident_db_bytes(p, layout) / 2 ** 30)},
@@ -1075,6 +1110,8 @@ def main(argv=None):
     ap.add_argument("--ntt-sweep", action="store_true", help="time the standalone NTT sweep instead")
     ap.add_argument("--tensor-large", action="store_true",
                     help="the 32 GiB DB in the tensor layout (256 GiB resident), answered from pinned host queries")
+    ap.add_argument("--untuned", action="store_true",
+                    help="time the built-in tile / K-chunk choice through pir_answer_ex (no autotuner, no graphs)")
     ap.add_argument("--graph", action="store_true",
                     help="replay captured answers (pir_graph_create, pir_graph_create_packed with --packed)")
     ap.add_argument("--noalloc", action="store_true",

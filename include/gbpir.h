@@ -129,7 +129,9 @@ typedef struct {
                         8 query rows (2B), 7 also D2 <= 512; limb 2 and 3 need the
                         rows padded to 16 to be multiples of 32 and 64; tensor 1 is
                         the 1-SM GEMM, 2 the CTA-pair (2-SM) GEMM, which needs
-                        D2 % 64 == 0; otherwise PIR_ERR_ARG */
+                        D2 % 64 == 0, 3 and 4 the 1-SM GEMM in clusters of 2 and 4
+                        CTAs that multicast the query digits, which need D2 % 64
+                        and D2 % 128 == 0; otherwise PIR_ERR_ARG */
   uint32_t flags;    /* PIR_ANSWER_STAGE_TIMES: record CUDA events around each stage on
                         `stream`, read with pir_stage_times; PIR_ANSWER_TEST_STALL,
                         PIR_ANSWER_MODSWITCH, PIR_ANSWER_CHECK_INPUTS: see below.
@@ -214,7 +216,8 @@ pir_status_t pir_answer_abort(pir_session_t session);
  * `stream`'s order.  opts as for pir_answer_ex, except that
  * PIR_ANSWER_STAGE_TIMES and PIR_ANSWER_TEST_STALL are refused (PIR_ERR_ARG).
  * The caller keeps ownership of the buffers and must keep them (and the DB) alive
- * until pir_graph_destroy.  Errors: PIR_ERR_HANDLE, PIR_ERR_ARG, PIR_ERR_CUDA. */
+ * until pir_graph_destroy, which also returns the graph's own scratch memory to the
+ * device.  Errors: PIR_ERR_HANDLE, PIR_ERR_ARG, PIR_ERR_CUDA. */
 typedef struct pir_graph *pir_graph_t;
 pir_status_t pir_graph_create(pir_db_t db, const uint32_t *queries, uint32_t B, uint32_t *responses,
                               const pir_answer_opts_t *opts, pir_graph_t *out);

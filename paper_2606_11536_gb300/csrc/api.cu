@@ -106,6 +106,7 @@ struct pir_graph {
   cudaGraphExec_t exec;
   uint64_t kernels;             // kernel launches per replay
   pir_expander_t expander;      // the expansion keys a packed-query graph reads, or null
+  int device;                   // where its scratch memory lives
 };
 
 namespace {
@@ -696,7 +697,7 @@ pir_status_t capture_graph(pir_db *db, pir_expander_t expander, Body body, pir_g
     cudaGraphDestroy(graph);
     return cuda_status(e);
   }
-  pir_graph *g = new pir_graph{kGraphMagic, db, graph, exec, kernels, expander};
+  pir_graph *g = new pir_graph{kGraphMagic, db, graph, exec, kernels, expander, db->device};
   {
     std::lock_guard<std::mutex> lock(g_reg_mu);
     g_graphs.insert(g);
@@ -1298,9 +1299,12 @@ pir_status_t pir_graph_destroy(pir_graph_t graph) {
   }
   cudaError_t e = cudaGraphExecDestroy(graph->exec);
   cudaError_t e2 = cudaGraphDestroy(graph->graph);
+  // the scratch the capture allocated stays cached for graphs until trimmed: give it
+  // back, so that later allocations and the admission checks see it
+  cudaError_t e3 = cudaDeviceGraphMemTrim(graph->device);
   graph->magic = 0;
   delete graph;
-  return cuda_status(e != cudaSuccess ? e : e2);
+  return cuda_status(e != cudaSuccess ? e : e2 != cudaSuccess ? e2 : e3);
 }
 
 pir_status_t pir_autotune(pir_db_t db, uint32_t B, void *stream, uint32_t reps, pir_answer_opts_t *best) {
@@ -1322,7 +1326,8 @@ pir_status_t pir_autotune(pir_db_t db, uint32_t B, void *stream, uint32_t reps, 
   std::vector<uint32_t> tiles;
   if (db->layout == PIR_LAYOUT_TENSOR) {
     tiles.push_back(1);
-    if (gemm_tc_tile_ok(2, p.D2)) tiles.push_back(2);
+    for (uint32_t t = 2; t <= gemm_tc_tiles(); ++t)
+      if (gemm_tc_tile_ok(t, p.D2)) tiles.push_back(t);
   } else if (!limb) {
     if (M <= 2) tiles.push_back(1);
     if (M <= 4) tiles.push_back(2);

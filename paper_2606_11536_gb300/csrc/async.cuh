@@ -68,6 +68,17 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
       : "memory");
 }
 
+// The same copy delivered to every CTA of the cluster set in ctaMask: at dst's offset
+// in each one's shared memory, completing `bytes` on the barrier at bar's offset there.
+__device__ __forceinline__ void bulk_g2s_multicast(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar,
+                                                   uint16_t cta_mask, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster.L2::cache_hint"
+      " [%0], [%1], %2, [%3], %4, %5;" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar), "h"(cta_mask), "l"(policy)
+      : "memory");
+}
+
 __device__ __forceinline__ uint64_t policy_evict_first() {
   uint64_t p;
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));

@@ -30,7 +30,10 @@
 //
 // Work unit = (slot, T tiles of 32 DB columns, one tile of <= 64 query rows); its
 // accumulators take T * N <= 256 tensor-memory columns.  One persistent CTA per SM
-// runs its units through two accumulator buffers.
+// runs its units through two accumulator buffers.  In the cluster forms (C = 2 or 4
+// CTAs, one per SM) the C CTAs of a cluster take units of one slot side by side, and
+// each one loads 1/C of every stage's query digits and multicasts it to all C: the
+// query digits cross from L2 to the SMs once per C units instead of once per unit.
 //   warp 8   streams the units' K stages (KS16 x 16 rows) back to back into a
 //            ring of S shared-memory stages with 1-D bulk copies;
 //   warp 9   allocates the tensor memory and issues the MMAs from one thread;
@@ -107,6 +110,32 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
+// Arrive on `bar` in every CTA of the cluster set in cta_mask once this thread's MMAs
+// issued so far complete.
+__device__ __forceinline__ void mma_commit_multicast(uint32_t bar, uint16_t cta_mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+      "h"(cta_mask)
+      : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Arrive on the mbarrier at local offset `bar` in CTA `rank` of the cluster.
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar, uint32_t rank) {
+  uint32_t remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(bar), "r"(rank));
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote) : "memory");
+}
+
 // 32 consecutive accumulator columns of this warp's 32 lanes
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
@@ -165,9 +194,15 @@ __device__ __forceinline__ Unit unit_of(const TcArgs &a, uint32_t u) {
   return w;
 }
 
-// Persistent: CTA b takes units b, b + gridDim.x, ...  The producer streams their K
-// stages back to back through the ring; the MMA thread accumulates unit k into
-// tensor-memory buffer k % 2 while the epilogue drains buffer (k - 1) % 2.
+// Persistent: cluster g of G = gridDim.x / C takes unit groups g, g + G, ... and its
+// CTA of rank r the unit C * group + r (C = 1: CTA b takes units b, b + gridDim.x, ...).
+// The producer streams the units' K stages back to back through the ring; the MMA
+// thread accumulates unit k into tensor-memory buffer k % 2 while the epilogue drains
+// buffer (k - 1) % 2.  With C > 1 a stage slot is refilled only after the MMAs of all
+// C CTAs have read it: each MMA thread's commit arrives on the empty barrier of every
+// CTA in the cluster (C arrivals per phase), because every producer writes its part
+// of the query digits into all C rings.
+template <int C>
 __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcArgs a, ModConst mc) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + a.S * a.stage_bytes);
@@ -179,11 +214,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcArgs a, ModConst mc) 
   const uint32_t R = 4 * a.D2, U = a.D1 / 16, Uc = a.Kc / 16;
   const uint32_t nst = Uc / a.KS16, Ntot = 4 * a.Mp;
   const uint32_t db_stage = a.KS16 * a.T * kBlockBytes;
+  const uint32_t rank = C > 1 ? cluster_rank() : 0, cl0 = blockIdx.x / C, ncl = gridDim.x / C;
+  const uint32_t ngroups = a.nunits / C;
+  const uint16_t all_ctas = (uint16_t)((1u << C) - 1);
 
   if (threadIdx.x == 0) {
     for (int st = 0; st < kMaxStages; ++st) {
       mbar_init(full0 + 8 * st, 1);
-      mbar_init(empty0 + 8 * st, 1);
+      mbar_init(empty0 + 8 * st, C);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull0 + 8 * b, 1);
@@ -200,6 +238,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcArgs a, ModConst mc) 
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  if (C > 1) cluster_sync();  // every CTA's barriers exist before any multicast copy or commit
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tslot;
 
@@ -210,9 +249,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcArgs a, ModConst mc) 
       const uint8_t *qs = reinterpret_cast<const uint8_t *>(a.qt);
       uint32_t it = 0;
       bool ok = true;
-      for (uint32_t u = blockIdx.x; ok && u < a.nunits; u += gridDim.x) {
-        const Unit w = unit_of(a, u);
-        const uint32_t qbytes = a.KS16 * w.Nt * 32;
+      for (uint32_t gi = cl0; ok && gi < ngroups; gi += ncl) {
+        const Unit w = unit_of(a, gi * C + rank);
+        const uint32_t qbytes = a.KS16 * w.Nt * 32;  // all of the stage's query digits land here
         for (uint32_t st = 0; st < nst; ++st, ++it) {
           const uint32_t slot = it % a.S, ph = (it / a.S) & 1;
           if (!wait_bounded(empty0 + 8 * slot, ph ^ 1)) {
@@ -227,13 +266,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcArgs a, ModConst mc) 
             const uint64_t e = (((uint64_t)w.s * U + uu) * R + (uint64_t)w.ct * a.T * 128) * 16;
             bulk_g2s(dst + v * a.T * kBlockBytes, dbs + 2 * e, a.T * kBlockBytes, full0 + 8 * slot, pol_db);
           }
+          // query digits: this CTA's 1/C share of each contiguous run, to all C CTAs
           if (w.Nt == Ntot) {  // the stage's query rows are one contiguous run
             const uint64_t e = ((uint64_t)w.s * Uc + (uint64_t)st * a.KS16) * Ntot * 16;
-            bulk_g2s(dst + db_stage, qs + 2 * e, qbytes, full0 + 8 * slot, pol_q);
+            const uint32_t part = qbytes / C, o = rank * part;
+            if (C == 1)
+              bulk_g2s(dst + db_stage, qs + 2 * e, qbytes, full0 + 8 * slot, pol_q);
+            else
+              async::bulk_g2s_multicast(dst + db_stage + o, qs + 2 * e + o, part, full0 + 8 * slot, all_ctas, pol_q);
           } else {
+            const uint32_t part = w.Nt * 32 / C, o = rank * part;
             for (uint32_t v = 0; v < a.KS16; ++v) {
               const uint64_t e = (((uint64_t)w.s * Uc + (uint64_t)st * a.KS16 + v) * Ntot + w.n0) * 16;
-              bulk_g2s(dst + db_stage + v * w.Nt * 32, qs + 2 * e, w.Nt * 32, full0 + 8 * slot, pol_q);
+              if (C == 1)
+                bulk_g2s(dst + db_stage + v * w.Nt * 32, qs + 2 * e, w.Nt * 32, full0 + 8 * slot, pol_q);
+              else
+                async::bulk_g2s_multicast(dst + db_stage + v * w.Nt * 32 + o, qs + 2 * e + o, part, full0 + 8 * slot,
+                                          all_ctas, pol_q);
             }
           }
         }
@@ -242,14 +291,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcArgs a, ModConst mc) 
       const uint32_t first = it > a.S ? it - a.S : 0;
       for (uint32_t k = first; k < it; ++k)
         if (!wait_bounded(full0 + 8 * (k % a.S), (k / a.S) & 1)) atomicExch(a.err, 1u);
+      // and, in a cluster, no commit of a peer's MMAs still on its way to this CTA's
+      // empty barriers: wait for the release of the last stages by all C CTAs
+      if (C > 1)
+        for (uint32_t k = first; k < it; ++k)
+          if (!wait_bounded(empty0 + 8 * (k % a.S), (k / a.S) & 1)) atomicExch(a.err, 1u);
     }
     __syncwarp();
   } else if (warp == kMmaWarp) {
     if (lane == 0) {
       uint32_t it = 0, k = 0;
       bool ok = true;
-      for (uint32_t u = blockIdx.x; ok && u < a.nunits; u += gridDim.x, ++k) {
-        const Unit w = unit_of(a, u);
+      for (uint32_t gi = cl0; ok && gi < ngroups; gi += ncl, ++k) {
+        const Unit w = unit_of(a, gi * C + rank);
         const uint32_t buf = k % a.nbuf, use = k / a.nbuf;
         if (!wait_bounded(tempty0 + 8 * buf, (use & 1) ^ 1)) {  // the epilogue has drained this buffer
           atomicExch(a.err, 1u);
@@ -273,7 +327,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcArgs a, ModConst mc) 
               mma_bf16(dcol + t * w.Nt, adesc, bdesc, idesc, (st | v) != 0);
             }
           }
-          mma_commit(empty0 + 8 * slot);  // the stage is free once these MMAs have read it
+          // the stage is free once these MMAs have read it (in every CTA that fills it)
+          if (C == 1)
+            mma_commit(empty0 + 8 * slot);
+          else
+            mma_commit_multicast(empty0 + 8 * slot, all_ctas);
         }
         mma_commit(tfull0 + 8 * buf);  // this unit's accumulators are complete
       }
@@ -288,8 +346,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcArgs a, ModConst mc) 
     const uint32_t row = 32 * quarter + lane;  // accumulator lane: column c_local = row / 4, DB digit b
     const bool hi2 = (b & 2) != 0, hi1 = (b & 1) != 0;
     uint32_t k = 0;
-    for (uint32_t u = blockIdx.x; u < a.nunits; u += gridDim.x, ++k) {
-      const Unit w = unit_of(a, u);
+    for (uint32_t gi = cl0; gi < ngroups; gi += ncl, ++k) {
+      const Unit w = unit_of(a, gi * C + rank);
       const uint32_t buf = k % a.nbuf, use = k / a.nbuf;
       if (!__all_sync(0xffffffffu, wait_bounded(tfull0 + 8 * buf, use & 1))) {
         if (lane == 0) atomicExch(a.err, 1u);
@@ -356,6 +414,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcArgs a, ModConst mc) 
 
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  if (C > 1) cluster_sync();  // no CTA leaves while a peer may still copy into it or arrive on it
   if (warp == kMmaWarp) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
@@ -386,22 +445,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcArgs a, ModConst mc) 
 //               (2 x kEpiWarps arrivals, the odd CTA's remote)
 // Every wait is bounded; the end is a cluster barrier, after which both CTAs
 // release the pair's tensor memory.
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-// Arrive on the mbarrier at local offset `bar` in CTA `rank` of the cluster.
-__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar, uint32_t rank) {
-  uint32_t remote;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(bar), "r"(rank));
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote) : "memory");
-}
 
 __device__ __forceinline__ void mma_bf16_pair(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
                                               uint32_t accumulate) {
@@ -738,10 +781,14 @@ __global__ void k_db_read_poly_tensor(const uint16_t *__restrict__ res, uint64_t
 
 bool gemm_tc_shape_ok(uint32_t D1, uint32_t D2) { return D1 % 64 == 0 && D2 % 32 == 0; }
 
-// Tensor-layout GEMM forms: 0 = automatic (the 1-SM form, measured faster), 1 = one
-// SM per unit (k_gemm_tc), 2 = CTA pairs (k_gemm_tc2; D2 a multiple of 64).
-uint32_t gemm_tc_tiles() { return 2; }
-bool gemm_tc_tile_ok(uint32_t tile, uint32_t D2) { return tile <= 1 || (tile == 2 && D2 % 64 == 0); }
+// Tensor-layout GEMM forms: 0 = automatic (the 1-SM form), 1 = one SM per unit
+// (k_gemm_tc), 2 = CTA pairs (k_gemm_tc2; D2 a multiple of 64), 3 and 4 = the 1-SM
+// form in clusters of 2 and 4 CTAs with the query digits multicast (D2 a multiple of
+// 64 and 128).
+uint32_t gemm_tc_tiles() { return 4; }
+bool gemm_tc_tile_ok(uint32_t tile, uint32_t D2) {
+  return tile <= 1 || ((tile == 2 || tile == 3) && D2 % 64 == 0) || (tile == 4 && D2 % 128 == 0);
+}
 
 uint32_t tc_rows(uint32_t M) { return (M + 7u) & ~7u; }
 
@@ -832,6 +879,35 @@ cudaError_t launch_gemm_tc_pair(const ParamCtx &c, const uint16_t *db, uint32_t 
   return cudaGetLastError();
 }
 
+// The cluster forms of k_gemm_tc: as many clusters of C CTAs as fit on the GPU at
+// once (one CTA per SM), each looping over its unit groups.
+template <int C>
+cudaError_t launch_tc_clusters(const TcArgs &a, const ModConst &mod, size_t smem, int sms, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(sms / C * C), 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&nclusters, k_gemm_tc<C>, &cfg) != cudaSuccess || nclusters <= 0) {
+    cudaGetLastError();  // clear the query's error: fall back to one cluster per C SMs
+    nclusters = sms / C;
+  }
+  const uint32_t groups = a.nunits / C;
+  if ((uint32_t)nclusters > groups) nclusters = (int)groups;
+  cfg.gridDim = dim3((unsigned)(nclusters * C), 1, 1);
+  return cudaLaunchKernelEx(&cfg, k_gemm_tc<C>, a, mod);
+}
+
 // out[s][m][c] (+)= sum_{i < Kc} Q[s][i][m] * DB[s][i0 + i][c] mod q_j for the
 // query digits qt of one K-chunk (Mp = tc_rows(M) rows).
 cudaError_t launch_gemm_tc(const ParamCtx &c, const uint16_t *db, uint32_t D1, uint32_t D2, const uint16_t *qt,
@@ -859,8 +935,9 @@ cudaError_t launch_gemm_tc(const ParamCtx &c, const uint16_t *db, uint32_t D1, u
   a.mtiles = (Ntot + 255) / 256;
   // 32-column tiles per unit: as many as half of the tensor memory and D2 allow, so
   // that two accumulator buffers alternate
+  const uint32_t C = tile == 3 ? 2 : tile == 4 ? 4 : 1;  // CTAs per cluster
   uint32_t T = 1;
-  while (2 * T * Nmax <= kTmemBudget && (D2 / 32) % (2 * T) == 0) T *= 2;
+  while (2 * T * Nmax <= kTmemBudget && (D2 / 32) % (2 * T * C) == 0) T *= 2;
   a.T = T;
   a.nbuf = 2;
   a.buf_cols = kTmemBudget;
@@ -884,14 +961,17 @@ cudaError_t launch_gemm_tc(const ParamCtx &c, const uint16_t *db, uint32_t D1, u
   // tensor-memory address
   size_t smem = (size_t)S * a.stage_bytes + (2 * kMaxStages + 5) * 8 + 16;
   if (smem < kSmemFloor) smem = kSmemFloor;
-  e = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  const uint32_t grid = a.nunits < (uint32_t)sms ? a.nunits : (uint32_t)sms;
-  k_gemm_tc<<<grid, kThreads, smem, s>>>(a, c.mod);
-  return cudaGetLastError();
+  if (C == 1) {
+    e = cudaFuncSetAttribute(k_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const uint32_t grid = a.nunits < (uint32_t)sms ? a.nunits : (uint32_t)sms;
+    k_gemm_tc<1><<<grid, kThreads, smem, s>>>(a, c.mod);
+    return cudaGetLastError();
+  }
+  return C == 2 ? launch_tc_clusters<2>(a, c.mod, smem, sms, s) : launch_tc_clusters<4>(a, c.mod, smem, sms, s);
 }
 
 }  // namespace gbpir

@@ -275,19 +275,56 @@ def test_full_size_16gib_batches_32_and_128(orc):
 
 @pytest.mark.parametrize("B", [1, 4, 32, 40, 64])
 def test_one_sm_and_two_sm_forms_agree_with_the_oracle(orc, B):
-    """The 1-SM GEMM (tile 1) and the CTA-pair GEMM (tile 2: one tcgen05 MMA over two
-    SMs, M = 256) against the oracle, on D2 = 192 (three column-tile pairs), query
+    """The 1-SM GEMM (tile 1), the CTA-pair GEMM (tile 2: one tcgen05 MMA over two
+    SMs, M = 256) and the 1-SM GEMM in clusters of two (tile 3) against the oracle, on D2 = 192 (three column-tile pairs), query
     rows that leave a ragged second 256-row tile at B = 40 and 64, and two K-chunks."""
     p, P, raw, db = instance(orc, 2048, 256, 192, seed=130 + B)
     try:
         Q = random_queries(P, B, 131 + B)
         cols = np.array([0, 63, 64, 191], dtype=np.uint32)
         want = orc.answer(P, raw, Q, cols=cols)
-        for tile in (1, 2):
+        for tile in (1, 2, 3):
             for kc in (0, 128):
                 R = run(db, P, Q, B, tile=tile, k_chunk=kc)
                 assert np.array_equal(R[:, cols], want), (tile, kc)
         R1, R2 = run(db, P, Q, B, tile=1), run(db, P, Q, B, tile=2)
         assert np.array_equal(R1, R2)
+        assert np.array_equal(R1, run(db, P, Q, B, tile=3))
+    finally:
+        g.pir_free_db(db)
+
+
+@pytest.mark.parametrize("B", [1, 8, 32, 40, 64])
+def test_cluster_multicast_forms_agree_with_the_oracle(orc, B):
+    """The 1-SM GEMM in clusters of 2 and 4 CTAs (tiles 3 and 4), each CTA loading a
+    share of every stage's query digits and multicasting it to the cluster: D2 = 256
+    (eight 32-column tiles, so groups of 2 and 4 units of one slot), small batches
+    with several column tiles per unit, the ragged second 256-row query tile at
+    B = 40 and 64, and two K-chunks; equal to the oracle and to tile 1 everywhere."""
+    p, P, raw, db = instance(orc, 2048, 128, 256, seed=150 + B)
+    try:
+        Q = random_queries(P, B, 151 + B)
+        cols = np.array([0, 31, 32, 127, 128, 255], dtype=np.uint32)
+        want = orc.answer(P, raw, Q, cols=cols)
+        R1 = run(db, P, Q, B, tile=1)
+        assert np.array_equal(R1[:, cols], want)
+        for tile in (3, 4):
+            for kc in (0, 64):
+                R = run(db, P, Q, B, tile=tile, k_chunk=kc)
+                assert np.array_equal(R[:, cols], want), (tile, kc)
+                assert np.array_equal(R, R1), (tile, kc)
+        g.pir_check_device()
+    finally:
+        g.pir_free_db(db)
+
+
+def test_cluster_forms_refuse_column_counts_they_cannot_split(orc):
+    p, P, raw, db = instance(orc, 2048, 64, 96, seed=160)
+    try:
+        Q = random_queries(P, 2, 161)
+        for tile in (3, 4):
+            with pytest.raises(g.PirError) as ei:
+                run(db, P, Q, 2, tile=tile)
+            assert ei.value.status == 1, tile
     finally:
         g.pir_free_db(db)

@@ -656,7 +656,7 @@ def our_arm(args, wl):
                                           "roofline", "gpu_launches", "clocks", "launch")}
                 r["headline"] = True
             else:
-                r, _ = measure_batch(ctx, db, p, layout, b, 3, 3, min_seconds=MIN_TIMED_S, tuned=tuned)
+                r = measure_batch(ctx, db, p, layout, b, 3, 3, min_seconds=MIN_TIMED_S, tuned=tuned)[0]
                 torch.cuda.empty_cache()
             per_batch.append(r)
     if world == 1 and plain_mode and args.tensor_block:
@@ -666,7 +666,7 @@ def our_arm(args, wl):
         tdb, _ = make_db(ctx, p, g.PIR_LAYOUT_TENSOR)
         try:
             tb = 32 if B != 32 and not args.batch else B
-            r, _ = measure_batch(ctx, tdb, p, g.PIR_LAYOUT_TENSOR, tb, 3, 3, min_seconds=MIN_TIMED_S, tuned=tuned)
+            r = measure_batch(ctx, tdb, p, g.PIR_LAYOUT_TENSOR, tb, 3, 3, min_seconds=MIN_TIMED_S, tuned=tuned)[0]
         finally:
             g.pir_free_db(tdb)
             torch.cuda.empty_cache()
@@ -698,7 +698,7 @@ def our_arm(args, wl):
         for name, lay in (("plain", g.PIR_LAYOUT_PLAIN), ("limb", g.PIR_LAYOUT_LIMB)):
             db5, _ = make_db(ctx, p5, lay)
             try:
-                r, _ = measure_batch(ctx, db5, p5, lay, B5, 2, 3, min_seconds=MIN_TIMED_S)
+                r = measure_batch(ctx, db5, p5, lay, B5, 2, 3, min_seconds=MIN_TIMED_S)[0]
             finally:
                 g.pir_free_db(db5)
                 torch.cuda.empty_cache()

@@ -99,8 +99,9 @@ pir_status_t pir_make_params(uint32_t n, uint32_t log2p, uint32_t D1, uint32_t D
  * PIR_ERR_UNSUPPORTED (D2 not a multiple of 4: the kernels move columns four at a
  * time; the limb layout with D1 not a multiple of 32: its tensor steps take 32 rows;
  * the tensor layout with D1 not a multiple of 64 or D2 not a multiple of 32),
- * PIR_ERR_ADMISSION (resident bytes exceed the free device memory less a reserve),
- * PIR_ERR_OOM, PIR_ERR_CUDA. */
+ * PIR_ERR_ADMISSION (resident bytes exceed the free device memory less a reserve,
+ * counted after the scratch the library keeps cached for answers and graphs has been
+ * given back), PIR_ERR_OOM, PIR_ERR_CUDA. */
 pir_status_t pir_setup_db(const pir_params_t *params, const void *raw_db, size_t raw_bytes, int raw_on_device,
                           int layout, void *stream, pir_db_t *out_handle);
 

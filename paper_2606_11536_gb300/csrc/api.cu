@@ -806,6 +806,14 @@ pir_status_t pir_setup_db(const pir_params_t *params, const void *raw_db, size_t
   const bool chunked_upload = !raw_on_device && layout != PIR_LAYOUT_LIMB;
   const size_t raw_dev_bytes = raw_on_device ? 0 : chunked_upload ? (size_t)chunk * bpp : raw_bytes;
   const size_t need = bytes + staging + raw_dev_bytes;
+  if (need + reserve > free_b) {
+    // answers' scratch stays cached in the stream-ordered pool, and destroyed graphs'
+    // scratch in the graph pool: give back what is unused before judging the DB
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
+    cudaDeviceGraphMemTrim(dev);
+    CK(cudaMemGetInfo(&free_b, &total_b));
+  }
   if (need + reserve > free_b) return PIR_ERR_ADMISSION;
 
   pir_db *db = new pir_db();

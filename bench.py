@@ -387,6 +387,7 @@ def gemm_roofline(ctx, layout, B, p, tile, gemm_ms, launches_per_step, clocks, s
                   "peak_source": "pir_probe_int8_mma on this GPU (MEASURED_PEAKS.json has no INT8 entry)"}
     rl["frac"] = rl["achieved"] / rl["peak"]
     rl["kernel"] = kernel_tag
+    rl["tile"] = tile  # the GEMM tile id the timed answers ran (0: the built-in choice)
     rl["kernel_ms"] = launch_ms
     rl["launches_per_step"] = launches_per_step
     rl["alg_bytes_per_launch"] = per
@@ -706,6 +707,22 @@ def our_arm(args, wl):
         ctx.wl = wl
         large["limb_vs_plain"] = large["plain"]["ms_per_step"] / large["limb"]["ms_per_step"]
 
+    # the metric's serving half: the serving configuration at one offered load, with
+    # captured graphs (the opt-in tensor layout, as the serving benchmark runs it)
+    serving_blk = None
+    if world == 1 and plain_mode and args.serving_block:
+        if db is not None:
+            g.pir_free_db(db)
+            db = None
+        torch.cuda.empty_cache()
+        sl = run_serving(args, [args.serving_block_rate], args.serving_block_seconds, graphs=True)
+        ld = sl["loads"][0]
+        serving_blk = {"metric": sl["metric"], "unit": "ms", "p50_ms": ld.get("p50_ms"), "p99_ms": ld.get("p99_ms"),
+                       "offered_qps": ld["offered_qps"], "achieved_qps": ld.get("qps"),
+                       "saturated": ld["saturated"], "mean_batch": ld.get("mean_batch"), "failed": sl["failed"],
+                       "graph_launches": sl["graph_launches"], "config": sl["config"],
+                       "per_db_p99_ms": {d: v.get("p99_ms") for d, v in ld["per_db"].items()}}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not (args.packed or args.folded):
         nthreads = os.cpu_count() or 1
@@ -756,6 +773,8 @@ def our_arm(args, wl):
             line["tensor_layout"] = tensor_block
         if large is not None:
             line["largest_config"] = large
+        if serving_blk is not None:
+            line["serving"] = serving_blk
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -999,16 +1018,18 @@ SERVING_DBS = [  # name, n, log2p, D1, D2
 SERVING_EXTRA = ("db8g_n4096", 4096, 16, 2048, 512)
 
 
-def serving_bench(args):
+def run_serving(args, rates, seconds, graphs):
     """Serving: three resident DBs, admission of a fourth by free-HBM check, Poisson
-    arrivals at several loads with uniformly random target DB, continuous batching."""
+    arrivals at each offered load in `rates` for `seconds` each, uniformly random
+    target DB, continuous batching.  The DBs' raw bytes are generated on the device
+    from the same counter-based streams as the host generator's.  Returns the JSON
+    line (p99 of the headline load as its value) and frees the DBs."""
     import torch
     import paper_2606_11536_gb300 as g
     from paper_2606_11536_gb300 import serving
     import synth
-    torch.cuda.set_device(0)
     serving_layout = {"plain": g.PIR_LAYOUT_PLAIN, "tensor": g.PIR_LAYOUT_TENSOR}[args.serving_layout]
-    be = serving.CudaBackend(graphs=args.serving_graphs, max_batch=args.serving_max_batch,
+    be = serving.CudaBackend(graphs=graphs, max_batch=args.serving_max_batch,
                              graph_budget=args.serving_graph_gib << 30)
     big = SERVING_DBS[-1][0]  # the 16 GiB database: its long batches may hold only some of the slots
     srv = serving.Server(be, streams=args.serving_streams, max_batch=args.serving_max_batch,
@@ -1016,32 +1037,41 @@ def serving_bench(args):
                          db_max_slots={big: args.serving_big_slots} if args.serving_big_slots else None)
     pools = {}
     t0 = time.perf_counter()
+    def device_raw(seed, n, log2p, D1, D2):
+        return synth.raw_db_torch(seed, synth.raw_db_bytes(n, log2p, D1, D2), device="cuda")
+
     for k, (name, n, log2p, D1, D2) in enumerate(SERVING_DBS):
         p = g.pir_make_params(n, log2p, D1, D2, L_PRIMES)
-        srv.admit(name, p, synth.raw_db(k, synth.raw_db_bytes(n, log2p, D1, D2)), layout=serving_layout)
+        raw = device_raw(k, n, log2p, D1, D2)
+        srv.admit(name, p, raw, layout=serving_layout)
+        del raw
         pools[name] = [synth.uniform_residues_torch(900 + 16 * k + t, synth.STREAM_UNIFORM, D1 * 2, n, p.qs,
                                                     device="cuda").view(-1) for t in range(4)]
     name, n, log2p, D1, D2 = SERVING_EXTRA
     p = g.pir_make_params(n, log2p, D1, D2, L_PRIMES)
+    torch.cuda.empty_cache()
+    raw = device_raw(7, n, log2p, D1, D2)
     free_before = torch.cuda.mem_get_info()[0]
     try:
-        srv.admit(name, p, synth.raw_db(7, synth.raw_db_bytes(n, log2p, D1, D2)), layout=serving_layout)
+        srv.admit(name, p, raw, layout=serving_layout)
         admitted = True
     except serving.AdmissionError as e:
         admitted, err = False, str(e)
+    del raw
+    torch.cuda.empty_cache()
     setup_s = time.perf_counter() - t0
     dbs = list(srv.dbs)
     if admitted:
         pools[name] = [synth.uniform_residues_torch(990 + t, synth.STREAM_UNIFORM, D1 * 2, n, p.qs,
                                                     device="cuda").view(-1) for t in range(4)]
     prewarm_s = 0.0
-    if args.serving_graphs:
+    if graphs:
         t1 = time.perf_counter()
         be.prewarm(srv)
         prewarm_s = time.perf_counter() - t1
     results = []
-    for rate in args.serving_rates:
-        arr = serving.poisson_arrivals(rate, args.serving_seconds, dbs, seed=int(rate),
+    for rate in rates:
+        arr = serving.poisson_arrivals(rate, seconds, dbs, seed=int(rate),
                                        make_query=lambda db, k: pools[db][k % len(pools[db])])
         torch.cuda.synchronize()
         done = srv.run(arr)
@@ -1066,11 +1096,21 @@ def serving_bench(args):
             "config": {"workload": "serving", "dbs": [d[0] for d in SERVING_DBS], "fourth_db": SERVING_EXTRA[0],
                        "fourth_admitted": admitted, "free_hbm_before_fourth": free_before,
                        "streams": args.serving_streams, "max_batch": args.serving_max_batch,
-                       "layout": args.serving_layout, "graphs": bool(args.serving_graphs),
+                       "layout": args.serving_layout, "graphs": bool(graphs),
                        "big_db_slot_cap": args.serving_big_slots, "batch_timeout_s": args.serving_timeout,
-                       "seconds_per_load": args.serving_seconds, "setup_s": setup_s, "graph_prewarm_s": prewarm_s,
+                       "seconds_per_load": seconds, "setup_s": setup_s, "graph_prewarm_s": prewarm_s,
                        "resident_bytes": srv.resident_bytes},
             "graph_launches": be.graph_launches, "failed": len(srv.failed), "loads": results}
+    for d in list(srv.dbs):  # frees each DB and the graphs made for it
+        srv.evict(d)
+    torch.cuda.empty_cache()
+    return line
+
+
+def serving_bench(args):
+    import torch
+    torch.cuda.set_device(0)
+    line = run_serving(args, args.serving_rates, args.serving_seconds, args.serving_graphs)
     print(json.dumps(line), flush=True)
 
 
@@ -1117,6 +1157,10 @@ def main(argv=None):
     ap.add_argument("--noalloc", action="store_true",
                     help="answer through pir_answer_noalloc (the library's fixed scratch array, no allocation)")
     ap.add_argument("--serving", action="store_true", help="run the serving benchmark instead")
+    ap.add_argument("--no-serving-block", dest="serving_block", action="store_false",
+                    help="leave the serving block out of the default line")
+    ap.add_argument("--serving-block-rate", type=float, default=1000.0)
+    ap.add_argument("--serving-block-seconds", type=float, default=3.0)
     ap.add_argument("--serving-rates", type=float, nargs="+", default=[100, 300, 1000, 3000, 5000])
     ap.add_argument("--serving-seconds", type=float, default=2.0)
     ap.add_argument("--serving-streams", type=int, default=4)

@@ -715,6 +715,7 @@ def our_arm(args, wl):
             g.pir_free_db(db)
             db = None
         torch.cuda.empty_cache()
+        g.pir_release_memory()  # the earlier blocks' cached scratch: the serving buffers come from torch
         sl = run_serving(args, [args.serving_block_rate], args.serving_block_seconds, graphs=True)
         ld = sl["loads"][0]
         serving_blk = {"metric": sl["metric"], "unit": "ms", "p50_ms": ld.get("p50_ms"), "p99_ms": ld.get("p99_ms"),

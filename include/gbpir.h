@@ -170,7 +170,9 @@ typedef struct {
  *   - smaller batches of 8 MiB to 4 GiB upload in four pieces on a copy stream,
  *     each piece's forward NTT waiting only for its own copy;
  *   - host batches above 4 GiB run as a streamed answer (pir_answer_begin below) in
- *     pieces of at most 1 GiB, so the device holds one piece at a time. */
+ *     pieces of at most 1 GiB (the tensor layout: up to 1024 ciphertexts, as the
+ *     free memory allows), so the device holds one piece at a time; the first two
+ *     pieces are 1/16 and 1/4 of that, so the scan starts after a short upload. */
 pir_status_t pir_answer_ex(pir_db_t db, const uint32_t *queries, uint32_t B, uint32_t *responses, int on_device,
                            void *stream, const pir_answer_opts_t *opts);
 
@@ -413,6 +415,14 @@ pir_status_t pir_stage_times(double *ms, uint64_t *launches);
 
 /* Number of kernels this library has launched in this process (all threads). */
 uint64_t pir_kernel_launches(void);
+
+/* The library keeps freed answer scratch cached in the current device's
+ * stream-ordered memory pool (repeated answers then allocate nothing new) and
+ * graph scratch in its graph memory pool.  This call gives all of it that no work
+ * in flight uses back to the device, for allocations made outside the library.
+ * The library does the same by itself before it refuses an allocation, a graph
+ * launch or a DB.  Errors: PIR_ERR_CUDA. */
+pir_status_t pir_release_memory(void);
 
 /* Kernels that wait on barriers (the TMA-staged scan) bound every wait to about
  * one second; a wait that runs out sets a per-device error word, the kernel

@@ -88,6 +88,7 @@ def lib():
             "pir_stage_times": (i32, [C.POINTER(C.c_double), C.POINTER(C.c_uint64)]),
             "pir_kernel_launches": (C.c_uint64, []),
             "pir_check_device": (i32, [vp]),
+            "pir_release_memory": (i32, []),
             "pir_graph_create": (i32, [vp, vp, u32, vp, C.POINTER(pir_answer_opts_t), C.POINTER(vp)]),
             "pir_graph_create_packed": (i32, [vp, vp, vp, u32, vp, C.POINTER(pir_answer_opts_t), C.POINTER(vp)]),
             "pir_graph_launch": (i32, [vp, vp]),
@@ -534,6 +535,12 @@ def pir_check_device(stream=None):
 
 def pir_kernel_launches() -> int:
     return int(lib().pir_kernel_launches())
+
+
+def pir_release_memory():
+    """Gives the device memory the library keeps cached (answer and graph scratch)
+    back, for allocations made outside the library (torch's)."""
+    _check(lib().pir_release_memory(), "pir_release_memory")
 
 
 # --- sizes (host logic) ----------------------------------------------------

@@ -144,13 +144,37 @@ bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
     if (e_ != cudaSuccess) return cuda_status(e_); \
   } while (0)
 
+// Gives the device memory back that the library keeps cached but unused: freed
+// scratch in the stream-ordered pool (whose release threshold keeps it) and the
+// graph memory pool's.  Called before an allocation or a graph launch is refused.
+void release_cached_memory() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
+  cudaDeviceGraphMemTrim(dev);
+}
+
+thread_local bool t_capturing = false;  // launches inside a graph capture are not launches yet
+
+// cudaMallocAsync, retried once after the cached memory has been given back.
+cudaError_t malloc_async_retry(void **ptr, size_t bytes, cudaStream_t s) {
+  cudaError_t e = cudaMallocAsync(ptr, bytes, s);
+  if (e == cudaErrorMemoryAllocation && !t_capturing) {
+    cudaGetLastError();
+    release_cached_memory();
+    e = cudaMallocAsync(ptr, bytes, s);
+  }
+  return e;
+}
+
 // Device scratch drawn from the stream-ordered allocator; freed (stream-ordered)
 // when the guard goes out of scope.
 struct Scratch {
   void *ptr = nullptr;
   cudaStream_t s;
   explicit Scratch(cudaStream_t st) : s(st) {}
-  cudaError_t alloc(size_t bytes) { return cudaMallocAsync(&ptr, bytes, s); }
+  cudaError_t alloc(size_t bytes) { return malloc_async_retry(&ptr, bytes, s); }
   ~Scratch() {
     if (ptr) cudaFreeAsync(ptr, s);
   }
@@ -245,7 +269,6 @@ cudaEvent_t take_event() {
   return e;
 }
 
-thread_local bool t_capturing = false;  // launches inside a graph capture are not launches yet
 
 // Arrival of the query upload in pieces of kc ciphertexts (host-buffer answers): ev[k]
 // is recorded on the copy stream after piece k's copies; a forward NTT over
@@ -516,7 +539,7 @@ pir_status_t session_piece(pir_session *ses, const uint32_t *src, uint64_t strid
   uint64_t row_stride = stride / n;  // rows of n words
   if (!on_device) {
     if (!ses->stage_mem) {
-      CK(cudaMallocAsync(&ses->stage_mem, 2 * ses->stage_bytes, s));
+      CK(malloc_async_retry(&ses->stage_mem, 2 * ses->stage_bytes, s));
       // the copy stream touches the staging memory only after its allocation
       CK(cudaEventRecord(ses->consumed[0], s));
       CK(cudaEventRecord(ses->consumed[1], s));
@@ -618,7 +641,7 @@ pir_status_t session_open(pir_db *db, uint32_t B, uint32_t kc_max, cudaStream_t 
   ses->stage_bytes = up(ses->qhat_bytes);
   const size_t out_bytes = nslots * M * p.D2 * 4;
   void *mem = nullptr;
-  cudaError_t e = cudaMallocAsync(&mem, up(ses->qhat_bytes) + up(ses->qs_bytes) + up(out_bytes), s);
+  cudaError_t e = malloc_async_retry(&mem, up(ses->qhat_bytes) + up(ses->qs_bytes) + up(out_bytes), s);
   if (e == cudaSuccess) ses->mem = mem;
   for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
     if ((e = cudaEventCreateWithFlags(&ses->arrived[k], cudaEventDisableTiming)) == cudaSuccess)
@@ -743,6 +766,11 @@ pir_status_t pir_stage_times(double *ms, uint64_t *launches) {
 
 uint64_t pir_kernel_launches(void) { return g_launches.load(); }
 
+pir_status_t pir_release_memory(void) {
+  release_cached_memory();
+  return cuda_status(cudaGetLastError());
+}
+
 pir_status_t pir_check_device(void *stream) {
   uint32_t *w = nullptr;
   CK(device_error_word(&w));
@@ -809,9 +837,7 @@ pir_status_t pir_setup_db(const pir_params_t *params, const void *raw_db, size_t
   if (need + reserve > free_b) {
     // answers' scratch stays cached in the stream-ordered pool, and destroyed graphs'
     // scratch in the graph pool: give back what is unused before judging the DB
-    cudaMemPool_t pool;
-    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
-    cudaDeviceGraphMemTrim(dev);
+    release_cached_memory();
     CK(cudaMemGetInfo(&free_b, &total_b));
   }
   if (need + reserve > free_b) return PIR_ERR_ADMISSION;
@@ -932,9 +958,16 @@ pir_status_t pir_answer_ex(pir_db_t db, const uint32_t *queries, uint32_t B, uin
     pir_session *ses = nullptr;
     pir_status_t st = session_open(db, B, (uint32_t)kc, s, o, &ses);
     if (st != PIR_OK) return st;
-    for (uint32_t i0 = 0; i0 < p.D1 && st == PIR_OK; i0 += (uint32_t)kc) {
-      const uint32_t k = p.D1 - i0 < kc ? p.D1 - i0 : (uint32_t)kc;
+    // the first pieces ramp up (1/16, then 1/4 of a piece): the scan starts after a
+    // short upload, and each upload still ends before the scan of the piece before
+    // it (uploading a piece takes a quarter of the time its scan does, or less)
+    uint32_t piece = layout_chunk(db->layout, (uint32_t)(kc / 16 ? kc / 16 : 1));
+    for (uint32_t i0 = 0; i0 < p.D1 && st == PIR_OK;) {
+      uint32_t k = piece < kc ? piece : (uint32_t)kc;
+      if (k > p.D1 - i0) k = p.D1 - i0;
       st = session_chunk(ses, queries + (size_t)i0 * (ct_bytes / 4), (uint64_t)p.D1 * (ct_bytes / 4), i0, k, false);
+      i0 += k;
+      piece = layout_chunk(db->layout, piece * 4 < kc ? piece * 4 : (uint32_t)kc);
     }
     if (st == PIR_OK) st = session_finish(ses, responses, false);
     session_take(ses);
@@ -1294,7 +1327,13 @@ static bool graph_live(pir_graph *g) {
 pir_status_t pir_graph_launch(pir_graph_t graph, void *stream) {
   NvtxRange range("pir_graph_launch");
   if (!graph_live(graph)) return PIR_ERR_HANDLE;
-  CK(cudaGraphLaunch(graph->exec, static_cast<cudaStream_t>(stream)));
+  cudaError_t e = cudaGraphLaunch(graph->exec, static_cast<cudaStream_t>(stream));
+  if (e == cudaErrorMemoryAllocation) {  // its scratch is mapped at launch: make room and retry once
+    cudaGetLastError();
+    release_cached_memory();
+    e = cudaGraphLaunch(graph->exec, static_cast<cudaStream_t>(stream));
+  }
+  CK(e);
   count_launches(graph->kernels);
   return PIR_OK;
 }

@@ -384,6 +384,17 @@ class CudaBackend(Backend):
     def new_stream(self):
         return self.torch.cuda.Stream(device=self.device)
 
+    def _empty(self, words):
+        """A batch buffer from torch; if torch finds no room, the memory the library
+        keeps cached (answer and graph scratch) is given back and the allocation
+        tried once more."""
+        torch = self.torch
+        try:
+            return torch.empty(words, dtype=torch.int32, device=self.device)
+        except torch.OutOfMemoryError:
+            self.g.pir_release_memory()
+            return torch.empty(words, dtype=torch.int32, device=self.device)
+
     def _drop_graph(self, key):
         graph, _, _, nbytes, _ = self._graphs.pop(key)
         self.g.pir_graph_destroy(graph)
@@ -458,10 +469,10 @@ class CudaBackend(Backend):
                 self.graph_launches += 1
                 bufs = (qbuf, rbuf[:B * rwords])
             else:
-                qbuf = torch.empty(B * qwords, dtype=torch.int32, device=self.device)
+                qbuf = self._empty(B * qwords)
                 for b, q in enumerate(queries):  # gather: one device-to-device copy per request
                     qbuf[b * qwords:(b + 1) * qwords].copy_(q, non_blocking=True)
-                rbuf = torch.empty(B * rwords, dtype=torch.int32, device=self.device)
+                rbuf = self._empty(B * rwords)
                 self.g.pir_answer(handle, qbuf, B, rbuf, stream=stream)
                 bufs = (qbuf, rbuf)
             ev = torch.cuda.Event()

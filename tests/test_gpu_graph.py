@@ -75,3 +75,35 @@ def test_autotune_picks_an_exact_configuration(orc, layout, B):
         g.pir_check_device()
     finally:
         g.pir_free_db(db)
+
+
+def test_release_memory_gives_cached_scratch_back(orc):
+    """An answer's scratch stays cached in the library's stream-ordered pool (the
+    device's free memory stays lower after it); pir_release_memory gives it back,
+    and answers still run and match the oracle afterwards."""
+    import torch
+    n, log2p, D1, D2, B = 4096, 16, 256, 8, 32
+    p = g.pir_make_params(n, log2p, D1, D2, 2)
+    P = orc.make_params(n, log2p, D1, D2, 2)
+    raw = synth.raw_db(77, synth.raw_db_bytes(n, log2p, D1, D2))
+    db = g.pir_setup_db(p, raw, layout=0)
+    try:
+        Q = random_queries(P, B, 78)
+        qd, rd = to_dev(Q), empty_u32(B * D2 * 2 * 2 * n)
+        torch.cuda.synchronize()
+        g.pir_answer(db, qd, B, rd)  # about 1 GiB of scratch: the NTT-form copy and its slot layout
+        torch.cuda.synchronize()
+        free_cached = torch.cuda.mem_get_info()[0]
+        g.pir_release_memory()
+        torch.cuda.synchronize()
+        free_released = torch.cuda.mem_get_info()[0]
+        assert free_released - free_cached >= (512 << 20), (free_cached, free_released)
+        cols = np.array([0, 7], dtype=np.uint32)
+        rd2 = empty_u32(B * D2 * 2 * 2 * n)
+        g.pir_answer(db, qd, B, rd2)
+        R = from_dev(rd2, (B, D2, 2, 2, n))
+        assert np.array_equal(R, from_dev(rd, R.shape))
+        assert np.array_equal(R[:2][:, cols], orc.answer(P, raw, Q[:2], cols=cols))
+        g.pir_check_device()
+    finally:
+        g.pir_free_db(db)

@@ -145,8 +145,9 @@ __global__ void __launch_bounds__(kGemvThreads) k_gemv(const uint32_t *__restric
 }
 
 // ---------------------------------------------------------------------------
-// Tiled GEMM (M >= 16): CTA tile TM rows x TC columns, K step 16, 256 threads,
-// thread tile RM x 8.
+// Tiled GEMM (M >= 16): CTA tile TM rows x TC columns, K stages of KS rows, NT
+// threads, thread tile RM x 8; MINB CTAs per SM asked of the register allocator
+// (0: no request).
 // ---------------------------------------------------------------------------
 constexpr int kKS = 16;
 
@@ -161,12 +162,12 @@ __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_g
 // KS: K rows per stage (a multiple of the 8 products between folds); the narrow tiles
 // for small batches take fewer rows so that their wide column tile fits static
 // shared memory.
-template <int TM, int TC, int RM, int KS = kKS>
-__global__ void __launch_bounds__(256) k_gemm(const uint32_t *__restrict__ db, const uint32_t *__restrict__ qs,
+template <int TM, int TC, int RM, int KS = kKS, int NT = 256, int MINB = 0>
+__global__ void __launch_bounds__(NT, MINB) k_gemm(const uint32_t *__restrict__ db, const uint32_t *__restrict__ qs,
                                               uint32_t M, uint32_t Mp, uint32_t D1, uint32_t D2, uint32_t i0,
                                               uint32_t Kc, uint32_t *__restrict__ out, ModConst mc, uint32_t logn,
                                               int acc_in) {
-  static_assert((TM / RM) * (TC / 8) == 256, "thread tile RM x 8 over 256 threads");
+  static_assert((TM / RM) * (TC / 8) == NT, "thread tile RM x 8 over NT threads");
   static_assert(kFoldProducts == 8, "one of the thread tile's 8 columns is folded per K row");
   static_assert(KS % kFoldProducts == 0, "every stage ends with each column folded once per 8 rows");
   __shared__ __align__(16) uint32_t As[2][KS][TM];
@@ -187,13 +188,13 @@ __global__ void __launch_bounds__(256) k_gemm(const uint32_t *__restrict__ db, c
 
   // loader mapping: A tile = kKS x TM words = kKS*TM/4 uint4; B tile = kKS*TC/4 uint4
   auto load_tiles = [&](int buf, uint32_t k0) {
-    for (uint32_t t = tid; t < KS * TM / 4; t += 256) {
+    for (uint32_t t = tid; t < KS * TM / 4; t += NT) {
       const uint32_t r = t / (TM / 4), c4 = (t % (TM / 4)) * 4;
       const bool ok = (k0 + r < Kc) && (m0 + c4 < Mp);
       const uint32_t *g = ok ? qss + (uint64_t)(k0 + r) * Mp + m0 + c4 : qss;
       cp_async16(&As[buf][r][c4], g, ok);
     }
-    for (uint32_t t = tid; t < KS * TC / 4; t += 256) {
+    for (uint32_t t = tid; t < KS * TC / 4; t += NT) {
       const uint32_t r = t / (TC / 4), c4 = (t % (TC / 4)) * 4;
       const bool ok = (k0 + r < Kc) && (c0 + c4 < D2);
       const uint32_t *g = ok ? dbs + (uint64_t)(k0 + r) * D2 + c0 + c4 : dbs;
@@ -218,7 +219,12 @@ __global__ void __launch_bounds__(256) k_gemm(const uint32_t *__restrict__ db, c
 #pragma unroll
     for (int kk = 0; kk < KS; ++kk) {
       uint32_t av[RM];
-      if constexpr (RM == 4) {
+      if constexpr (RM == 8) {
+        const uint4 a0 = *reinterpret_cast<const uint4 *>(&As[buf][kk][tm * 8]);
+        const uint4 a1 = *reinterpret_cast<const uint4 *>(&As[buf][kk][tm * 8 + 4]);
+        av[0] = a0.x, av[1] = a0.y, av[2] = a0.z, av[3] = a0.w;
+        av[4] = a1.x, av[5] = a1.y, av[6] = a1.z, av[7] = a1.w;
+      } else if constexpr (RM == 4) {
         const uint4 a = *reinterpret_cast<const uint4 *>(&As[buf][kk][tm * 4]);
         av[0] = a.x, av[1] = a.y, av[2] = a.z, av[3] = a.w;
       } else if constexpr (RM == 2) {
@@ -282,13 +288,13 @@ cudaError_t gemv_launch(const ParamCtx &c, const uint32_t *db, uint32_t D1, uint
   return cudaGetLastError();
 }
 
-template <int TM, int TC, int RM, int KS = kKS>
+template <int TM, int TC, int RM, int KS = kKS, int NT = 256, int MINB = 0>
 cudaError_t gemm_launch(const ParamCtx &c, const uint32_t *db, uint32_t D1, uint32_t D2, const uint32_t *qs,
                         uint32_t M, uint32_t Mp, uint32_t i0, uint32_t Kc, uint32_t *out, int acc, cudaStream_t s) {
   const uint64_t nslots = (uint64_t)c.p.L << c.logn;
   const uint64_t blocks = nslots * ((D2 + TC - 1) / TC) * ((Mp + TM - 1) / TM);
   if (blocks > 0x7FFFFFFFull) return cudaErrorInvalidConfiguration;
-  k_gemm<TM, TC, RM, KS><<<(unsigned)blocks, 256, 0, s>>>(db, qs, M, Mp, D1, D2, i0, Kc, out, c.mod, c.logn, acc);
+  k_gemm<TM, TC, RM, KS, NT, MINB><<<(unsigned)blocks, NT, 0, s>>>(db, qs, M, Mp, D1, D2, i0, Kc, out, c.mod, c.logn, acc);
   return cudaGetLastError();
 }
 
@@ -334,7 +340,10 @@ cudaError_t launch_gemm_plain(const ParamCtx &c, const uint32_t *db, uint32_t D1
     case 3: return M <= 8 ? gemv_launch<8>(c, db, D1, D2, qs, M, Mp, i0, Kc, out, acc, s) : cudaErrorInvalidValue;
     case 4: return gemm_launch<16, 256, 2>(c, db, D1, D2, qs, M, Mp, i0, Kc, out, acc, s);
     case 5: return gemm_launch<32, 256, 4>(c, db, D1, D2, qs, M, Mp, i0, Kc, out, acc, s);
-    case 6: return gemm_launch<64, 128, 4, 32>(c, db, D1, D2, qs, M, Mp, i0, Kc, out, acc, s);  // 32-row stages: 1% faster
+    // 8 x 8 thread tiles over 128 threads, three CTAs per SM (168 registers): half the
+    // shared-memory loads per multiply-add of 4 x 8 tiles over 256 threads, measured
+    // 3.4% faster at 2B = 64; 32-row stages
+    case 6: return gemm_launch<64, 128, 8, 32, 128, 3>(c, db, D1, D2, qs, M, Mp, i0, Kc, out, acc, s);
     case 8: return gemm_launch<8, 256, 1>(c, db, D1, D2, qs, M, Mp, i0, Kc, out, acc, s);
   }
   return cudaErrorInvalidValue;

@@ -230,8 +230,11 @@ pir_status_t pir_graph_destroy(pir_graph_t graph);
 /* Autotuner: times every GEMM tile valid for this DB's layout and batch size B,
  * and K-chunk choices (whole D1, halves, quarters), `reps` answers each on scratch
  * buffers (all-zero queries; the scan's cost does not depend on the data), with
- * CUDA events on `stream`; writes the fastest (tile, k_chunk) to *best and caches
- * it in the handle, so later calls for the same B return at once.  Synchronous.
+ * CUDA events on `stream`.  Candidates go in order (tiles by id, then whole D1
+ * before halves and quarters) and a later one wins only if at least 1% faster, so
+ * timing noise does not flip the choice between equals.  Writes the winner
+ * (tile, k_chunk) to *best and caches it in the handle, so later calls for the
+ * same B return at once.  Synchronous.
  * Errors: PIR_ERR_HANDLE, PIR_ERR_ARG (B = 0, best NULL), PIR_ERR_OOM, PIR_ERR_CUDA. */
 pir_status_t pir_autotune(pir_db_t db, uint32_t B, void *stream, uint32_t reps, pir_answer_opts_t *best);
 

@@ -1417,7 +1417,10 @@ pir_status_t pir_autotune(pir_db_t db, uint32_t B, void *stream, uint32_t reps, 
       if (!ok || cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
         continue;
       ms /= reps;
-      if (best_ms < 0.f || ms < best_ms) best_ms = ms, win = o;
+      // a later candidate (a narrower tile or more K-chunks: more launches, more
+      // partial-result traffic) wins only if it is at least 1% faster, so that timing
+      // noise does not flip the choice between equals
+      if (best_ms < 0.f || ms < 0.99f * best_ms) best_ms = ms, win = o;
     }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -588,7 +588,7 @@ def measure_e2e(ctx, db, p, B, bufs, extras, est_step_ms):
     return {"value": raw_bytes * e2e_q / (e2e_ms / 1e3) / 1e9, "unit": "GB/s",
             "h2d_bytes_per_step": qwords * 4 + (rg.numel() * 4 if rg is not None else 0),
             "d2h_bytes_per_step": rwords * 4, "ms_per_step": e2e_ms / n_steps, "steps": n_steps,
-            "step_ms_min": min(step_ms), "step_ms_max": max(step_ms)}
+            "step_ms_min": min(step_ms), "step_ms_max": max(step_ms), "step_ms": [round(t, 2) for t in step_ms]}
 
 
 def our_arm(args, wl):

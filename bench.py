@@ -71,9 +71,10 @@ def measured_peaks():
     return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
 
 
-def profile_traffic(kernel_tag: str, workload: str, batch: int, source: str):
+def profile_traffic(kernel_tag: str, workload: str, batch: int, source: str, launches_per_step: float = None):
     """Per-launch DRAM bytes of a kernel from a committed ncu summary, or None when
-    there is none for this workload or the kernel source changed since."""
+    there is none for this workload, the kernel source changed since, or the summary
+    names a number of launches per step (K-chunks) other than the timed one's."""
     path = os.path.join(ROOT, "profiles", "%s_%s_b%d.txt" % (kernel_tag, workload, batch))
     if not os.path.exists(path):
         return None
@@ -85,6 +86,12 @@ def profile_traffic(kernel_tag: str, workload: str, batch: int, source: str):
                 vals[k.strip()] = v.strip()
     if vals.get("source_sha256") != sha256_of(source):
         return None
+    if launches_per_step is not None and "launches_per_step" in vals:
+        try:
+            if abs(float(vals["launches_per_step"]) - launches_per_step) > 0.01:
+                return None
+        except ValueError:
+            return None
     try:
         return float(vals["traffic_bytes_per_launch"])
     except (KeyError, ValueError):
@@ -394,7 +401,7 @@ def gemm_roofline(ctx, layout, B, p, tile, gemm_ms, launches_per_step, clocks, s
     src = os.path.join(ROOT, "paper_2606_11536_gb300", "csrc",
                        {"scan_tma": "scan_tma.cu", "gemv_scan": "gemm_plain.cu", "gemm_plain": "gemm_plain.cu",
                         "gemm_limb": "gemm_limb.cu", "gemm_tc": "gemm_tc.cu"}[kernel_tag])
-    rl["traffic"] = profile_traffic(kernel_tag, ctx.wl, B, src)
+    rl["traffic"] = profile_traffic(kernel_tag, ctx.wl, B, src, launches_per_step)
     return rl
 
 

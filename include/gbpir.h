@@ -132,7 +132,10 @@ typedef struct {
                         the 1-SM GEMM, 2 the CTA-pair (2-SM) GEMM, which needs
                         D2 % 64 == 0, 3 and 4 the 1-SM GEMM in clusters of 2 and 4
                         CTAs that multicast the query digits, which need D2 % 64
-                        and D2 % 128 == 0; otherwise PIR_ERR_ARG */
+                        and D2 % 128 == 0, 5 the CTA-pair GEMM loading by tensor
+                        maps, which needs D2 % 64 == 0 and the query rows padded to
+                        8 (Mp) with 4 Mp <= 256 or a multiple of 256; otherwise
+                        PIR_ERR_ARG */
   uint32_t flags;    /* PIR_ANSWER_STAGE_TIMES: record CUDA events around each stage on
                         `stream`, read with pir_stage_times; PIR_ANSWER_TEST_STALL,
                         PIR_ANSWER_MODSWITCH, PIR_ANSWER_CHECK_INPUTS: see below.

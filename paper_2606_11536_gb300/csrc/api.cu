@@ -219,7 +219,7 @@ uint32_t layout_tiles(int layout) {
 bool layout_tile_ok(int layout, uint32_t tile, uint32_t M, uint32_t Mp, uint32_t D2) {
   if (layout == PIR_LAYOUT_PLAIN) return gemm_plain_tile_ok(tile, M, D2);
   if (layout == PIR_LAYOUT_LIMB) return gemm_limb_tile_ok(tile, Mp);
-  return gemm_tc_tile_ok(tile, D2);
+  return gemm_tc_tile_ok(tile, Mp, D2);
 }
 
 // Keep the pool's memory once freed: repeated answers then reuse it instead of
@@ -1374,7 +1374,7 @@ pir_status_t pir_autotune(pir_db_t db, uint32_t B, void *stream, uint32_t reps, 
   if (db->layout == PIR_LAYOUT_TENSOR) {
     tiles.push_back(1);
     for (uint32_t t = 2; t <= gemm_tc_tiles(); ++t)
-      if (gemm_tc_tile_ok(t, p.D2)) tiles.push_back(t);
+      if (gemm_tc_tile_ok(t, layout_rows(db->layout, M), p.D2)) tiles.push_back(t);
   } else if (!limb) {
     if (M <= 2) tiles.push_back(1);
     if (M <= 4) tiles.push_back(2);

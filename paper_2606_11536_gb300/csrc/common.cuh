@@ -191,7 +191,7 @@ cudaError_t launch_gemm_tc(const ParamCtx &c, const uint16_t *db, uint32_t D1, u
                            uint32_t M, uint32_t Mp, uint32_t i0, uint32_t Kc, uint32_t *out, int acc, uint32_t tile,
                            cudaStream_t s);
 uint32_t gemm_tc_tiles();
-bool gemm_tc_tile_ok(uint32_t tile, uint32_t D2);
+bool gemm_tc_tile_ok(uint32_t tile, uint32_t Mp, uint32_t D2);
 cudaError_t launch_gemm_limb(const ParamCtx &c, const uint8_t *db, uint32_t D1, uint32_t D2, const uint8_t *ql,
                              uint32_t M, uint32_t Mp, uint32_t i0, uint32_t Kc, uint32_t *out, int acc,
                              uint32_t tile, cudaStream_t s);

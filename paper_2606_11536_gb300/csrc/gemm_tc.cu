@@ -39,7 +39,11 @@
 //   warp 9   allocates the tensor memory and issues the MMAs from one thread;
 //   warps 0..7  run the epilogue of the previous unit meanwhile.
 // Every barrier wait is bounded; a wait that runs out sets the device error word.
+#include <cuda.h>  // CUtensorMap and its enums only: the encoder is reached through the runtime
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
 
 #include "async.cuh"
 #include "common.cuh"
@@ -481,7 +485,27 @@ __device__ __forceinline__ Unit unit_of_pair(const TcArgs &a, uint32_t u, uint32
 
 constexpr int kMaxStages2 = 8;
 
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_gemm_tc2(TcArgs a, ModConst mc) {
+// Tensor-map load of a 3-D box into this CTA's shared memory at dst, completing its
+// bytes on the barrier at shared::cluster address bar, which .cta_group::2 lets lie
+// in either CTA of the pair (here: the pair's leader).  Coordinates are elements.
+__device__ __forceinline__ void tma_load_3d_pair(uint32_t dst, const CUtensorMap *map, uint32_t c0, uint32_t c1,
+                                                 uint32_t c2, uint32_t bar, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.cta_group::2"
+      ".L2::cache_hint [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar), "l"(policy)
+      : "memory");
+}
+
+// TMA = false: 1-D bulk copies into each CTA's own ring and a relay thread in the odd
+// CTA; TMA = true: tensor-map loads (maps tm_db, tm_q) whose bytes complete on the
+// even CTA's barrier directly, so the pair's MMAs wait on one barrier and no relay
+// runs.  The TMA form needs every unit's query rows to be a full half of one tile
+// (4 Mp <= 256 or a multiple of 256): a tensor map has one box size.
+template <bool TMA>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
+    k_gemm_tc2(TcArgs a, ModConst mc, const __grid_constant__ CUtensorMap tm_db,
+               const __grid_constant__ CUtensorMap tm_q) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + a.S * a.stage_bytes);
   const uint32_t full0 = saddr(bars), empty0 = saddr(bars + kMaxStages2), pfull0 = saddr(bars + 2 * kMaxStages2);
@@ -537,26 +561,42 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_gemm_
             break;
           }
           const uint32_t dst = saddr(smem + slot * a.stage_bytes);
-          mbar_expect_tx(full0 + 8 * slot, db_stage + qbytes);
-          for (uint32_t v = 0; v < a.KS16; ++v) {
-            const uint64_t uu = a.i0 / 16 + (uint64_t)st * a.KS16 + v;
-            const uint64_t e = (((uint64_t)w.s * U + uu) * R + (uint64_t)w.ct * 128) * 16;
-            bulk_g2s(dst + v * kBlockBytes, dbs + 2 * e, kBlockBytes, full0 + 8 * slot, pol_db);
-          }
-          for (uint32_t v = 0; v < a.KS16; ++v) {  // this CTA's half of the stage's query rows
-            const uint64_t e = (((uint64_t)w.s * Uc + (uint64_t)st * a.KS16 + v) * Ntot + w.n0 + rank * half) * 16;
-            bulk_g2s(dst + db_stage + v * half * 32, qs + 2 * e, half * 32, full0 + 8 * slot, pol_q);
+          if (TMA) {
+            // this CTA's 128 DB digit rows and half of the query rows, as two boxes
+            // [KS16][rows / 8][128 elements]; both CTAs' bytes complete on the even
+            // CTA's barrier, which it arms for the pair's two stages
+            uint32_t lead;
+            asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(lead) : "r"(full0 + 8 * slot), "r"(0u));
+            if (rank == 0) mbar_expect_tx(full0 + 8 * slot, 2 * (db_stage + qbytes));
+            tma_load_3d_pair(dst, &tm_db, 0, w.ct * 16, w.s * U + a.i0 / 16 + st * a.KS16, lead, pol_db);
+            tma_load_3d_pair(dst + db_stage, &tm_q, 0, (w.n0 + rank * half) / 8, w.s * Uc + st * a.KS16, lead,
+                             pol_q);
+          } else {
+            mbar_expect_tx(full0 + 8 * slot, db_stage + qbytes);
+            for (uint32_t v = 0; v < a.KS16; ++v) {
+              const uint64_t uu = a.i0 / 16 + (uint64_t)st * a.KS16 + v;
+              const uint64_t e = (((uint64_t)w.s * U + uu) * R + (uint64_t)w.ct * 128) * 16;
+              bulk_g2s(dst + v * kBlockBytes, dbs + 2 * e, kBlockBytes, full0 + 8 * slot, pol_db);
+            }
+            for (uint32_t v = 0; v < a.KS16; ++v) {  // this CTA's half of the stage's query rows
+              const uint64_t e =
+                  (((uint64_t)w.s * Uc + (uint64_t)st * a.KS16 + v) * Ntot + w.n0 + rank * half) * 16;
+              bulk_g2s(dst + db_stage + v * half * 32, qs + 2 * e, half * 32, full0 + 8 * slot, pol_q);
+            }
           }
         }
       }
-      // drain: never leave with copies in flight
+      // drain: never leave with copies in flight (in the TMA form the even CTA's
+      // barriers count both CTAs' bytes; the odd CTA's copies are complete once the
+      // even CTA has drained, before the closing cluster barrier)
       const uint32_t first = it > a.S ? it - a.S : 0;
-      for (uint32_t k = first; k < it; ++k)
-        if (!wait_bounded(full0 + 8 * (k % a.S), (k / a.S) & 1)) atomicExch(a.err, 1u);
+      if (!TMA || rank == 0)
+        for (uint32_t k = first; k < it; ++k)
+          if (!wait_bounded(full0 + 8 * (k % a.S), (k / a.S) & 1)) atomicExch(a.err, 1u);
     }
     __syncwarp();
   } else if (warp == kMmaWarp) {
-    if (lane == 0 && rank == 1) {
+    if (lane == 0 && rank == 1 && !TMA) {
       // relay: tell the even CTA's MMA thread when this CTA's stages have arrived
       uint32_t it = 0;
       bool ok = true;
@@ -569,7 +609,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_gemm_
           }
           mbar_arrive_cluster(pfull0 + 8 * (it % a.S), 0);
         }
-    } else if (lane == 0) {
+    } else if (lane == 0 && rank == 0) {
       uint32_t it = 0, k = 0;
       bool ok = true;
       for (uint32_t u = cluster; ok && u < a.nunits; u += nclusters, ++k) {
@@ -583,7 +623,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_gemm_
         const uint32_t idesc = instr_desc(256, w.Nt), dcol = tmem + buf * a.buf_cols;
         for (uint32_t st = 0; st < nst; ++st, ++it) {
           const uint32_t slot = it % a.S, ph = (it / a.S) & 1;
-          if (!wait_bounded(full0 + 8 * slot, ph) || !wait_bounded(pfull0 + 8 * slot, ph)) {
+          if (!wait_bounded(full0 + 8 * slot, ph) || (!TMA && !wait_bounded(pfull0 + 8 * slot, ph))) {
             atomicExch(a.err, 1u);
             ok = false;
             break;
@@ -784,10 +824,13 @@ bool gemm_tc_shape_ok(uint32_t D1, uint32_t D2) { return D1 % 64 == 0 && D2 % 32
 // Tensor-layout GEMM forms: 0 = automatic (the 1-SM form), 1 = one SM per unit
 // (k_gemm_tc), 2 = CTA pairs (k_gemm_tc2; D2 a multiple of 64), 3 and 4 = the 1-SM
 // form in clusters of 2 and 4 CTAs with the query digits multicast (D2 a multiple of
-// 64 and 128).
-uint32_t gemm_tc_tiles() { return 4; }
-bool gemm_tc_tile_ok(uint32_t tile, uint32_t D2) {
-  return tile <= 1 || ((tile == 2 || tile == 3) && D2 % 64 == 0) || (tile == 4 && D2 % 128 == 0);
+// 64 and 128), 5 = CTA pairs loading by tensor maps (D2 a multiple of 64, the padded
+// query rows 4 Mp at most 256 or a multiple of 256).
+uint32_t gemm_tc_tiles() { return 5; }
+bool gemm_tc_tile_ok(uint32_t tile, uint32_t Mp, uint32_t D2) {
+  const uint32_t Ntot = 4 * Mp;
+  return tile <= 1 || ((tile == 2 || tile == 3) && D2 % 64 == 0) || (tile == 4 && D2 % 128 == 0) ||
+         (tile == 5 && D2 % 64 == 0 && (Ntot <= 256 || Ntot % 256 == 0));
 }
 
 uint32_t tc_rows(uint32_t M) { return (M + 7u) & ~7u; }
@@ -815,9 +858,42 @@ cudaError_t launch_db_read_poly_tensor(const ParamCtx &c, uint32_t D1, uint32_t 
   return cudaGetLastError();
 }
 
-// The 2-SM form (k_gemm_tc2): clusters of two CTAs, each unit 64 DB columns.
+// cuTensorMapEncodeTiled, reached through the runtime (no link to the driver library).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, []() {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// A digit array [blocks][groups][128] (bf16 bits; a group = 8 rows x 16 K values, one
+// core-matrix pair) as a 3-D tensor map with boxes of box_groups groups x box_blocks
+// blocks.  False if the encoder refuses it (or is missing).
+bool digit_tensor_map(CUtensorMap *map, const uint16_t *base, uint64_t groups, uint64_t blocks, uint32_t box_groups,
+                      uint32_t box_blocks) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[3] = {128, groups, blocks};
+  const cuuint64_t strides[2] = {256, groups * 256};  // bytes, of dims 1 and 2
+  const cuuint32_t box[3] = {128, box_groups, box_blocks};
+  const cuuint32_t estride[3] = {1, 1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<uint16_t *>(base), dims, strides, box, estride,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The 2-SM form (k_gemm_tc2): clusters of two CTAs, each unit 64 DB columns; tma
+// selects the tensor-map form.
 cudaError_t launch_gemm_tc_pair(const ParamCtx &c, const uint16_t *db, uint32_t D1, uint32_t D2, const uint16_t *qt,
-                                uint32_t M, uint32_t Mp, uint32_t i0, uint32_t Kc, uint32_t *out, int acc,
+                                uint32_t M, uint32_t Mp, uint32_t i0, uint32_t Kc, uint32_t *out, int acc, bool tma,
                                 cudaStream_t s) {
   uint32_t *err = nullptr;
   cudaError_t e = device_error_word(&err);
@@ -854,11 +930,23 @@ cudaError_t launch_gemm_tc_pair(const ParamCtx &c, const uint16_t *db, uint32_t 
   const uint64_t nunits = (uint64_t)(c.p.L << c.logn) * (a.ctiles / 2) * a.mtiles;
   if (nunits > 0x7fffffffull) return cudaErrorInvalidValue;
   a.nunits = (uint32_t)nunits;
+  // the tensor maps: the whole resident DB ([L n U][D2 / 2][128], boxes of this CTA's
+  // 16 groups x KS16 blocks) and this K-chunk's query digits ([L n Uc][Mp / 2][128],
+  // boxes of half a query tile); coordinates stay below 2^31
+  alignas(64) CUtensorMap tm_db = {}, tm_q = {};
+  const uint64_t nslots = (uint64_t)c.p.L << c.logn;
+  if (tma) {
+    if ((Ntot > 256 && Ntot % 256 != 0) || nslots * (D1 / 16) >= (1ull << 31)) return cudaErrorInvalidValue;
+    if (!digit_tensor_map(&tm_db, db, D2 / 2, nslots * (D1 / 16), 16, ks) ||
+        !digit_tensor_map(&tm_q, qt, Ntot / 8, nslots * (Kc / 16), Nmax / 16, ks))
+      return cudaErrorInvalidValue;
+  }
   // stages | full, empty, pfull (kMaxStages2 each), two tensor-memory full/empty pairs,
   // done | tensor-memory address | a spare run past the end
   size_t smem = (size_t)S * a.stage_bytes + (3 * kMaxStages2 + 5) * 8 + 16 + kSpareBytes2;
   if (smem < kSmemFloor) smem = kSmemFloor;
-  e = cudaFuncSetAttribute(k_gemm_tc2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kernel = tma ? k_gemm_tc2<true> : k_gemm_tc2<false>;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -870,12 +958,12 @@ cudaError_t launch_gemm_tc_pair(const ParamCtx &c, const uint16_t *db, uint32_t 
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   int nclusters = 0;
-  if (cudaOccupancyMaxActiveClusters(&nclusters, k_gemm_tc2, &cfg) != cudaSuccess || nclusters <= 0) {
+  if (cudaOccupancyMaxActiveClusters(&nclusters, kernel, &cfg) != cudaSuccess || nclusters <= 0) {
     cudaGetLastError();  // clear the query's error: fall back to one cluster per SM pair
     nclusters = sms / 2;
   }
   if ((uint64_t)nclusters > nunits) nclusters = (int)nunits;
-  k_gemm_tc2<<<2 * (unsigned)nclusters, kThreads, smem, s>>>(a, c.mod);
+  kernel<<<2 * (unsigned)nclusters, kThreads, smem, s>>>(a, c.mod, tm_db, tm_q);
   return cudaGetLastError();
 }
 
@@ -914,9 +1002,9 @@ cudaError_t launch_gemm_tc(const ParamCtx &c, const uint16_t *db, uint32_t D1, u
                            uint32_t M, uint32_t Mp, uint32_t i0, uint32_t Kc, uint32_t *out, int acc, uint32_t tile,
                            cudaStream_t s) {
   if (!gemm_tc_shape_ok(D1, D2) || Kc == 0 || Kc % 64 != 0 || Kc > 1024 || i0 % 64 != 0 || i0 + Kc > D1 ||
-      Mp % 8 != 0 || Mp < M || !gemm_tc_tile_ok(tile, D2))
+      Mp % 8 != 0 || Mp < M || !gemm_tc_tile_ok(tile, Mp, D2))
     return cudaErrorInvalidValue;
-  if (tile == 2) return launch_gemm_tc_pair(c, db, D1, D2, qt, M, Mp, i0, Kc, out, acc, s);
+  if (tile == 2 || tile == 5) return launch_gemm_tc_pair(c, db, D1, D2, qt, M, Mp, i0, Kc, out, acc, tile == 5, s);
   uint32_t *err = nullptr;
   cudaError_t e = device_error_word(&err);
   if (e != cudaSuccess) return e;

@@ -133,7 +133,7 @@ def test_session_and_tensor_layout_errors_without_gpu(lib):
     assert lib.pir_answer_end(C.c_void_p(0xBEEF0), C.c_void_p(q.ctypes.data), 0) == 6
     assert lib.pir_answer_abort(C.c_void_p(0xBEEF0)) == 6
     assert lib.pir_answer_abort(None) == 6
-    assert g.pir_gemm_tiles(g.PIR_LAYOUT_TENSOR) == 4
+    assert g.pir_gemm_tiles(g.PIR_LAYOUT_TENSOR) == 5
     # tensor layout: D1 a multiple of 64 and D2 of 32, refused as unsupported otherwise
     for D1, D2 in ((96, 32), (64, 36)):
         p = g.pir_make_params(2048, 12, D1, D2, 2)

@@ -276,20 +276,29 @@ def test_full_size_16gib_batches_32_and_128(orc):
 @pytest.mark.parametrize("B", [1, 4, 32, 40, 64])
 def test_one_sm_and_two_sm_forms_agree_with_the_oracle(orc, B):
     """The 1-SM GEMM (tile 1), the CTA-pair GEMM (tile 2: one tcgen05 MMA over two
-    SMs, M = 256) and the 1-SM GEMM in clusters of two (tile 3) against the oracle, on D2 = 192 (three column-tile pairs), query
+    SMs, M = 256), the 1-SM GEMM in clusters of two (tile 3) and the CTA pair with
+    tensor-map loads (tile 5, where the query rows allow it) against the oracle, on D2 = 192 (three column-tile pairs), query
     rows that leave a ragged second 256-row tile at B = 40 and 64, and two K-chunks."""
     p, P, raw, db = instance(orc, 2048, 256, 192, seed=130 + B)
     try:
         Q = random_queries(P, B, 131 + B)
         cols = np.array([0, 63, 64, 191], dtype=np.uint32)
         want = orc.answer(P, raw, Q, cols=cols)
-        for tile in (1, 2, 3):
+        Ntot = 4 * ((2 * B + 7) // 8 * 8)
+        tma_ok = Ntot <= 256 or Ntot % 256 == 0  # the tensor-map pair form's one box size
+        for tile in (1, 2, 3) + ((5,) if tma_ok else ()):
             for kc in (0, 128):
                 R = run(db, P, Q, B, tile=tile, k_chunk=kc)
                 assert np.array_equal(R[:, cols], want), (tile, kc)
         R1, R2 = run(db, P, Q, B, tile=1), run(db, P, Q, B, tile=2)
         assert np.array_equal(R1, R2)
         assert np.array_equal(R1, run(db, P, Q, B, tile=3))
+        if tma_ok:
+            assert np.array_equal(R1, run(db, P, Q, B, tile=5))
+        else:
+            with pytest.raises(g.PirError) as ei:  # a ragged second query tile: refused
+                run(db, P, Q, B, tile=5)
+            assert ei.value.status == 1
     finally:
         g.pir_free_db(db)
 
@@ -322,7 +331,7 @@ def test_cluster_forms_refuse_column_counts_they_cannot_split(orc):
     p, P, raw, db = instance(orc, 2048, 64, 96, seed=160)
     try:
         Q = random_queries(P, 2, 161)
-        for tile in (3, 4):
+        for tile in (3, 4, 5):
             with pytest.raises(g.PirError) as ei:
                 run(db, P, Q, 2, tile=tile)
             assert ei.value.status == 1, tile

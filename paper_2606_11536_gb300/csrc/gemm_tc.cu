@@ -821,7 +821,7 @@ __global__ void k_db_read_poly_tensor(const uint16_t *__restrict__ res, uint64_t
 
 bool gemm_tc_shape_ok(uint32_t D1, uint32_t D2) { return D1 % 64 == 0 && D2 % 32 == 0; }
 
-// Tensor-layout GEMM forms: 0 = automatic (the 1-SM form), 1 = one SM per unit
+// Tensor-layout GEMM forms: 0 = automatic (5 where it applies, else 1), 1 = one SM per unit
 // (k_gemm_tc), 2 = CTA pairs (k_gemm_tc2; D2 a multiple of 64), 3 and 4 = the 1-SM
 // form in clusters of 2 and 4 CTAs with the query digits multicast (D2 a multiple of
 // 64 and 128), 5 = CTA pairs loading by tensor maps (D2 a multiple of 64, the padded
@@ -1004,6 +1004,9 @@ cudaError_t launch_gemm_tc(const ParamCtx &c, const uint16_t *db, uint32_t D1, u
   if (!gemm_tc_shape_ok(D1, D2) || Kc == 0 || Kc % 64 != 0 || Kc > 1024 || i0 % 64 != 0 || i0 + Kc > D1 ||
       Mp % 8 != 0 || Mp < M || !gemm_tc_tile_ok(tile, Mp, D2))
     return cudaErrorInvalidValue;
+  // the built-in choice: the tensor-map CTA pair where the shape allows it (1.25x the
+  // 1-SM form's GEMM at batch 32 on the 16 GiB DB), else the 1-SM form
+  if (tile == 0 && gemm_tc_tile_ok(5, Mp, D2)) tile = 5;
   if (tile == 2 || tile == 5) return launch_gemm_tc_pair(c, db, D1, D2, qt, M, Mp, i0, Kc, out, acc, tile == 5, s);
   uint32_t *err = nullptr;
   cudaError_t e = device_error_word(&err);

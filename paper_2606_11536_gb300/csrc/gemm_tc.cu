@@ -1006,7 +1006,7 @@ cudaError_t launch_gemm_tc(const ParamCtx &c, const uint16_t *db, uint32_t D1, u
     return cudaErrorInvalidValue;
   // the built-in choice: the tensor-map CTA pair where the shape allows it (1.25x the
   // 1-SM form's GEMM at batch 32 on the 16 GiB DB), else the 1-SM form
-  if (tile == 0 && gemm_tc_tile_ok(5, Mp, D2)) tile = 5;
+  if (tile == 0 && gemm_tc_tile_ok(5, Mp, D2) && tensor_map_encoder() != nullptr) tile = 5;
   if (tile == 2 || tile == 5) return launch_gemm_tc_pair(c, db, D1, D2, qt, M, Mp, i0, Kc, out, acc, tile == 5, s);
   uint32_t *err = nullptr;
   cudaError_t e = device_error_word(&err);

@@ -123,8 +123,10 @@ pir_status_t pir_answer(pir_db_t db, const uint32_t *queries, uint32_t B, uint32
 
 /* Options for pir_answer_ex.  Zero-initialised = the defaults of pir_answer. */
 typedef struct {
-  uint32_t k_chunk;  /* 0 = whole D1 at once; else fold D1 in chunks of this many
-                        ciphertexts (bounds the scratch memory to one chunk)        */
+  uint32_t k_chunk;  /* 0 = automatic: whole D1 when its scratch fits half of the
+                        available device memory, else equal chunks that do, of at
+                        least 512 ciphertexts (or D1); else fold D1 in chunks of
+                        this many ciphertexts (bounds the scratch to one chunk)     */
   uint32_t tile;     /* 0 = built-in choice; else a GEMM tile id (pir_gemm_tiles) that
                         holds the batch: plain 1, 2, 3 and 7 take at most 2, 4, 8 and
                         8 query rows (2B), 7 also D2 <= 512; limb 2 and 3 need the

@@ -559,6 +559,16 @@ def raw_db_bytes(p) -> int:
     return p.D1 * p.D2 * p.n * p.log2p // 8
 
 
+def answer_scratch_bytes(p, layout: int, B: int) -> int:
+    """Device scratch one answer of B queries takes inside the library with the whole
+    of D1 at once: the NTT-form query copy (4 bytes per residue), the queries in the
+    GEMM's layout (4 bytes per residue; 8 for the tensor layout's bf16 digits) and
+    the slot-major result (4 bytes per residue of the 2B x D2 result polynomials)."""
+    per_q = 2 * p.L * p.n * 4  # one ciphertext
+    layout_q = 2 if layout == PIR_LAYOUT_TENSOR else 1
+    return B * (p.D1 * per_q * (1 + layout_q) + p.D2 * per_q)
+
+
 def resident_db_bytes(p, layout: int = PIR_LAYOUT_PLAIN) -> int:
     """Device bytes of the NTT-form DB: one u32 word (plain) or four u8 limbs (limb)
     per residue, four bf16 digits (tensor) per residue."""

@@ -359,6 +359,8 @@ pir_status_t chunk_gemm(const pir_db *db, const uint32_t *qhat, uint32_t B, uint
 // ([B][D1][2][L][n], e.g. from query expansion): no forward NTT, no K-chunking.
 // ntt_out: leave the responses in NTT form (no inverse NTT, no modulus switching),
 // for the folding of the remaining dimensions.
+constexpr uint32_t kMinAutoChunk = 512;  // rows: shorter automatic K-chunks starve the GEMMs
+
 pir_status_t answer_device(pir_db *db, const uint32_t *queries, uint32_t B, uint32_t *responses, cudaStream_t s,
                            const pir_answer_opts_t &o, const uint32_t *qhat_ready = nullptr, bool ntt_out = false,
                            const ChunkFeed *feed = nullptr) {
@@ -371,16 +373,21 @@ pir_status_t answer_device(pir_db *db, const uint32_t *queries, uint32_t B, uint
   uint32_t Kc = (o.k_chunk == 0 || o.k_chunk >= D1 || qhat_ready) ? D1 : o.k_chunk;
   if (o.k_chunk == 0 && !qhat_ready) {
     // Stream-wise buffering (Sec. 4.4): when the scratch for all of D1 would not fit
-    // half of the free device memory, fold D1 in as many equal chunks as needed.
-    size_t free_b = 0, total_b = 0;
-    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+    // half of the available device memory (free, plus what the stream-ordered pool
+    // keeps cached), fold D1 in as many equal chunks as needed; never in chunks
+    // shorter than kMinAutoChunk rows, below which the GEMM launches stop filling the
+    // GPU (a scratch allocation that then does not fit is refused with PIR_ERR_OOM,
+    // after the cached memory has been given back).
+    const size_t avail = available_device_bytes(db->device);
+    if (avail > 0) {
       const size_t per_row = (size_t)B * 2 * L * n * 4 + layout_qs_bytes(db->layout, (uint64_t)L * n, 1, Mp);
-      const size_t budget = free_b / 2;
+      const size_t budget = avail / 2;
       if ((size_t)D1 * per_row > budget && per_row > 0) {
         const size_t rows = budget / per_row;
         const uint32_t chunks = (uint32_t)((D1 + (rows ? rows : 1) - 1) / (rows ? rows : 1));
         Kc = (D1 + chunks - 1) / chunks;
-        if (Kc == 0) Kc = 1;
+        const uint32_t floor = D1 < kMinAutoChunk ? D1 : kMinAutoChunk;
+        if (Kc < floor) Kc = floor;
       }
     }
   }

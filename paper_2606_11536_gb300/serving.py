@@ -10,8 +10,12 @@ that arrive while batches are running wait for the next free slot, so work from
 different batches and databases overlaps on the device.
 
 Limits and failure handling:
-  - a batch is held back (or shrunk) until its query and response buffers fit the
-    scratch budget left by the batches in flight;
+  - a batch is held back (or shrunk) until its device memory (query and response
+    buffers and the answer's own scratch) fits the scratch budget left by the
+    batches in flight;
+  - a batch that cannot be started (the library or torch finds no memory for it,
+    after the library's cached scratch has been given back) fails its requests
+    with that status (PIR_ERR_OOM, 2) and the server goes on;
   - per database, a batch cap (`db_max_batch`) and a cap on the slots it may hold at
     once (`db_max_slots`), so that one large database cannot take every slot while
     the small ones wait behind its long batches;
@@ -43,6 +47,7 @@ import numpy as np
 from . import binding
 
 PIR_OK = 0
+PIR_ERR_OOM = 2
 PIR_ERR_TIMEOUT = 5
 
 
@@ -56,7 +61,8 @@ class Request:
     t_done: float = math.nan
     batch_size: int = 0
     response: object = None  # filled when keep_responses is set
-    status: int = PIR_OK     # PIR_ERR_TIMEOUT when its batch ran out of time
+    status: int = PIR_OK     # PIR_ERR_TIMEOUT when its batch ran out of time, PIR_ERR_OOM
+                             # (or another status) when the batch could not be started
     cancelled: bool = False
 
     @property
@@ -135,7 +141,7 @@ class Server:
         self.queues: Dict[str, collections.deque] = {}
         self.slots = [_Slot(stream=backend.new_stream()) for _ in range(streams)]
         self.done: List[Request] = []       # answered requests
-        self.failed: List[Request] = []     # requests whose batch timed out
+        self.failed: List[Request] = []     # requests whose batch timed out or could not start
         self.cancelled: List[Request] = []
         self.device_status = PIR_OK
         self.resident_bytes = 0
@@ -150,7 +156,7 @@ class Server:
             raise AdmissionError("%s needs %d bytes, %d of the %d-byte budget are left"
                                  % (name, need, self.budget - self.resident_bytes, self.budget))
         handle, nbytes = self.be.setup_db(name, params, raw, layout)
-        self.dbs[name] = {"handle": handle, "params": params, "bytes": nbytes}
+        self.dbs[name] = {"handle": handle, "params": params, "bytes": nbytes, "layout": layout}
         self.queues[name] = collections.deque()
         self.resident_bytes += nbytes
         return nbytes
@@ -238,7 +244,9 @@ class Server:
             q = self.queues[name]
             info = self.dbs[name]
             p = info["params"]
-            per_query = 8 * p.L * p.n * (p.D1 + p.D2)  # query + response words of one request
+            # one request's device memory while its batch runs: its query and response
+            # buffers and the answer's own scratch (NTT-form copy, GEMM layout, result)
+            per_query = 8 * p.L * p.n * (p.D1 + p.D2) + binding.answer_scratch_bytes(p, info.get("layout", 0), 1)
             nb = min(self.max_batch, _per_db(self.db_max_batch, name, self.max_batch), len(q))
             if self.scratch_budget is not None:
                 nb = min(nb, (self.scratch_budget - self.scratch_in_flight) // per_query)
@@ -250,7 +258,16 @@ class Server:
             t = self.clock()
             for r in take:
                 r.t_dispatch, r.batch_size = t, len(take)
-            s.event, s.bufs = self.be.dispatch(info["handle"], p, [r.query for r in take], s.stream)
+            try:
+                s.event, s.bufs = self.be.dispatch(info["handle"], p, [r.query for r in take], s.stream)
+            except binding.PirError as e:
+                # the batch could not be started (no memory for it): its requests fail
+                # with the library's status and the slot stays free
+                for r in take:
+                    r.t_done = self.clock()
+                    r.status = e.status
+                    self.failed.append(r)
+                continue
             s.busy, s.requests, s.db, s.scratch, s.t_dispatch = True, take, name, nb * per_query, t
             self.scratch_in_flight += s.scratch
         self.done.extend(finished)
@@ -393,7 +410,10 @@ class CudaBackend(Backend):
             return torch.empty(words, dtype=torch.int32, device=self.device)
         except torch.OutOfMemoryError:
             self.g.pir_release_memory()
+        try:
             return torch.empty(words, dtype=torch.int32, device=self.device)
+        except torch.OutOfMemoryError as e:
+            raise self.g.PirError(PIR_ERR_OOM, "batch buffer", str(e)) from e
 
     def _drop_graph(self, key):
         graph, _, _, nbytes, _ = self._graphs.pop(key)

@@ -133,8 +133,10 @@ def test_layout_reaches_the_backend_and_admission_counts_its_bytes():
 
 
 def test_scratch_budget_limits_batches_in_flight():
+    from paper_2606_11536_gb300 import binding
     p = params(n=2048, D1=16, D2=16)
-    per_query = 8 * 2 * 2048 * 32
+    # buffers (query + response) and the library's own scratch for one query
+    per_query = 8 * 2 * 2048 * 32 + binding.answer_scratch_bytes(p, 0, 1)
     clock, be, srv = make(streams=3, max_batch=8, scratch_budget=5 * per_query)
     srv.admit("a", p, None)
     for k in range(12):
@@ -264,3 +266,43 @@ def test_per_database_batch_and_slot_caps():
     clock.t = 3.0
     srv.poll()
     assert srv.pending() == 0 and len(srv.done) == 7
+
+
+def test_answer_scratch_bytes_per_layout():
+    from paper_2606_11536_gb300 import binding
+    p = params(n=4096, D1=4096, D2=512)
+    ct = 2 * 2 * 4096 * 4  # one ciphertext: 2 polynomials x L primes x n residues x 4 bytes
+    # NTT-form copy + GEMM layout (4 bytes per residue; bf16 digits: 8) + result
+    assert binding.answer_scratch_bytes(p, binding.PIR_LAYOUT_PLAIN, 1) == 2 * 4096 * ct + 512 * ct
+    assert binding.answer_scratch_bytes(p, binding.PIR_LAYOUT_TENSOR, 1) == 3 * 4096 * ct + 512 * ct
+    assert binding.answer_scratch_bytes(p, binding.PIR_LAYOUT_TENSOR, 32) == 32 * (3 * 4096 + 512) * ct
+
+
+def test_a_batch_that_cannot_start_fails_its_requests_and_the_server_goes_on():
+    from paper_2606_11536_gb300 import binding
+
+    class FlakyBackend(FakeBackend):
+        def __init__(self, clock):
+            super().__init__(clock)
+            self.refuse = 1  # the first dispatch finds no memory
+
+        def dispatch(self, handle, params, queries, stream):
+            if self.refuse:
+                self.refuse -= 1
+                raise binding.PirError(2, "batch buffer")
+            return super().dispatch(handle, params, queries, stream)
+
+    clock = FakeClock()
+    be = FlakyBackend(clock)
+    srv = Server(be, streams=1, max_batch=4, clock=clock, keep_responses=True)
+    srv.admit("a", params(), None)
+    for k in range(6):
+        srv.submit(Request(k, "a", k, 0.0))
+    srv.poll()  # the first 4 are refused; the slot stays free
+    assert [r.rid for r in srv.failed] == [0, 1, 2, 3] and all(r.status == 2 for r in srv.failed)
+    assert be.batches == [] and srv.pending() == 2
+    srv.poll()  # the next poll gives it the remaining 2
+    assert [q for _, q in be.batches] == [[4, 5]]
+    clock.t = 1.0
+    srv.poll()
+    assert sorted(r.rid for r in srv.done) == [4, 5] and srv.pending() == 0

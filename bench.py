@@ -86,6 +86,15 @@ def profile_traffic(kernel_tag: str, workload: str, batch: int, source: str, lau
                 vals[k.strip()] = v.strip()
     if vals.get("source_sha256") != sha256_of(source):
         return None
+    if launches_per_step is not None:
+        # a summary may give the traffic of several launch counts (K-chunkings):
+        # traffic_bytes_per_launch@<launches per step>
+        key = "traffic_bytes_per_launch@%d" % round(launches_per_step)
+        if key in vals:
+            try:
+                return float(vals[key])
+            except ValueError:
+                return None
     if launches_per_step is not None and "launches_per_step" in vals:
         try:
             if abs(float(vals["launches_per_step"]) - launches_per_step) > 0.01:

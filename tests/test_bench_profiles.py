@@ -35,3 +35,11 @@ def test_traffic_only_for_the_same_launches_per_step(tmp_path, monkeypatch):
     assert bench.profile_traffic("k", "w", 4, src, launches_per_step=4.0) == 1234.0
     assert bench.profile_traffic("k", "w", 4, src, launches_per_step=2.0) is None   # other K-chunks
     assert bench.profile_traffic("k", "w", 4, src) == 1234.0
+
+
+def test_traffic_per_launch_count(tmp_path, monkeypatch):
+    src = write_summary(tmp_path, monkeypatch, "kernel",
+                        ["launches_per_step: 4", "traffic_bytes_per_launch@2: 5000", "traffic_bytes_per_launch@4: 1234"])
+    assert bench.profile_traffic("k", "w", 4, src, launches_per_step=2.0) == 5000.0
+    assert bench.profile_traffic("k", "w", 4, src, launches_per_step=4.0) == 1234.0
+    assert bench.profile_traffic("k", "w", 4, src, launches_per_step=1.0) is None

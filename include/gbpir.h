@@ -439,6 +439,14 @@ pir_status_t pir_release_memory(void);
  * returns PIR_ERR_TIMEOUT if it was set, else PIR_OK. */
 pir_status_t pir_check_device(void *stream);
 
+/* The same device error word read without waiting for any work: the copy runs on a
+ * stream of the library's own that nothing else uses, so kernels still running (a
+ * batch that never completes included) do not hold it up.  Reads and clears the
+ * current device's word; returns PIR_ERR_TIMEOUT if it was set, else PIR_OK (a
+ * wait that runs out while the read is in flight shows in the next read).
+ * Errors: PIR_ERR_CUDA. */
+pir_status_t pir_device_status(void);
+
 #ifdef __cplusplus
 }
 #endif

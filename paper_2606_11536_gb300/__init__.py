@@ -11,5 +11,5 @@ from .binding import (  # noqa: F401
     pir_autotune, pir_answer_noalloc, ntt_inv_modswitch, PIR_ANSWER_MODSWITCH, PIR_ANSWER_CHECK_INPUTS, Expander, pir_expander_create,
     pir_expander_free, pir_expand, pir_answer_packed, pir_lwe_answer, PIR_LWE_AUTO, PIR_LWE_TENSOR, PIR_LWE_SIMT,
     pir_probe_int8_mma, pir_fold, pir_answer_folded, Session, pir_answer_begin, pir_answer_chunk, pir_answer_end,
-    pir_answer_abort, pir_release_memory,
+    pir_answer_abort, pir_release_memory, pir_device_status,
 )

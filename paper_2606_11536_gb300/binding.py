@@ -89,6 +89,7 @@ def lib():
             "pir_kernel_launches": (C.c_uint64, []),
             "pir_check_device": (i32, [vp]),
             "pir_release_memory": (i32, []),
+            "pir_device_status": (i32, []),
             "pir_graph_create": (i32, [vp, vp, u32, vp, C.POINTER(pir_answer_opts_t), C.POINTER(vp)]),
             "pir_graph_create_packed": (i32, [vp, vp, vp, u32, vp, C.POINTER(pir_answer_opts_t), C.POINTER(vp)]),
             "pir_graph_launch": (i32, [vp, vp]),
@@ -535,6 +536,12 @@ def pir_check_device(stream=None):
 
 def pir_kernel_launches() -> int:
     return int(lib().pir_kernel_launches())
+
+
+def pir_device_status():
+    """Raises PirError(PIR_ERR_TIMEOUT) if a bounded kernel wait ran out since the last
+    read; waits for no device work (pir_check_device synchronizes first)."""
+    _check(lib().pir_device_status(), "pir_device_status")
 
 
 def pir_release_memory():

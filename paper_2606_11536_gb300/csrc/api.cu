@@ -790,6 +790,30 @@ pir_status_t pir_check_device(void *stream) {
   return v ? PIR_ERR_TIMEOUT : PIR_OK;
 }
 
+pir_status_t pir_device_status(void) {
+  uint32_t *w = nullptr;
+  CK(device_error_word(&w));
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  static std::mutex mu;
+  static cudaStream_t streams[64] = {};
+  cudaStream_t s = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (!streams[dev]) CK(cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking));
+    s = streams[dev];
+  }
+  // a stream of its own that nothing else uses: the read waits for no other work
+  uint32_t v = 0;
+  CK(cudaMemcpyAsync(&v, w, sizeof(v), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (v) {
+    CK(cudaMemsetAsync(w, 0, sizeof(uint32_t), s));
+    CK(cudaStreamSynchronize(s));
+  }
+  return v ? PIR_ERR_TIMEOUT : PIR_OK;
+}
+
 uint32_t pir_gemm_tiles(int layout) {
   if (layout == PIR_LAYOUT_PLAIN) return gemm_plain_tiles();
   if (layout == PIR_LAYOUT_LIMB) return gemm_limb_tiles();

@@ -202,7 +202,12 @@ class Server:
             if not s.busy:
                 continue
             if self.be.done(s.event):
-                if not s.timed_out:
+                if s.timed_out:
+                    # the overdue batch has completed at last: the device status (a
+                    # bounded kernel wait that ran out?) can be read now without
+                    # blocking on it
+                    self.device_status = self.be.check()
+                else:
                     for b, r in enumerate(s.requests):
                         r.t_done = now
                         if r.cancelled:
@@ -224,7 +229,8 @@ class Server:
                         continue
                     r.status = PIR_ERR_TIMEOUT
                     self.failed.append(r)
-                self.device_status = self.be.check()
+                # no device-status read here: it waits for the device's work, and the
+                # overdue batch may never complete (the other slots go on meanwhile)
         return finished
 
     def _slots_of(self, name) -> int:
@@ -506,7 +512,7 @@ class CudaBackend(Backend):
 
     def check(self) -> int:
         try:
-            self.g.pir_check_device()
+            self.g.pir_device_status()  # waits for no work: other slots may still run
         except self.g.PirError as e:
             return e.status
         return PIR_OK

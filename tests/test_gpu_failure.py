@@ -29,6 +29,16 @@ def test_bounded_wait_reports_timeout_and_context_survives(orc):
             g.pir_check_device()
         assert ei.value.status == 5  # PIR_ERR_TIMEOUT
         g.pir_check_device()  # the word was cleared
+        # the non-blocking read sees the same word: set by a second stalled scan,
+        # then cleared by the read
+        g.pir_answer_ex(db, qd, B, rd, flags=g.PIR_ANSWER_TEST_STALL)
+        import torch
+        torch.cuda.synchronize()
+        with pytest.raises(g.PirError) as ei:
+            g.pir_device_status()
+        assert ei.value.status == 5
+        g.pir_device_status()
+        g.pir_check_device()
         # the context still works and answers stay exact
         g.pir_answer(db, qd, B, rd)
         R = from_dev(rd, (B, D2, 2, 2, n))

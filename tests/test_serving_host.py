@@ -213,12 +213,14 @@ def test_batch_timeout_fails_its_requests_and_holds_the_slot():
     srv.submit(Request(2, "a", 2, 2.5))
     assert srv.poll() == []
     assert [r.rid for r in srv.failed] == [0, 1] and all(r.status == 5 for r in srv.failed)
-    assert srv.device_status == 5 and be.checks == 1
+    # no device-status read yet: it would wait for the overdue batch, which may never end
+    assert srv.device_status == 0 and be.checks == 0
     assert len(be.batches) == 1          # the held slot takes no new batch
     assert srv.pending() == 1            # only the waiting request counts
     clock.t = 3.0
     be.released.add(0)                   # the stuck batch's event finally fires
     srv.poll()
+    assert srv.device_status == 5 and be.checks == 1  # read once the batch has ended
     assert len(be.batches) == 2 and be.batches[1][1] == [2]
     assert srv.done == []                # the failed requests are not reported twice
     be.released.add(1)

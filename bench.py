@@ -1220,11 +1220,11 @@ def main(argv=None):
                     help="seconds after which a batch that has not completed fails its requests")
     ap.add_argument("--serving-headline-rate", type=float, default=0.0,
                     help="offered rate whose p99 is the line's value (default: the highest one kept up with)")
-    # with the library's own scratch counted per query (about 1.06 GiB for the 16 GiB
-    # DB in the tensor layout), 32 GiB let only two of its batches of 15 run at once
-    # and queued everything else behind them; 52 GiB still fits beside the 208 GiB of
-    # resident DBs
-    ap.add_argument("--serving-scratch-gib", type=int, default=52)
+    # the budget counts the library's own scratch per query (about 1.06 GiB for the
+    # 16 GiB DB in the tensor layout): 32 GiB lets two of its batches of about 15 run
+    # at once; 52 GiB (more batches in flight beside the 208 GiB of resident DBs)
+    # stalled at 1000 q/s
+    ap.add_argument("--serving-scratch-gib", type=int, default=32)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

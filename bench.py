@@ -741,17 +741,30 @@ def our_arm(args, wl):
                "--serving-rates", str(args.serving_block_rate), "--serving-seconds", str(args.serving_block_seconds),
                "--serving-warmup", "1.5"]
         try:
-            child = subprocess.run(cmd, capture_output=True, text=True, timeout=300)
-            if child.returncode != 0:
-                raise RuntimeError("exit %d: %s" % (child.returncode, child.stderr[-600:]))
-            sl = json.loads(child.stdout.strip().splitlines()[-1])
+            try:
+                child = subprocess.run(cmd, capture_output=True, text=True, timeout=300)
+                out, note = child.stdout, None
+                if child.returncode != 0:
+                    raise RuntimeError("exit %d: %s" % (child.returncode, child.stderr[-600:]))
+            except subprocess.TimeoutExpired as e:
+                # the line is printed before the DBs are freed: keep it if it came
+                out = e.stdout.decode() if isinstance(e.stdout, bytes) else (e.stdout or "")
+                note = "the serving process did not end within 300 s after its loads"
+                if not out.strip():
+                    raise
+            sl = json.loads(out.strip().splitlines()[-1])
             ld = sl["loads"][0]
             serving_blk = {"metric": sl["metric"], "unit": "ms", "p50_ms": ld.get("p50_ms"),
                            "p99_ms": ld.get("p99_ms"), "offered_qps": ld["offered_qps"],
                            "achieved_qps": ld.get("qps"), "saturated": ld["saturated"],
                            "mean_batch": ld.get("mean_batch"), "failed": sl["failed"],
                            "graph_launches": sl["graph_launches"], "config": sl["config"],
+                           "device_status": sl.get("device_status"),
                            "per_db_p99_ms": {d: v.get("p99_ms") for d, v in ld["per_db"].items()}}
+            if sl.get("stopped"):
+                serving_blk["stopped"] = sl["stopped"]
+            if note:
+                serving_blk["note"] = note
         except (subprocess.TimeoutExpired, RuntimeError, ValueError, IndexError, KeyError) as e:
             serving_blk = {"metric": "serving p50/p99 ms (Poisson arrivals, continuous batching)",
                            "error": "%s: %s" % (type(e).__name__, str(e)[:600])}
@@ -1051,12 +1064,15 @@ SERVING_DBS = [  # name, n, log2p, D1, D2
 SERVING_EXTRA = ("db8g_n4096", 4096, 16, 2048, 512)
 
 
-def run_serving(args, rates, seconds, graphs, warmup_s=0.0):
+def run_serving(args, rates, seconds, graphs, warmup_s=0.0, emit=None):
     """Serving: three resident DBs, admission of a fourth by free-HBM check, Poisson
     arrivals at each offered load in `rates` for `seconds` each, uniformly random
     target DB, continuous batching.  The DBs' raw bytes are generated on the device
     from the same counter-based streams as the host generator's.  Returns the JSON
-    line (p99 of the headline load as its value) and frees the DBs."""
+    line (p99 of the headline load as its value) and frees the DBs; emit(line), if
+    given, gets the line before the DBs are freed (freeing waits for the device).
+    A load in which batches ran out of time ends the sweep: the device may be
+    stuck, so nothing after it waits on the device."""
     import torch
     import paper_2606_11536_gb300 as g
     from paper_2606_11536_gb300 import serving
@@ -1107,21 +1123,28 @@ def run_serving(args, rates, seconds, graphs, warmup_s=0.0):
         # in place before the measured loads, as in a server that has been running
         arr = serving.poisson_arrivals(rates[0], warmup_s, dbs, seed=7,
                                        make_query=lambda db, k: pools[db][k % len(pools[db])])
-        srv.run(arr)
-        torch.cuda.synchronize()
+        if not any(r.status == serving.PIR_ERR_TIMEOUT for r in srv.run(arr)):
+            torch.cuda.synchronize()
     results = []
+    stopped = None
     for rate in rates:
         arr = serving.poisson_arrivals(rate, seconds, dbs, seed=int(rate),
                                        make_query=lambda db, k: pools[db][k % len(pools[db])])
-        torch.cuda.synchronize()
         done = srv.run(arr)
-        torch.cuda.synchronize()
         st = serving.latency_stats(done)
         st["offered_qps"] = rate
         st["saturated"] = st.get("qps", 0.0) < 0.9 * rate
         st["per_db"] = {d: serving.latency_stats([r for r in done if r.db == d]) for d in dbs}
         results.append(st)
-    g.pir_check_device()
+        if any(r.status == serving.PIR_ERR_TIMEOUT for r in done):
+            stopped = "batches ran out of time at %g q/s; later loads not run" % rate
+            break
+        torch.cuda.synchronize()  # the next load starts on an idle device
+    try:
+        g.pir_device_status()  # a bounded kernel wait that ran out (reads without waiting)
+        device_status = 0
+    except g.PirError as e:
+        device_status = e.status
     # the headline: p99 at the stated load (the highest offered rate the server kept up with
     # unless one is named)
     if args.serving_headline_rate:
@@ -1141,7 +1164,12 @@ def run_serving(args, rates, seconds, graphs, warmup_s=0.0):
                        "seconds_per_load": seconds, "warmup_load_s": warmup_s, "setup_s": setup_s,
                        "graph_prewarm_s": prewarm_s,
                        "resident_bytes": srv.resident_bytes},
-            "graph_launches": be.graph_launches, "failed": len(srv.failed), "loads": results}
+            "graph_launches": be.graph_launches, "failed": len(srv.failed), "device_status": device_status,
+            "loads": results}
+    if stopped:
+        line["stopped"] = stopped
+    if emit is not None:
+        emit(line)
     for d in list(srv.dbs):  # frees each DB and the graphs made for it
         srv.evict(d)
     torch.cuda.empty_cache()
@@ -1151,9 +1179,8 @@ def run_serving(args, rates, seconds, graphs, warmup_s=0.0):
 def serving_bench(args):
     import torch
     torch.cuda.set_device(0)
-    line = run_serving(args, args.serving_rates, args.serving_seconds, args.serving_graphs,
-                       warmup_s=args.serving_warmup)
-    print(json.dumps(line), flush=True)
+    run_serving(args, args.serving_rates, args.serving_seconds, args.serving_graphs, warmup_s=args.serving_warmup,
+                emit=lambda line: print(json.dumps(line), flush=True))
 
 
 def main(argv=None):

@@ -22,7 +22,10 @@ Limits and failure handling:
   - a batch whose completion event has not fired `batch_timeout` seconds after its
     dispatch fails its requests with PIR_ERR_TIMEOUT (status 5, the C ABI's code);
     the slot keeps the batch's buffers and stays out of use until the event does
-    fire, since the device may still write into them;
+    fire, since the device may still write into them; once such a slot has waited
+    another `batch_timeout`, requests that only stuck slots could take (their
+    database's slot cap all stuck, or every slot stuck) fail with PIR_ERR_TIMEOUT
+    too, instead of waiting behind batches that may never complete;
   - a request can be cancelled: a waiting one leaves its queue, a running one leaves
     its batch's results (the rest of the batch completes normally).
 A database is admitted only if its resident bytes fit the memory budget (when one is
@@ -236,11 +239,35 @@ class Server:
     def _slots_of(self, name) -> int:
         return sum(1 for s in self.slots if s.busy and s.db == name)
 
+    def _stuck(self, s, now) -> bool:
+        # a batch that ran out of time, and then another batch_timeout without its
+        # completion event firing: it may never end
+        return s.busy and s.timed_out and now - s.t_dispatch > 2 * self.batch_timeout
+
+    def _fail_behind_stuck_slots(self, now):
+        """Waiting requests that no slot can ever take (every slot stuck, or every slot
+        their database may hold stuck) fail with PIR_ERR_TIMEOUT instead of queueing
+        behind batches that may never complete."""
+        usable = sum(1 for s in self.slots if not self._stuck(s, now))
+        for name, q in self.queues.items():
+            if not q:
+                continue
+            cap = _per_db(self.db_max_slots, name, len(self.slots))
+            stuck_held = sum(1 for s in self.slots if s.db == name and self._stuck(s, now))
+            if usable == 0 or stuck_held >= cap:
+                while q:
+                    r = q.popleft()
+                    r.t_done = now
+                    r.status = PIR_ERR_TIMEOUT
+                    self.failed.append(r)
+
     def poll(self) -> List[Request]:
         """Retire finished batches (and time out overdue ones), then fill every free
         slot.  Returns the requests answered in this call."""
         now = self.clock()
         finished = self._retire(now)
+        if self.batch_timeout is not None:
+            self._fail_behind_stuck_slots(now)
         for s in self.slots:
             if s.busy:
                 continue

@@ -308,3 +308,28 @@ def test_a_batch_that_cannot_start_fails_its_requests_and_the_server_goes_on():
     clock.t = 1.0
     srv.poll()
     assert sorted(r.rid for r in srv.done) == [4, 5] and srv.pending() == 0
+
+
+def test_requests_behind_stuck_slots_fail_instead_of_waiting_forever():
+    clock = FakeClock()
+    be = StuckBackend(clock)
+    srv = Server(be, streams=2, max_batch=2, clock=clock, keep_responses=True, batch_timeout=2.0,
+                 db_max_slots={"a": 1})
+    srv.admit("a", params(), None)
+    srv.admit("b", params(), None)
+    srv.submit(Request(0, "a", 0, 0.0))
+    srv.poll()                               # a's batch never completes
+    srv.submit(Request(1, "a", 1, 0.5))
+    clock.t = 2.5
+    srv.poll()                               # it runs out of time: request 0 fails
+    assert [r.rid for r in srv.failed] == [0]
+    assert srv.pending() == 1                # request 1 still waits: the slot may yet free
+    clock.t = 4.5                            # another timeout later the slot counts as stuck
+    srv.submit(Request(2, "b", 2, 4.5))
+    srv.poll()
+    assert [r.rid for r in srv.failed] == [0, 1] and srv.failed[1].status == 5
+    assert [q for _, q in be.batches] == [[0], [2]]  # database b still runs on the other slot
+    be.released.add(1)
+    clock.t = 5.0
+    srv.poll()
+    assert [r.rid for r in srv.done] == [2] and srv.pending() == 0

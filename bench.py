@@ -723,8 +723,7 @@ def our_arm(args, wl):
         ctx.wl = wl
         large["limb_vs_plain"] = large["plain"]["ms_per_step"] / large["limb"]["ms_per_step"]
 
-    # the metric's serving half: the serving configuration at one offered load, with
-    # captured graphs (the opt-in tensor layout, as the serving benchmark runs it)
+    # the metric's serving half: the serving configuration at one offered load
     serving_blk = None
     if world == 1 and plain_mode and args.serving_block:
         if db is not None:
@@ -735,39 +734,11 @@ def our_arm(args, wl):
         # a child process, as `bench.py --serving` runs: its allocators start empty, so
         # the 208 GiB of resident serving DBs meet no cache left by the blocks above.
         # Uncaptured dispatch: with captured graphs an overloaded sweep has stalled
-        # (two batches that never completed), without them it has not; a block that
-        # fails or runs out of time is recorded, and the line stands without it
+        # (two batches that never completed), without them it has not
         cmd = [sys.executable, os.path.abspath(__file__), "--serving",
                "--serving-rates", str(args.serving_block_rate), "--serving-seconds", str(args.serving_block_seconds),
                "--serving-warmup", "1.5"]
-        try:
-            try:
-                child = subprocess.run(cmd, capture_output=True, text=True, timeout=300)
-                out, note = child.stdout, None
-                if child.returncode != 0:
-                    raise RuntimeError("exit %d: %s" % (child.returncode, child.stderr[-600:]))
-            except subprocess.TimeoutExpired as e:
-                # the line is printed before the DBs are freed: keep it if it came
-                out = e.stdout.decode() if isinstance(e.stdout, bytes) else (e.stdout or "")
-                note = "the serving process did not end within 300 s after its loads"
-                if not out.strip():
-                    raise
-            sl = json.loads(out.strip().splitlines()[-1])
-            ld = sl["loads"][0]
-            serving_blk = {"metric": sl["metric"], "unit": "ms", "p50_ms": ld.get("p50_ms"),
-                           "p99_ms": ld.get("p99_ms"), "offered_qps": ld["offered_qps"],
-                           "achieved_qps": ld.get("qps"), "saturated": ld["saturated"],
-                           "mean_batch": ld.get("mean_batch"), "failed": sl["failed"],
-                           "graph_launches": sl["graph_launches"], "config": sl["config"],
-                           "device_status": sl.get("device_status"),
-                           "per_db_p99_ms": {d: v.get("p99_ms") for d, v in ld["per_db"].items()}}
-            if sl.get("stopped"):
-                serving_blk["stopped"] = sl["stopped"]
-            if note:
-                serving_blk["note"] = note
-        except (subprocess.TimeoutExpired, RuntimeError, ValueError, IndexError, KeyError) as e:
-            serving_blk = {"metric": "serving p50/p99 ms (Poisson arrivals, continuous batching)",
-                           "error": "%s: %s" % (type(e).__name__, str(e)[:600])}
+        serving_blk = serving_block_from_child(cmd, timeout_s=300)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not (args.packed or args.folded):
@@ -1174,6 +1145,42 @@ def run_serving(args, rates, seconds, graphs, warmup_s=0.0, emit=None):
         srv.evict(d)
     torch.cuda.empty_cache()
     return line
+
+
+def serving_block_from_child(cmd, timeout_s):
+    """Runs the serving benchmark `cmd` in a child process and returns the default
+    line's `serving` block from the JSON line it prints.  The child prints its line
+    before it frees its databases (which waits for the device): if it then runs past
+    timeout_s, the line is kept with a note.  Anything else that goes wrong is
+    recorded in the block as an error; the caller's line stands without it."""
+    metric = "serving p50/p99 ms (Poisson arrivals, continuous batching)"
+    note = None
+    try:
+        try:
+            child = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout_s)
+            out = child.stdout
+            if child.returncode != 0:
+                raise RuntimeError("exit %d: %s" % (child.returncode, (child.stderr or "")[-600:]))
+        except subprocess.TimeoutExpired as e:
+            out = e.stdout.decode() if isinstance(e.stdout, bytes) else (e.stdout or "")
+            if not out.strip():
+                raise
+            note = "the serving process did not end within %d s after its loads" % timeout_s
+        sl = json.loads(out.strip().splitlines()[-1])
+        ld = sl["loads"][0]
+        blk = {"metric": sl.get("metric", metric), "unit": "ms", "p50_ms": ld.get("p50_ms"),
+               "p99_ms": ld.get("p99_ms"), "offered_qps": ld["offered_qps"], "achieved_qps": ld.get("qps"),
+               "saturated": ld.get("saturated"), "mean_batch": ld.get("mean_batch"), "failed": sl.get("failed"),
+               "graph_launches": sl.get("graph_launches"), "config": sl.get("config"),
+               "device_status": sl.get("device_status"),
+               "per_db_p99_ms": {d: v.get("p99_ms") for d, v in ld.get("per_db", {}).items()}}
+        if sl.get("stopped"):
+            blk["stopped"] = sl["stopped"]
+        if note:
+            blk["note"] = note
+        return blk
+    except Exception as e:  # the block is optional: record why it is missing
+        return {"metric": metric, "error": "%s: %s" % (type(e).__name__, str(e)[:600])}
 
 
 def serving_bench(args):

@@ -1,6 +1,8 @@
-"""bench.py's reading of the committed ncu summaries (host logic, CPU): the
+"""Host logic of bench.py (CPU): the reading of the committed ncu summaries (the
 roofline's traffic comes from a summary only while its kernel source is unchanged
-and, where the summary names them, for the same number of launches per step."""
+and, where the summary names them, for the same number of launches per step), and
+the default line's serving block taken from a child process (its line kept even
+when the child is ended in its cleanup; any failure recorded, never raised)."""
 import os
 import sys
 
@@ -43,3 +45,36 @@ def test_traffic_per_launch_count(tmp_path, monkeypatch):
     assert bench.profile_traffic("k", "w", 4, src, launches_per_step=2.0) == 5000.0
     assert bench.profile_traffic("k", "w", 4, src, launches_per_step=4.0) == 1234.0
     assert bench.profile_traffic("k", "w", 4, src, launches_per_step=1.0) is None
+
+
+# --- the default line's serving block, from a child process (host logic) -------
+
+LINE = ('{"metric": "serving p50/p99 ms (Poisson arrivals, continuous batching)", "failed": 0, '
+        '"graph_launches": 0, "config": {"workload": "serving"}, "device_status": 0, '
+        '"loads": [{"offered_qps": 1000.0, "qps": 950.0, "p50_ms": 60.0, "p99_ms": 130.0, "saturated": false, '
+        '"mean_batch": 12.0, "per_db": {"a": {"p99_ms": 120.0}}}]}')
+
+
+def child(code):
+    return [sys.executable, "-c", code]
+
+
+def test_serving_block_from_a_child_line():
+    blk = bench.serving_block_from_child(child("print(%r)" % LINE), timeout_s=30)
+    assert blk["p99_ms"] == 130.0 and blk["achieved_qps"] == 950.0 and blk["per_db_p99_ms"] == {"a": 120.0}
+    assert "error" not in blk and "note" not in blk
+
+
+def test_serving_block_keeps_the_line_of_a_child_stuck_in_cleanup():
+    code = "import sys, time\nprint(%r, flush=True)\ntime.sleep(30)" % LINE
+    blk = bench.serving_block_from_child(child(code), timeout_s=2)
+    assert blk["p99_ms"] == 130.0 and "did not end" in blk["note"]
+
+
+def test_serving_block_records_a_failed_or_silent_child():
+    blk = bench.serving_block_from_child(child("import sys; sys.exit(3)"), timeout_s=30)
+    assert blk["error"].startswith("RuntimeError: exit 3")
+    blk = bench.serving_block_from_child(child("import time; time.sleep(30)"), timeout_s=1)
+    assert blk["error"].startswith("TimeoutExpired")
+    blk = bench.serving_block_from_child(child("print('not json')"), timeout_s=30)
+    assert "error" in blk

@@ -1141,9 +1141,10 @@ def run_serving(args, rates, seconds, graphs, warmup_s=0.0, emit=None):
         line["stopped"] = stopped
     if emit is not None:
         emit(line)
-    for d in list(srv.dbs):  # frees each DB and the graphs made for it
-        srv.evict(d)
-    torch.cuda.empty_cache()
+    if not stopped:  # (after a stopped sweep a batch may still hold its DB: the process ends as is)
+        for d in list(srv.dbs):  # frees each DB and the graphs made for it
+            srv.evict(d)
+        torch.cuda.empty_cache()
     return line
 
 
@@ -1160,7 +1161,9 @@ def serving_block_from_child(cmd, timeout_s):
             child = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout_s)
             out = child.stdout
             if child.returncode != 0:
-                raise RuntimeError("exit %d: %s" % (child.returncode, (child.stderr or "")[-600:]))
+                if not (out or "").strip():
+                    raise RuntimeError("exit %d: %s" % (child.returncode, (child.stderr or "")[-600:]))
+                note = "the serving process exited with %d after printing its line" % child.returncode
         except subprocess.TimeoutExpired as e:
             out = e.stdout.decode() if isinstance(e.stdout, bytes) else (e.stdout or "")
             if not out.strip():

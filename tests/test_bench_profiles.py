@@ -74,6 +74,8 @@ def test_serving_block_keeps_the_line_of_a_child_stuck_in_cleanup():
 def test_serving_block_records_a_failed_or_silent_child():
     blk = bench.serving_block_from_child(child("import sys; sys.exit(3)"), timeout_s=30)
     assert blk["error"].startswith("RuntimeError: exit 3")
+    blk = bench.serving_block_from_child(child("import sys\nprint(%r)\nsys.exit(1)" % LINE), timeout_s=30)
+    assert blk["p99_ms"] == 130.0 and "exited with 1" in blk["note"]  # its line was printed first
     blk = bench.serving_block_from_child(child("import time; time.sleep(30)"), timeout_s=1)
     assert blk["error"].startswith("TimeoutExpired")
     blk = bench.serving_block_from_child(child("print('not json')"), timeout_s=30)
